@@ -1,0 +1,284 @@
+"""FP64 CPU oracle of the periodic QEq solve.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import this module.  It
+shares no code with the CUDA path (``paper_2607_17978_b300``): only the seeded
+input generators are common to both.
+
+What it computes (RuNNer 2.0 paper, Sec. 2.4 "Electrostatics and Charge
+Equilibration" and SI "Fourth-Generation HDNNPs and Charge Equilibration"):
+
+* the Coulomb kernel of normalised Gaussian charges, eq. (elec_energy):
+  E_ii = 1/(sigma_i sqrt(pi)), E_ij = erf(r_ij / (sqrt(2) gamma_ij)) / r_ij,
+  gamma_ij = sqrt(sigma_i^2 + sigma_j^2), summed over the periodic images of a
+  cell with the G = 0 term of the density dropped (the neutralising
+  background that the plane-wave kernel 4 pi / G^2 of eq. (matvec) implies):
+
+      A_ij = k_e (4 pi / V) sum_{G != 0} exp(-G^2 gamma_ij^2 / 2) cos(G.(r_i - r_j)) / G^2
+
+  (``coulomb_matrix_definition``; the Ewald-split assembly of SI "Ewald
+  Summation" is ``coulomb_matrix``; both give the same matrix);
+* the QEq energy E_QEq = 1/2 q^T (E + diag J) q + chi^T q, eq. (qeq_energy),
+  reading the garbled "J^T I" as diag(J) as the SI energy expression states;
+* the bordered (N+1) x (N+1) Lagrange system of eq. (4G_qeq_prime),
+  [A 1; 1^T 0][q; lambda] = [-chi; q_tot], solved by dense LU; the SI form
+  (A + J) q = -chi + mu 1 (eq. qeq) gives mu = -lambda;
+* for cells too large for a dense matrix, the FP64 Ewald matrix-vector product
+  (C, ``ewald_oracle.c``), the projected residual and the certified bound
+  ||q - q*||_2 <= ||P (A q + chi)||_2 / J_min  (A >= diag(J) on the
+  constraint plane because E_elec >= 0).
+
+Units: the caller passes k_e (14.3996454784 eV*A/e^2 for eV, Angstrom, e;
+1 for atomic units, which the paper uses internally).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+from scipy.linalg import blas as _blas
+from scipy.special import erfc as _erfc  # noqa: F401  (used by tests through this module)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_ewald_oracle.so")
+_lib = None
+
+
+def build_c(force: bool = False) -> str:
+    """Compile ewald_oracle.c (plain C + OpenMP) next to this file."""
+    src = os.path.join(_HERE, "ewald_oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-o", _SO, src, "-lm"])
+    return _SO
+
+
+def _clib():
+    global _lib
+    if _lib is None:
+        build_c()
+        lib = ctypes.CDLL(_SO)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_realspace_dense.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_realspace_dense.restype = ctypes.c_int
+        lib.oracle_ewald_matvec.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, ip, dp]
+        lib.oracle_ewald_matvec.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------- geometry
+
+def volume(cell: np.ndarray) -> float:
+    return abs(float(np.linalg.det(cell)))
+
+
+def reciprocal_vectors(cell: np.ndarray) -> np.ndarray:
+    """Rows b_k with a_j . b_k = delta_jk, so that G(m) = 2 pi m @ B."""
+    return np.linalg.inv(cell).T
+
+
+def plane_widths(cell: np.ndarray) -> np.ndarray:
+    V = volume(cell)
+    return np.array([V / np.linalg.norm(np.cross(cell[(d + 1) % 3], cell[(d + 2) % 3])) for d in range(3)])
+
+
+def g_vectors_half(cell: np.ndarray, g_cut: float):
+    """G = 2 pi m B for integer m in the half-space m > 0 (lexicographic), |G| <= g_cut."""
+    B = reciprocal_vectors(cell)
+    wd = plane_widths(cell)
+    M = (np.floor(g_cut * wd / (2 * math.pi)) + 1).astype(int)
+    r = [np.arange(-M[d], M[d] + 1) for d in range(3)]
+    m = np.stack(np.meshgrid(*r, indexing="ij"), -1).reshape(-1, 3)
+    half = (m[:, 0] > 0) | ((m[:, 0] == 0) & (m[:, 1] > 0)) | ((m[:, 0] == 0) & (m[:, 1] == 0) & (m[:, 2] > 0))
+    m = m[half]
+    G = 2 * math.pi * m @ B
+    G2 = np.einsum("ij,ij->i", G, G)
+    keep = G2 <= g_cut * g_cut
+    return G[keep], G2[keep]
+
+
+# --------------------------------------------------------------------------- Coulomb matrix
+
+def coulomb_matrix_definition(cell, pos, sigma, k_e=1.0, tol=1e-17):
+    """A without hardness, straight from the definition: the reciprocal sum with gamma_ij.
+
+    Only for tiny cells (cost N^2 * n_G); sigma must be > 0.
+    """
+    sigma = np.asarray(sigma, float)
+    assert np.all(sigma > 0)
+    V = volume(cell)
+    gmin = math.sqrt(2.0) * float(sigma.min())
+    # exp(-G^2 gmin^2/2) < tol  ->  G_cut
+    g_cut = math.sqrt(2.0 * math.log(1.0 / tol)) / gmin
+    G, G2 = g_vectors_half(cell, g_cut)
+    n = len(pos)
+    A = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            gam2 = sigma[i] ** 2 + sigma[j] ** 2
+            ph = G @ (pos[i] - pos[j])
+            A[i, j] = 2.0 * (4 * math.pi / V) * np.sum(np.exp(-0.5 * G2 * gam2) * np.cos(ph) / G2)
+    return k_e * A
+
+
+def default_omega(cell, sigma) -> float:
+    """Ewald width for the dense assembly (any value gives the same matrix)."""
+    L = volume(cell) ** (1.0 / 3.0)
+    return max(2.0, 0.05 * L, 0.5 * math.sqrt(2.0) * float(np.max(sigma)) if len(sigma) else 2.0)
+
+
+def realspace_cut(omega: float, tol: float) -> float:
+    """r with erfc(r/(sqrt2 omega)) <= tol (bisection on the monotone erfc)."""
+    lo, hi = 0.0, 60.0 * omega
+    from scipy.special import erfc
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if erfc(mid / (math.sqrt(2.0) * omega)) > tol:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def recip_cut(omega: float, tol: float) -> float:
+    """|G| with exp(-G^2 omega^2/2) <= tol."""
+    return math.sqrt(2.0 * math.log(1.0 / tol)) / omega
+
+
+def coulomb_matrix(cell, pos, sigma, k_e=1.0, omega=None, tol=1e-15):
+    """A without hardness by the Ewald split (SI "Ewald Summation"), dense FP64.
+
+    sigma may contain zeros (point charges; the divergent self energy is left
+    out).  The reciprocal part is grouped by distinct pair width w_ij so that
+    each group is one BLAS rank-k update over the structure-factor matrices.
+    """
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    n = len(pos)
+    if omega is None:
+        omega = default_omega(cell, sigma)
+    V = volume(cell)
+    A = np.zeros((n, n))
+    r_cut = realspace_cut(omega, tol * 1e-2)
+    rc = _clib().oracle_realspace_dense(n, _dp(cell), _dp(pos), _dp(sigma), float(omega), float(r_cut), _dp(A))
+    if rc != 0:
+        raise MemoryError("oracle_realspace_dense failed")
+    # reciprocal part: w_ij = max(gamma_ij, omega); group atoms by sigma
+    uniq, inv = np.unique(sigma, return_inverse=True)
+    gam = np.sqrt(uniq[:, None] ** 2 + uniq[None, :] ** 2)
+    W = np.maximum(gam, omega)
+    g_cut = recip_cut(float(W.min()), tol)
+    G_all, G2_all = g_vectors_half(cell, g_cut)
+    groups = [np.nonzero(inv == a)[0] for a in range(len(uniq))]
+    chunk = max(256, int(2.0e8 // max(n, 1) // 8))
+    for c0 in range(0, len(G2_all), chunk):
+        G, G2 = G_all[c0:c0 + chunk], G2_all[c0:c0 + chunk]
+        ph = pos @ G.T                                    # n x nG
+        C, S = np.cos(ph), np.sin(ph)
+        for a in range(len(uniq)):
+            for b in range(a, len(uniq)):
+                f = 2.0 * (4 * math.pi / V) * np.exp(-0.5 * G2 * W[a, b] ** 2) / G2
+                sq = np.sqrt(f)
+                ia, ib = groups[a], groups[b]
+                Ca, Sa = C[ia] * sq, S[ia] * sq
+                if a == b:
+                    blk = _blas.dsyrk(1.0, np.asfortranarray(Ca)) + _blas.dsyrk(1.0, np.asfortranarray(Sa))
+                    blk = np.triu(blk) + np.triu(blk, 1).T
+                    A[np.ix_(ia, ia)] += blk
+                else:
+                    Cb, Sb = C[ib] * sq, S[ib] * sq
+                    blk = Ca @ Cb.T + Sa @ Sb.T
+                    A[np.ix_(ia, ib)] += blk
+                    A[np.ix_(ib, ia)] += blk.T
+    return k_e * A
+
+
+# --------------------------------------------------------------------------- solve
+
+@dataclass
+class QEqSolution:
+    q: np.ndarray
+    mu: float
+    E_qeq: float
+    E_elec: float
+
+
+def solve_bordered(A_elec, J, chi, q_tot) -> tuple[np.ndarray, float]:
+    """Dense LU of the bordered system (eq. 4G_qeq_prime); returns q and mu = -lambda."""
+    n = len(chi)
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = A_elec + np.diag(J)
+    M[:n, n] = 1.0
+    M[n, :n] = 1.0
+    rhs = np.concatenate([-np.asarray(chi, float), [float(q_tot)]])
+    x = np.linalg.solve(M, rhs)
+    return x[:n], -float(x[n])
+
+
+def energies(A_elec, J, chi, q) -> tuple[float, float]:
+    """E_QEq = chi.q + 1/2 q.(E + diag J) q (eq. qeq_energy) and E_elec = 1/2 q.E q (eq. elec_energy)."""
+    Eq = A_elec @ q
+    E_elec = 0.5 * float(q @ Eq)
+    return float(chi @ q) + 0.5 * float(np.sum(J * q * q)) + E_elec, E_elec
+
+
+def solve_structure(st, k_e=1.0, omega=None) -> QEqSolution:
+    """Oracle solve of a ``synth.Structure``."""
+    A = coulomb_matrix(st.cell, st.pos, st.sigma, k_e=k_e, omega=omega)
+    q, mu = solve_bordered(A, st.J, st.chi, st.q_tot)
+    E, Ee = energies(A, st.J, st.chi, q)
+    return QEqSolution(q, mu, E, Ee)
+
+
+# --------------------------------------------------------------------------- large cells
+
+def ewald_matvec(cell, pos, sigma, q, k_e=1.0, omega=None, tol=1e-13, rows=None):
+    """y = A_elec q (no hardness) for large cells; ``rows`` selects output rows."""
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = len(pos)
+    gmax = math.sqrt(2.0) * float(sigma.max())
+    if omega is None:
+        # balance O(n_G) structure factors against O(neighbours) real space
+        V = volume(cell)
+        omega = max(gmax, 0.9 * (V / 1.0e4) ** (1.0 / 6.0) * 2.0)
+    omega = max(float(omega), gmax)
+    r_cut = realspace_cut(omega, tol * 1e-1)
+    g_cut = recip_cut(omega, tol)
+    if rows is None:
+        y = np.zeros(n)
+        rc = _clib().oracle_ewald_matvec(n, _dp(cell), _dp(pos), _dp(sigma), _dp(q), omega, r_cut, g_cut,
+                                         0, None, _dp(y))
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        y = np.zeros(len(rows))
+        rc = _clib().oracle_ewald_matvec(n, _dp(cell), _dp(pos), _dp(sigma), _dp(q), omega, r_cut, g_cut,
+                                         len(rows), rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(y))
+    if rc != 0:
+        raise RuntimeError(f"oracle_ewald_matvec failed ({rc})")
+    return k_e * y
+
+
+def projected_residual(y_elec, J, chi, q):
+    """r = A q + chi with A = E + diag J, projected onto 1^T r = 0; also mu = mean(A q + chi)."""
+    r = y_elec + J * q + chi
+    mu = float(np.mean(r))
+    return r - mu, mu
+
+
+def certified_bound(Pr, J) -> float:
+    """||q - q*||_2 <= ||P(Aq + chi)||_2 / J_min (A - diag J is PSD on 1^perp)."""
+    return float(np.linalg.norm(Pr) / np.min(J))

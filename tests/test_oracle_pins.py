@@ -1,0 +1,234 @@
+"""Pins of the FP64 oracle against textbook physics, closed forms and invariants.
+
+The paper prints no worked QEq example, so the oracle is pinned by what the
+mathematics fixes (SURVEY-style pins P1-P7):
+  * the rock-salt Madelung constant (point-charge limit of the Ewald machinery);
+  * the Ewald split equals the plain reciprocal-sum definition for any omega;
+  * the single-Gaussian self term in a cubic box against the simple-cubic
+    self-image constant xi (closed form);
+  * Gaussian-minus-point energy against a direct, absolutely convergent erfc sum;
+  * the large-box pair limit approaching erf(r/(sqrt2 gamma))/r of eq. (elec_energy);
+  * N = 1 and N = 2 solves by hand, neutrality, the energy identity at the optimum,
+    symmetry of perfect rock salt, translation and permutation invariance;
+  * the large-cell C matrix-vector product against the dense matrix.
+Each pin fails for a plausible slip (dropped self / width term, sign of mu,
+transposed cell, wrong image range).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erf, erfc
+
+from oracle import qeq_oracle as O
+from paper_2607_17978_b300 import synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "lattice_constants.json")))
+MADELUNG = GOLD["madelung_nacl_nn"]["value"]
+XI_SC = GOLD["wigner_sc_xi"]["value"]
+
+
+def _tri_cell():
+    return np.array([[7.0, 0.3, 0.5], [0.0, 6.5, -0.4], [0.0, 0.0, 8.0]])
+
+
+@pytest.mark.parametrize("ncell,omega", [(1, 1.2), (2, 1.5), (2, 2.5)])
+def test_madelung_rocksalt_point_charges(ncell, omega):
+    frac, spec = synth.rocksalt_sites(ncell, ncell, ncell)
+    a = 5.64
+    cell = np.eye(3) * ncell * a
+    pos = frac @ cell
+    q = np.where(spec == 0, 1.0, -1.0)
+    A = O.coulomb_matrix(cell, pos, np.zeros(len(q)), omega=omega)
+    E = 0.5 * q @ A @ q
+    M = -E / (len(q) / 2) * (a / 2)
+    assert abs(M - MADELUNG) < 1e-11
+
+
+def test_madelung_via_large_cell_matvec():
+    frac, spec = synth.rocksalt_sites(2, 2, 2)
+    a = 5.64
+    cell = np.eye(3) * 2 * a
+    pos = frac @ cell
+    q = np.where(spec == 0, 1.0, -1.0)
+    y = O.ewald_matvec(cell, pos, np.zeros(len(q)), q, omega=2.0)
+    M = -(0.5 * q @ y) / (len(q) / 2) * (a / 2)
+    assert abs(M - MADELUNG) < 1e-10
+
+
+@pytest.mark.parametrize("omega", [0.8, 1.0, 2.0, 3.0])
+def test_ewald_split_equals_definition(omega):
+    rng = np.random.default_rng(11)
+    cell = _tri_cell()
+    pos = rng.random((5, 3)) @ cell
+    sig = np.array([1.0, 1.8, 1.0, 1.8, 1.3])
+    Ad = O.coulomb_matrix_definition(cell, pos, sig)
+    Ae = O.coulomb_matrix(cell, pos, sig, omega=omega)
+    assert np.abs(Ae - Ad).max() < 1e-12 * np.abs(Ad).max()
+    assert np.abs(Ad - Ad.T).max() < 1e-14 * np.abs(Ad).max()
+
+
+@pytest.mark.parametrize("sigma,L", [(1.0, 20.0), (1.3, 25.0), (0.7, 14.0)])
+def test_single_gaussian_self_term_cubic_box(sigma, L):
+    cell = np.eye(3) * L
+    pos = np.array([[0.3, 1.1, -0.2]])
+    expect = 1.0 / (sigma * math.sqrt(math.pi)) + XI_SC / L + 4 * math.pi * sigma ** 2 / L ** 3
+    Ad = O.coulomb_matrix_definition(cell, pos, [sigma])
+    Ae = O.coulomb_matrix(cell, pos, np.array([sigma]), omega=max(1.5, sigma * 1.6))
+    assert abs(Ad[0, 0] - expect) < 1e-12
+    assert abs(Ae[0, 0] - expect) < 1e-12
+
+
+def _direct_erfc_sum(cell, pos, sigma, q, rmax=40.0):
+    """sum over i, j, images n (excluding i = j, n = 0) of q_i q_j erfc(r/(sqrt2 gamma))/r, brute force."""
+    n = len(pos)
+    wd = O.plane_widths(cell)
+    nm = [int(math.ceil(rmax / wd[d])) + 1 for d in range(3)]
+    tot = 0.0
+    for i in range(n):
+        for j in range(n):
+            g = math.sqrt(sigma[i] ** 2 + sigma[j] ** 2)
+            for a in range(-nm[0], nm[0] + 1):
+                for b in range(-nm[1], nm[1] + 1):
+                    for c in range(-nm[2], nm[2] + 1):
+                        if i == j and a == 0 and b == 0 and c == 0:
+                            continue
+                        d = pos[j] - pos[i] + a * cell[0] + b * cell[1] + c * cell[2]
+                        r = float(np.linalg.norm(d))
+                        if r < rmax:
+                            tot += q[i] * q[j] * erfc(r / (math.sqrt(2) * g)) / r
+    return tot
+
+
+def test_gaussian_minus_point_energy_direct_sum():
+    rng = np.random.default_rng(5)
+    cell = _tri_cell()
+    pos = rng.random((4, 3)) @ cell
+    sig = np.array([1.0, 1.8, 0.9, 1.4])
+    q = np.array([0.7, -0.3, -0.9, 0.5])       # neutral
+    Eg = 0.5 * q @ O.coulomb_matrix_definition(cell, pos, sig) @ q
+    Ep = 0.5 * q @ O.coulomb_matrix(cell, pos, np.zeros(4), omega=1.5) @ q
+    rhs = np.sum(q ** 2 / (2 * sig * math.sqrt(math.pi))) - 0.5 * _direct_erfc_sum(cell, pos, sig, q)
+    assert abs((Eg - Ep) - rhs) < 1e-12
+
+
+def test_large_box_pair_limit():
+    L, r, s1, s2 = 60.0, 1.7, 1.0, 1.8
+    cell = np.eye(3) * L
+    pos = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    A = O.coulomb_matrix(cell, pos, np.array([s1, s2]), omega=3.0)
+    g = math.sqrt(s1 ** 2 + s2 ** 2)
+    pair = erf(r / (math.sqrt(2) * g)) / r
+    expect = pair + XI_SC / L + (2 * math.pi / 3) * r ** 2 / L ** 3 + 2 * math.pi * g ** 2 / L ** 3
+    # neglected: the cubic-harmonic r^4/L^5 term of the periodic point potential
+    assert abs(A[0, 1] - expect) < 5 * r ** 4 / L ** 5
+    assert abs(A[0, 0] - (1 / (s1 * math.sqrt(math.pi)) + XI_SC / L + 4 * math.pi * s1 ** 2 / L ** 3)) < 1e-12
+
+
+def test_solve_single_atom():
+    cell = np.eye(3) * 9.0
+    pos = np.array([[1.0, 2.0, 3.0]])
+    A = O.coulomb_matrix(cell, pos, np.array([1.2]))
+    q, mu = O.solve_bordered(A, np.array([1.7]), np.array([-0.4]), 1.0)
+    assert abs(q[0] - 1.0) < 1e-14
+    assert abs(mu - ((A[0, 0] + 1.7) * 1.0 - 0.4)) < 1e-12
+
+
+def test_solve_two_atoms_by_hand():
+    rng = np.random.default_rng(3)
+    cell = _tri_cell()
+    pos = rng.random((2, 3)) @ cell
+    sig = np.array([1.0, 1.8])
+    A = O.coulomb_matrix(cell, pos, sig)
+    J = np.array([2.0, 1.5])
+    chi = np.array([-1.1, 0.8])
+    qt = 0.4
+    H = A + np.diag(J)
+    # eliminate q2 = qt - q1 from the stationarity condition (H q + chi) equal in both rows
+    q1 = (qt * (H[1, 1] - H[0, 1]) + chi[1] - chi[0]) / (H[0, 0] + H[1, 1] - 2 * H[0, 1])
+    q, mu = O.solve_bordered(A, J, chi, qt)
+    assert abs(q[0] - q1) < 1e-13 and abs(q[1] - (qt - q1)) < 1e-13
+    assert abs(mu - (H[0] @ q + chi[0])) < 1e-12
+
+
+def test_neutrality_energy_identity_and_mu_sign():
+    st = synth.rocksalt(1, 5.64, 0.2, synth.rng_for(99, 0))
+    st.q_tot = 0.5
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=synth.COULOMB_K_EV_A)
+    q, mu = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+    assert abs(q.sum() - st.q_tot) < 1e-12
+    # stationarity (SI eq. qeq): (A + J) q + chi = mu 1
+    r = A @ q + st.J * q + st.chi
+    assert np.abs(r - mu).max() < 1e-11
+    E, Ee = O.energies(A, st.J, st.chi, q)
+    assert abs(E - (0.5 * st.chi @ q + 0.5 * mu * st.q_tot)) < 1e-11
+    assert Ee >= 0
+
+
+def test_coulomb_matrix_psd_on_random_cells():
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        cell = _tri_cell() * rng.uniform(0.8, 1.3)
+        pos = rng.random((12, 3)) @ cell
+        sig = rng.uniform(0.8, 2.0, 12)
+        A = O.coulomb_matrix(cell, pos, sig)
+        assert np.linalg.eigvalsh(A).min() > -1e-12
+
+
+def test_symmetry_perfect_rocksalt():
+    frac, spec = synth.rocksalt_sites(1, 1, 1)
+    a = 5.64
+    cell = np.eye(3) * a
+    pos = frac @ cell
+    sig = np.where(spec == 0, 1.0, 1.8)
+    A = O.coulomb_matrix_definition(cell, pos, sig)
+    chiA, chiB, JA, JB = -2.0, 2.0, 2.0, 1.5
+    chi = np.where(spec == 0, chiA, chiB)
+    J = np.where(spec == 0, JA, JB)
+    q, mu = O.solve_bordered(A, J, chi, 0.0)
+    qa, qb = q[spec == 0], q[spec == 1]
+    assert np.ptp(qa) < 1e-12 and np.ptp(qb) < 1e-12
+    assert abs(qa[0] + qb[0]) < 1e-12
+    s = np.where(spec == 0, 1.0, -1.0)
+    cA = (A @ s)[spec == 0][0]
+    cB = -(A @ s)[spec == 1][0]
+    assert abs(qa[0] - (chiB - chiA) / (JA + JB + cA + cB)) < 1e-12
+
+
+def test_translation_and_permutation_invariance():
+    st = synth.rocksalt(1, 5.64, 0.2, synth.rng_for(98, 0))
+    base = O.solve_structure(st, k_e=synth.COULOMB_K_EV_A)
+    t = st.copy()
+    t.pos = t.pos + np.array([1.234, -0.77, 3.1])
+    tr = O.solve_structure(t, k_e=synth.COULOMB_K_EV_A)
+    assert np.abs(tr.q - base.q).max() < 1e-12
+    perm = np.random.default_rng(0).permutation(st.n)
+    p = st.copy()
+    p.pos, p.species, p.chi, p.J = st.pos[perm], st.species[perm], st.chi[perm], st.J[perm]
+    pr = O.solve_structure(p, k_e=synth.COULOMB_K_EV_A)
+    assert np.abs(pr.q - base.q[perm]).max() < 1e-12
+    assert abs(pr.E_qeq - base.E_qeq) < 1e-10 * abs(base.E_qeq)
+
+
+def test_large_cell_matvec_matches_dense():
+    st = synth.rocksalt(2, 5.64, 0.15, synth.rng_for(97, 0), vacancy_frac=0.05, shear_deg=8.0)
+    q = np.random.default_rng(2).normal(size=st.n)
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma)
+    y = O.ewald_matvec(st.cell, st.pos, st.sigma, q)
+    assert np.abs(y - A @ q).max() < 1e-10 * np.abs(A @ q).max()
+    rows = np.array([0, 5, st.n - 1])
+    yr = O.ewald_matvec(st.cell, st.pos, st.sigma, q, rows=rows)
+    assert np.abs(yr - (A @ q)[rows]).max() < 1e-10 * np.abs(A @ q).max()
+
+
+def test_certified_bound_holds():
+    st = synth.rocksalt(1, 5.64, 0.2, synth.rng_for(96, 0))
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=synth.COULOMB_K_EV_A)
+    q, _ = O.solve_bordered(A, st.J, st.chi, 0.0)
+    pert = np.random.default_rng(1).normal(size=st.n) * 1e-3
+    pert -= pert.mean()
+    qp = q + pert
+    Pr, _ = O.projected_residual(A @ qp, st.J, st.chi, qp)
+    assert np.linalg.norm(pert) <= O.certified_bound(Pr, st.J) * (1 + 1e-12)
