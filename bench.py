@@ -1,0 +1,362 @@
+"""Benchmark of the periodic QEq solve on one B300 (or N replicas).
+
+One step = one complete cold-start QEq solve of the workload cell through the
+C ABI (charges to 1e-5 e, final FP64 residual check included), inputs resident
+on the device.  The default workload is the 13,824-atom rock-salt cell
+(12x12x12 conventional cells, jitter 0.15 A, r_cut 8 A, ewald_tol 1e-6); the
+chosen form is mixed precision (FP32 mesh, FP64 reductions) with the PCG
+iterations captured in a CUDA graph.  Beside it: the plain FP64 GPU PCG (no
+graph), the roofline of the dominant matvec kernel (CUDA events on the plan's
+stream), an end-to-end number through the public API with host buffers, and
+the FP64 CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2|1|3|5]
+
+--gpus N > 1 runs under torch.distributed.run: each rank solves its own
+replica (independent problems, no collective on the data path); value = all
+ranks' solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QEq solves/s and atoms*CG-iters/s at 1e-5 e vs plain FP64 GPU PCG; % HBM roofline"
+UNIT = "solves/s"
+# Jacobi-PCG iterations of a full solve of the default workload at 1e-5 e, used to
+# extrapolate the CPU oracle's matvec time to a solve (the oracle's own solve is
+# a dense LU that does not fit the time budget at this size).
+PCG_ITERS_REFERENCE = 40
+WORKLOAD_OPTS = {
+    1: dict(ewald_tol=1e-7, r_cut=9.0),
+    2: dict(ewald_tol=1e-6, r_cut=8.0),
+    3: dict(ewald_tol=1e-6, r_cut=8.0),
+    5: dict(ewald_tol=1e-6, r_cut=8.0),
+}
+WORKLOAD_NAME = {
+    1: "rocksalt 3x3x3 (216 atoms), chi_A~N(-2,.3) chi_B~N(2,.3), J 2/1.5, sigma 1.0/1.8, r_cut 9, ewald_tol 1e-7",
+    2: "rocksalt 12x12x12 (13,824 atoms), jitter 0.15 A, r_cut 8 A, ewald_tol 1e-6, Jacobi PCG",
+    3: "rocksalt 24x24x24 -5% vacancies, triclinic shear <=10 deg (105,062 atoms), r_cut 8, ewald_tol 1e-6",
+    5: "rocksalt 50x50x50 -2% vacancies, jitter 0.2 A (980,000 atoms), r_cut 8, ewald_tol 1e-6",
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- byte model
+def stage_bytes(plan, prec: str, n_atoms: int, pairs: int):
+    """Algorithmic DRAM bytes per launch of each matvec stage (all structures of the plan)."""
+    cs = 8 if prec == "mixed" else 16          # complex element
+    rs = 4 if prec == "mixed" else 8           # real element
+    mesh = 0
+    for s in range(plan.n_struct):
+        qi = plan.query(s)
+        K = qi["mesh"]
+        mesh += K[0] * K[1] * K[2] * ((qi["n_species"] + 1) // 2)
+    p = plan.query(0)["spline_order"]
+    atom_in = n_atoms * (3 * p * rs + 4 + 4 + 8)  # spline weights, stencil base, species, x
+    return {
+        "species_sums": n_atoms * (8 + 4),
+        "spread": mesh * cs + atom_in,
+        "fft_z": 2 * mesh * cs,
+        "fft_y": 2 * mesh * cs,
+        "fft_x_green": 2 * mesh * cs,
+        "ifft_y": 2 * mesh * cs,
+        "ifft_z": 2 * mesh * cs,
+        "gather": mesh * cs + atom_in + n_atoms * (8 + 8 + 8) + pairs * (rs + 4),
+    }
+
+
+def load_traffic():
+    """DRAM traffic per launch of the dominant kernel from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_matvec_time(st, budget_s: float = 20.0):
+    from oracle import qeq_oracle as O
+    from paper_2607_17978_b300 import synth
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    O.build_c()
+    q = np.random.default_rng(0).normal(size=st.n)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s * 0.5 or len(times) >= 5:
+            break
+    return min(times), cores, len(times)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2607_17978_b300 import synth
+    st = synth.workload(args.workload)
+    cores = len(os.sched_getaffinity(0))
+    from oracle import qeq_oracle as O
+    O.build_c()
+    q = np.random.default_rng(0).normal(size=st.n)
+    for _ in range(args.warmup):
+        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+    t = (time.perf_counter() - t0) / args.steps
+    solve_s = t * PCG_ITERS_REFERENCE
+    value = 1.0 / solve_s
+    sample = (f"one FP64 Ewald matvec of the full {st.n}-atom cell per step by the CPU oracle, "
+              f"x {PCG_ITERS_REFERENCE} PCG iterations (extrapolated to a solve)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": st.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2607_17978_b300 import build, qeq, synth
+    build.build()
+    st = synth.workload(args.workload)
+    opts = WORKLOAD_OPTS[args.workload]
+    pos, spc, chi, J, qt = qeq.pack([st])
+    d_pos = torch.tensor(pos, device=dev)
+    d_spc = torch.tensor(spc, device=dev)
+    d_chi = torch.tensor(chi, device=dev)
+    d_J = torch.tensor(J, device=dev)
+    plan = qeq.plan_for_structures([st], precision=args.precision, device=dev, **opts)
+    q_out = torch.empty(st.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+
+    def solve():
+        return plan.solve(d_pos, d_spc, d_chi, d_J, qt, out=q_out)
+
+    for _ in range(max(args.warmup, 1)):
+        res = solve()
+    torch.cuda.synchronize()
+    launches0 = plan.query(0)["kernel_launches"]
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = []
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))                       # evict the previous step's data from L2 (untimed)
+        plan.stream.wait_stream(torch.cuda.current_stream(dev))
+        ev0[k].record(plan.stream)
+        res = solve()
+        ev1[k].record(plan.stream)
+        iters.append(res.info[0]["iterations"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms = sum(t_steps) / len(t_steps)
+    launches = (plan.query(0)["kernel_launches"] - launches0)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    status = res.info[0]["status"]
+    it_mean = float(np.mean(iters))
+
+    # ---- roofline of the dominant kernel (per-stage CUDA events on the plan's stream)
+    prof = plan.profile_matvec(20)
+    pairs_est = 0
+    sb = stage_bytes(plan, args.precision, st.n, pairs_est)
+    dom = max(prof, key=prof.get)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6400.0
+    achieved = sb[dom] / (prof[dom] * 1e-3) / 1e9
+    traffic = load_traffic().get(f"{dom}:{args.workload}:{args.precision}")
+    matvec_ms = sum(prof.values())
+    matvec_bytes = sum(sb.values())
+
+    # ---- plain FP64 GPU PCG (one structure per launch, no graph): the comparison denominator
+    plain = qeq.plan_for_structures([st], precision="fp64", graph=False, device=dev, **opts)
+    plain.solve(d_pos, d_spc, d_chi, d_J, qt)
+    torch.cuda.synchronize()
+    n_plain = max(1, min(3, args.steps))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(0.0)
+    plain.stream.wait_stream(torch.cuda.current_stream(dev))
+    a.record(plain.stream)
+    for _ in range(n_plain):
+        rp = plain.solve(d_pos, d_spc, d_chi, d_J, qt)
+    b.record(plain.stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b) / n_plain
+    plain_iters = rp.info[0]["iterations"]
+    q_plain = rp.q.clone()
+    plain.close()
+
+    # ---- end to end through the public API with pinned host buffers
+    h_pos = torch.tensor(pos).pin_memory()
+    h_spc = torch.tensor(spc).pin_memory()
+    h_chi = torch.tensor(chi).pin_memory()
+    h_J = torch.tensor(J).pin_memory()
+    h_q = torch.empty(st.n, dtype=torch.float64).pin_memory()
+    n_e2e = max(1, min(5, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        d_pos.copy_(h_pos, non_blocking=True)
+        d_spc.copy_(h_spc, non_blocking=True)
+        d_chi.copy_(h_chi, non_blocking=True)
+        d_J.copy_(h_J, non_blocking=True)
+        r = plan.solve(d_pos, d_spc, d_chi, d_J, qt, out=q_out)
+        torch.cuda.current_stream(dev).wait_stream(plan.stream)
+        h_q.copy_(q_out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    h2d = int(pos.nbytes + spc.nbytes + chi.nbytes + J.nbytes)
+    d2h = int(st.n * 8)
+    dq_plain = float((q_out - q_plain).abs().max().item())
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        t_mv, cores, reps = cpu_oracle_matvec_time(st)
+        v = 1.0 / (t_mv * PCG_ITERS_REFERENCE)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 Ewald matvec of the full {st.n}-atom cell by the CPU oracle (best of {reps}), "
+                          f"x {PCG_ITERS_REFERENCE} PCG iterations: extrapolated to one solve")}
+    value = world * 1000.0 / ms
+    qi = plan.query(0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": st.n, "mesh": list(qi["mesh"]),
+                   "spline_order": qi["spline_order"], "omega_A": round(qi["omega"], 4), "precision": args.precision,
+                   "graph": True, "charge_tol_e": 1e-5, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "atoms_iters_per_s": world * st.n * it_mean / (ms * 1e-3),
+        "pcg_iterations": it_mean, "status": status,
+        "plain_fp64": {"value": 1000.0 / plain_ms, "unit": UNIT, "ms_per_step": plain_ms, "iterations": plain_iters,
+                       "speedup_of_chosen": plain_ms / ms, "max_dq_vs_chosen_e": dq_plain},
+        "matvec": {"ms": matvec_ms, "algorithmic_bytes": matvec_bytes,
+                   "GBps": matvec_bytes / (matvec_ms * 1e-3) / 1e9,
+                   "frac_hbm": matvec_bytes / (matvec_ms * 1e-3) / 1e9 / hbm,
+                   "stages_ms": {k: round(v, 5) for k, v in prof.items()}},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_launch": sb[dom], "launch_ms": prof[dom]},
+        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 5])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * qeq.h -- C ABI of libqeq.so, a B300 (sm_103a) periodic charge-equilibration
+ * (QEq) solver for Gaussian charges.
+ *
+ * The operation (RuNNer 2.0 paper, Sec. 2.4 "Electrostatics and Charge
+ * Equilibration"; SI "Fourth-Generation HDNNPs and Charge Equilibration"):
+ * given per-atom electronegativities chi_i, hardnesses J_i > 0 and Gaussian
+ * widths sigma_i of a periodic cell, find the charges q that minimise
+ *
+ *     E_QEq = 1/2 q^T (E + diag J) q + chi^T q        (eq. qeq_energy)
+ *
+ * subject to sum_i q_i = q_tot (the bordered system of eq. 4G_qeq_prime; SI
+ * eq. qeq: (E + J) q = -chi + mu 1).  E is the Coulomb matrix of normalised
+ * Gaussians (eq. elec_energy: E_ii = 1/(sigma_i sqrt pi), E_ij =
+ * erf(r_ij/(sqrt2 gamma_ij))/r_ij, gamma_ij^2 = sigma_i^2 + sigma_j^2),
+ * summed over periodic images with the G = 0 Fourier term of the charge
+ * density dropped (the neutralising background implied by the plane-wave
+ * kernel 4 pi/G^2 of eq. matvec).  Scaled by coulomb_k.
+ *
+ * The solve is a Jacobi-preconditioned conjugate gradient projected onto the
+ * charge constraint, around the plane-wave matrix-vector product of eq.
+ * (matvec) (Sec. 2.4 "Electrostatics Solvers"): an Ewald split (SI "Ewald
+ * Summation") into a screened real-space pair term, B-spline charge
+ * spreading, 3D FFT, a width-corrected Gaussian reciprocal multiply, inverse
+ * FFT and B-spline interpolation back, plus self and width-correction terms.
+ * A is never formed.
+ *
+ * Conventions
+ *   units        eV, Angstrom, e (coulomb_k = 14.3996454784 eV A / e^2); any
+ *                consistent system works (coulomb_k = 1 for atomic units).
+ *   cells        row-major 3x3 per structure, rows are the lattice vectors
+ *                a1, a2, a3; any non-singular (triclinic) cell.
+ *   atoms        packed over structures: structure s owns atoms
+ *                [atom_offsets[s], atom_offsets[s+1]).
+ *   pointers     "h_" = host memory, "d_" = device memory of the plan's GPU.
+ *                The caller owns every pointer; the library never keeps one
+ *                after a call returns.  Device pointers may be PyTorch
+ *                tensors' data_ptr().
+ *   streams      all device work of a plan is enqueued on the stream given to
+ *                qeq_plan_create; calls return after that stream has finished
+ *                the call's work (the host reads per-structure results).
+ *   allocation   qeq_plan_create allocates every device buffer the plan
+ *                needs; qeq_solve, qeq_energy and qeq_matvec allocate nothing.
+ *   errors       every call returns a qeq_status and never aborts the process;
+ *                qeq_last_error gives a message.  Invalid input leaves outputs
+ *                unspecified.
+ *   threads      a plan is not thread-safe; distinct plans are independent.
+ */
+#ifndef QEQ_H
+#define QEQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QEQ_OK = 0,
+  QEQ_ERR_INVALID = 1,   /* bad argument, non-finite input, species out of range, singular cell */
+  QEQ_ERR_NOT_PD = 2,    /* some J_i <= 0 or sigma <= 0: the QEq matrix is not positive definite */
+  QEQ_ERR_NOCONV = 3,    /* PCG did not reach the tolerance within max_iter (best q returned) */
+  QEQ_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+  QEQ_ERR_OOM = 5,       /* device allocation failed in qeq_plan_create */
+  QEQ_ERR_TIMEOUT = 6,   /* a bounded device wait gave up */
+  QEQ_ERR_CAPACITY = 7   /* real-space pair list larger than the plan's capacity */
+} qeq_status;
+
+enum { QEQ_FP64 = 0, QEQ_MIXED = 1 };
+enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
+enum { QEQ_FLAG_NO_GRAPH = 1 };
+
+typedef struct qeq_plan_s* qeq_plan;
+
+/* Plan description.  Zero / negative numeric fields select defaults. */
+typedef struct {
+  int32_t n_struct;             /* >= 1 structures solved together                          */
+  const int64_t* atom_offsets;  /* h_, n_struct+1, CSR offsets into the packed atom arrays   */
+  const double* cells;          /* h_, n_struct*9, rows a1 a2 a3 [A]                          */
+  int32_t n_species;            /* species table width, 1..8                                 */
+  const double* sigma;          /* h_, n_struct*n_species Gaussian widths [A], > 0            */
+  double coulomb_k;             /* default 14.3996454784                                      */
+  double charge_tol;            /* stop: max-abs projected residual <= 0.5*charge_tol*J_min;  */
+                                /* default 1e-5 e                                            */
+  double ewald_tol;             /* relative accuracy of the matvec; default 1e-6              */
+  double r_cut;                 /* real-space cutoff [A]; default 8                           */
+  int32_t spline_order;         /* B-spline order p in {4,6,8}, one per plan; 0: autotuned    */
+  double mesh_spacing;          /* target spacing between lattice planes [A]; <= 0: the      */
+                                /* autotuner picks the cheapest mesh whose predicted matvec  */
+                                /* error meets ewald_tol (mesh sizes are 2^a 3^b 5^c)        */
+  int32_t precision;            /* QEQ_FP64 (all FP64) or QEQ_MIXED (FP32 mesh/FFT/pairs,    */
+                                /* FP64 reductions, projection, multiplier, final check)     */
+  int32_t max_iter;             /* PCG iterations per structure; default 1000                 */
+  double residual_tol;          /* optional extra stop: ||P r||_2 <= residual_tol*||P chi||_2 */
+  int32_t flags;                /* QEQ_FLAG_*                                                 */
+} qeq_plan_desc;
+
+/* Per-structure result of qeq_solve. */
+typedef struct {
+  int32_t status;          /* qeq_status of this structure                                  */
+  int32_t iterations;      /* PCG iterations (matvecs after the first residual)             */
+  int32_t restarts;        /* residual replacements after a final check failed              */
+  int32_t warm_used;       /* 1 when the warm start was kept, 0 when it fell back to cold   */
+  double residual_inf;     /* final max-abs of P(Aq + chi) [eV/e], P = I - 11^T/N           */
+  double residual_l2;      /* final ||P(Aq + chi)||_2 [eV/e]                                 */
+  double error_bound_l2;   /* certified ||q - q*||_2 <= residual_l2 / J_min for the plan's   */
+                           /* matrix (the mesh approximation of A is not included)          */
+} qeq_info;
+
+/* Mesh / split parameters the plan chose for one structure. */
+typedef struct {
+  int32_t mesh[3];         /* K1, K2, K3                                                     */
+  int32_t spline_order;
+  int32_t n_species;
+  int32_t narrow_pairs;    /* species pairs carried partly in real space                     */
+  double omega;            /* Ewald split width [A]                                          */
+  double r_cut;            /* real-space cutoff [A]                                          */
+  double volume;           /* [A^3]                                                          */
+  int64_t n_atoms;
+  int64_t pair_capacity;   /* real-space pair slots of the whole plan                        */
+  int64_t workspace_bytes; /* device bytes held by the whole plan                            */
+  int64_t kernel_launches; /* CUDA kernels this plan has launched so far (graph replays count  */
+                           /* every kernel in the graph)                                     */
+} qeq_plan_info;
+
+/* Create a plan: validate the description, choose mesh, B-spline order and
+ * Ewald split per structure, and allocate all device workspace on the current
+ * CUDA device.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: QEQ_ERR_INVALID / QEQ_ERR_NOT_PD for bad descriptions (sigma <= 0,
+ * singular cell, n_species out of range), QEQ_ERR_OOM. */
+qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stream, qeq_plan* out);
+
+/* Release a plan and its device memory (NULL is ignored). */
+void qeq_plan_destroy(qeq_plan plan);
+
+/* Per-structure parameters chosen by the plan. */
+qeq_status qeq_plan_query(qeq_plan plan, int32_t s, qeq_plan_info* out);
+
+/* Solve the QEq problem of every structure of the plan.
+ *   d_pos      N x 3 Cartesian positions [A] (any image; wrapped internally)
+ *   d_species  N species indices in [0, n_species)
+ *   d_chi      N electronegativities [eV/e]
+ *   d_J        N hardnesses [eV/e^2], all > 0 (else QEQ_ERR_NOT_PD)
+ *   h_qtot     n_struct total charges [e]
+ *   warm       QEQ_WARM_COLD: start from q_tot/N; QEQ_WARM_USER: start from
+ *              d_q (projected onto the constraint); QEQ_WARM_MLP: reserved
+ *              (currently treated as cold)
+ *   d_q        N charges [e]: input for QEQ_WARM_USER, output always
+ *   d_mu       n_struct Lagrange multipliers mu with (A + J) q + chi = mu 1
+ *              (the bordered lambda of eq. 4G_qeq_prime is -mu); may be NULL
+ *   h_info     n_struct qeq_info records; may be NULL
+ * Returns the worst per-structure status (QEQ_ERR_NOCONV if any structure
+ * stopped at max_iter). */
+qeq_status qeq_solve(qeq_plan plan, const double* d_pos, const int32_t* d_species,
+                     const double* d_chi, const double* d_J, const double* h_qtot,
+                     int32_t warm, double* d_q, double* d_mu, qeq_info* h_info);
+
+/* Energies of given charges: d_E_qeq[s] = chi.q + 1/2 q.(E + diag J) q
+ * (eq. qeq_energy) and d_E_elec[s] = 1/2 q.E q (eq. elec_energy), per
+ * structure, evaluated with the FP64 matvec.  Either output may be NULL. */
+qeq_status qeq_energy(qeq_plan plan, const double* d_pos, const int32_t* d_species,
+                      const double* d_chi, const double* d_J, const double* d_q,
+                      double* d_E_qeq, double* d_E_elec);
+
+/* One plane-wave matrix-vector product d_y = (E + diag J) d_x (eq. matvec),
+ * in the plan's precision (QEQ_FP64 or QEQ_MIXED) or FP64 when force_fp64.
+ * d_J may be NULL (then diag J is left out).  Same atom layout as qeq_solve. */
+qeq_status qeq_matvec(qeq_plan plan, const double* d_pos, const int32_t* d_species,
+                      const double* d_J, const double* d_x, double* d_y, int32_t force_fp64);
+
+/* Time each stage of the matvec with CUDA events on the plan's stream.
+ * Runs n_rep matvecs of the plan's precision on the atoms of the last
+ * qeq_solve / qeq_matvec call and writes the mean milliseconds per launch of
+ * each stage to h_ms[0..QEQ_N_STAGES).  Stage order: species sums, spread,
+ * FFT z, FFT y, FFT x + reciprocal multiply + inverse FFT x, inverse FFT y,
+ * inverse FFT z, gather + real space + local terms. */
+#define QEQ_N_STAGES 8
+qeq_status qeq_profile_matvec(qeq_plan plan, int32_t n_rep, float* h_ms);
+
+/* Static description of one status code. */
+const char* qeq_status_str(qeq_status s);
+
+/* Message of the last error of this plan (never NULL). */
+const char* qeq_last_error(qeq_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QEQ_H */

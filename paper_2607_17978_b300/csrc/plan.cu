@@ -1,0 +1,599 @@
+// Plan creation: per-structure Ewald split, mesh and B-spline choice, FFT
+// radix plans and work lists, and all device workspace (qeq_solve allocates
+// nothing).  Parameter choice follows the paper's particle-mesh solver (SI
+// "Particle-Particle-Particle-Mesh Method": the split width is tied to the
+// Gaussian widths and the mesh resolves the narrowest reciprocal Gaussian) and
+// SI "Ewald Summation" (real-space cutoff from the target accuracy).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qeq_internal.cuh"
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+double det3(const double* h) {
+  return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+         h[2] * (h[3] * h[7] - h[4] * h[6]);
+}
+
+void inv3(const double* h, double* hi) {
+  double d = det3(h);
+  hi[0] = (h[4] * h[8] - h[5] * h[7]) / d;
+  hi[1] = (h[2] * h[7] - h[1] * h[8]) / d;
+  hi[2] = (h[1] * h[5] - h[2] * h[4]) / d;
+  hi[3] = (h[5] * h[6] - h[3] * h[8]) / d;
+  hi[4] = (h[0] * h[8] - h[2] * h[6]) / d;
+  hi[5] = (h[2] * h[3] - h[0] * h[5]) / d;
+  hi[6] = (h[3] * h[7] - h[4] * h[6]) / d;
+  hi[7] = (h[1] * h[6] - h[0] * h[7]) / d;
+  hi[8] = (h[0] * h[4] - h[1] * h[3]) / d;
+}
+
+// x with erfc(x) = y, by bisection (erfc is decreasing)
+double erfc_inv(double y) {
+  double lo = 0.0, hi = 30.0;
+  for (int i = 0; i < 200; ++i) {
+    double mid = 0.5 * (lo + hi);
+    if (erfc(mid) > y)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+bool smooth235(int n) {
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+int next_smooth(int n) {
+  while (!smooth235(n)) ++n;
+  return n;
+}
+
+std::vector<int> radices(int K) {
+  std::vector<int> r;
+  int n = K;
+  while (n % 4 == 0) {
+    r.push_back(4);
+    n /= 4;
+  }
+  while (n % 2 == 0) {
+    r.push_back(2);
+    n /= 2;
+  }
+  while (n % 3 == 0) {
+    r.push_back(3);
+    n /= 3;
+  }
+  while (n % 5 == 0) {
+    r.push_back(5);
+    n /= 5;
+  }
+  return r;
+}
+
+// cardinal B-spline M_p at the integers 0..p-1 (same order recursion as prep.cu, at w = 0)
+void bspline_at_integers(int p, double* out) {
+  double a[QEQ_MAXP + 1] = {0};
+  a[0] = 0.0;
+  a[1] = 1.0;
+  for (int n = 2; n < p; ++n) {
+    a[n] = 0.0;
+    for (int j = n; j >= 0; --j) {
+      double x = j;
+      double left = a[j], right = (j > 0) ? a[j - 1] : 0.0;
+      a[j] = (x * left + (n + 1 - x) * right) / n;
+    }
+  }
+  for (int j = 0; j < p; ++j) out[j] = a[j];
+}
+
+// |b(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K)|^2  (smooth PME moduli)
+void bspline_moduli(int K, int p, double* out) {
+  double M[QEQ_MAXP];
+  bspline_at_integers(p, M);
+  for (int m = 0; m < K; ++m) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k <= p - 2; ++k) {
+      double ph = 2.0 * kPi * (double)m * k / K;
+      re += M[k + 1] * cos(ph);
+      im += M[k + 1] * sin(ph);
+    }
+    double d = re * re + im * im;
+    out[m] = d > 1e-30 ? 1.0 / d : 0.0;
+  }
+}
+
+template <typename T>
+cudaError_t dalloc(qeq_plan_s* P, T** ptr, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e == cudaSuccess) P->workspace_bytes += bytes;
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(qeq_plan_s* P, T** ptr, const std::vector<T>& v) {
+  QEQ_CUDA_TRY(dalloc(P, ptr, v.size()));
+  if (!v.empty()) QEQ_CUDA_TRY(cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return cudaSuccess;
+}
+
+// int_0^rc r erfc(r/a) dr = a^2/4 - [(a^2/4 - rc^2/2) erfc(rc/a) + a rc/(2 sqrt pi) exp(-rc^2/a^2)]
+double sphere_int(double a, double rc) {
+  double tail = (0.25 * a * a - 0.5 * rc * rc) * erfc(rc / a) + a * rc / (2.0 * sqrt(kPi)) * exp(-rc * rc / (a * a));
+  return 0.25 * a * a - tail;
+}
+
+// perpendicular distances between opposite faces of the cell
+void plane_widths(const double* h, double V, double* wd) {
+  for (int d = 0; d < 3; ++d) {
+    const double* a1 = h + 3 * ((d + 1) % 3);
+    const double* a2 = h + 3 * ((d + 2) % 3);
+    double cx = a1[1] * a2[2] - a1[2] * a2[1], cy = a1[2] * a2[0] - a1[0] * a2[2], cz = a1[0] * a2[1] - a1[1] * a2[0];
+    wd[d] = V / sqrt(cx * cx + cy * cy + cz * cz);
+  }
+}
+
+// Ewald split width from the real-space cutoff: erfc(r_cut / (sqrt2 omega)) = ewald_tol / 10
+double split_width(const qeq_plan_desc& D) { return D.r_cut / (sqrt(2.0) * erfc_inv(0.1 * D.ewald_tol)); }
+
+// narrowest reciprocal Gaussian width w_st = max(gamma_st, omega) of a structure
+double narrowest_width(const double* sig, int S, double omega) {
+  double wmin = 1e300;
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b < S; ++b) {
+      double g = sqrt(sig[a] * sig[a] + sig[b] * sig[b]);
+      wmin = std::min(wmin, g < 0.999 * omega ? omega : g);
+    }
+  return wmin;
+}
+
+// Mesh for B-spline order pp.  An explicit mesh_spacing is honoured; otherwise
+// the spacing comes from an error model fitted to measured smooth-PME errors
+// of the matvec on equilibrium (solution) charge vectors against the dense
+// Ewald matrix: rel. error ~ max(10^(a_p + b_p h / w_min), floor_p), h the
+// spacing between lattice planes.  Returns false if no mesh of at most 1000
+// points per direction is predicted to reach ewald_tol / 2.
+// cost ~ mesh traffic + spline work per atom.
+bool choose_mesh(const double* h, double V, double wmin, double n_atoms, int pp, const qeq_plan_desc& D, int* K,
+                 double* cost) {
+  double a = (pp == 4) ? -7.0 : (pp == 6 ? -9.5 : -11.5);
+  double b = (pp == 4) ? 10.0 : (pp == 6 ? 10.8 : 12.6);
+  double floor_p = (pp == 4) ? 1e-5 : (pp == 6 ? 7e-7 : 2e-8);
+  double target = 0.5 * D.ewald_tol;
+  double hsp;
+  if (D.mesh_spacing > 0) {
+    hsp = D.mesh_spacing;
+  } else {
+    if (floor_p > target) return false;
+    hsp = (log10(target) - a) / b * wmin;
+  }
+  if (!(hsp > 0)) return false;
+  double wd[3];
+  plane_widths(h, V, wd);
+  for (int d = 0; d < 3; ++d) {
+    int k = (int)ceil(wd[d] / hsp - 1e-9);
+    k = next_smooth(std::max(k, std::max(2 * pp, 12)));
+    if (k > 1000) return false;
+    K[d] = k;
+  }
+  double M = (double)K[0] * K[1] * K[2];
+  *cost = M * (14.0 + 0.2 * log2(M)) + n_atoms * pp * pp * pp * 0.25;
+  return true;
+}
+
+const int kSlotBudget = 4096;  // complex elements per FFT buffer of one CTA
+
+}  // namespace
+
+static qeq_status fail(qeq_plan_s* P, qeq_status st, const std::string& msg) {
+  if (P) P->last_error = msg;
+  return st;
+}
+
+static void free_plan(qeq_plan_s* P) {
+  if (!P) return;
+  void* ptrs[] = {P->d_st,     P->d_fft,     P->d_tw64,    P->d_tw32,     P->d_bmod,    P->d_bmod32,
+                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_xpairs,   P->d_bin_struct, P->d_atom_struct,
+                  P->d_chunks, P->d_key,     P->d_bin_count, P->d_bin_start, P->d_bin_fill, P->d_perm,
+                  P->d_scan_tmp, P->d_base,  P->d_wts,     P->d_wts32,    P->d_spec,    P->d_J,
+                  P->d_chi,    P->d_dinv,    P->d_posc,    P->d_row,      P->d_row_cnt, P->d_col,
+                  P->d_val64,  P->d_val32,   P->d_q,       P->d_r,        P->d_z,       P->d_p,
+                  P->d_Ap,     P->d_x,       P->d_mesh,    P->d_part,     P->d_counter, P->d_sc,
+                  P->d_err,    P->d_done};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (P->h_done) cudaFreeHost(P->h_done);
+  if (P->ev_done) cudaEventDestroy(P->ev_done);
+  if (P->graph_iter) cudaGraphExecDestroy(P->graph_iter);
+}
+
+extern "C" const char* qeq_status_str(qeq_status s) {
+  switch (s) {
+    case QEQ_OK: return "ok";
+    case QEQ_ERR_INVALID: return "invalid argument or input";
+    case QEQ_ERR_NOT_PD: return "QEq matrix not positive definite (J <= 0 or sigma <= 0)";
+    case QEQ_ERR_NOCONV: return "PCG did not converge within max_iter";
+    case QEQ_ERR_CUDA: return "CUDA runtime error";
+    case QEQ_ERR_OOM: return "device allocation failed";
+    case QEQ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case QEQ_ERR_CAPACITY: return "real-space pair list exceeds the plan's capacity";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* qeq_last_error(qeq_plan plan) {
+  if (!plan) return "null plan";
+  return plan->last_error.c_str();
+}
+
+extern "C" void qeq_plan_destroy(qeq_plan plan) {
+  if (!plan) return;
+  free_plan(plan);
+  delete plan;
+}
+
+extern "C" qeq_status qeq_plan_query(qeq_plan P, int32_t s, qeq_plan_info* out) {
+  if (!P || !out) return QEQ_ERR_INVALID;
+  if (s < 0 || s >= P->n_struct) return fail(P, QEQ_ERR_INVALID, "structure index out of range");
+  const StructDev& S = P->hs[s];
+  for (int d = 0; d < 3; ++d) out->mesh[d] = S.K[d];
+  out->spline_order = S.p;
+  out->n_species = S.S;
+  int nn = 0;
+  for (int a = 0; a < S.S; ++a)
+    for (int b = a; b < S.S; ++b) nn += (S.narrow[a] >> b) & 1u;
+  out->narrow_pairs = nn;
+  out->omega = S.omega;
+  out->r_cut = S.r_cut;
+  out->volume = S.V;
+  out->n_atoms = S.atom_end - S.atom_begin;
+  out->pair_capacity = P->pair_cap;
+  out->workspace_bytes = P->workspace_bytes;
+  out->kernel_launches = P->launches;
+  return QEQ_OK;
+}
+
+static qeq_status build_plan(qeq_plan_s* P) {
+  qeq_plan_desc& D = P->desc;
+  const int ns = D.n_struct;
+  const int S = D.n_species;
+  const int p = D.spline_order;
+  P->n_struct = ns;
+  P->offsets.assign(D.atom_offsets, D.atom_offsets + ns + 1);
+  P->n_atoms = P->offsets[ns];
+  P->precision = D.precision;
+  P->max_p = 0;
+  P->max_S = S;
+  P->max_ncm = (S + 1) / 2;
+
+  std::vector<StructDev> hs(ns);
+  std::map<int, int> fft_index;
+  std::vector<FftPlanDev> fplans;
+  std::vector<double2> tw64;
+  std::vector<float2> tw32;
+  std::vector<double> bmod;
+  std::vector<float> bmod32;
+  std::vector<int4> zit, yit, xit;
+  std::vector<int2> xpairs;
+  std::vector<int> bin_struct;
+  std::vector<Chunk> chunks;
+  int64_t mesh_off = 0;
+  int bin_off = 0;
+  int64_t pair_cap = 0;
+  int64_t smem_elems = 0;
+  const int ly = 8;
+  P->ly = ly;
+
+  // B-spline order: one per plan (the kernels are specialised on it); when not
+  // given, the order with the smallest summed cost over all structures
+  int pbest = p;
+  if (pbest == 0) {
+    const double omega = split_width(D);
+    double best = 1e300;
+    for (int pp : {4, 6, 8}) {
+      double tot = 0.0;
+      bool ok = true;
+      for (int s = 0; s < ns && ok; ++s) {
+        const double* h = D.cells + 9 * s;
+        double V = fabs(det3(h)), c = 0;
+        int K[3];
+        ok = V > 1e-9 && choose_mesh(h, V, narrowest_width(D.sigma + (size_t)S * s, S, omega),
+                                     (double)(P->offsets[s + 1] - P->offsets[s]), pp, D, K, &c);
+        tot += c;
+      }
+      if (ok && tot < best) {
+        best = tot;
+        pbest = pp;
+      }
+    }
+    if (pbest == 0) return fail(P, QEQ_ERR_INVALID, "no mesh meets ewald_tol within 1000 points per direction");
+  }
+  P->max_p = pbest;
+
+  auto fft_plan_for = [&](int K) {
+    auto it = fft_index.find(K);
+    if (it != fft_index.end()) return it->second;
+    FftPlanDev f;
+    memset(&f, 0, sizeof(f));
+    f.K = K;
+    std::vector<int> r = radices(K);
+    f.nst = (int)r.size();
+    for (size_t i = 0; i < r.size(); ++i) f.radix[i] = r[i];
+    f.tw_off = (int)tw64.size();
+    for (int m = 0; m < K; ++m) {
+      double ang = -2.0 * kPi * (double)m / K;
+      tw64.push_back(make_double2(cos(ang), sin(ang)));
+      tw32.push_back(make_float2((float)cos(ang), (float)sin(ang)));
+    }
+    int idx = (int)fplans.size();
+    fplans.push_back(f);
+    fft_index[K] = idx;
+    return idx;
+  };
+
+  for (int s = 0; s < ns; ++s) {
+    StructDev& T = hs[s];
+    memset(&T, 0, sizeof(T));
+    const double* h = D.cells + 9 * s;
+    for (int k = 0; k < 9; ++k) {
+      if (!std::isfinite(h[k])) return fail(P, QEQ_ERR_INVALID, "non-finite cell");
+      T.h[k] = h[k];
+    }
+    double V = fabs(det3(h));
+    if (!(V > 1e-9)) return fail(P, QEQ_ERR_INVALID, "singular cell");
+    inv3(h, T.hinv);
+    T.V = V;
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) T.B[3 * d + c] = 2.0 * kPi * T.hinv[3 * c + d];
+    T.green_pref = D.coulomb_k * 4.0 * kPi / V;
+    T.S = S;
+    T.ncm = (S + 1) / 2;
+    T.p = pbest;
+    T.atom_begin = P->offsets[s];
+    T.atom_end = P->offsets[s + 1];
+    if (T.atom_end <= T.atom_begin) return fail(P, QEQ_ERR_INVALID, "structure without atoms");
+    const double* sig = D.sigma + (size_t)S * s;
+    for (int a = 0; a < S; ++a)
+      if (!(sig[a] > 0.0) || !std::isfinite(sig[a])) return fail(P, QEQ_ERR_NOT_PD, "sigma must be finite and > 0");
+    // --- Ewald split: omega from the real-space cutoff and the target accuracy
+    double rc = D.r_cut;
+    double omega = split_width(D);
+    T.r_cut = rc;
+    T.omega = omega;
+    double wmin = 1e300;
+    int any = 0;
+    for (int a = 0; a < S; ++a) {
+      for (int b = 0; b < S; ++b) {
+        double g = sqrt(sig[a] * sig[a] + sig[b] * sig[b]);
+        bool narrow = g < 0.999 * omega;
+        double w = narrow ? omega : g;
+        int k = a * QEQ_MAX_SPECIES + b;
+        T.w2[k] = w * w;
+        // G = 0 width term restricted to the real-space sphere r < r_cut, the same
+        // region the pair sum covers: k_e (4 pi / V) int_0^rc r [erfc(r/(sqrt2 w)) - erfc(r/(sqrt2 g))] dr.
+        // With rc -> infinity this is k_e (2 pi / V)(w^2 - g^2); truncating both
+        // consistently leaves only the charge fluctuations beyond r_cut unaccounted.
+        T.corr[k] = narrow ? D.coulomb_k * (4.0 * kPi / V) * (sphere_int(sqrt(2.0) * w, rc) - sphere_int(sqrt(2.0) * g, rc))
+                           : 0.0;
+        T.inv_sw[k] = 1.0 / (sqrt(2.0) * w);
+        T.inv_sg[k] = 1.0 / (sqrt(2.0) * g);
+        if (narrow) {
+          T.narrow[a] |= 1u << b;
+          any = 1;
+        }
+        wmin = std::min(wmin, w);
+      }
+      double g = sqrt(2.0) * sig[a];
+      double w = (g < 0.999 * omega) ? omega : g;
+      T.self_s[a] = D.coulomb_k * sqrt(2.0 / kPi) * (1.0 / g - 1.0 / w);
+      T.diag_s[a] = D.coulomb_k / (sig[a] * sqrt(kPi));
+    }
+    T.any_narrow = any;
+    // --- mesh for the plan's B-spline order
+    double wd[3];
+    plane_widths(h, V, wd);
+    int Kbest[3];
+    double cst;
+    if (!choose_mesh(h, V, wmin, (double)(T.atom_end - T.atom_begin), pbest, D, Kbest, &cst))
+      return fail(P, QEQ_ERR_INVALID, "no mesh meets ewald_tol within 1000 points per direction");
+    for (int d = 0; d < 3; ++d) {
+      int K = Kbest[d];
+      T.K[d] = K;
+      (void)cst;
+      T.nb[d] = (K + QEQ_BIN - 1) / QEQ_BIN;
+      // bins that can hold an atom within r_cut (plus one for a ragged last bin)
+      double l = rc / wd[d] * K / QEQ_BIN;
+      int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
+      T.rs_range[d] = std::max(1, R);
+    }
+    T.M = (int64_t)T.K[0] * T.K[1] * T.K[2];
+    T.mesh_off = mesh_off;
+    mesh_off += T.M * T.ncm;
+    T.bin_off = bin_off;
+    int nbins = T.nb[0] * T.nb[1] * T.nb[2];
+    for (int b = 0; b < nbins; ++b) bin_struct.push_back(s);
+    bin_off += nbins;
+    for (int d = 0; d < 3; ++d) {
+      T.fft_plan[d] = fft_plan_for(T.K[d]);
+      T.bmod_off[d] = (int)bmod.size();
+      std::vector<double> bm(T.K[d]);
+      bspline_moduli(T.K[d], T.p, bm.data());
+      for (double v : bm) {
+        bmod.push_back(v);
+        bmod32.push_back((float)v);
+      }
+    }
+    // --- FFT work lists
+    const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
+    int lz = std::max(1, kSlotBudget / K2);
+    for (int c = 0; c < T.ncm; ++c)
+      for (int l = 0; l < K0 * K1; l += lz) zit.push_back(make_int4(s, c, l, std::min(lz, K0 * K1 - l)));
+    smem_elems = std::max<int64_t>(smem_elems, (int64_t)K2 * (1 + 2 * std::min(lz, K0 * K1)));
+    int lyy = std::max(1, std::min(ly, kSlotBudget / K1));
+    if (lyy < ly) return fail(P, QEQ_ERR_INVALID, "mesh too large for the y-pass tile");
+    for (int c = 0; c < T.ncm; ++c)
+      for (int x = 0; x < K0; ++x)
+        for (int z0 = 0; z0 < K2; z0 += ly) yit.push_back(make_int4(s, c, x, z0));
+    smem_elems = std::max<int64_t>(smem_elems, (int64_t)K1 * (1 + 2 * ly));
+    T.xpair_off = (int)xpairs.size();
+    for (int y = 0; y < K1; ++y)
+      for (int z = 0; z < K2; ++z) {
+        int l = y * K2 + z;
+        int lm = ((K1 - y) % K1) * K2 + (K2 - z) % K2;
+        if (l <= lm) xpairs.push_back(make_int2(l, lm));
+      }
+    int npairs = (int)xpairs.size() - T.xpair_off;
+    int np = std::max(1, kSlotBudget / (2 * T.ncm * K0));
+    for (int j = 0; j < npairs; j += np)
+      xit.push_back(make_int4(s, T.xpair_off + j, std::min(np, npairs - j), 0));
+    smem_elems = std::max<int64_t>(smem_elems, (int64_t)K0 * (1 + 2 * 2 * std::min(np, npairs) * T.ncm));
+    // --- real-space pair capacity: local density bound with margin
+    if (any) {
+      int64_t n = T.atom_end - T.atom_begin;
+      double per = (double)n / V * (4.0 / 3.0) * kPi * rc * rc * rc;
+      pair_cap += n * (int64_t)ceil(1.5 * per + 16.0);
+    }
+    // --- reduction chunks
+    int first = (int)chunks.size();
+    int64_t nat = T.atom_end - T.atom_begin;
+    int cnt = (int)((nat + QEQ_CHUNK - 1) / QEQ_CHUNK);
+    for (int c = 0; c < cnt; ++c) {
+      Chunk ch;
+      ch.s = s;
+      ch.begin = T.atom_begin + (int64_t)c * QEQ_CHUNK;
+      ch.end = std::min<int64_t>(T.atom_end, ch.begin + QEQ_CHUNK);
+      ch.first = first;
+      ch.count = cnt;
+      ch.last = (c == cnt - 1);
+      chunks.push_back(ch);
+    }
+  }
+  P->hs = hs;
+  P->hfft = fplans;
+  P->total_bins = bin_off;
+  P->total_mesh = mesh_off;
+  P->pair_cap = pair_cap;
+  P->n_chunks = (int)chunks.size();
+  P->n_zitems = (int)zit.size();
+  P->n_yitems = (int)yit.size();
+  P->n_xitems = (int)xit.size();
+  P->fft_smem_elems = smem_elems;
+  if ((size_t)smem_elems * sizeof(double2) > 200 * 1024)
+    return fail(P, QEQ_ERR_INVALID, "FFT tile exceeds shared memory");
+
+  // atom -> structure (input order)
+  std::vector<int> atom_struct(P->n_atoms);
+  for (int s = 0; s < ns; ++s)
+    for (int64_t a = P->offsets[s]; a < P->offsets[s + 1]; ++a) atom_struct[a] = s;
+
+  cudaError_t e = cudaSuccess;
+#define ALLOC(expr)                                                                       \
+  do {                                                                                    \
+    e = (expr);                                                                           \
+    if (e != cudaSuccess) return fail(P, e == cudaErrorMemoryAllocation ? QEQ_ERR_OOM : QEQ_ERR_CUDA, \
+                                      std::string("plan allocation: ") + cudaGetErrorString(e));     \
+  } while (0)
+  ALLOC(upload(P, &P->d_st, hs));
+  ALLOC(upload(P, &P->d_fft, fplans));
+  ALLOC(upload(P, &P->d_tw64, tw64));
+  ALLOC(upload(P, &P->d_tw32, tw32));
+  ALLOC(upload(P, &P->d_bmod, bmod));
+  ALLOC(upload(P, &P->d_bmod32, bmod32));
+  ALLOC(upload(P, &P->d_zitems, zit));
+  ALLOC(upload(P, &P->d_yitems, yit));
+  ALLOC(upload(P, &P->d_xitems, xit));
+  ALLOC(upload(P, &P->d_xpairs, xpairs));
+  ALLOC(upload(P, &P->d_bin_struct, bin_struct));
+  ALLOC(upload(P, &P->d_atom_struct, atom_struct));
+  ALLOC(upload(P, &P->d_chunks, chunks));
+  const int64_t N = P->n_atoms;
+  ALLOC(dalloc(P, &P->d_key, N));
+  ALLOC(dalloc(P, &P->d_bin_count, P->total_bins + 1));
+  ALLOC(dalloc(P, &P->d_bin_start, P->total_bins + 1));
+  ALLOC(dalloc(P, &P->d_bin_fill, P->total_bins + 1));
+  ALLOC(dalloc(P, &P->d_perm, N));
+  // scan scratch: per-1024 block sums of either scan (int64 for the pair rows)
+  ALLOC(dalloc(P, (int64_t**)&P->d_scan_tmp, (size_t)(std::max<int64_t>(N, P->total_bins) / 1024 + 8)));
+  ALLOC(dalloc(P, &P->d_base, N));
+  ALLOC(dalloc(P, &P->d_wts, (size_t)N * 3 * QEQ_MAXP));
+  ALLOC(dalloc(P, &P->d_wts32, (size_t)N * 3 * QEQ_MAXP));
+  ALLOC(dalloc(P, &P->d_spec, N));
+  ALLOC(dalloc(P, &P->d_J, N));
+  ALLOC(dalloc(P, &P->d_chi, N));
+  ALLOC(dalloc(P, &P->d_dinv, N));
+  ALLOC(dalloc(P, &P->d_posc, (size_t)N * 3));
+  ALLOC(dalloc(P, &P->d_row, N + 1));
+  ALLOC(dalloc(P, &P->d_row_cnt, N));
+  ALLOC(dalloc(P, &P->d_col, pair_cap));
+  ALLOC(dalloc(P, &P->d_val64, pair_cap));
+  ALLOC(dalloc(P, &P->d_val32, pair_cap));
+  for (double** v : {&P->d_q, &P->d_r, &P->d_z, &P->d_p, &P->d_Ap, &P->d_x}) ALLOC(dalloc(P, v, N));
+  ALLOC(dalloc(P, &P->d_mesh, (size_t)P->total_mesh));
+  ALLOC(dalloc(P, &P->d_part, (size_t)P->n_chunks * QEQ_MAX_SPECIES * 2 + P->total_bins + 64));
+  ALLOC(dalloc(P, &P->d_counter, (size_t)ns * 4));
+  ALLOC(cudaMemset(P->d_counter, 0, sizeof(int) * ns * 4));
+  ALLOC(dalloc(P, &P->d_sc, ns));
+  ALLOC(cudaMemset(P->d_sc, 0, sizeof(PcgScalars) * ns));
+  ALLOC(dalloc(P, &P->d_err, 4));
+  ALLOC(cudaMemset(P->d_err, 0, sizeof(int) * 4));
+  ALLOC(dalloc(P, &P->d_done, 4));
+  ALLOC(cudaHostAlloc((void**)&P->h_done, sizeof(int) * 8, cudaHostAllocDefault));
+  ALLOC(cudaEventCreateWithFlags(&P->ev_done, cudaEventDisableTiming));
+  ALLOC(matvec_set_attributes());
+#undef ALLOC
+  return QEQ_OK;
+}
+
+extern "C" qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stream, qeq_plan* out) {
+  if (!desc || !out) return QEQ_ERR_INVALID;
+  *out = nullptr;
+  if (desc->n_struct < 1 || !desc->atom_offsets || !desc->cells || !desc->sigma) return QEQ_ERR_INVALID;
+  if (desc->n_species < 1 || desc->n_species > QEQ_MAX_SPECIES) return QEQ_ERR_INVALID;
+  if (desc->atom_offsets[0] != 0) return QEQ_ERR_INVALID;
+  for (int s = 0; s < desc->n_struct; ++s)
+    if (desc->atom_offsets[s + 1] <= desc->atom_offsets[s]) return QEQ_ERR_INVALID;
+  if (desc->atom_offsets[desc->n_struct] > (int64_t)INT32_MAX / 4) return QEQ_ERR_INVALID;
+  qeq_plan_s* P = new qeq_plan_s();
+  P->desc = *desc;
+  qeq_plan_desc& D = P->desc;
+  if (!(D.coulomb_k > 0)) D.coulomb_k = 14.3996454784;
+  if (!(D.charge_tol > 0)) D.charge_tol = 1e-5;
+  if (!(D.ewald_tol > 0)) D.ewald_tol = 1e-6;
+  if (!(D.r_cut > 0)) D.r_cut = 8.0;
+  if (D.max_iter <= 0) D.max_iter = 1000;
+  if (D.spline_order != 0 && D.spline_order != 4 && D.spline_order != 6 && D.spline_order != 8) {
+    delete P;
+    return QEQ_ERR_INVALID;
+  }
+  if (D.precision != QEQ_FP64 && D.precision != QEQ_MIXED) {
+    delete P;
+    return QEQ_ERR_INVALID;
+  }
+  P->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&P->device);
+  P->graph_ok = (P->stream != nullptr) && !(D.flags & QEQ_FLAG_NO_GRAPH);
+  qeq_status st = build_plan(P);
+  // the caller's description arrays are not kept
+  D.atom_offsets = nullptr;
+  D.cells = nullptr;
+  D.sigma = nullptr;
+  if (st != QEQ_OK) {
+    free_plan(P);
+    delete P;
+    return st;
+  }
+  *out = P;
+  return QEQ_OK;
+}

@@ -1,0 +1,602 @@
+// The QEq solve (Sec. 2.4, bordered system eq. 4G_qeq_prime; SI eq. qeq):
+// Jacobi-preconditioned conjugate gradient restricted to the charge-constraint
+// plane sum_i q_i = q_tot, around the plane-wave matvec of matvec.cu.
+//
+//   r = -chi - A q                       (A = E + diag J)
+//   z = D^-1 (r - s 1),  s = (1^T D^-1 r)/(1^T D^-1 1)     so that 1^T z = 0
+//   p = z + beta p,  alpha = r.z / p.Ap,  q += alpha p,  r -= alpha Ap
+//
+// Every search direction sums to zero, so q stays on the constraint plane.
+// At convergence A q + chi = mu 1 with mu = -mean(r) (the bordered lambda is
+// -mu).  All vector arithmetic, dot products, the projection and mu are FP64;
+// in QEQ_MIXED the matvec inside the iteration is FP32, and a final FP64
+// matvec recomputes the true residual; if that residual misses the tolerance
+// the iteration restarts from it (residual replacement, i.e. iterative
+// refinement).  Structures of a batch iterate together and drop out as they
+// converge; a block of iterations is captured once in a CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "qeq_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double wmin(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+enum { RED_SUM = 0, RED_MAX = 1, RED_MIN = 2 };
+
+// Block reduction of NV values (op per value), written to part[chunk*8 + k];
+// returns true in thread 0 of the last chunk of the structure, which then
+// combines the chunk partials in chunk order (deterministic).
+template <int NV>
+__device__ bool chunk_reduce(double (&v)[NV], const int (&op)[NV], const Chunk& ch, double* part, int* counter,
+                             double (&tot)[NV]) {
+  __shared__ double red[NV][32];
+  __shared__ bool last;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = op[k] == RED_SUM ? wsum(v[k]) : (op[k] == RED_MAX ? wmax(v[k]) : wmin(v[k]));
+    if (lane == 0) red[k][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) {
+      double x = red[k][0];
+      for (int i = 1; i < nw; ++i)
+        x = op[k] == RED_SUM ? x + red[k][i] : (op[k] == RED_MAX ? fmax(x, red[k][i]) : fmin(x, red[k][i]));
+      part[(size_t)blockIdx.x * 8 + k] = x;
+    }
+    __threadfence();
+    int prev = atomicAdd(counter + ch.s, 1);
+    last = (prev == ch.count - 1);
+    if (last) {
+      __threadfence();
+      for (int k = 0; k < NV; ++k) {
+        double x = ((volatile double*)part)[(size_t)ch.first * 8 + k];
+        for (int i = 1; i < ch.count; ++i) {
+          double y = ((volatile double*)part)[(size_t)(ch.first + i) * 8 + k];
+          x = op[k] == RED_SUM ? x + y : (op[k] == RED_MAX ? fmax(x, y) : fmin(x, y));
+        }
+        tot[k] = x;
+      }
+      counter[ch.s] = 0;
+    }
+  }
+  __syncthreads();
+  return threadIdx.x == 0 && last;
+}
+
+// q0: user charges (permuted to sorted order) or zero; sums for the projection.
+__global__ void k_init(const Chunk* __restrict__ chunks, const int* __restrict__ perm, const double* __restrict__ q_user,
+                       int warm, const double* __restrict__ dinv, const double* __restrict__ chi,
+                       const double* __restrict__ J, double* __restrict__ q, PcgScalars* __restrict__ sc,
+                       double* part, int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  double v[6] = {0, 0, 0, 0, 1e300, 0};
+  const int op[6] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM, RED_MIN, RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    double qa = (warm == QEQ_WARM_USER) ? q_user[perm[a]] : 0.0;
+    if (!isfinite(qa)) qa = 0.0;
+    q[a] = qa;
+    v[0] += qa;
+    v[1] += dinv[a];
+    v[2] += chi[a];
+    v[3] += chi[a] * chi[a];
+    v[4] = fmin(v[4], J[a]);
+  }
+  double tot[6];
+  if (chunk_reduce<6>(v, op, ch, part, counter, tot)) {
+    PcgScalars& c = sc[ch.s];
+    double n = (double)c.n;
+    c.qsum = tot[0];
+    c.s0 = tot[1];
+    c.chi_p2 = fmax(tot[3] - tot[2] * tot[2] / n, 0.0);
+    c.j_min = tot[4];
+  }
+}
+
+// project q onto the constraint plane: q += (q_tot - sum q)/n
+__global__ void k_project(const Chunk* __restrict__ chunks, double* __restrict__ q, const PcgScalars* __restrict__ sc) {
+  const Chunk ch = chunks[blockIdx.x];
+  const PcgScalars& c = sc[ch.s];
+  double d = (c.q_tot - c.qsum) / (double)c.n;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) q[a] += d;
+}
+
+// residual statistics -> convergence test (thread 0 of the last chunk)
+__device__ void residual_test(PcgScalars& c, const double* tot, int max_iter, int final_check) {
+  double n = (double)c.n;
+  c.r_sum = tot[1];
+  c.r_sq = tot[2];
+  c.r_max = tot[3];
+  c.r_min = tot[4];
+  c.shift = tot[0] / c.s0;
+  double mean = c.r_sum / n;
+  double pinf = fmax(c.r_max - mean, mean - c.r_min);
+  double pl2 = sqrt(fmax(c.r_sq - c.r_sum * mean, 0.0));
+  bool ok = pinf <= c.tol_inf && (c.tol_l2 <= 0.0 || pl2 <= c.tol_l2);
+  if (!isfinite(pinf)) ok = false;
+  if (final_check) {
+    c.converged = ok ? 1 : 0;
+  } else {
+    if (ok) {
+      c.converged = 1;
+      c.active = 0;
+    } else if (c.iters >= max_iter) {
+      c.active = 0;
+    }
+  }
+}
+
+// r = -chi - Aq (true residual) + statistics
+__global__ void k_resid(const Chunk* __restrict__ chunks, const double* __restrict__ chi, const double* __restrict__ Aq,
+                        const double* __restrict__ dinv, double* __restrict__ r, PcgScalars* __restrict__ sc,
+                        int only_flagged, double* part, int* counter, int max_iter) {
+  const Chunk ch = chunks[blockIdx.x];
+  double v[5] = {0, 0, 0, -1e300, 1e300};
+  const int op[5] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX, RED_MIN};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    double ra = -chi[a] - Aq[a];
+    r[a] = ra;
+    v[0] += dinv[a] * ra;
+    v[1] += ra;
+    v[2] += ra * ra;
+    v[3] = fmax(v[3], ra);
+    v[4] = fmin(v[4], ra);
+  }
+  double tot[5];
+  if (chunk_reduce<5>(v, op, ch, part, counter, tot)) residual_test(sc[ch.s], tot, max_iter, 1);
+  (void)only_flagged;
+}
+
+// q += alpha p ; r -= alpha Ap ; statistics of the new r
+__global__ void k_update(const Chunk* __restrict__ chunks, const double* __restrict__ p, const double* __restrict__ Ap,
+                         const double* __restrict__ dinv, double* __restrict__ q, double* __restrict__ r,
+                         PcgScalars* __restrict__ sc, double* part, int* counter, int max_iter) {
+  const Chunk ch = chunks[blockIdx.x];
+  if (!sc[ch.s].active) return;
+  const double alpha = sc[ch.s].alpha;
+  double v[5] = {0, 0, 0, -1e300, 1e300};
+  const int op[5] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX, RED_MIN};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    q[a] += alpha * p[a];
+    double ra = r[a] - alpha * Ap[a];
+    r[a] = ra;
+    v[0] += dinv[a] * ra;
+    v[1] += ra;
+    v[2] += ra * ra;
+    v[3] = fmax(v[3], ra);
+    v[4] = fmin(v[4], ra);
+  }
+  double tot[5];
+  if (chunk_reduce<5>(v, op, ch, part, counter, tot)) {
+    PcgScalars& c = sc[ch.s];
+    c.iters += 1;
+    residual_test(c, tot, max_iter, 0);
+  }
+}
+
+// z = D^-1 (r - shift); rz_new = r.z; beta
+__global__ void k_precond(const Chunk* __restrict__ chunks, const double* __restrict__ r, const double* __restrict__ dinv,
+                          double* __restrict__ z, PcgScalars* __restrict__ sc, int restart, double* part, int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  if (!sc[ch.s].active) return;
+  const double sh = sc[ch.s].shift;
+  double v[1] = {0};
+  const int op[1] = {RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    double za = dinv[a] * (r[a] - sh);
+    z[a] = za;
+    v[0] += r[a] * za;
+  }
+  double tot[1];
+  if (chunk_reduce<1>(v, op, ch, part, counter, tot)) {
+    PcgScalars& c = sc[ch.s];
+    c.beta = (restart || c.rz == 0.0) ? 0.0 : tot[0] / c.rz;
+    c.rz = tot[0];
+  }
+}
+
+// p = z + beta p
+__global__ void k_direction(const Chunk* __restrict__ chunks, const double* __restrict__ z, double* __restrict__ p,
+                            const PcgScalars* __restrict__ sc) {
+  const Chunk ch = chunks[blockIdx.x];
+  if (!sc[ch.s].active) return;
+  const double beta = sc[ch.s].beta;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) p[a] = z[a] + beta * p[a];
+}
+
+// all structures inactive?
+__global__ void k_done(const PcgScalars* __restrict__ sc, int ns, int* __restrict__ done) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < ns; s += blockDim.x)
+    if (sc[s].active) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *done = any ? 0 : 1;
+}
+
+// after a final check: restart the failing structures (bounded), settle the rest
+__global__ void k_after_check(PcgScalars* __restrict__ sc, int ns, int max_restarts, int max_iter, int* __restrict__ done) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    PcgScalars& c = sc[s];
+    if (c.converged) {
+      c.status = QEQ_OK;
+      c.active = 0;
+    } else if (c.restarts < max_restarts && c.iters < max_iter) {
+      c.restarts += 1;
+      c.active = 1;
+      any = 1;
+    } else {
+      c.status = QEQ_ERR_NOCONV;
+      c.active = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *done = any ? 0 : 1;
+}
+
+__global__ void k_energy(const Chunk* __restrict__ chunks, const double* __restrict__ q, const double* __restrict__ Aq,
+                         const double* __restrict__ chi, const double* __restrict__ J, PcgScalars* __restrict__ sc,
+                         double* part, int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  double v[3] = {0, 0, 0};
+  const int op[3] = {RED_SUM, RED_SUM, RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    v[0] += chi[a] * q[a];
+    v[1] += q[a] * Aq[a];
+    v[2] += J[a] * q[a] * q[a];
+  }
+  double tot[3];
+  if (chunk_reduce<3>(v, op, ch, part, counter, tot)) {
+    PcgScalars& c = sc[ch.s];
+    c.E_lin = tot[0];
+    c.E_quad = tot[1];
+    c.E_J = tot[2];
+  }
+}
+
+__global__ void k_unsort(const int* __restrict__ perm, int64_t n, const double* __restrict__ src, double* __restrict__ dst) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) dst[perm[a]] = src[a];
+}
+
+__global__ void k_sort_in(const int* __restrict__ perm, int64_t n, const double* __restrict__ src, double* __restrict__ dst) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) dst[a] = src[perm[a]];
+}
+
+__global__ void k_write_mu(const PcgScalars* __restrict__ sc, int ns, double* __restrict__ mu,
+                           double* __restrict__ E_qeq, double* __restrict__ E_elec) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const PcgScalars& c = sc[s];
+  if (mu) mu[s] = -c.r_sum / (double)c.n;
+  if (E_qeq) E_qeq[s] = c.E_lin + 0.5 * c.E_quad;
+  if (E_elec) E_elec[s] = 0.5 * (c.E_quad - c.E_J);
+}
+
+// ------------------------------------------------------------------ host orchestration
+qeq_status cuda_fail(qeq_plan_s* P, cudaError_t e, const char* where) {
+  P->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return QEQ_ERR_CUDA;
+}
+
+#define TRY(expr)                                        \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(P, e_, #expr); \
+  } while (0)
+
+int* red_counter(qeq_plan_s* P) { return P->d_counter + 2 * P->n_struct; }
+double* red_part(qeq_plan_s* P) { return P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES + P->total_bins + 8; }
+
+cudaError_t one_iteration(qeq_plan_s* P, int prec) {
+  cudaStream_t s = P->stream;
+  int nc = P->n_chunks;
+  int max_iter = P->desc.max_iter;
+  QEQ_CUDA_TRY(launch_matvec(P, prec, P->d_p, P->d_Ap, 1, 1, 1, nullptr));
+  count_launch(P);
+  k_update<<<nc, 256, 0, s>>>(P->d_chunks, P->d_p, P->d_Ap, P->d_dinv, P->d_q, P->d_r, P->d_sc, red_part(P),
+                              red_counter(P), max_iter);
+  count_launch(P);
+  k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 0, red_part(P), red_counter(P));
+  count_launch(P);
+  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
+  return cudaGetLastError();
+}
+
+const int kItersPerCheck = 4;
+
+cudaError_t run_iterations(qeq_plan_s* P, int prec) {
+  cudaStream_t s = P->stream;
+  if (P->graph_ok) {
+    if (!P->graph_iter || P->graph_iter_prec != prec) {
+      if (P->graph_iter) {
+        cudaGraphExecDestroy(P->graph_iter);
+        P->graph_iter = nullptr;
+      }
+      cudaGraph_t g;
+      QEQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      P->capturing = true;
+      P->graph_kernels = 0;
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < kItersPerCheck && e == cudaSuccess; ++k) e = one_iteration(P, prec);
+      if (e == cudaSuccess) {
+        count_launch(P);
+        k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_done);
+        e = cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(s, &g);
+      P->capturing = false;
+      if (e != cudaSuccess) return e;
+      QEQ_CUDA_TRY(e2);
+      e = cudaGraphInstantiate(&P->graph_iter, g, 0);
+      cudaGraphDestroy(g);
+      QEQ_CUDA_TRY(e);
+      P->graph_iter_prec = prec;
+    }
+    QEQ_CUDA_TRY(cudaGraphLaunch(P->graph_iter, s));
+    P->launches += P->graph_kernels;
+  } else {
+    for (int k = 0; k < kItersPerCheck; ++k) QEQ_CUDA_TRY(one_iteration(P, prec));
+    count_launch(P);
+    k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_done);
+    QEQ_CUDA_TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  return cudaStreamSynchronize(s);
+}
+
+qeq_status check_inputs(qeq_plan_s* P) {
+  int err = 0;
+  TRY(cudaMemcpyAsync(P->h_done + 4, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  TRY(cudaStreamSynchronize(P->stream));
+  err = P->h_done[4];
+  if (err) {
+    TRY(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->stream));
+    if (err & ERRBIT_J) {
+      P->last_error = "hardness J must be > 0";
+      return QEQ_ERR_NOT_PD;
+    }
+    if (err & ERRBIT_PAIRCAP) {
+      P->last_error = "real-space pair list exceeds capacity";
+      return QEQ_ERR_CAPACITY;
+    }
+    P->last_error = (err & ERRBIT_SPECIES) ? "species index out of range" : "non-finite input";
+    return QEQ_ERR_INVALID;
+  }
+  return QEQ_OK;
+}
+
+qeq_status prepare(qeq_plan_s* P, const double* d_pos, const int32_t* d_species, const double* d_chi,
+                   const double* d_J) {
+  if (!d_pos || !d_species || !d_chi || !d_J) {
+    P->last_error = "null input pointer";
+    return QEQ_ERR_INVALID;
+  }
+  TRY(cudaSetDevice(P->device));
+  TRY(launch_prepare_atoms(P, d_pos, d_species, d_chi, d_J, P->pair_cap > 0));
+  return check_inputs(P);
+}
+
+qeq_status init_scalars(qeq_plan_s* P, const double* h_qtot) {
+  std::vector<PcgScalars> h(P->n_struct);
+  for (int s = 0; s < P->n_struct; ++s) {
+    PcgScalars& c = h[s];
+    memset(&c, 0, sizeof(c));
+    c.n = (int)(P->hs[s].atom_end - P->hs[s].atom_begin);
+    c.q_tot = h_qtot ? h_qtot[s] : 0.0;
+    c.active = 1;
+    c.status = QEQ_OK;
+  }
+  TRY(cudaMemcpyAsync(P->d_sc, h.data(), sizeof(PcgScalars) * h.size(), cudaMemcpyHostToDevice, P->stream));
+  TRY(cudaStreamSynchronize(P->stream));  // h goes out of scope
+  return QEQ_OK;
+}
+
+__global__ void k_set_tol(PcgScalars* sc, int ns, double charge_tol, double rel_tol) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  PcgScalars& c = sc[s];
+  c.tol_inf = 0.5 * charge_tol * c.j_min;
+  c.tol_l2 = rel_tol > 0 ? rel_tol * sqrt(c.chi_p2) : 0.0;
+}
+
+}  // namespace
+
+extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_chi,
+                                const double* d_J, const double* h_qtot, int32_t warm, double* d_q, double* d_mu,
+                                qeq_info* h_info) {
+  if (!P) return QEQ_ERR_INVALID;
+  if (!d_q) {
+    P->last_error = "d_q is required";
+    return QEQ_ERR_INVALID;
+  }
+  if (!h_qtot) {
+    P->last_error = "h_qtot is required";
+    return QEQ_ERR_INVALID;
+  }
+  for (int s = 0; s < P->n_struct; ++s)
+    if (!std::isfinite(h_qtot[s])) {
+      P->last_error = "non-finite q_tot";
+      return QEQ_ERR_INVALID;
+    }
+  qeq_status st = prepare(P, d_pos, d_species, d_chi, d_J);
+  if (st != QEQ_OK) return st;
+  st = init_scalars(P, h_qtot);
+  if (st != QEQ_OK) return st;
+  cudaStream_t s = P->stream;
+  const int nc = P->n_chunks, ns = P->n_struct;
+  const int prec = P->precision;
+  const int max_iter = P->desc.max_iter;
+  int wm = (warm == QEQ_WARM_USER) ? QEQ_WARM_USER : QEQ_WARM_COLD;
+  count_launch(P);
+  k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q, wm, P->d_dinv, P->d_chi, P->d_J, P->d_q, P->d_sc,
+                            red_part(P), red_counter(P));
+  count_launch(P);
+  k_project<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_sc);
+  count_launch(P);
+  k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol);
+  TRY(cudaGetLastError());
+  // first residual with the iteration's matvec
+  TRY(launch_matvec(P, prec, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
+  count_launch(P);
+  k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
+                             red_counter(P), max_iter);
+  count_launch(P);
+  k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 1, red_part(P), red_counter(P));
+  count_launch(P);
+  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
+  TRY(cudaGetLastError());
+  const int max_restarts = 4;
+  for (int outer = 0; outer <= max_restarts + 1; ++outer) {
+    // inner iterations (structures drop out as they converge); the device
+    // stops every structure at max_iter, the host bound is a second guard
+    const int max_launches = max_iter / kItersPerCheck + 2;
+    for (int l = 0; l < max_launches; ++l) {
+      TRY(run_iterations(P, prec));
+      if (P->h_done[0]) break;
+    }
+    // final FP64 check: true residual of every structure
+    TRY(launch_matvec(P, QEQ_FP64, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
+    count_launch(P);
+    k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
+                               red_counter(P), max_iter);
+    count_launch(P);
+    k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_done);
+    count_launch(P);
+    k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 1, red_part(P), red_counter(P));
+    count_launch(P);
+    k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
+    TRY(cudaGetLastError());
+    TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (P->h_done[0]) break;
+  }
+  // energy terms from the final FP64 matvec, outputs in input order
+  count_launch(P);
+  k_energy<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_Ap, P->d_chi, P->d_J, P->d_sc, red_part(P), red_counter(P));
+  int nb = (int)((P->n_atoms + 255) / 256);
+  count_launch(P);
+  k_unsort<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, P->d_q, d_q);
+  count_launch(P);
+  k_write_mu<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, d_mu, nullptr, nullptr);
+  TRY(cudaGetLastError());
+  std::vector<PcgScalars> h(ns);
+  TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  qeq_status worst = QEQ_OK;
+  for (int i = 0; i < ns; ++i) {
+    const PcgScalars& c = h[i];
+    double n = (double)c.n, mean = c.r_sum / n;
+    double pinf = fmax(c.r_max - mean, mean - c.r_min);
+    double pl2 = sqrt(fmax(c.r_sq - c.r_sum * mean, 0.0));
+    if (h_info) {
+      h_info[i].status = c.status;
+      h_info[i].iterations = c.iters;
+      h_info[i].restarts = c.restarts;
+      h_info[i].warm_used = (wm == QEQ_WARM_USER) ? 1 : 0;
+      h_info[i].residual_inf = pinf;
+      h_info[i].residual_l2 = pl2;
+      h_info[i].error_bound_l2 = pl2 / c.j_min;
+    }
+    if (c.status != QEQ_OK && worst == QEQ_OK) worst = (qeq_status)c.status;
+  }
+  if (worst == QEQ_ERR_NOCONV) P->last_error = "some structure did not converge within max_iter";
+  return worst;
+}
+
+extern "C" qeq_status qeq_energy(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_chi,
+                                 const double* d_J, const double* d_q, double* d_E_qeq, double* d_E_elec) {
+  if (!P) return QEQ_ERR_INVALID;
+  if (!d_q) {
+    P->last_error = "d_q is required";
+    return QEQ_ERR_INVALID;
+  }
+  qeq_status st = prepare(P, d_pos, d_species, d_chi, d_J);
+  if (st != QEQ_OK) return st;
+  st = init_scalars(P, nullptr);
+  if (st != QEQ_OK) return st;
+  cudaStream_t s = P->stream;
+  const int nc = P->n_chunks, ns = P->n_struct;
+  int nb = (int)((P->n_atoms + 255) / 256);
+  count_launch(P);
+  k_sort_in<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, d_q, P->d_x);
+  TRY(cudaGetLastError());
+  TRY(launch_matvec(P, QEQ_FP64, P->d_x, P->d_Ap, 1, 0, 0, nullptr));
+  count_launch(P);
+  k_energy<<<nc, 256, 0, s>>>(P->d_chunks, P->d_x, P->d_Ap, P->d_chi, P->d_J, P->d_sc, red_part(P), red_counter(P));
+  count_launch(P);
+  k_write_mu<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, nullptr, d_E_qeq, d_E_elec);
+  TRY(cudaGetLastError());
+  TRY(cudaStreamSynchronize(s));
+  return QEQ_OK;
+}
+
+extern "C" qeq_status qeq_matvec(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_J,
+                                 const double* d_x, double* d_y, int32_t force_fp64) {
+  if (!P) return QEQ_ERR_INVALID;
+  if (!d_x || !d_y || !d_pos || !d_species) {
+    P->last_error = "null pointer";
+    return QEQ_ERR_INVALID;
+  }
+  TRY(cudaSetDevice(P->device));
+  TRY(launch_prepare_atoms(P, d_pos, d_species, nullptr, d_J, P->pair_cap > 0));
+  qeq_status st = check_inputs(P);
+  if (st != QEQ_OK) return st;
+  st = init_scalars(P, nullptr);
+  if (st != QEQ_OK) return st;
+  cudaStream_t s = P->stream;
+  int nb = (int)((P->n_atoms + 255) / 256);
+  count_launch(P);
+  k_sort_in<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, d_x, P->d_x);
+  TRY(cudaGetLastError());
+  TRY(launch_matvec(P, force_fp64 ? QEQ_FP64 : P->precision, P->d_x, P->d_Ap, d_J ? 1 : 0, 0, 0, nullptr));
+  count_launch(P);
+  k_unsort<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, P->d_Ap, d_y);
+  TRY(cudaGetLastError());
+  TRY(cudaStreamSynchronize(s));
+  return QEQ_OK;
+}
+
+extern "C" qeq_status qeq_profile_matvec(qeq_plan P, int32_t n_rep, float* h_ms) {
+  if (!P || !h_ms || n_rep < 1) return QEQ_ERR_INVALID;
+  if (!P->have_atoms) {
+    P->last_error = "no atoms prepared: call qeq_solve or qeq_matvec first";
+    return QEQ_ERR_INVALID;
+  }
+  cudaEvent_t ev[QEQ_N_STAGES + 1];
+  for (auto& e : ev) TRY(cudaEventCreate(&e));
+  std::vector<double> acc(QEQ_N_STAGES, 0.0);
+  for (int r = 0; r < n_rep; ++r) {
+    TRY(launch_matvec(P, P->precision, P->d_x, P->d_Ap, 1, 0, 0, ev));
+    TRY(cudaEventSynchronize(ev[QEQ_N_STAGES]));
+    for (int k = 0; k < QEQ_N_STAGES; ++k) {
+      float ms = 0.f;
+      TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      acc[k] += ms;
+    }
+  }
+  for (int k = 0; k < QEQ_N_STAGES; ++k) h_ms[k] = (float)(acc[k] / n_rep);
+  for (auto& e : ev) cudaEventDestroy(e);
+  return QEQ_OK;
+}

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libqeq.so (include/qeq.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Device arrays are torch CUDA tensors (float64 / int32, contiguous); the plan
+owns a private CUDA stream that waits for the caller's current stream before
+each call.  If the library is missing the import fails loudly: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqeq.so")
+
+QEQ_OK, QEQ_ERR_INVALID, QEQ_ERR_NOT_PD, QEQ_ERR_NOCONV, QEQ_ERR_CUDA, QEQ_ERR_OOM, QEQ_ERR_TIMEOUT, \
+    QEQ_ERR_CAPACITY = range(8)
+QEQ_FP64, QEQ_MIXED = 0, 1
+QEQ_WARM_COLD, QEQ_WARM_USER, QEQ_WARM_MLP = 0, 1, 2
+QEQ_FLAG_NO_GRAPH = 1
+QEQ_N_STAGES = 8
+STAGE_NAMES = ["species_sums", "spread", "fft_z", "fft_y", "fft_x_green", "ifft_y", "ifft_z", "gather"]
+
+EXPORTED = ["qeq_plan_create", "qeq_plan_destroy", "qeq_plan_query", "qeq_solve", "qeq_energy", "qeq_matvec",
+            "qeq_profile_matvec", "qeq_status_str", "qeq_last_error"]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_struct", ctypes.c_int32),
+        ("atom_offsets", ctypes.POINTER(ctypes.c_int64)),
+        ("cells", ctypes.POINTER(ctypes.c_double)),
+        ("n_species", ctypes.c_int32),
+        ("sigma", ctypes.POINTER(ctypes.c_double)),
+        ("coulomb_k", ctypes.c_double),
+        ("charge_tol", ctypes.c_double),
+        ("ewald_tol", ctypes.c_double),
+        ("r_cut", ctypes.c_double),
+        ("spline_order", ctypes.c_int32),
+        ("mesh_spacing", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("max_iter", ctypes.c_int32),
+        ("residual_tol", ctypes.c_double),
+        ("flags", ctypes.c_int32),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("iterations", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+        ("warm_used", ctypes.c_int32),
+        ("residual_inf", ctypes.c_double),
+        ("residual_l2", ctypes.c_double),
+        ("error_bound_l2", ctypes.c_double),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("mesh", ctypes.c_int32 * 3),
+        ("spline_order", ctypes.c_int32),
+        ("n_species", ctypes.c_int32),
+        ("narrow_pairs", ctypes.c_int32),
+        ("omega", ctypes.c_double),
+        ("r_cut", ctypes.c_double),
+        ("volume", ctypes.c_double),
+        ("n_atoms", ctypes.c_int64),
+        ("pair_capacity", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqeq.so and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2607_17978_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+    lib.qeq_plan_create.argtypes = [ctypes.POINTER(PlanDesc), vp, ctypes.POINTER(vp)]
+    lib.qeq_plan_create.restype = ctypes.c_int
+    lib.qeq_plan_destroy.argtypes = [vp]
+    lib.qeq_plan_destroy.restype = None
+    lib.qeq_plan_query.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(PlanInfo)]
+    lib.qeq_plan_query.restype = ctypes.c_int
+    lib.qeq_solve.argtypes = [vp, vp, vp, vp, vp, dp, ctypes.c_int32, vp, vp, ctypes.POINTER(Info)]
+    lib.qeq_solve.restype = ctypes.c_int
+    lib.qeq_energy.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.qeq_energy.restype = ctypes.c_int
+    lib.qeq_matvec.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int32]
+    lib.qeq_matvec.restype = ctypes.c_int
+    lib.qeq_profile_matvec.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+    lib.qeq_profile_matvec.restype = ctypes.c_int
+    lib.qeq_status_str.argtypes = [ctypes.c_int]
+    lib.qeq_status_str.restype = ctypes.c_char_p
+    lib.qeq_last_error.argtypes = [vp]
+    lib.qeq_last_error.restype = ctypes.c_char_p
+    del ip
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+class QEqError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+@dataclass
+class SolveResult:
+    q: "object"          # torch tensor (N,) float64, input atom order
+    mu: "object"         # torch tensor (n_struct,) float64
+    info: list           # list of dicts
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """A solve plan for fixed cells, atom counts and species widths."""
+
+    def __init__(self, cells, atom_offsets, sigma, *, coulomb_k=14.3996454784, charge_tol=1e-5,
+                 ewald_tol=1e-6, r_cut=8.0, spline_order=0, mesh_spacing=0.0, precision="fp64",
+                 max_iter=1000, residual_tol=0.0, graph=True, device=None):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda")
+        cells = np.ascontiguousarray(np.asarray(cells, np.float64).reshape(-1, 9))
+        offs = np.ascontiguousarray(np.asarray(atom_offsets, np.int64))
+        sigma = np.ascontiguousarray(np.atleast_2d(np.asarray(sigma, np.float64)))
+        self.n_struct = int(cells.shape[0])
+        if sigma.shape[0] != self.n_struct:
+            raise ValueError("sigma must have one row per structure")
+        self.n_species = int(sigma.shape[1])
+        self.n_atoms = int(offs[-1])
+        self._keep = (cells, offs, sigma)
+        prec = {"fp64": QEQ_FP64, "mixed": QEQ_MIXED}[precision]
+        self.precision = precision
+        d = PlanDesc(self.n_struct, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                     cells.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.n_species,
+                     sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), coulomb_k, charge_tol, ewald_tol,
+                     r_cut, spline_order, mesh_spacing, prec, max_iter, residual_tol,
+                     0 if graph else QEQ_FLAG_NO_GRAPH)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(device=self.device)
+            h = ctypes.c_void_p()
+            st = self.lib.qeq_plan_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_plan_create: " + self.lib.qeq_status_str(st).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qeq_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st not in (QEQ_OK,):
+            msg = self.lib.qeq_last_error(self.h).decode()
+            raise QEqError(st, f"{what}: {self.lib.qeq_status_str(st).decode()}: {msg}")
+
+    def _dev(self, x, dtype):
+        t = self.torch.as_tensor(x, dtype=dtype, device=self.device)
+        return t.contiguous()
+
+    def query(self, s: int = 0) -> dict:
+        pi = PlanInfo()
+        self._check(self.lib.qeq_plan_query(self.h, s, ctypes.byref(pi)), "qeq_plan_query")
+        return {"mesh": tuple(pi.mesh), "spline_order": pi.spline_order, "n_species": pi.n_species,
+                "narrow_pairs": pi.narrow_pairs, "omega": pi.omega, "r_cut": pi.r_cut, "volume": pi.volume,
+                "n_atoms": pi.n_atoms, "pair_capacity": pi.pair_capacity, "workspace_bytes": pi.workspace_bytes,
+                "kernel_launches": pi.kernel_launches}
+
+    def _sync_in(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def solve(self, pos, species, chi, J, q_tot=None, q0=None, raise_on_noconv=True, out=None):
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        chi = self._dev(chi, torch.float64)
+        J = self._dev(J, torch.float64)
+        if q_tot is None:
+            q_tot = np.zeros(self.n_struct)
+        qt = np.ascontiguousarray(np.broadcast_to(np.asarray(q_tot, np.float64), (self.n_struct,)))
+        warm = QEQ_WARM_COLD
+        q = out if out is not None else torch.empty(self.n_atoms, dtype=torch.float64, device=self.device)
+        if q0 is not None:
+            q.copy_(self._dev(q0, torch.float64))
+            warm = QEQ_WARM_USER
+        mu = torch.empty(self.n_struct, dtype=torch.float64, device=self.device)
+        info = (Info * self.n_struct)()
+        self._sync_in()
+        st = self.lib.qeq_solve(self.h, _ptr(pos), _ptr(species), _ptr(chi), _ptr(J),
+                                qt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), warm, _ptr(q), _ptr(mu), info)
+        if st != QEQ_OK and not (st == QEQ_ERR_NOCONV and not raise_on_noconv):
+            self._check(st, "qeq_solve")
+        infos = [{k: getattr(i, k) for k, _ in Info._fields_} for i in info]
+        return SolveResult(q, mu, infos)
+
+    def energy(self, pos, species, chi, J, q):
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        chi = self._dev(chi, torch.float64)
+        J = self._dev(J, torch.float64)
+        q = self._dev(q, torch.float64)
+        E = torch.empty(self.n_struct, dtype=torch.float64, device=self.device)
+        Ee = torch.empty(self.n_struct, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_energy(self.h, _ptr(pos), _ptr(species), _ptr(chi), _ptr(J), _ptr(q), _ptr(E),
+                                        _ptr(Ee)), "qeq_energy")
+        return E, Ee
+
+    def matvec(self, pos, species, x, J=None, fp64=False):
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        x = self._dev(x, torch.float64)
+        Jt = self._dev(J, torch.float64) if J is not None else None
+        y = torch.empty(self.n_atoms, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_matvec(self.h, _ptr(pos), _ptr(species), _ptr(Jt), _ptr(x), _ptr(y),
+                                        1 if fp64 else 0), "qeq_matvec")
+        return y
+
+    def profile_matvec(self, n_rep: int = 10) -> dict:
+        ms = (ctypes.c_float * QEQ_N_STAGES)()
+        self._check(self.lib.qeq_profile_matvec(self.h, n_rep, ms), "qeq_profile_matvec")
+        return dict(zip(STAGE_NAMES, [float(v) for v in ms]))
+
+
+def plan_for_structures(structs, **kw) -> Plan:
+    """Plan for a list of ``synth.Structure`` (same species-table width)."""
+    ns = max(s.n_species for s in structs)
+    cells = np.stack([s.cell for s in structs]).reshape(-1, 9)
+    offs = np.concatenate([[0], np.cumsum([s.n for s in structs])]).astype(np.int64)
+    sig = np.ones((len(structs), ns))
+    for i, s in enumerate(structs):
+        sig[i, :s.n_species] = s.sigma_s
+    return Plan(cells, offs, sig, **kw)
+
+
+def pack(structs):
+    """Concatenate per-structure atom arrays (positions, species, chi, J, q_tot)."""
+    pos = np.concatenate([s.pos for s in structs])
+    spc = np.concatenate([s.species for s in structs]).astype(np.int32)
+    chi = np.concatenate([s.chi for s in structs])
+    J = np.concatenate([s.J for s in structs])
+    qt = np.array([s.q_tot for s in structs])
+    return pos, spc, chi, J, qt

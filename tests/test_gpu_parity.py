@@ -1,0 +1,182 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle (through the C ABI).
+
+Tolerances: charges within 1e-5 e max-abs and energies within 1e-6 relative of
+the dense oracle; matvec relative RMS within the plan's ewald_tol.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qeq_oracle as O
+from paper_2607_17978_b300 import synth
+
+KE = synth.COULOMB_K_EV_A
+pytestmark = pytest.mark.gpu
+
+
+def _plan(structs, **kw):
+    from paper_2607_17978_b300 import build, qeq
+    build.build()
+    return qeq.plan_for_structures(structs, **kw)
+
+
+def _oracle(st):
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=KE)
+    q, mu = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+    E, Ee = O.energies(A, st.J, st.chi, q)
+    return A, q, mu, E, Ee
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    st = synth.workload(1)
+    return st, _oracle(st)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_matvec_parity_config1(cfg1, precision):
+    from paper_2607_17978_b300 import qeq
+    st, (A, q, *_r) = cfg1
+    tol = 1e-7
+    plan = _plan([st], precision=precision, ewald_tol=tol, r_cut=9.0)
+    pos, spc, chi, J, _ = qeq.pack([st])
+    rng = np.random.default_rng(0)
+    for x in (rng.normal(size=st.n), q):
+        y = plan.matvec(pos, spc, x, J=J).cpu().numpy()
+        ref = A @ x + st.J * x
+        err = np.sqrt(np.mean((y - ref) ** 2)) / np.sqrt(np.mean(ref ** 2))
+        # FP32 mesh arithmetic: single-precision rounding of potentials much larger than (A q)_i
+        assert err < (tol if precision == "fp64" else 5e-6), err
+    y64 = plan.matvec(pos, spc, q, J=J, fp64=True).cpu().numpy()
+    ref = A @ q + st.J * q
+    assert np.sqrt(np.mean((y64 - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_parity_config1(cfg1, precision):
+    from paper_2607_17978_b300 import qeq
+    st, (A, q, mu, E, Ee) = cfg1
+    plan = _plan([st], precision=precision, ewald_tol=1e-7, r_cut=9.0)
+    pos, spc, chi, J, qt = qeq.pack([st])
+    res = plan.solve(pos, spc, chi, J, qt)
+    qg = res.q.cpu().numpy()
+    assert np.abs(qg - q).max() < 1e-5
+    assert abs(qg.sum() - st.q_tot) < 1e-10
+    assert abs(res.mu.cpu().numpy()[0] - mu) < 1e-5 * max(1.0, abs(mu))
+    Eg, Eeg = plan.energy(pos, spc, chi, J, res.q)
+    assert abs(Eg.item() - E) < 1e-6 * abs(E)
+    assert abs(Eeg.item() - Ee) < 1e-6 * abs(Ee)
+    assert res.info[0]["status"] == 0 and res.info[0]["iterations"] > 0
+
+
+def _small_structs():
+    rng = synth.rng_for(40, 0)
+    out = [synth.rocksalt(3, 5.64, 0.15, rng, vacancy_frac=0.05, shear_deg=10.0)]      # triclinic, vacancies
+    out.append(synth.rocksalt((2, 3, 2), 5.64, 0.2, synth.rng_for(40, 1)))              # ragged mesh bins
+    for s in range(3):
+        out.append(synth.batch_workload(1, cfg_id=41, n_min=64, n_max=600, first=s)[0])
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_solve_parity_uneven_structures(precision):
+    from paper_2607_17978_b300 import qeq
+    structs = _small_structs()
+    plan = _plan(structs, precision=precision)
+    pos, spc, chi, J, qt = qeq.pack(structs)
+    res = plan.solve(pos, spc, chi, J, qt)
+    qg = res.q.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+    for i, st in enumerate(structs):
+        _, q, mu, E, _ = _oracle(st)
+        assert np.abs(qg[off[i]:off[i + 1]] - q).max() < 1e-5, (i, plan.query(i))
+        assert abs(qg[off[i]:off[i + 1]].sum() - st.q_tot) < 1e-9
+    # batched == one structure at a time
+    for i, st in enumerate(structs[:3]):
+        p1 = _plan([st], precision=precision)
+        a, b, c, d, e = qeq.pack([st])
+        r1 = p1.solve(a, b, c, d, e).q.cpu().numpy()
+        assert np.abs(r1 - qg[off[i]:off[i + 1]]).max() < 2e-6
+
+
+def test_reduced_config2_dense():
+    from paper_2607_17978_b300 import qeq
+    st = synth.rocksalt(5, 5.64, 0.15, synth.rng_for(2, 7))
+    _, q, mu, E, _ = _oracle(st)
+    for precision in ("fp64", "mixed"):
+        plan = _plan([st], precision=precision, r_cut=8.0)
+        pos, spc, chi, J, qt = qeq.pack([st])
+        res = plan.solve(pos, spc, chi, J, qt)
+        assert np.abs(res.q.cpu().numpy() - q).max() < 1e-5
+
+
+def test_edge_cases_single_atom_two_atoms_and_charged():
+    from paper_2607_17978_b300 import qeq
+    one = synth.Structure(np.eye(3) * 9.0, np.array([[1.0, 2.0, 3.0]]), np.array([0], np.int32),
+                          np.array([-0.4]), np.array([1.7]), np.array([1.2]), 1.0)
+    two = synth.Structure(np.diag([8.0, 9.0, 10.0]), np.array([[0.5, 0.5, 0.5], [3.0, 4.0, 5.5]]),
+                          np.array([0, 1], np.int32), np.array([-1.1, 0.8]), np.array([2.0, 1.5]),
+                          np.array([1.0, 1.8]), 0.4)
+    for st in (one, two):
+        _, q, mu, *_ = _oracle(st)
+        plan = _plan([st])
+        res = plan.solve(*qeq.pack([st]))
+        assert np.abs(res.q.cpu().numpy() - q).max() < 1e-6
+        assert abs(res.mu.cpu().numpy()[0] - mu) < 1e-5
+
+
+def test_user_warm_start_and_determinism(cfg1):
+    from paper_2607_17978_b300 import qeq
+    st, (A, q, *_r) = cfg1
+    plan = _plan([st], ewald_tol=1e-7, r_cut=9.0)
+    pos, spc, chi, J, qt = qeq.pack([st])
+    r1 = plan.solve(pos, spc, chi, J, qt)
+    r2 = plan.solve(pos, spc, chi, J, qt)
+    assert np.array_equal(r1.q.cpu().numpy(), r2.q.cpu().numpy())
+    r3 = plan.solve(pos, spc, chi, J, qt, q0=r1.q)
+    assert r3.info[0]["iterations"] <= 4
+    assert np.abs(r3.q.cpu().numpy() - q).max() < 1e-5
+
+
+def test_translation_invariance_within_mesh_error(cfg1):
+    from paper_2607_17978_b300 import qeq
+    st, (A, q, *_r) = cfg1
+    t = st.copy()
+    t.pos = t.pos + np.array([0.37, -1.21, 2.93])
+    plan = _plan([t], ewald_tol=1e-7, r_cut=9.0)
+    res = plan.solve(*qeq.pack([t]))
+    assert np.abs(res.q.cpu().numpy() - q).max() < 1e-5
+
+
+def test_invalid_inputs_are_reported():
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(1)
+    plan = _plan([st])
+    pos, spc, chi, J, qt = qeq.pack([st])
+    Jb = J.copy()
+    Jb[5] = -1.0
+    with pytest.raises(qeq.QEqError) as e:
+        plan.solve(pos, spc, chi, Jb, qt)
+    assert e.value.status == qeq.QEQ_ERR_NOT_PD
+    sb = spc.copy()
+    sb[3] = 7
+    with pytest.raises(qeq.QEqError) as e:
+        plan.solve(pos, sb, chi, J, qt)
+    assert e.value.status == qeq.QEQ_ERR_INVALID
+    pb = pos.copy()
+    pb[2, 1] = np.nan
+    with pytest.raises(qeq.QEqError) as e:
+        plan.solve(pb, spc, chi, J, qt)
+    assert e.value.status == qeq.QEQ_ERR_INVALID
+    # the plan still works afterwards
+    res = plan.solve(pos, spc, chi, J, qt)
+    assert res.info[0]["status"] == 0
+
+
+def test_iteration_cap_reports_noconv():
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(1)
+    plan = _plan([st], max_iter=2)
+    res = plan.solve(*qeq.pack([st]), raise_on_noconv=False)
+    assert res.info[0]["status"] == qeq.QEQ_ERR_NOCONV
