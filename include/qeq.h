@@ -177,6 +177,42 @@ qeq_status qeq_matvec(qeq_plan plan, const double* d_pos, const int32_t* d_speci
 #define QEQ_N_STAGES 8
 qeq_status qeq_profile_matvec(qeq_plan plan, int32_t n_rep, float* h_ms);
 
+/* ------------------------------------------------------------------------
+ * qeq_matvec_static -- the FP64 matvec of qeq_matvec for ONE small cell,
+ * with no device allocation at all.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (code running while
+ * another component owns the device memory pool or a fixed arena, code that
+ * must not trigger the implicit synchronisation of cudaMalloc/cudaFree, or an
+ * embedding that only passes input and output buffers).
+ *
+ * Scratch lives in a file-scope __device__ array of QEQ_STATIC_SCRATCH_BYTES
+ * that every GPU loading the library keeps until process exit.  Limits:
+ * n_atoms <= QEQ_STATIC_MAX_ATOMS, n_species <= QEQ_STATIC_MAX_SPECIES, at
+ * most QEQ_STATIC_MAX_MESH mesh points per direction (the mesh, B-spline order
+ * and Ewald split are chosen exactly as qeq_plan_create does) and at most
+ * QEQ_STATIC_MAX_PAIRS real-space pair slots; larger inputs return
+ * QEQ_ERR_CAPACITY without touching the GPU.
+ *   h_cell     9 doubles, rows a1 a2 a3 [A]     h_sigma  n_species widths [A]
+ *   d_pos      n_atoms x 3 [A]    d_species  n_atoms indices
+ *   d_J        n_atoms hardnesses or NULL (diag J left out)
+ *   d_x, d_y   input / output vectors of n_atoms
+ *   coulomb_k, ewald_tol, r_cut   as in qeq_plan_desc (<= 0: defaults)
+ *   cuda_stream                   a cudaStream_t (NULL = legacy stream)
+ * The call returns after the stream has finished.  All calls share the
+ * scratch array, which keeps the last call's contents: calls that overlap on
+ * the GPU, or come from several host threads at once, race.  The first call on
+ * a device sets up that device (it looks up the array's device address and
+ * the kernels' shared-memory limits); make it before any stream capture. */
+#define QEQ_STATIC_MAX_ATOMS 4096
+#define QEQ_STATIC_MAX_SPECIES 4
+#define QEQ_STATIC_MAX_MESH 64
+#define QEQ_STATIC_MAX_PAIRS 1048576
+#define QEQ_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+qeq_status qeq_matvec_static(const double* h_cell, const double* h_sigma, int32_t n_species, int32_t n_atoms,
+                             const double* d_pos, const int32_t* d_species, const double* d_J,
+                             const double* d_x, double* d_y, double coulomb_k, double ewald_tol,
+                             double r_cut, void* cuda_stream);
+
 /* Static description of one status code. */
 const char* qeq_status_str(qeq_status s);
 

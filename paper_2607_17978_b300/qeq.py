@@ -26,7 +26,7 @@ QEQ_N_STAGES = 8
 STAGE_NAMES = ["species_sums", "spread", "fft_z", "fft_y", "fft_x_green", "ifft_y", "ifft_z", "gather"]
 
 EXPORTED = ["qeq_plan_create", "qeq_plan_destroy", "qeq_plan_query", "qeq_solve", "qeq_energy", "qeq_matvec",
-            "qeq_profile_matvec", "qeq_status_str", "qeq_last_error"]
+            "qeq_profile_matvec", "qeq_status_str", "qeq_last_error", "qeq_matvec_static"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -107,6 +107,9 @@ def load_library(path: str = LIB_PATH):
     lib.qeq_status_str.restype = ctypes.c_char_p
     lib.qeq_last_error.argtypes = [vp]
     lib.qeq_last_error.restype = ctypes.c_char_p
+    lib.qeq_matvec_static.argtypes = [dp, dp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, vp]
+    lib.qeq_matvec_static.restype = ctypes.c_int
     del ip
     if path == LIB_PATH:
         _lib = lib
@@ -249,6 +252,28 @@ class Plan:
         ms = (ctypes.c_float * QEQ_N_STAGES)()
         self._check(self.lib.qeq_profile_matvec(self.h, n_rep, ms), "qeq_profile_matvec")
         return dict(zip(STAGE_NAMES, [float(v) for v in ms]))
+
+
+def matvec_static(cell, sigma_s, pos, species, x, J=None, *, coulomb_k=14.3996454784, ewald_tol=1e-6,
+                  r_cut=8.0, stream=None):
+    """FP64 matvec of one small cell through qeq_matvec_static (no device allocation in the library).
+
+    Device inputs are torch CUDA tensors; the output tensor is allocated here by
+    the caller side (torch), the library itself allocates nothing.
+    """
+    import torch
+    lib = load_library()
+    cell = np.ascontiguousarray(np.asarray(cell, np.float64).reshape(9))
+    sig = np.ascontiguousarray(np.asarray(sigma_s, np.float64))
+    n = int(x.shape[0])
+    y = torch.empty(n, dtype=torch.float64, device=x.device)
+    st = lib.qeq_matvec_static(cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sig), n, _ptr(pos),
+                               _ptr(species), _ptr(J), _ptr(x), _ptr(y), coulomb_k, ewald_tol, r_cut,
+                               ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
+    if st != QEQ_OK:
+        raise QEqError(st, "qeq_matvec_static: " + lib.qeq_status_str(st).decode())
+    return y
 
 
 def plan_for_structures(structs, **kw) -> Plan:
