@@ -35,10 +35,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QEq solves/s and atoms*CG-iters/s at 1e-5 e vs plain FP64 GPU PCG; % HBM roofline"
 UNIT = "solves/s"
-# Jacobi-PCG iterations of a full solve of the default workload at 1e-5 e, used to
+# Jacobi-PCG iterations of a full solve of the default workload at 1e-5 e (about 100 on
+# this 13,824-atom cell), used to
 # extrapolate the CPU oracle's matvec time to a solve (the oracle's own solve is
 # a dense LU that does not fit the time budget at this size).
-PCG_ITERS_REFERENCE = 40
+PCG_ITERS_REFERENCE = 100
 WORKLOAD_OPTS = {
     1: dict(ewald_tol=1e-7, r_cut=9.0),
     2: dict(ewald_tol=1e-6, r_cut=8.0),
@@ -190,6 +191,24 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def run_profile(args):
+    """A few solves of a rock-salt cell of --cells^3 conventional cells (config-5 recipe),
+    for ncu captures: no plain-FP64 leg, no end-to-end leg, no CPU oracle."""
+    import torch
+    from paper_2607_17978_b300 import build, qeq, synth
+    build.build()
+    st = synth.rocksalt(args.cells, synth.ROCKSALT_A, 0.2, synth.rng_for(5, 1), vacancy_frac=0.02)
+    plan = qeq.plan_for_structures([st], precision=args.precision, ewald_tol=1e-6, r_cut=8.0)
+    pos, spc, chi, J, qt = qeq.pack([st])
+    d = [torch.tensor(a, device="cuda") for a in (pos, spc, chi, J)]
+    for _ in range(args.steps):
+        r = plan.solve(*d, qt)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": f"rocksalt {args.cells}^3", "atoms": st.n, "mesh": plan.query(0)["mesh"],
+                      "iterations": r.info[0]["iterations"], "stages_ms": plan.profile_matvec(5)}))
+    return 0
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -350,11 +369,15 @@ def main():
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 5])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-cells", dest="cells", type=int, default=0,
+                    help="profiling mode: solve a rock-salt cell of N^3 conventional cells only")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.cells > 0:
+        return run_profile(args)
     return run_ours(args)
 
 

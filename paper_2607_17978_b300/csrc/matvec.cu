@@ -58,6 +58,18 @@ __device__ __forceinline__ V cscale(V a, T s) {
   return {a.x * s, a.y * s};
 }
 
+// Asynchronous global -> shared copy of one complex element (cp.async): a thread
+// issues all its copies back to back and waits once, so many loads are in flight.
+__device__ __forceinline__ void cp_async_elem(float2* smem, const float2* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* smem, const double2* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ const typename C2<T>::t* twiddles(const double2* tw64, const float2* tw32);
 template <>
@@ -119,18 +131,20 @@ __device__ __forceinline__ void dft5(V* v, T sgn) {
 // One Stockham radix-R stage over all lines in shared memory.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(const typename C2<T>::t* __restrict__ src,
-                                               typename C2<T>::t* __restrict__ dst, int nlines, int K, int Ns,
-                                               const typename C2<T>::t* __restrict__ tw, T sgn) {
+                                               typename C2<T>::t* __restrict__ dst, int nlines, int K, int ld, int Ns,
+                                               const typename C2<T>::t* __restrict__ tw, T sgn,
+                                               const FastDiv& fnbf, const FastDiv& fns) {
   using V = typename C2<T>::t;
-  int nbf = K / R;
-  int tws = K / (Ns * R);
-  int total = nlines * nbf;
+  const int nbf = K / R;
+  const int tws = K / (Ns * R);
+  const int total = nlines * nbf;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    int line = w / nbf;
-    int j = w - line * nbf;
-    int k = j % Ns;
-    const V* s = src + line * K;
-    V* d = dst + line * K;
+    const int line = (int)fdiv((uint32_t)w, fnbf);
+    const int j = w - line * nbf;
+    const int jq = (int)fdiv((uint32_t)j, fns);
+    const int k = j - jq * Ns;
+    const V* s = src + line * ld;
+    V* d = dst + line * ld;
     V v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
@@ -144,7 +158,7 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t* __restri
     if (R == 3) dft3<T, V>(v, sgn);
     if (R == 4) dft4<T, V>(v, sgn);
     if (R == 5) dft5<T, V>(v, sgn);
-    int o = (j / Ns) * Ns * R + k;
+    const int o = jq * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
   }
@@ -152,19 +166,19 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t* __restri
 
 // Unnormalised FFT of nlines lines of length K held in a; returns the buffer with the result.
 template <typename T>
-__device__ typename C2<T>::t* fft_lines(typename C2<T>::t* a, typename C2<T>::t* b, int nlines, int K,
+__device__ typename C2<T>::t* fft_lines(typename C2<T>::t* a, typename C2<T>::t* b, int nlines, int K, int ld,
                                         const FftPlanDev& fp, const typename C2<T>::t* tw, T sgn) {
   int Ns = 1;
   for (int st = 0; st < fp.nst; ++st) {
     int R = fp.radix[st];
     if (R == 4)
-      stockham_stage<T, 4>(a, b, nlines, K, Ns, tw, sgn);
+      stockham_stage<T, 4>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
     else if (R == 2)
-      stockham_stage<T, 2>(a, b, nlines, K, Ns, tw, sgn);
+      stockham_stage<T, 2>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
     else if (R == 3)
-      stockham_stage<T, 3>(a, b, nlines, K, Ns, tw, sgn);
+      stockham_stage<T, 3>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
     else
-      stockham_stage<T, 5>(a, b, nlines, K, Ns, tw, sgn);
+      stockham_stage<T, 5>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
     __syncthreads();
     typename C2<T>::t* t = a;
     a = b;
@@ -178,67 +192,94 @@ template <typename T>
 __device__ __forceinline__ void load_twiddles(typename C2<T>::t* tw_s, const double2* tw64, const float2* tw32,
                                               const FftPlanDev& fp) {
   const typename C2<T>::t* g = twiddles<T>(tw64, tw32) + fp.tw_off;
-  for (int m = threadIdx.x; m < fp.K; m += blockDim.x) tw_s[m] = g[m];
+  for (int m = threadIdx.x; m < fp.K; m += blockDim.x) cp_async_elem(tw_s + m, g + m);
 }
 
-// ------------------------------------------------------------------ FFT along z (contiguous lines)
-template <typename T>
-__global__ void k_fft_z(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
-                        const int4* __restrict__ items, const double2* __restrict__ tw64,
-                        const float2* __restrict__ tw32, const PcgScalars* __restrict__ sc, int use_active,
-                        typename C2<T>::t* __restrict__ mesh, T sgn) {
-  using V = typename C2<T>::t;
-  int4 it = items[blockIdx.x];
-  const StructDev& S = st[it.x];
-  if (use_active && !sc[it.x].active) return;
-  const FftPlanDev fp = fpl[S.fft_plan[2]];
-  int K = S.K[2], nl = it.w;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw_s = reinterpret_cast<V*>(smem_raw);
-  V* a = tw_s + K;
-  V* b = a + nl * K;
-  load_twiddles<T>(tw_s, tw64, tw32, fp);
-  V* g = mesh + S.mesh_off + (int64_t)it.y * S.M + (int64_t)it.z * K;
-  for (int e = threadIdx.x; e < nl * K; e += blockDim.x) a[e] = g[e];
-  __syncthreads();
-  V* res = fft_lines<T>(a, b, nl, K, fp, tw_s, sgn);
-  for (int e = threadIdx.x; e < nl * K; e += blockDim.x) g[e] = res[e];
-}
+// ------------------------------------------------------------------ transposing FFT passes
+// Mesh layouts (complex elements, one complex mesh after another):
+//   L0 [x][y][z]   spreading writes it, gathering reads it
+//   L1 [x][z][y]
+//   L2 [z][y][x]   the x pass (FFT, reciprocal multiply, inverse FFT) works on it in place
+// Every pass reads whole contiguous lines or tiles of TL consecutive lines, and
+// writes the other way round, so global loads and stores are full segments:
+//   ZF: L0 -> L1 (FFT z)   YF: L1 -> L2 (FFT y)   X: L2 in place
+//   YI: L2 -> L1 (inverse FFT y)                  ZI: L1 -> L0 (inverse FFT z)
+enum { PASS_ZF = 0, PASS_YF = 1, PASS_YI = 2, PASS_ZI = 3 };
 
-// ------------------------------------------------------------------ FFT along y (stride K2)
-template <typename T>
-__global__ void k_fft_y(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
-                        const int4* __restrict__ items, const double2* __restrict__ tw64,
-                        const float2* __restrict__ tw32, const PcgScalars* __restrict__ sc, int use_active,
-                        typename C2<T>::t* __restrict__ mesh, T sgn, int lines_per_item) {
+template <typename T, int PASS>
+__global__ void __launch_bounds__(256) k_fft_pass(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
+                                                  const int4* __restrict__ items, const double2* __restrict__ tw64,
+                                                  const float2* __restrict__ tw32, const PcgScalars* __restrict__ sc,
+                                                  int use_active, const typename C2<T>::t* __restrict__ src,
+                                                  typename C2<T>::t* __restrict__ dst, int TL) {
   using V = typename C2<T>::t;
-  int4 it = items[blockIdx.x];  // {struct, cmesh, x, z0}
+  constexpr bool isZ = (PASS == PASS_ZF || PASS == PASS_ZI);
+  constexpr bool fwd = (PASS == PASS_ZF || PASS == PASS_YF);
+  const int4 it = items[blockIdx.x];  // Z passes: {s, c, x, y0};  Y passes: {s, c, z, x0}
   const StructDev& S = st[it.x];
   if (use_active && !sc[it.x].active) return;
-  const FftPlanDev fp = fpl[S.fft_plan[1]];
-  int K = S.K[1], K2 = S.K[2];
-  int nl = min(lines_per_item, K2 - it.w);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw_s = reinterpret_cast<V*>(smem_raw);
-  V* a = tw_s + K;
-  V* b = a + nl * K;
-  load_twiddles<T>(tw_s, tw64, tw32, fp);
-  V* g = mesh + S.mesh_off + (int64_t)it.y * S.M + (int64_t)it.z * K * K2 + it.w;
-  for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
-    int l = idx % nl, e = idx / nl;
-    a[l * K + e] = g[(int64_t)e * K2 + l];
+  const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
+  const FftPlanDev& fp = fpl[S.fft_plan[isZ ? 2 : 1]];
+  const int K = isZ ? K2 : K1;
+  const int nl = min(TL, (isZ ? K1 : K0) - it.w);
+  const int64_t mb = S.mesh_off + (int64_t)it.y * S.M;
+  // element e of line l is at base + l * ls + e * es
+  int64_t ib, ob, ils, ies, ols, oes;
+  if (PASS == PASS_ZF) {        // L0 (x, y0+l, e) -> L1 (x, e, y0+l)
+    ib = ((int64_t)it.z * K1 + it.w) * K2; ils = K2; ies = 1;
+    ob = (int64_t)it.z * K2 * K1 + it.w; ols = 1; oes = K1;
+  } else if (PASS == PASS_ZI) { // L1 -> L0
+    ib = (int64_t)it.z * K2 * K1 + it.w; ils = 1; ies = K1;
+    ob = ((int64_t)it.z * K1 + it.w) * K2; ols = K2; oes = 1;
+  } else if (PASS == PASS_YF) { // L1 (x0+l, z, e) -> L2 (z, e, x0+l)
+    ib = ((int64_t)it.w * K2 + it.z) * K1; ils = (int64_t)K2 * K1; ies = 1;
+    ob = (int64_t)it.z * K1 * K0 + it.w; ols = 1; oes = K0;
+  } else {                      // L2 -> L1
+    ib = (int64_t)it.z * K1 * K0 + it.w; ils = 1; ies = K0;
+    ob = ((int64_t)it.w * K2 + it.z) * K1; ols = (int64_t)K2 * K1; oes = 1;
   }
+  const int ld = K + 1;  // padded shared line stride: transposed accesses spread over the banks
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tw_s = reinterpret_cast<V*>(smem_raw);
+  V* a = tw_s + K;
+  V* b = a + nl * ld;
+  load_twiddles<T>(tw_s, tw64, tw32, fp);
+  const FastDiv fnl = make_fastdiv(nl);
+  const V* g = src + mb + ib;
+  if (ies == 1) {
+    for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+      int l = (int)fdiv((uint32_t)idx, fp.k), e = idx - l * K;
+      cp_async_elem(a + l * ld + e, g + l * ils + e);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+      int e = (int)fdiv((uint32_t)idx, fnl), l = idx - e * nl;
+      cp_async_elem(a + l * ld + e, g + e * ies + l);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
-  V* res = fft_lines<T>(a, b, nl, K, fp, tw_s, sgn);
-  for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
-    int l = idx % nl, e = idx / nl;
-    g[(int64_t)e * K2 + l] = res[l * K + e];
+  V* res = fft_lines<T>(a, b, nl, K, ld, fp, tw_s, fwd ? (T)-1 : (T)1);
+  V* o = dst + mb + ob;
+  if (oes == 1) {
+    for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+      int l = (int)fdiv((uint32_t)idx, fp.k), e = idx - l * K;
+      o[l * ols + e] = res[l * ld + e];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+      int e = (int)fdiv((uint32_t)idx, fnl), l = idx - e * nl;
+      o[e * oes + l] = res[l * ld + e];
+    }
   }
 }
 
 // ------------------------------------------------------------------ x: FFT, reciprocal multiply, inverse FFT
+// Works in place on layout L2 [z][y][x], where every x line is contiguous.
+// An item holds pairs of lines (z, y) and (-z, -y): the reciprocal multiply
+// needs Z(m) and Z(-m) of every complex mesh to separate its two species.
 template <typename T>
-__global__ void k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
+__global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                               const int4* __restrict__ items, const int2* __restrict__ xpairs,
                               const T* __restrict__ bmod, const double2* __restrict__ tw64,
                               const float2* __restrict__ tw32, const PcgScalars* __restrict__ sc,
@@ -247,26 +288,28 @@ __global__ void k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev
   int4 it = items[blockIdx.x];  // {struct, first pair (global), npairs, -}
   const StructDev& S = st[it.x];
   if (use_active && !sc[it.x].active) return;
-  const FftPlanDev fp = fpl[S.fft_plan[0]];
+  const FftPlanDev& fp = fpl[S.fft_plan[0]];
   const int K = S.K[0], K1 = S.K[1], K2 = S.K[2];
   const int ncm = S.ncm, np = it.z;
   const int nslot = 2 * np * ncm;
-  const int64_t estride = (int64_t)K1 * K2;
+  const int ld = K + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw_s = reinterpret_cast<V*>(smem_raw);
   V* a = tw_s + K;
-  V* b = a + nslot * K;
+  V* b = a + nslot * ld;
   load_twiddles<T>(tw_s, tw64, tw32, fp);
-  // slot = (j*2 + ab)*ncm + c
+  // slot = (j*2 + ab)*ncm + c; line l = z*K1 + y starts at l*K (layout L2)
+  const FastDiv fncm = make_fastdiv(ncm), fK1 = make_fastdiv(K1);
   for (int idx = threadIdx.x; idx < nslot * K; idx += blockDim.x) {
-    int slot = idx % nslot, e = idx / nslot;
-    int c = slot % ncm, jab = slot / ncm;
+    int slot = (int)fdiv((uint32_t)idx, fp.k), e = idx - slot * K;
+    int jab = (int)fdiv((uint32_t)slot, fncm), c = slot - jab * ncm;
     int2 pr = xpairs[it.y + (jab >> 1)];
     int l = (jab & 1) ? pr.y : pr.x;
-    a[slot * K + e] = mesh[S.mesh_off + (int64_t)c * S.M + l + (int64_t)e * estride];
+    cp_async_elem(a + slot * ld + e, mesh + S.mesh_off + (int64_t)c * S.M + (int64_t)l * K + e);
   }
+  cp_async_wait_all();
   __syncthreads();
-  V* R = fft_lines<T>(a, b, nslot, K, fp, tw_s, (T)-1);
+  V* R = fft_lines<T>(a, b, nslot, K, ld, fp, tw_s, (T)-1);
   V* other = (R == a) ? b : a;
   // reciprocal multiply
   const T* bm0 = bmod + S.bmod_off[0];
@@ -275,13 +318,11 @@ __global__ void k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev
   const T B0 = (T)S.B[0], B1 = (T)S.B[1], B2 = (T)S.B[2], B3 = (T)S.B[3], B4 = (T)S.B[4], B5 = (T)S.B[5],
           B6 = (T)S.B[6], B7 = (T)S.B[7], B8 = (T)S.B[8];
   const T gpref = (T)S.green_pref;
-  T w2h[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];
-  for (int k = 0; k < S.S * QEQ_MAX_SPECIES; ++k) w2h[k] = (T)(0.5 * S.w2[k]);
   for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) {
-    int j = idx / K, mx = idx - j * K;
+    int j = (int)fdiv((uint32_t)idx, fp.k), mx = idx - j * K;
     int mmx = (mx == 0) ? 0 : K - mx;
     int2 pr = xpairs[it.y + j];
-    int my = pr.x / K2, mz = pr.x - my * K2;
+    int mz = (int)fdiv((uint32_t)pr.x, fK1), my = pr.x - mz * K1;
     int c0 = (mx <= K / 2) ? mx : mx - K;
     int c1 = (my <= K1 / 2) ? my : my - K1;
     int c2 = (mz <= K2 / 2) ? mz : mz - K2;
@@ -291,144 +332,149 @@ __global__ void k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev
     T G2 = Gx * Gx + Gy * Gy + Gz * Gz;
     T pref = (G2 > (T)0) ? gpref * bm0[mx] * bm1[my] * bm2[mz] / G2 : (T)0;
     V Qh[QEQ_MAX_SPECIES];
-    for (int c = 0; c < ncm; ++c) {
-      V za = R[((j * 2 + 0) * ncm + c) * K + mx];
-      V zb = R[((j * 2 + 1) * ncm + c) * K + mmx];
+#pragma unroll
+    for (int c = 0; c < QEQ_MAX_SPECIES / 2; ++c) {
+      if (c >= ncm) break;
+      V za = R[((j * 2 + 0) * ncm + c) * ld + mx];
+      V zb = R[((j * 2 + 1) * ncm + c) * ld + mmx];
       // F[Q_2c] = (Z(m) + conj Z(-m))/2,  F[Q_2c+1] = (Z(m) - conj Z(-m))/(2i)
       Qh[2 * c] = {(T)0.5 * (za.x + zb.x), (T)0.5 * (za.y - zb.y)};
       Qh[2 * c + 1] = {(T)0.5 * (za.y + zb.y), (T)-0.5 * (za.x - zb.x)};
     }
-    V Ph[QEQ_MAX_SPECIES];
-    for (int s = 0; s < 2 * ncm; ++s) Ph[s] = {(T)0, (T)0};
-    if (pref != (T)0) {
-      for (int s = 0; s < S.S; ++s)
+#pragma unroll
+    for (int c = 0; c < QEQ_MAX_SPECIES / 2; ++c) {
+      if (c >= ncm) break;
+      V p0 = {(T)0, (T)0}, p1 = {(T)0, (T)0};
+      if (pref != (T)0) {
         for (int t = 0; t < S.S; ++t) {
-          T gst = pref * exp(-G2 * w2h[s * QEQ_MAX_SPECIES + t]);
-          Ph[s].x += gst * Qh[t].x;
-          Ph[s].y += gst * Qh[t].y;
+          T g0 = pref * exp(-G2 * (T)(0.5 * S.w2[(2 * c) * QEQ_MAX_SPECIES + t]));
+          p0.x += g0 * Qh[t].x;
+          p0.y += g0 * Qh[t].y;
+          if (2 * c + 1 < S.S) {
+            T g1 = pref * exp(-G2 * (T)(0.5 * S.w2[(2 * c + 1) * QEQ_MAX_SPECIES + t]));
+            p1.x += g1 * Qh[t].x;
+            p1.y += g1 * Qh[t].y;
+          }
         }
-    }
-    for (int c = 0; c < ncm; ++c) {
-      V p0 = Ph[2 * c], p1 = Ph[2 * c + 1];
+      }
       // W(m) = P_2c + i P_2c+1 ; W(-m) = conj(P_2c) + i conj(P_2c+1)
-      R[((j * 2 + 0) * ncm + c) * K + mx] = {p0.x - p1.y, p0.y + p1.x};
-      R[((j * 2 + 1) * ncm + c) * K + mmx] = {p0.x + p1.y, -p0.y + p1.x};
+      R[((j * 2 + 0) * ncm + c) * ld + mx] = {p0.x - p1.y, p0.y + p1.x};
+      R[((j * 2 + 1) * ncm + c) * ld + mmx] = {p0.x + p1.y, -p0.y + p1.x};
     }
   }
   __syncthreads();
-  V* res = fft_lines<T>(R, other, nslot, K, fp, tw_s, (T)1);
+  V* res = fft_lines<T>(R, other, nslot, K, ld, fp, tw_s, (T)1);
   for (int idx = threadIdx.x; idx < nslot * K; idx += blockDim.x) {
-    int slot = idx % nslot, e = idx / nslot;
-    int c = slot % ncm, jab = slot / ncm;
+    int slot = (int)fdiv((uint32_t)idx, fp.k), e = idx - slot * K;
+    int jab = (int)fdiv((uint32_t)slot, fncm), c = slot - jab * ncm;
     int2 pr = xpairs[it.y + (jab >> 1)];
     if ((jab & 1) && pr.y == pr.x) continue;  // self-paired line: written from its A copy
     int l = (jab & 1) ? pr.y : pr.x;
-    mesh[S.mesh_off + (int64_t)c * S.M + l + (int64_t)e * estride] = res[slot * K + e];
+    mesh[S.mesh_off + (int64_t)c * S.M + (int64_t)l * K + e] = res[slot * ld + e];
   }
 }
 
+// ------------------------------------------------------------------ brick geometry
+struct Brick {
+  int x0[3], ext[3];
+};
+
+__device__ __forceinline__ Brick brick_of(const StructDev& S, int g) {
+  Brick B;
+  int gl = g - S.brick_off;
+  int bc2 = gl % S.nbr[2];
+  int bc1 = (gl / S.nbr[2]) % S.nbr[1];
+  int bc0 = gl / (S.nbr[2] * S.nbr[1]);
+  int bc[3] = {bc0, bc1, bc2};
+  for (int d = 0; d < 3; ++d) {
+    B.x0[d] = bc[d] * QEQ_BRICK;
+    B.ext[d] = min(QEQ_BRICK, S.K[d] - B.x0[d]);
+  }
+  return B;
+}
+
 // ------------------------------------------------------------------ spreading
+// One CTA per 16^3 brick and complex mesh.  Candidate atoms: the bins whose
+// stencils can reach the brick.  A warp takes one atom at a time; its lanes
+// own stencil rows (jx, jy) and run along z, adding into the brick in shared
+// memory (shared atomics; each mesh point is then written to global memory
+// exactly once, so the mesh needs no clearing and global memory sees no atomics).
 template <typename T, int P>
-__global__ void k_spread(const StructDev* __restrict__ st, const int* __restrict__ bin_struct,
+__global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
                          const int* __restrict__ bin_start, const int* __restrict__ base,
                          const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ x,
                          const PcgScalars* __restrict__ sc, int use_active, typename C2<T>::t* __restrict__ mesh) {
   using V = typename C2<T>::t;
   const int g = blockIdx.x;
-  const int s = bin_struct[g];
+  const int s = brick_struct[g];
   const StructDev& S = st[s];
   if (use_active && !sc[s].active) return;
-  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncm = S.ncm;
-  int gl = g - S.bin_off;
-  int bc[3];
-  bc[2] = gl % S.nb[2];
-  bc[1] = (gl / S.nb[2]) % S.nb[1];
-  bc[0] = gl / (S.nb[2] * S.nb[1]);
-  int x0[3], ext[3];
-  for (int d = 0; d < 3; ++d) {
-    x0[d] = bc[d] * QEQ_BIN;
-    ext[d] = min(QEQ_BIN, S.K[d] - x0[d]);
-  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Brick B = brick_of(S, g);
+  // re and im planes [16][16][QEQ_RS]: a z row padded to 24 elements so that the
+  // 4 rows x 8 z points a warp touches at once fall in distinct banks
+  const int psz = QEQ_BRICK * QEQ_BRICK * QEQ_RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* acc = reinterpret_cast<T*>(smem_raw);  // [nw][ncm][512][2]
-  const int bsz = QEQ_BIN * QEQ_BIN * QEQ_BIN;
-  T* wsm = acc + (size_t)nw * ncm * bsz * 2;  // [nw][3][P] weights
-  int* lsm = reinterpret_cast<int*>(wsm + nw * 3 * P);  // [nw][3][P] local indices
-  int* cnt = lsm + nw * 3 * P;                          // [nw][3]
-  for (int i = threadIdx.x; i < nw * ncm * bsz * 2; i += blockDim.x) acc[i] = (T)0;
-  // candidate bins per direction: the bins of points x0 .. x0+ext+P-2 (mod K)
+  T* acc = reinterpret_cast<T*>(smem_raw);
   __shared__ int cand[3][8], ncand[3];
   if (threadIdx.x < 3) {
     int d = threadIdx.x, nc = 0;
-    int span = ext[d] + P - 1;
-    if (span > S.K[d]) span = S.K[d];
+    int span = min(B.ext[d] + P - 1, S.K[d]);
     for (int k = 0; k < span; ++k) {
-      int bn = ((x0[d] + k) % S.K[d]) / QEQ_BIN;
+      int bn = ((B.x0[d] + k) % S.K[d]) / QEQ_BIN;
       bool seen = false;
       for (int q = 0; q < nc; ++q) seen |= (cand[d][q] == bn);
       if (!seen && nc < 8) cand[d][nc++] = bn;
     }
     ncand[d] = nc;
   }
-  __syncthreads();
-  T* my = acc + (size_t)w * ncm * bsz * 2;
-  T* mw = wsm + w * 3 * P;
-  int* ml = lsm + w * 3 * P;
-  int* mc = cnt + w * 3;
-  int order = 0;
-  for (int i0 = 0; i0 < ncand[0]; ++i0)
-    for (int i1 = 0; i1 < ncand[1]; ++i1)
-      for (int i2 = 0; i2 < ncand[2]; ++i2) {
-        int gb = S.bin_off + (cand[0][i0] * S.nb[1] + cand[1][i1]) * S.nb[2] + cand[2][i2];
-        int t0 = bin_start[gb], t1 = bin_start[gb + 1];
-        for (int t = t0; t < t1; ++t, ++order) {
-          if ((order % nw) != w) continue;
-          int bs = base[t];
-          int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
-          if (lane < 3) {
-            int d = lane, n = 0;
-            for (int j = 0; j < P; ++j) {
-              int k = f[d] - (P - 1) + j;
-              if (k < 0) k += S.K[d];
-              int loc = k - x0[d];
-              if (loc >= 0 && loc < ext[d]) {
-                ml[d * P + n] = loc;
-                mw[d * P + n] = wts[(size_t)t * 3 * QEQ_MAXP + d * QEQ_MAXP + (P - 1 - j)];
-                ++n;
-              }
+  const int jz = lane & 7, rsub = lane >> 3;
+  for (int cm = 0; cm < S.ncm; ++cm) {
+    for (int i = threadIdx.x; i < 2 * psz; i += blockDim.x) acc[i] = (T)0;
+    __syncthreads();
+    int order = 0;
+    for (int i0 = 0; i0 < ncand[0]; ++i0)
+      for (int i1 = 0; i1 < ncand[1]; ++i1)
+        for (int i2 = 0; i2 < ncand[2]; ++i2) {
+          int gb = S.bin_off + (cand[0][i0] * S.nb[1] + cand[1][i1]) * S.nb[2] + cand[2][i2];
+          int t0 = bin_start[gb], t1 = bin_start[gb + 1];
+          for (int t = t0; t < t1; ++t, ++order) {
+            if ((order & 7) != w) continue;  // 8 warps
+            int sp = spec[t];
+            if ((sp >> 1) != cm) continue;
+            const int bs = base[t];
+            const int f0 = bs & 1023, f1 = (bs >> 10) & 1023, f2 = (bs >> 20) & 1023;
+            const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
+            int kz = f2 - (P - 1) + jz;
+            if (kz < 0) kz += S.K[2];
+            const int lz = kz - B.x0[2];
+            const bool zok = (jz < P) && lz >= 0 && lz < B.ext[2];
+            const T wzq = zok ? (T)x[t] * wt[2 * QEQ_MAXP + P - 1 - jz] : (T)0;
+            T* plane = acc + (sp & 1) * psz;
+            for (int r = rsub; r < P * P; r += 4) {
+              const int jx = r / P, jy = r - (r / P) * P;
+              int kx = f0 - (P - 1) + jx;
+              if (kx < 0) kx += S.K[0];
+              const int lx = kx - B.x0[0];
+              int ky = f1 - (P - 1) + jy;
+              if (ky < 0) ky += S.K[1];
+              const int ly = ky - B.x0[1];
+              if (!zok || lx < 0 || lx >= B.ext[0] || ly < 0 || ly >= B.ext[1]) continue;
+              atomicAdd(plane + (lx * QEQ_BRICK + ly) * QEQ_RS + lz, wzq * wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy]);
             }
-            mc[d] = n;
           }
-          __syncwarp();
-          int n0 = mc[0], n1 = mc[1], n2 = mc[2];
-          int tot = n0 * n1 * n2;
-          int sp = spec[t];
-          int cm = sp >> 1, part = sp & 1;
-          T qv = (T)x[t];
-          T* dst = my + (size_t)cm * bsz * 2 + part;
-          for (int c = lane; c < tot; c += 32) {
-            int iz = c % n2, r = c / n2;
-            int iy = r % n1, ix = r / n1;
-            int pt = (ml[ix] * QEQ_BIN + ml[P + iy]) * QEQ_BIN + ml[2 * P + iz];
-            dst[pt * 2] += qv * mw[ix] * mw[P + iy] * mw[2 * P + iz];
-          }
-          __syncwarp();
         }
-      }
-  __syncthreads();
-  for (int i = threadIdx.x; i < ncm * bsz; i += blockDim.x) {
-    int cm = i / bsz, pt = i - cm * bsz;
-    int lz = pt % QEQ_BIN, ly = (pt / QEQ_BIN) % QEQ_BIN, lx = pt / (QEQ_BIN * QEQ_BIN);
-    if (lx >= ext[0] || ly >= ext[1] || lz >= ext[2]) continue;
-    V v = {(T)0, (T)0};
-    for (int ww = 0; ww < nw; ++ww) {
-      v.x += acc[(((size_t)ww * ncm + cm) * bsz + pt) * 2];
-      v.y += acc[(((size_t)ww * ncm + cm) * bsz + pt) * 2 + 1];
+    __syncthreads();
+    V* mg = mesh + S.mesh_off + (int64_t)cm * S.M;
+    const int bsz = QEQ_BRICK * QEQ_BRICK * QEQ_BRICK;
+    for (int i = threadIdx.x; i < bsz; i += blockDim.x) {
+      int lz = i % QEQ_BRICK, ly = (i / QEQ_BRICK) % QEQ_BRICK, lx = i / (QEQ_BRICK * QEQ_BRICK);
+      if (lx >= B.ext[0] || ly >= B.ext[1] || lz >= B.ext[2]) continue;
+      int o = (lx * QEQ_BRICK + ly) * QEQ_RS + lz;
+      V v = {acc[o], acc[psz + o]};
+      mg[((int64_t)(B.x0[0] + lx) * S.K[1] + (B.x0[1] + ly)) * S.K[2] + (B.x0[2] + lz)] = v;
     }
-    int64_t gi = S.mesh_off + (int64_t)cm * S.M + ((int64_t)(x0[0] + lx) * S.K[1] + (x0[1] + ly)) * S.K[2] +
-                 (x0[2] + lz);
-    mesh[gi] = v;
+    __syncthreads();
   }
 }
 
@@ -450,8 +496,14 @@ __device__ __forceinline__ const double* pair_vals<double>(const double* v64, co
   return v64;
 }
 
+// One CTA per 16^3 brick: the brick plus its (P-1)-point low-side halo of the
+// potential mesh is staged in shared memory (one complex mesh at a time); a warp
+// takes one of the brick's atoms, lanes own stencil rows and run along z, and a
+// warp reduction gives the mesh part of y_i.  The same warp adds the real-space
+// pair row and the local terms, and the CTA contributes x.y to a per-structure
+// sum when fuse_pAp is set.
 template <typename T, int P>
-__global__ void k_gather(const StructDev* __restrict__ st, const int* __restrict__ bin_struct,
+__global__ void __launch_bounds__(256) k_gather(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
                          const int* __restrict__ bin_start, const int* __restrict__ base,
                          const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ J,
                          const double* __restrict__ x, const int64_t* __restrict__ row, const int* __restrict__ col,
@@ -461,73 +513,103 @@ __global__ void k_gather(const StructDev* __restrict__ st, const int* __restrict
                          double* __restrict__ y) {
   using V = typename C2<T>::t;
   const int g = blockIdx.x;
-  const int s = bin_struct[g];
+  const int s = brick_struct[g];
   const StructDev& S = st[s];
   if (use_active && !sc[s].active) return;
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncm = S.ncm;
-  int gl = g - S.bin_off;
-  int bc[3];
-  bc[2] = gl % S.nb[2];
-  bc[1] = (gl / S.nb[2]) % S.nb[1];
-  bc[0] = gl / (S.nb[2] * S.nb[1]);
-  int x0[3], len[3];
-  for (int d = 0; d < 3; ++d) {
-    x0[d] = bc[d] * QEQ_BIN;
-    len[d] = min(QEQ_BIN, S.K[d] - x0[d]) + P - 1;
-  }
+  const Brick B = brick_of(S, g);
+  int len[3];
+  for (int d = 0; d < 3; ++d) len[d] = B.ext[d] + P - 1;
+  // the brick plus its low-side halo, complex, rows (lx, ly) padded to QEQ_RS elements
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* reg = reinterpret_cast<V*>(smem_raw);  // [ncm][len0][len1][len2]
-  const int rsz = len[0] * len[1] * len[2];
-  for (int i = threadIdx.x; i < ncm * rsz; i += blockDim.x) {
-    int cm = i / rsz, pt = i - cm * rsz;
-    int lz = pt % len[2], ly = (pt / len[2]) % len[1], lx = pt / (len[2] * len[1]);
-    int kx = x0[0] - (P - 1) + lx, ky = x0[1] - (P - 1) + ly, kz = x0[2] - (P - 1) + lz;
-    kx = ((kx % S.K[0]) + S.K[0]) % S.K[0];
-    ky = ((ky % S.K[1]) + S.K[1]) % S.K[1];
-    kz = ((kz % S.K[2]) + S.K[2]) % S.K[2];
-    reg[i] = mesh[S.mesh_off + (int64_t)cm * S.M + ((int64_t)kx * S.K[1] + ky) * S.K[2] + kz];
+  V* reg = reinterpret_cast<V*>(smem_raw);
+  // the brick's atoms: its (up to) 2 x 2 x 2 bins
+  __shared__ int bstart[8], bcount[8], nbin;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 2; ++c) {
+          int i0 = B.x0[0] / QEQ_BIN + a, i1 = B.x0[1] / QEQ_BIN + b, i2 = B.x0[2] / QEQ_BIN + c;
+          if (i0 >= S.nb[0] || i1 >= S.nb[1] || i2 >= S.nb[2]) continue;
+          int gb = S.bin_off + (i0 * S.nb[1] + i1) * S.nb[2] + i2;
+          bstart[n] = bin_start[gb];
+          bcount[n] = bin_start[gb + 1] - bin_start[gb];
+          ++n;
+        }
+    nbin = n;
   }
-  __syncthreads();
   const T* vals = pair_vals<T>(v64, v32);
+  const int jz = lane & 7, rsub = lane >> 3;
   double blk = 0.0;
-  int t0 = bin_start[g], t1 = bin_start[g + 1];
-  for (int t = t0 + w; t < t1; t += nw) {
-    int bs = base[t];
-    int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
-    int sp = spec[t];
-    int cm = sp >> 1, part = sp & 1;
-    const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
-    const V* rg = reg + (size_t)cm * rsz;
-    // stencil point f - (P-1) + j sits at local index f - x0 + j and carries weight M_p(w + P-1-j)
-    int o0 = f[0] - x0[0], o1 = f[1] - x0[1], o2 = f[2] - x0[2];
-    T acc = (T)0;
-    for (int c = lane; c < P * P * P; c += 32) {
-      int jz = c % P, r = c / P;
-      int jy = r % P, jx = r / P;
-      V v = rg[((o0 + jx) * len[1] + (o1 + jy)) * len[2] + (o2 + jz)];
-      T val = part ? v.y : v.x;
-      acc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * wt[2 * QEQ_MAXP + P - 1 - jz] * val;
+  for (int cm = 0; cm < S.ncm; ++cm) {
+    __syncthreads();
+    const V* mg = mesh + S.mesh_off + (int64_t)cm * S.M;
+    // rows (lx, ly) over warps, z over lanes; every index wraps at most once
+    // because the region is shorter than twice the mesh in each direction
+    for (int rrow = w; rrow < len[0] * len[1]; rrow += nw) {
+      const int lx = rrow / len[1], ly = rrow - (rrow / len[1]) * len[1];
+      int kx = B.x0[0] - (P - 1) + lx, ky = B.x0[1] - (P - 1) + ly;
+      if (kx < 0) kx += S.K[0];
+      if (kx >= S.K[0]) kx -= S.K[0];
+      if (ky < 0) ky += S.K[1];
+      if (ky >= S.K[1]) ky -= S.K[1];
+      const V* src = mg + ((int64_t)kx * S.K[1] + ky) * S.K[2];
+      V* dre = reg + rrow * QEQ_RS;
+      for (int lz = lane; lz < len[2]; lz += 32) {
+        int kz = B.x0[2] - (P - 1) + lz;
+        if (kz < 0) kz += S.K[2];
+        if (kz >= S.K[2]) kz -= S.K[2];
+        cp_async_elem(dre + lz, src + kz);
+      }
     }
-    if (with_pairs) {
-      int64_t r0 = row[t], r1 = row[t + 1];
-      for (int64_t k = r0 + lane; k < r1; k += 32) acc += vals[k] * (T)x[col[k]];
-    }
-    acc = warp_sum<T>(acc);
-    if (lane == 0) {
-      double xi = x[t];
-      double loc = S.self_s[sp] * xi;
-      if (with_J) loc += J[t] * xi;
-      const PcgScalars& c = sc[s];
-      for (int tt = 0; tt < S.S; ++tt) loc -= S.corr[sp * QEQ_MAX_SPECIES + tt] * c.xsum[tt];
-      double yi = (double)acc + loc;
-      y[t] = yi;
-      blk += xi * yi;
+    cp_async_wait_all();
+    __syncthreads();
+    int total = 0;
+    for (int b = 0; b < nbin; ++b) total += bcount[b];
+    for (int idx = w; idx < total; idx += nw) {
+      int b = 0, off = idx;
+      while (off >= bcount[b]) off -= bcount[b++];
+      const int t = bstart[b] + off;
+      const int sp = spec[t];
+      if ((sp >> 1) != cm) continue;
+      const int bs = base[t];
+      const int o0 = (bs & 1023) - B.x0[0], o1 = ((bs >> 10) & 1023) - B.x0[1], o2 = ((bs >> 20) & 1023) - B.x0[2];
+      const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
+      const int part_ = sp & 1;
+      // stencil point f - (P-1) + j is at local index f - x0 + j, weight M_p(w + P-1-j)
+      T acc = (T)0;
+      if (jz < P) {
+        const T wzj = wt[2 * QEQ_MAXP + P - 1 - jz];
+        for (int r = rsub; r < P * P; r += 4) {
+          const int jx = r / P, jy = r - (r / P) * P;
+          const V v = reg[((o0 + jx) * len[1] + (o1 + jy)) * QEQ_RS + o2 + jz];
+          acc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
+        }
+        acc *= wzj;
+      }
+      if (with_pairs) {
+        int64_t r0 = row[t], r1 = row[t + 1];
+        for (int64_t k = r0 + lane; k < r1; k += 32) acc += vals[k] * (T)x[col[k]];
+      }
+      acc = warp_sum<T>(acc);
+      if (lane == 0) {
+        double xi = x[t];
+        double loc = S.self_s[sp] * xi;
+        if (with_J) loc += J[t] * xi;
+        const PcgScalars& c = sc[s];
+        for (int tt = 0; tt < S.S; ++tt) loc -= S.corr[sp * QEQ_MAX_SPECIES + tt] * c.xsum[tt];
+        double yi = (double)acc + loc;
+        y[t] = yi;
+        blk += xi * yi;
+      }
     }
   }
   if (fuse_pAp) {
-    // deterministic per-structure reduction of x.y over the structure's bins
+    // deterministic per-structure reduction of x.y over the structure's bricks
     __shared__ double wsum[32];
+    __shared__ double red[256];
+    __shared__ bool last;
     if (lane == 0) wsum[w] = blk;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -535,12 +617,14 @@ __global__ void k_gather(const StructDev* __restrict__ st, const int* __restrict
       for (int i = 0; i < nw; ++i) b += wsum[i];
       part[g] = b;
       __threadfence();
-      int nbs = S.nb[0] * S.nb[1] * S.nb[2];
       int prev = atomicAdd(&counter[s], 1);
-      if (prev == nbs - 1) {
-        __threadfence();
-        double tot = 0.0;
-        for (int i = 0; i < nbs; ++i) tot += ((volatile double*)part)[S.bin_off + i];
+      last = (prev == S.nbr[0] * S.nbr[1] * S.nbr[2] - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double tot = ordered_block_sum(part, S.brick_off, S.nbr[0] * S.nbr[1] * S.nbr[2], 1, 0, red);
+      if (threadIdx.x == 0) {
         PcgScalars& c = sc[s];
         c.pAp = tot;
         c.alpha = (tot != 0.0) ? c.rz / tot : 0.0;
@@ -571,22 +655,24 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
     double v = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[threadIdx.x][i];
     part[(size_t)blockIdx.x * QEQ_MAX_SPECIES + threadIdx.x] = v;
+    __threadfence();  // each writer publishes its partial before the block is counted
   }
+  __shared__ bool last;
+  __shared__ double red2[256];
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     int prev = atomicAdd(&counter[ch.s], 1);
-    if (prev == ch.count - 1) {
-      __threadfence();
-      PcgScalars& c = sc[ch.s];
-      for (int k = 0; k < QEQ_MAX_SPECIES; ++k) {
-        double tot = 0.0;
-        for (int i = 0; i < ch.count; ++i)
-          tot += ((volatile double*)part)[(size_t)(ch.first + i) * QEQ_MAX_SPECIES + k];
-        c.xsum[k] = tot;
-      }
-      counter[ch.s] = 0;
+    last = (prev == ch.count - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int k = 0; k < QEQ_MAX_SPECIES; ++k) {
+      double tot = ordered_block_sum(part, ch.first, ch.count, QEQ_MAX_SPECIES, k, red2);
+      if (threadIdx.x == 0) sc[ch.s].xsum[k] = tot;
     }
+    if (threadIdx.x == 0) counter[ch.s] = 0;
   }
 }
 
@@ -601,8 +687,6 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   const T* wts = F32 ? (const T*)(const void*)Pl->d_wts32 : (const T*)(const void*)Pl->d_wts;
   const T* bmod = F32 ? (const T*)(const void*)Pl->d_bmod32 : (const T*)(const void*)Pl->d_bmod;
   const size_t csz = sizeof(V);
-  const int nw_spread = F32 ? 8 : 4;
-  const int maxncm = Pl->max_ncm;
   int rec = 0;
   auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[rec++], s) : cudaSuccess; };
   count_launch(Pl, 8);
@@ -614,42 +698,42 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   QEQ_CUDA_TRY(mark());
   // stage 1: spreading
   {
-    size_t sm = (size_t)nw_spread * maxncm * 512 * 2 * sizeof(T) +
-                (size_t)nw_spread * 3 * P * (sizeof(T) + sizeof(int)) + nw_spread * 3 * sizeof(int) + 64;
-    k_spread<T, P><<<Pl->total_bins, nw_spread * 32, sm, s>>>(Pl->d_st, Pl->d_bin_struct, Pl->d_bin_start,
-                                                              Pl->d_base, wts, Pl->d_spec, x, Pl->d_sc, use_active,
-                                                              mesh);
+    size_t sm = (size_t)2 * QEQ_BRICK * QEQ_BRICK * QEQ_RS * sizeof(T);
+    k_spread<T, P><<<Pl->total_bricks, 256, sm, s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
+                                                      Pl->d_spec, x, Pl->d_sc, use_active, mesh);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   QEQ_CUDA_TRY(mark());
   const size_t smf = csz * (size_t)Pl->fft_smem_elems;
-  // stages 2-6: forward z, forward y, x + reciprocal multiply + inverse x, inverse y, inverse z
-  k_fft_z<T><<<Pl->n_zitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_zitems, Pl->d_tw64, Pl->d_tw32, Pl->d_sc,
-                                             use_active, mesh, (T)-1);
+  V* mesh2 = reinterpret_cast<V*>(Pl->d_mesh2);
+  // stages 2-6: FFT z (L0 -> L1), FFT y (L1 -> L2), x + reciprocal multiply + inverse x (L2),
+  //             inverse y (L2 -> L1), inverse z (L1 -> L0)
+  k_fft_pass<T, PASS_ZF><<<Pl->n_zitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_zitems, Pl->d_tw64, Pl->d_tw32,
+                                                        Pl->d_sc, use_active, mesh, mesh2, Pl->tl);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
-  k_fft_y<T><<<Pl->n_yitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_yitems, Pl->d_tw64, Pl->d_tw32, Pl->d_sc,
-                                             use_active, mesh, (T)-1, Pl->ly);
+  k_fft_pass<T, PASS_YF><<<Pl->n_yitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_yitems, Pl->d_tw64, Pl->d_tw32,
+                                                        Pl->d_sc, use_active, mesh2, mesh, Pl->tl);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
   k_fft_x_green<T><<<Pl->n_xitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_xitems, Pl->d_xpairs, bmod,
                                                    Pl->d_tw64, Pl->d_tw32, Pl->d_sc, use_active, mesh);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
-  k_fft_y<T><<<Pl->n_yitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_yitems, Pl->d_tw64, Pl->d_tw32, Pl->d_sc,
-                                             use_active, mesh, (T)1, Pl->ly);
+  k_fft_pass<T, PASS_YI><<<Pl->n_yitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_yitems, Pl->d_tw64, Pl->d_tw32,
+                                                        Pl->d_sc, use_active, mesh, mesh2, Pl->tl);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
-  k_fft_z<T><<<Pl->n_zitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_zitems, Pl->d_tw64, Pl->d_tw32, Pl->d_sc,
-                                             use_active, mesh, (T)1);
+  k_fft_pass<T, PASS_ZI><<<Pl->n_zitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_zitems, Pl->d_tw64, Pl->d_tw32,
+                                                        Pl->d_sc, use_active, mesh2, mesh, Pl->tl);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
   // stage 7: gathering + real-space pairs + local terms (+ x.y per structure)
   {
-    int reg = QEQ_BIN + P - 1;
-    size_t sm = csz * (size_t)maxncm * reg * reg * reg + 64;
+    int reg = QEQ_BRICK + P - 1;
+    size_t sm = (size_t)reg * reg * QEQ_RS * sizeof(V);
     int with_pairs = Pl->pair_cap > 0;
-    k_gather<T, P><<<Pl->total_bins, 256, sm, s>>>(Pl->d_st, Pl->d_bin_struct, Pl->d_bin_start, Pl->d_base, wts,
+    k_gather<T, P><<<Pl->total_bricks, 256, sm, s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
                                                    Pl->d_spec, Pl->d_J, x, Pl->d_row, Pl->d_col, Pl->d_val64,
                                                    Pl->d_val32, with_J, with_pairs, Pl->d_sc, use_active, fuse_pAp,
                                                    Pl->d_part + (size_t)Pl->n_chunks * QEQ_MAX_SPECIES,
@@ -665,8 +749,10 @@ cudaError_t set_smem_attrs() {
   const int big = 200 * 1024;
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_gather<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_ZI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return cudaSuccess;
 }

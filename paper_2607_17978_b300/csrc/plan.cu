@@ -193,7 +193,6 @@ bool choose_mesh(const double* h, double V, double wmin, double n_atoms, int pp,
   return true;
 }
 
-const int kSlotBudget = 4096;  // complex elements per FFT buffer of one CTA
 
 }  // namespace
 
@@ -205,12 +204,12 @@ static qeq_status fail(qeq_plan_s* P, qeq_status st, const std::string& msg) {
 static void free_plan(qeq_plan_s* P) {
   if (!P) return;
   void* ptrs[] = {P->d_st,     P->d_fft,     P->d_tw64,    P->d_tw32,     P->d_bmod,    P->d_bmod32,
-                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_xpairs,   P->d_bin_struct, P->d_atom_struct,
+                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_xpairs,   P->d_bin_struct, P->d_atom_struct, P->d_brick_struct,
                   P->d_chunks, P->d_key,     P->d_bin_count, P->d_bin_start, P->d_bin_fill, P->d_perm,
                   P->d_scan_tmp, P->d_base,  P->d_wts,     P->d_wts32,    P->d_spec,    P->d_J,
                   P->d_chi,    P->d_dinv,    P->d_posc,    P->d_row,      P->d_row_cnt, P->d_col,
                   P->d_val64,  P->d_val32,   P->d_q,       P->d_r,        P->d_z,       P->d_p,
-                  P->d_Ap,     P->d_x,       P->d_mesh,    P->d_part,     P->d_counter, P->d_sc,
+                  P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -287,14 +286,13 @@ static qeq_status build_plan(qeq_plan_s* P) {
   std::vector<float> bmod32;
   std::vector<int4> zit, yit, xit;
   std::vector<int2> xpairs;
-  std::vector<int> bin_struct;
+  std::vector<int> bin_struct, brick_struct;
   std::vector<Chunk> chunks;
   int64_t mesh_off = 0;
   int bin_off = 0;
   int64_t pair_cap = 0;
   int64_t smem_elems = 0;
-  const int ly = 8;
-  P->ly = ly;
+
 
   // B-spline order: one per plan (the kernels are specialised on it); when not
   // given, the order with the smallest summed cost over all structures
@@ -321,6 +319,22 @@ static qeq_status build_plan(qeq_plan_s* P) {
     if (pbest == 0) return fail(P, QEQ_ERR_INVALID, "no mesh meets ewald_tol within 1000 points per direction");
   }
   P->max_p = pbest;
+  // lines per tile of the transposing FFT passes: from the largest mesh of the plan
+  int maxK = 12;
+  {
+    const double omega = split_width(D);
+    for (int s = 0; s < ns; ++s) {
+      const double* h = D.cells + 9 * s;
+      double V = fabs(det3(h)), c = 0;
+      int K[3] = {12, 12, 12};
+      if (V > 1e-9)
+        choose_mesh(h, V, narrowest_width(D.sigma + (size_t)S * s, S, omega),
+                    (double)(P->offsets[s + 1] - P->offsets[s]), pbest, D, K, &c);
+      for (int d = 0; d < 3; ++d) maxK = std::max(maxK, K[d]);
+    }
+  }
+  const int tl = fft_tile_lines(maxK);
+  P->tl = tl;
 
   auto fft_plan_for = [&](int K) {
     auto it = fft_index.find(K);
@@ -331,6 +345,11 @@ static qeq_status build_plan(qeq_plan_s* P) {
     std::vector<int> r = radices(K);
     f.nst = (int)r.size();
     for (size_t i = 0; i < r.size(); ++i) f.radix[i] = r[i];
+    for (int i = 0, ns = 1; i < f.nst; ns *= f.radix[i], ++i) {
+      f.nbf[i] = make_fastdiv(K / f.radix[i]);
+      f.ns[i] = make_fastdiv(ns);
+    }
+    f.k = make_fastdiv(K);
     f.tw_off = (int)tw64.size();
     for (int m = 0; m < K; ++m) {
       double ang = -2.0 * kPi * (double)m / K;
@@ -413,6 +432,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
       T.K[d] = K;
       (void)cst;
       T.nb[d] = (K + QEQ_BIN - 1) / QEQ_BIN;
+      T.nbr[d] = (K + QEQ_BRICK - 1) / QEQ_BRICK;
       // bins that can hold an atom within r_cut (plus one for a ragged last bin)
       double l = rc / wd[d] * K / QEQ_BIN;
       int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
@@ -425,6 +445,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
     int nbins = T.nb[0] * T.nb[1] * T.nb[2];
     for (int b = 0; b < nbins; ++b) bin_struct.push_back(s);
     bin_off += nbins;
+    T.brick_off = (int)brick_struct.size();
+    for (int b = 0; b < T.nbr[0] * T.nbr[1] * T.nbr[2]; ++b) brick_struct.push_back(s);
     for (int d = 0; d < 3; ++d) {
       T.fft_plan[d] = fft_plan_for(T.K[d]);
       T.bmod_off[d] = (int)bmod.size();
@@ -435,30 +457,12 @@ static qeq_status build_plan(qeq_plan_s* P) {
         bmod32.push_back((float)v);
       }
     }
-    // --- FFT work lists
-    const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
-    int lz = std::max(1, kSlotBudget / K2);
-    for (int c = 0; c < T.ncm; ++c)
-      for (int l = 0; l < K0 * K1; l += lz) zit.push_back(make_int4(s, c, l, std::min(lz, K0 * K1 - l)));
-    smem_elems = std::max<int64_t>(smem_elems, (int64_t)K2 * (1 + 2 * std::min(lz, K0 * K1)));
-    int lyy = std::max(1, std::min(ly, kSlotBudget / K1));
-    if (lyy < ly) return fail(P, QEQ_ERR_INVALID, "mesh too large for the y-pass tile");
-    for (int c = 0; c < T.ncm; ++c)
-      for (int x = 0; x < K0; ++x)
-        for (int z0 = 0; z0 < K2; z0 += ly) yit.push_back(make_int4(s, c, x, z0));
-    smem_elems = std::max<int64_t>(smem_elems, (int64_t)K1 * (1 + 2 * ly));
+    // --- FFT work lists (transposing passes)
     T.xpair_off = (int)xpairs.size();
-    for (int y = 0; y < K1; ++y)
-      for (int z = 0; z < K2; ++z) {
-        int l = y * K2 + z;
-        int lm = ((K1 - y) % K1) * K2 + (K2 - z) % K2;
-        if (l <= lm) xpairs.push_back(make_int2(l, lm));
-      }
-    int npairs = (int)xpairs.size() - T.xpair_off;
-    int np = std::max(1, kSlotBudget / (2 * T.ncm * K0));
-    for (int j = 0; j < npairs; j += np)
-      xit.push_back(make_int4(s, T.xpair_off + j, std::min(np, npairs - j), 0));
-    smem_elems = std::max<int64_t>(smem_elems, (int64_t)K0 * (1 + 2 * 2 * std::min(np, npairs) * T.ncm));
+    smem_elems = std::max<int64_t>(
+        smem_elems, fft_work_lists(T, s, tl, T.xpair_off, [&](int4 v) { zit.push_back(v); },
+                                   [&](int4 v) { yit.push_back(v); }, [&](int2 v) { xpairs.push_back(v); },
+                                   [&](int4 v) { xit.push_back(v); }));
     // --- real-space pair capacity: local density bound with margin
     if (any) {
       int64_t n = T.atom_end - T.atom_begin;
@@ -483,6 +487,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->hs = hs;
   P->hfft = fplans;
   P->total_bins = bin_off;
+  P->total_bricks = (int)brick_struct.size();
   P->total_mesh = mesh_off;
   P->pair_cap = pair_cap;
   P->n_chunks = (int)chunks.size();
@@ -516,6 +521,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(upload(P, &P->d_xitems, xit));
   ALLOC(upload(P, &P->d_xpairs, xpairs));
   ALLOC(upload(P, &P->d_bin_struct, bin_struct));
+  ALLOC(upload(P, &P->d_brick_struct, brick_struct));
   ALLOC(upload(P, &P->d_atom_struct, atom_struct));
   ALLOC(upload(P, &P->d_chunks, chunks));
   const int64_t N = P->n_atoms;
@@ -541,6 +547,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(dalloc(P, &P->d_val32, pair_cap));
   for (double** v : {&P->d_q, &P->d_r, &P->d_z, &P->d_p, &P->d_Ap, &P->d_x}) ALLOC(dalloc(P, v, N));
   ALLOC(dalloc(P, &P->d_mesh, (size_t)P->total_mesh));
+  ALLOC(dalloc(P, &P->d_mesh2, (size_t)P->total_mesh));
   ALLOC(dalloc(P, &P->d_part, (size_t)P->n_chunks * QEQ_MAX_SPECIES * 2 + P->total_bins + 64));
   ALLOC(dalloc(P, &P->d_counter, (size_t)ns * 4));
   ALLOC(cudaMemset(P->d_counter, 0, sizeof(int) * ns * 4));

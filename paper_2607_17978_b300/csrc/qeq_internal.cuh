@@ -10,10 +10,12 @@
 #include "qeq.h"
 
 #define QEQ_MAX_SPECIES 8
-#define QEQ_BIN 8          // mesh points per edge of an atom bin / spread-gather brick
+#define QEQ_BIN 8          // mesh points per edge of an atom bin (sorting, real-space search)
+#define QEQ_BRICK 16       // mesh points per edge of a spread / gather brick (2 x 2 x 2 bins)
+#define QEQ_RS 24          // shared-memory z-row stride of a brick (conflict-free for 4 rows x 8 z)
 #define QEQ_MAXP 8         // largest supported B-spline order
 #define QEQ_MAX_STAGES 16  // radix stages of one FFT length
-#define QEQ_CHUNK 2048     // atoms per reduction chunk (one CTA)
+#define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
 
 // ---------------------------------------------------------------------------
 // Per-structure constants, built on the host by qeq_plan_create.
@@ -38,7 +40,9 @@ struct StructDev {
   int fft_plan[3];        // FFT plan index per direction
   int bmod_off[3];        // offsets into the B-spline modulus table per direction
   int xpair_off;          // first entry of this structure in the x-pass line-pair table
-  int pad_;
+  int brick_off;          // first global brick of this structure
+  int nbr[3];             // bricks per direction (ceil(K/QEQ_BRICK))
+  int pad2_;
   double w2[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];     // reciprocal Gaussian width^2 w_st^2
   double corr[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];   // G = 0 width term over r < r_cut (narrow pairs)
   double inv_sw[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES]; // 1/(sqrt2 w_st) (narrow pairs)
@@ -48,12 +52,36 @@ struct StructDev {
   uint32_t narrow[QEQ_MAX_SPECIES];                 // bit t set: pair (s,t) has a real-space term
 };
 
+// Division by a runtime-invariant divisor d with a multiply and a shift
+// (round-up method of Granlund & Montgomery): n / d = (umulhi(n, m) + n) >> s
+// for 0 <= n < 2^31.
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t s = 0;
+  while ((1ull << s) < d) ++s;
+  f.s = s;
+  f.m = (uint32_t)(((((1ull << s) - d) << 32) / d) + 1);
+  return f;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.s; }
+#endif
+
 struct FftPlanDev {
   int K;
   int nst;
   int radix[QEQ_MAX_STAGES];
   int tw_off;  // offset of exp(-2 pi i m / K), m < K, in the twiddle tables
   int pad_;
+  FastDiv nbf[QEQ_MAX_STAGES];  // K / radix of each stage
+  FastDiv ns[QEQ_MAX_STAGES];   // product of the radices before each stage
+  FastDiv k;                    // K
 };
 
 // Per-structure scalars of the PCG (device resident).
@@ -120,13 +148,14 @@ struct qeq_plan_s {
   double* d_bmod = nullptr;
   float* d_bmod32 = nullptr;
   int max_ncm = 1;                 // largest complex-mesh count of any structure
-  int ly = 8;                      // lines per y-pass item
   int64_t fft_smem_elems = 0;      // complex elements of shared memory per FFT CTA
   int4* d_zitems = nullptr;
   int4* d_yitems = nullptr;
   int4* d_xitems = nullptr;
   int2* d_xpairs = nullptr;
   int* d_bin_struct = nullptr;     // structure of each global bin
+  int* d_brick_struct = nullptr;   // structure of each global brick
+  int total_bricks = 0;
   int* d_atom_struct = nullptr;    // structure of each atom (input order)
   Chunk* d_chunks = nullptr;
   // per-solve atom data (sorted order)
@@ -153,12 +182,58 @@ struct qeq_plan_s {
   // vectors (sorted order)
   double *d_q = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_x = nullptr;
   // mesh (reinterpreted as float2 in mixed precision)
-  double2* d_mesh = nullptr;
+  double2* d_mesh = nullptr;       // layouts L0 / L2 (see matvec.cu)
+  double2* d_mesh2 = nullptr;      // layout L1
+  int tl = 8;                      // lines per tile of the transposing FFT passes
   // reductions
   double* d_part = nullptr;        // n_chunks * 16 partials
   int* d_counter = nullptr;        // n_struct counters for last-block reductions
   PcgScalars* d_sc = nullptr;
-  int* d_err = nullptr;            // device error bits
+  int* d_err = nullptr;            // Work lists of the FFT passes of one structure (shared by qeq_plan_create and
+// the allocation-free entry point).  Z items {s, c, x, y0} and Y items
+// {s, c, z, x0} cover tiles of tl lines; X items {s, first pair, npairs, 0}
+// cover pairs of x lines (z, y) and (-z, -y), lines indexed l = z*K1 + y.
+// Returns the shared-memory size (complex elements) the passes need.
+template <class AddZ, class AddY, class AddPair, class AddX>
+inline int64_t fft_work_lists(const StructDev& T, int s, int tl, int pair_base, AddZ addz, AddY addy,
+                              AddPair addpair, AddX addx) {
+  const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
+  for (int c = 0; c < T.ncm; ++c)
+    for (int x = 0; x < K0; ++x)
+      for (int y0 = 0; y0 < K1; y0 += tl) addz(make_int4(s, c, x, y0));
+  for (int c = 0; c < T.ncm; ++c)
+    for (int z = 0; z < K2; ++z)
+      for (int x0 = 0; x0 < K0; x0 += tl) addy(make_int4(s, c, z, x0));
+  int npairs = 0;
+  for (int z = 0; z < K2; ++z)
+    for (int y = 0; y < K1; ++y) {
+      int l = z * K1 + y;
+      int lm = ((K2 - z) % K2) * K1 + (K1 - y) % K1;
+      if (l <= lm) {
+        addpair(make_int2(l, lm));
+        ++npairs;
+      }
+    }
+  int np = 4096 / (2 * T.ncm * K0);
+  if (np < 1) np = 1;
+  for (int j = 0; j < npairs; j += np) addx(make_int4(s, pair_base + j, (npairs - j < np) ? npairs - j : np, 0));
+  int64_t e = 0;
+  auto mx = [&](int64_t v) { e = v > e ? v : e; };
+  mx(K2 + 2 * (int64_t)tl * (K2 + 1));
+  mx(K1 + 2 * (int64_t)tl * (K1 + 1));
+  int nsl = 2 * (np < npairs ? np : npairs) * T.ncm;
+  mx(K0 + 2 * (int64_t)nsl * (K0 + 1));
+  return e;
+}
+
+// lines per tile: a power of two, at most 16 and at most 4096 / K elements per buffer
+inline int fft_tile_lines(int maxK) {
+  int tl = 16;
+  while (tl > 1 && tl * maxK > 4096) tl >>= 1;
+  return tl;
+}
+
+// device error bits
   int* d_done = nullptr;           // all-structures-inactive flag
   int* h_done = nullptr;           // pinned mirror
   cudaEvent_t ev_done = nullptr;
@@ -169,6 +244,50 @@ struct qeq_plan_s {
   int graph_iter_prec = -1;
   int graph_iter_k = 0;
 };
+
+// Work lists of the FFT passes of one structure (shared by qeq_plan_create and
+// the allocation-free entry point).  Z items {s, c, x, y0} and Y items
+// {s, c, z, x0} cover tiles of tl lines; X items {s, first pair, npairs, 0}
+// cover pairs of x lines (z, y) and (-z, -y), lines indexed l = z*K1 + y.
+// Returns the shared-memory size (complex elements) the passes need.
+template <class AddZ, class AddY, class AddPair, class AddX>
+inline int64_t fft_work_lists(const StructDev& T, int s, int tl, int pair_base, AddZ addz, AddY addy,
+                              AddPair addpair, AddX addx) {
+  const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
+  for (int c = 0; c < T.ncm; ++c)
+    for (int x = 0; x < K0; ++x)
+      for (int y0 = 0; y0 < K1; y0 += tl) addz(make_int4(s, c, x, y0));
+  for (int c = 0; c < T.ncm; ++c)
+    for (int z = 0; z < K2; ++z)
+      for (int x0 = 0; x0 < K0; x0 += tl) addy(make_int4(s, c, z, x0));
+  int npairs = 0;
+  for (int z = 0; z < K2; ++z)
+    for (int y = 0; y < K1; ++y) {
+      int l = z * K1 + y;
+      int lm = ((K2 - z) % K2) * K1 + (K1 - y) % K1;
+      if (l <= lm) {
+        addpair(make_int2(l, lm));
+        ++npairs;
+      }
+    }
+  int np = 4096 / (2 * T.ncm * K0);
+  if (np < 1) np = 1;
+  for (int j = 0; j < npairs; j += np) addx(make_int4(s, pair_base + j, (npairs - j < np) ? npairs - j : np, 0));
+  int64_t e = 0;
+  auto mx = [&](int64_t v) { e = v > e ? v : e; };
+  mx(K2 + 2 * (int64_t)tl * (K2 + 1));
+  mx(K1 + 2 * (int64_t)tl * (K1 + 1));
+  int nsl = 2 * (np < npairs ? np : npairs) * T.ncm;
+  mx(K0 + 2 * (int64_t)nsl * (K0 + 1));
+  return e;
+}
+
+// lines per tile: a power of two, at most 16 and at most 4096 / K elements per buffer
+inline int fft_tile_lines(int maxK) {
+  int tl = 16;
+  while (tl > 1 && tl * maxK > 4096) tl >>= 1;
+  return tl;
+}
 
 // device error bits
 enum {
@@ -187,6 +306,23 @@ cudaError_t launch_prepare_atoms(qeq_plan_s* P, const double* pos, const int32_t
 cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, int with_J,
                           int use_active, int fuse_pAp, cudaEvent_t* ev /* QEQ_N_STAGES+1 or NULL */);
 cudaError_t matvec_set_attributes();
+
+// Deterministic block-wide sum of part[(first + i) * stride + k], i < count:
+// thread t adds the entries i = t, t + blockDim, ... in order, then thread 0
+// adds the per-thread sums in thread order.  Every thread must call it; the
+// result is valid in thread 0.  red: blockDim.x doubles of shared memory.
+__device__ __forceinline__ double ordered_block_sum(const double* part, int first, int count, int stride, int k,
+                                                    double* red) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) a += ((const volatile double*)part)[(size_t)(first + i) * stride + k];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)blockDim.x; ++i) tot += red[i];
+  __syncthreads();
+  return tot;
+}
 
 inline void count_launch(qeq_plan_s* P, int n = 1) {
   if (P->capturing)

@@ -46,6 +46,7 @@ template <int NV>
 __device__ bool chunk_reduce(double (&v)[NV], const int (&op)[NV], const Chunk& ch, double* part, int* counter,
                              double (&tot)[NV]) {
   __shared__ double red[NV][32];
+  __shared__ double red2[256];
   __shared__ bool last;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -64,21 +65,29 @@ __device__ bool chunk_reduce(double (&v)[NV], const int (&op)[NV], const Chunk& 
     __threadfence();
     int prev = atomicAdd(counter + ch.s, 1);
     last = (prev == ch.count - 1);
-    if (last) {
-      __threadfence();
-      for (int k = 0; k < NV; ++k) {
-        double x = ((volatile double*)part)[(size_t)ch.first * 8 + k];
-        for (int i = 1; i < ch.count; ++i) {
-          double y = ((volatile double*)part)[(size_t)(ch.first + i) * 8 + k];
-          x = op[k] == RED_SUM ? x + y : (op[k] == RED_MAX ? fmax(x, y) : fmin(x, y));
-        }
-        tot[k] = x;
-      }
-      counter[ch.s] = 0;
-    }
   }
   __syncthreads();
-  return threadIdx.x == 0 && last;
+  if (!last) return false;
+  __threadfence();
+  // the structure's last chunk combines all its chunk partials in a fixed order
+  for (int k = 0; k < NV; ++k) {
+    double a = op[k] == RED_SUM ? 0.0 : (op[k] == RED_MAX ? -1e300 : 1e300);
+    for (int i = threadIdx.x; i < ch.count; i += blockDim.x) {
+      double y = ((volatile double*)part)[(size_t)(ch.first + i) * 8 + k];
+      a = op[k] == RED_SUM ? a + y : (op[k] == RED_MAX ? fmax(a, y) : fmin(a, y));
+    }
+    red2[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double x = red2[0];
+      for (int i = 1; i < (int)blockDim.x; ++i)
+        x = op[k] == RED_SUM ? x + red2[i] : (op[k] == RED_MAX ? fmax(x, red2[i]) : fmin(x, red2[i]));
+      tot[k] = x;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) counter[ch.s] = 0;
+  return threadIdx.x == 0;
 }
 
 // q0: user charges (permuted to sorted order) or zero; sums for the projection.

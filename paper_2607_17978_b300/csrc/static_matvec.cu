@@ -34,8 +34,6 @@ namespace {
 
 const double kPiS = 3.14159265358979323846;
 const int kMaxDev = 64;
-const int kSlotBudgetS = 4096;
-const int kLy = 8;
 
 // File-scope scratch: every buffer of one matvec, carved at 256-byte offsets.
 static __device__ __align__(256) unsigned char g_static_scratch[QEQ_STATIC_SCRATCH_BYTES];
@@ -51,9 +49,9 @@ struct Staging {
   float2 tw32[3 * QEQ_STATIC_MAX_MESH];
   double bmod[3 * QEQ_STATIC_MAX_MESH];
   float bmod32[3 * QEQ_STATIC_MAX_MESH];
-  int4 zit[512];
-  int4 yit[QEQ_STATIC_MAX_MESH * ((QEQ_STATIC_MAX_MESH + kLy - 1) / kLy) * (QEQ_STATIC_MAX_SPECIES / 2)];
-  int4 xit[1024];
+  int4 zit[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH * (QEQ_STATIC_MAX_SPECIES / 2)];
+  int4 yit[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH * (QEQ_STATIC_MAX_SPECIES / 2)];
+  int4 xit[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH];
   int2 xpairs[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH / 2 + 4];
   int bin_struct[(QEQ_STATIC_MAX_MESH / QEQ_BIN) * (QEQ_STATIC_MAX_MESH / QEQ_BIN) * (QEQ_STATIC_MAX_MESH / QEQ_BIN)];
   int atom_struct[QEQ_STATIC_MAX_ATOMS];
@@ -271,6 +269,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     int K = Kb[d];
     T.K[d] = K;
     T.nb[d] = (K + QEQ_BIN - 1) / QEQ_BIN;
+    T.nbr[d] = (K + QEQ_BRICK - 1) / QEQ_BRICK;
     double l = r_cut / wd[d] * K / QEQ_BIN;
     int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
     T.rs_range[d] = std::max(1, R);
@@ -280,6 +279,8 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   T.bin_off = 0;
   const int nbins = T.nb[0] * T.nb[1] * T.nb[2];
   for (int b = 0; b < nbins; ++b) G.bin_struct[b] = 0;
+  T.brick_off = 0;
+  const int nbricks = T.nbr[0] * T.nbr[1] * T.nbr[2];
   double Mp[QEQ_MAXP];
   bspline_int_s(T.p, Mp);
   for (int d = 0; d < 3; ++d) {
@@ -294,6 +295,11 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
         n /= r;
       }
     f.nst = ns;
+    for (int i = 0, prod = 1; i < f.nst; prod *= f.radix[i], ++i) {
+      f.nbf[i] = make_fastdiv(K / f.radix[i]);
+      f.ns[i] = make_fastdiv(prod);
+    }
+    f.k = make_fastdiv(K);
     f.tw_off = d * QEQ_STATIC_MAX_MESH;
     T.fft_plan[d] = d;
     T.bmod_off[d] = d * QEQ_STATIC_MAX_MESH;
@@ -313,28 +319,13 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
       G.bmod32[d * QEQ_STATIC_MAX_MESH + m] = (float)v;
     }
   }
-  // FFT work lists
-  const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
+  // FFT work lists (transposing passes)
   int nz = 0, ny = 0, nx = 0, npairs = 0;
-  int64_t smem_elems = 0;
-  const int lz = std::max(1, kSlotBudgetS / K2);
-  for (int c = 0; c < T.ncm; ++c)
-    for (int l = 0; l < K0 * K1; l += lz) G.zit[nz++] = make_int4(0, c, l, std::min(lz, K0 * K1 - l));
-  smem_elems = std::max<int64_t>(smem_elems, (int64_t)K2 * (1 + 2 * std::min(lz, K0 * K1)));
-  for (int c = 0; c < T.ncm; ++c)
-    for (int x = 0; x < K0; ++x)
-      for (int z0 = 0; z0 < K2; z0 += kLy) G.yit[ny++] = make_int4(0, c, x, z0);
-  smem_elems = std::max<int64_t>(smem_elems, (int64_t)K1 * (1 + 2 * kLy));
+  const int tl = fft_tile_lines(std::max(T.K[0], std::max(T.K[1], T.K[2])));
   T.xpair_off = 0;
-  for (int y = 0; y < K1; ++y)
-    for (int z = 0; z < K2; ++z) {
-      int l = y * K2 + z;
-      int lm = ((K1 - y) % K1) * K2 + (K2 - z) % K2;
-      if (l <= lm) G.xpairs[npairs++] = make_int2(l, lm);
-    }
-  const int np = std::max(1, kSlotBudgetS / (2 * T.ncm * K0));
-  for (int j = 0; j < npairs; j += np) G.xit[nx++] = make_int4(0, j, std::min(np, npairs - j), 0);
-  smem_elems = std::max<int64_t>(smem_elems, (int64_t)K0 * (1 + 2 * 2 * std::min(np, npairs) * T.ncm));
+  const int64_t smem_elems = fft_work_lists(
+      T, 0, tl, 0, [&](int4 v) { G.zit[nz++] = v; }, [&](int4 v) { G.yit[ny++] = v; },
+      [&](int2 v) { G.xpairs[npairs++] = v; }, [&](int4 v) { G.xit[nx++] = v; });
   int64_t pair_cap = 0;
   if (any) {
     double per = (double)n_atoms / V * (4.0 / 3.0) * kPiS * r_cut * r_cut * r_cut;
@@ -363,9 +354,10 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.max_S = S;
   P.max_p = T.p;
   P.max_ncm = T.ncm;
-  P.ly = kLy;
+  P.tl = tl;
   P.fft_smem_elems = smem_elems;
   P.total_bins = nbins;
+  P.total_bricks = nbricks;
   P.total_mesh = T.M * T.ncm;
   P.pair_cap = pair_cap;
   P.n_chunks = nchunks;
@@ -386,6 +378,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.d_xitems = cv.take<int4>(nx);
   P.d_xpairs = cv.take<int2>(npairs);
   P.d_bin_struct = cv.take<int>(nbins);
+  P.d_brick_struct = cv.take<int>(nbricks);
   P.d_atom_struct = cv.take<int>(N);
   P.d_chunks = cv.take<Chunk>(nchunks);
   P.d_key = cv.take<int>(N);
@@ -410,6 +403,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.d_x = cv.take<double>(N);
   P.d_Ap = cv.take<double>(N);
   P.d_mesh = cv.take<double2>((size_t)P.total_mesh);
+  P.d_mesh2 = cv.take<double2>((size_t)P.total_mesh);
   P.d_part = cv.take<double>((size_t)nchunks * QEQ_MAX_SPECIES * 2 + nbins + 64);
   P.d_counter = cv.take<int>(4);
   P.d_sc = cv.take<PcgScalars>(1);
@@ -433,6 +427,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   SCOPY(P.d_xitems, G.xit, sizeof(int4) * nx);
   SCOPY(P.d_xpairs, G.xpairs, sizeof(int2) * npairs);
   SCOPY(P.d_bin_struct, G.bin_struct, sizeof(int) * nbins);
+  SCOPY(P.d_brick_struct, G.bin_struct, sizeof(int) * nbricks);
   SCOPY(P.d_atom_struct, G.atom_struct, sizeof(int) * N);
   SCOPY(P.d_chunks, G.chunks, sizeof(Chunk) * nchunks);
 #undef SCOPY
