@@ -44,14 +44,22 @@ WORKLOAD_OPTS = {
     1: dict(ewald_tol=1e-7, r_cut=9.0),
     2: dict(ewald_tol=1e-6, r_cut=8.0),
     3: dict(ewald_tol=1e-6, r_cut=8.0),
+    4: dict(ewald_tol=1e-6, r_cut=8.0),
     5: dict(ewald_tol=1e-6, r_cut=8.0),
 }
 WORKLOAD_NAME = {
     1: "rocksalt 3x3x3 (216 atoms), chi_A~N(-2,.3) chi_B~N(2,.3), J 2/1.5, sigma 1.0/1.8, r_cut 9, ewald_tol 1e-7",
     2: "rocksalt 12x12x12 (13,824 atoms), jitter 0.15 A, r_cut 8 A, ewald_tol 1e-6, Jacobi PCG",
     3: "rocksalt 24x24x24 -5% vacancies, triclinic shear <=10 deg (105,062 atoms), r_cut 8, ewald_tol 1e-6",
+    4: ("512 uneven periodic cells, N log-uniform 64-4096 (519,537 atoms), density 0.045/A^3, orthorhombic or "
+        "triclinic, 2-4 species, chi~N(0,1.5), J~U(1,3), sigma~U(0.8,2.0), q_tot in {-1,0,1}; one batched solve"),
     5: "rocksalt 50x50x50 -2% vacancies, jitter 0.2 A (980,000 atoms), r_cut 8, ewald_tol 1e-6",
 }
+
+
+def workload_structs(w: int):
+    from paper_2607_17978_b300 import synth
+    return synth.batch_workload(512) if w == 4 else [synth.workload(w)]
 
 
 def dist_env():
@@ -160,31 +168,62 @@ def cpu_oracle_matvec_time(st, budget_s: float = 20.0):
     return min(times), cores, len(times)
 
 
+def cpu_oracle_dense_batch(structs, every: int = 64):
+    """Dense bordered oracle solves of a stratified sample of a batch: solves/s."""
+    from oracle import qeq_oracle as O
+    from paper_2607_17978_b300 import synth
+    cores = len(os.sched_getaffinity(0))
+    O.build_c()
+    sample = list(range(0, len(structs), every))
+    t0 = time.perf_counter()
+    for k in sample:
+        O.solve_structure(structs[k], k_e=synth.COULOMB_K_EV_A)
+    t = time.perf_counter() - t0
+    return (len(sample) / t, cores,
+            f"dense FP64 oracle solves (Ewald assembly + bordered LU) of {len(sample)} of {len(structs)} structures "
+            f"(every {every}th), {t:.1f} s")
+
+
 def run_reference(args):
+    """The CPU oracle as it stands, timed on the host cores on this workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_2607_17978_b300 import synth
-    st = synth.workload(args.workload)
-    cores = len(os.sched_getaffinity(0))
     from oracle import qeq_oracle as O
+    from paper_2607_17978_b300 import synth
+    structs = workload_structs(args.workload)
+    cores = len(os.sched_getaffinity(0))
     O.build_c()
-    q = np.random.default_rng(0).normal(size=st.n)
-    for _ in range(args.warmup):
-        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
-    t = (time.perf_counter() - t0) / args.steps
-    solve_s = t * PCG_ITERS_REFERENCE
+    if len(structs) > 1:
+        # one dense bordered solve per step, cycling through every 64th structure
+        sample = list(range(0, len(structs), 64))
+        for k in range(args.warmup):
+            O.solve_structure(structs[sample[k % len(sample)]], k_e=synth.COULOMB_K_EV_A)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            O.solve_structure(structs[sample[k % len(sample)]], k_e=synth.COULOMB_K_EV_A)
+        solve_s = (time.perf_counter() - t0) / args.steps
+        desc = (f"dense FP64 oracle solve (Ewald assembly + bordered LU) of one structure per step, cycling through "
+                f"every 64th of the {len(structs)} structures")
+        atoms = sum(x.n for x in structs)
+    else:
+        st = structs[0]
+        q = np.random.default_rng(0).normal(size=st.n)
+        for _ in range(args.warmup):
+            O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+        solve_s = (time.perf_counter() - t0) / args.steps * PCG_ITERS_REFERENCE
+        desc = (f"one FP64 Ewald matvec of the full {st.n}-atom cell per step by the CPU oracle, "
+                f"x {PCG_ITERS_REFERENCE} PCG iterations (extrapolated to a solve)")
+        atoms = st.n
     value = 1.0 / solve_s
-    sample = (f"one FP64 Ewald matvec of the full {st.n}-atom cell per step by the CPU oracle, "
-              f"x {PCG_ITERS_REFERENCE} PCG iterations (extrapolated to a solve)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": st.n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": atoms, "structures": len(structs)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -219,15 +258,18 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2607_17978_b300 import build, qeq, synth
     build.build()
-    st = synth.workload(args.workload)
+    structs = workload_structs(args.workload)
+    n_struct = len(structs)
+    n_atoms = sum(x.n for x in structs)
+    st = structs[0]
     opts = WORKLOAD_OPTS[args.workload]
-    pos, spc, chi, J, qt = qeq.pack([st])
+    pos, spc, chi, J, qt = qeq.pack(structs)
     d_pos = torch.tensor(pos, device=dev)
     d_spc = torch.tensor(spc, device=dev)
     d_chi = torch.tensor(chi, device=dev)
     d_J = torch.tensor(J, device=dev)
-    plan = qeq.plan_for_structures([st], precision=args.precision, device=dev, **opts)
-    q_out = torch.empty(st.n, dtype=torch.float64, device=dev)
+    plan = qeq.plan_for_structures(structs, precision=args.precision, device=dev, **opts)
+    q_out = torch.empty(n_atoms, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
 
     def solve():
@@ -250,7 +292,7 @@ def run_ours(args):
         ev0[k].record(plan.stream)
         res = solve()
         ev1[k].record(plan.stream)
-        iters.append(res.info[0]["iterations"])
+        iters.append([i["iterations"] for i in res.info])
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -262,13 +304,15 @@ def run_ours(args):
         tt = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms = float(tt.item())
-    status = res.info[0]["status"]
-    it_mean = float(np.mean(iters))
+    status = max(i["status"] for i in res.info)
+    it_arr = np.array(iters, dtype=np.float64)               # steps x structures
+    atoms_iters = float(np.mean(it_arr @ np.array([x.n for x in structs], dtype=np.float64)))
+    it_mean = float(it_arr.mean())
 
     # ---- roofline of the dominant kernel (per-stage CUDA events on the plan's stream)
     prof = plan.profile_matvec(20)
     pairs_est = 0
-    sb = stage_bytes(plan, args.precision, st.n, pairs_est)
+    sb = stage_bytes(plan, args.precision, n_atoms, pairs_est)
     dom = max(prof, key=prof.get)
     pk = peaks()
     hbm = pk.get("hbm_gbs")
@@ -280,29 +324,37 @@ def run_ours(args):
     matvec_bytes = sum(sb.values())
 
     # ---- plain FP64 GPU PCG (one structure per launch, no graph): the comparison denominator
-    plain = qeq.plan_for_structures([st], precision="fp64", graph=False, device=dev, **opts)
-    plain.solve(d_pos, d_spc, d_chi, d_J, qt)
-    torch.cuda.synchronize()
-    n_plain = max(1, min(3, args.steps))
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.fill_(0.0)
-    plain.stream.wait_stream(torch.cuda.current_stream(dev))
-    a.record(plain.stream)
-    for _ in range(n_plain):
-        rp = plain.solve(d_pos, d_spc, d_chi, d_J, qt)
-    b.record(plain.stream)
-    torch.cuda.synchronize()
-    plain_ms = a.elapsed_time(b) / n_plain
-    plain_iters = rp.info[0]["iterations"]
-    q_plain = rp.q.clone()
-    plain.close()
+    sample = list(range(0, n_struct, 16)) if n_struct > 1 else [0]
+    plain_ms_sum, plain_iters, dq_plain = 0.0, [], 0.0
+    offs = np.concatenate([[0], np.cumsum([x.n for x in structs])])
+    for k in sample:
+        s1 = structs[k]
+        plain = qeq.plan_for_structures([s1], precision="fp64", graph=False, device=dev, **opts)
+        a1 = [torch.tensor(v, device=dev) for v in qeq.pack([s1])[:4]]
+        q1 = np.array([s1.q_tot])
+        plain.solve(*a1, q1)
+        torch.cuda.synchronize()
+        n_plain = max(1, min(3, args.steps)) if n_struct == 1 else 1
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(0.0)
+        plain.stream.wait_stream(torch.cuda.current_stream(dev))
+        a.record(plain.stream)
+        for _ in range(n_plain):
+            rp = plain.solve(*a1, q1)
+        b.record(plain.stream)
+        torch.cuda.synchronize()
+        plain_ms_sum += a.elapsed_time(b) / n_plain
+        plain_iters.append(rp.info[0]["iterations"])
+        dq_plain = max(dq_plain, float((q_out[offs[k]:offs[k + 1]] - rp.q).abs().max().item()))
+        plain.close()
+    plain_ms = plain_ms_sum * n_struct / len(sample)     # one structure after another, extrapolated
 
     # ---- end to end through the public API with pinned host buffers
     h_pos = torch.tensor(pos).pin_memory()
     h_spc = torch.tensor(spc).pin_memory()
     h_chi = torch.tensor(chi).pin_memory()
     h_J = torch.tensor(J).pin_memory()
-    h_q = torch.empty(st.n, dtype=torch.float64).pin_memory()
+    h_q = torch.empty(n_atoms, dtype=torch.float64).pin_memory()
     n_e2e = max(1, min(5, args.steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -317,32 +369,40 @@ def run_ours(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / n_e2e
     h2d = int(pos.nbytes + spc.nbytes + chi.nbytes + J.nbytes)
-    d2h = int(st.n * 8)
-    dq_plain = float((q_out - q_plain).abs().max().item())
+    d2h = int(n_atoms * 8)
 
     if rank != 0:
         return 0
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        t_mv, cores, reps = cpu_oracle_matvec_time(st)
-        v = 1.0 / (t_mv * PCG_ITERS_REFERENCE)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": (f"FP64 Ewald matvec of the full {st.n}-atom cell by the CPU oracle (best of {reps}), "
-                          f"x {PCG_ITERS_REFERENCE} PCG iterations: extrapolated to one solve")}
-    value = world * 1000.0 / ms
+        if n_struct > 1:
+            v, cores, smp = cpu_oracle_dense_batch(structs)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp}
+        else:
+            t_mv, cores, reps = cpu_oracle_matvec_time(st)
+            v = 1.0 / (t_mv * PCG_ITERS_REFERENCE)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": (f"FP64 Ewald matvec of the full {st.n}-atom cell by the CPU oracle (best of {reps}), "
+                              f"x {PCG_ITERS_REFERENCE} PCG iterations: extrapolated to one solve")}
+    value = world * n_struct * 1000.0 / ms
     qi = plan.query(0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": st.n, "mesh": list(qi["mesh"]),
+        "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": n_atoms, "structures": n_struct,
+                   "mesh": list(qi["mesh"]) if n_struct == 1 else "per structure (autotuned)",
                    "spline_order": qi["spline_order"], "omega_A": round(qi["omega"], 4), "precision": args.precision,
                    "graph": True, "charge_tol_e": 1e-5, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "atoms_iters_per_s": world * st.n * it_mean / (ms * 1e-3),
+        "atoms_iters_per_s": world * atoms_iters / (ms * 1e-3),
         "pcg_iterations": it_mean, "status": status,
-        "plain_fp64": {"value": 1000.0 / plain_ms, "unit": UNIT, "ms_per_step": plain_ms, "iterations": plain_iters,
-                       "speedup_of_chosen": plain_ms / ms, "max_dq_vs_chosen_e": dq_plain},
+        "plain_fp64": {"value": n_struct * 1000.0 / plain_ms, "unit": UNIT, "ms_per_step": plain_ms,
+                       "iterations": float(np.mean(plain_iters)), "speedup_of_chosen": plain_ms / ms,
+                       "max_dq_vs_chosen_e": dq_plain,
+                       "sample": ("every structure" if n_struct == 1 else
+                                  f"{len(sample)} of {n_struct} structures (every 16th) solved one at a time, "
+                                  f"time scaled by {n_struct}/{len(sample)}")},
         "matvec": {"ms": matvec_ms, "algorithmic_bytes": matvec_bytes,
                    "GBps": matvec_bytes / (matvec_ms * 1e-3) / 1e9,
                    "frac_hbm": matvec_bytes / (matvec_ms * 1e-3) / 1e9 / hbm,
@@ -350,7 +410,7 @@ def run_ours(args):
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "algorithmic_bytes_per_launch": sb[dom], "launch_ms": prof[dom]},
-        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": world * n_struct / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -366,7 +426,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 5])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-cells", dest="cells", type=int, default=0,

@@ -78,7 +78,8 @@ typedef struct {
   const int64_t* atom_offsets;  /* h_, n_struct+1, CSR offsets into the packed atom arrays   */
   const double* cells;          /* h_, n_struct*9, rows a1 a2 a3 [A]                          */
   int32_t n_species;            /* species table width, 1..8                                 */
-  const double* sigma;          /* h_, n_struct*n_species Gaussian widths [A], > 0            */
+  const double* sigma;          /* h_, n_struct*n_species Gaussian widths [A], > 0; trailing  */
+                                /* entries <= 0 mark species absent from that structure     */
   double coulomb_k;             /* default 14.3996454784                                      */
   double charge_tol;            /* stop: max-abs projected residual <= 0.5*charge_tol*J_min;  */
                                 /* default 1e-5 e                                            */

@@ -153,6 +153,7 @@ double narrowest_width(const double* sig, int S, double omega) {
   double wmin = 1e300;
   for (int a = 0; a < S; ++a)
     for (int b = 0; b < S; ++b) {
+      if (!(sig[a] > 0.0) || !(sig[b] > 0.0)) continue;
       double g = sqrt(sig[a] * sig[a] + sig[b] * sig[b]);
       wmin = std::min(wmin, g < 0.999 * omega ? omega : g);
     }
@@ -377,14 +378,17 @@ static qeq_status build_plan(qeq_plan_s* P) {
     for (int d = 0; d < 3; ++d)
       for (int c = 0; c < 3; ++c) T.B[3 * d + c] = 2.0 * kPi * T.hinv[3 * c + d];
     T.green_pref = D.coulomb_k * 4.0 * kPi / V;
-    T.S = S;
-    T.ncm = (S + 1) / 2;
+    // species of this structure: the table width minus trailing entries with sigma <= 0
+    int Ss = S;
+    while (Ss > 1 && !(D.sigma[(size_t)S * s + Ss - 1] > 0.0)) --Ss;
+    T.S = Ss;
+    T.ncm = (Ss + 1) / 2;
     T.p = pbest;
     T.atom_begin = P->offsets[s];
     T.atom_end = P->offsets[s + 1];
     if (T.atom_end <= T.atom_begin) return fail(P, QEQ_ERR_INVALID, "structure without atoms");
     const double* sig = D.sigma + (size_t)S * s;
-    for (int a = 0; a < S; ++a)
+    for (int a = 0; a < Ss; ++a)
       if (!(sig[a] > 0.0) || !std::isfinite(sig[a])) return fail(P, QEQ_ERR_NOT_PD, "sigma must be finite and > 0");
     // --- Ewald split: omega from the real-space cutoff and the target accuracy
     double rc = D.r_cut;
@@ -393,8 +397,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
     T.omega = omega;
     double wmin = 1e300;
     int any = 0;
-    for (int a = 0; a < S; ++a) {
-      for (int b = 0; b < S; ++b) {
+    for (int a = 0; a < Ss; ++a) {
+      for (int b = 0; b < Ss; ++b) {
         double g = sqrt(sig[a] * sig[a] + sig[b] * sig[b]);
         bool narrow = g < 0.999 * omega;
         double w = narrow ? omega : g;

@@ -281,7 +281,7 @@ def plan_for_structures(structs, **kw) -> Plan:
     ns = max(s.n_species for s in structs)
     cells = np.stack([s.cell for s in structs]).reshape(-1, 9)
     offs = np.concatenate([[0], np.cumsum([s.n for s in structs])]).astype(np.int64)
-    sig = np.ones((len(structs), ns))
+    sig = np.zeros((len(structs), ns))          # trailing zeros: species absent from that structure
     for i, s in enumerate(structs):
         sig[i, :s.n_species] = s.sigma_s
     return Plan(cells, offs, sig, **kw)

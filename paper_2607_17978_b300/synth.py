@@ -123,50 +123,51 @@ def rocksalt(n_cells, a: float, jitter: float, rng: np.random.Generator, *,
     return Structure(cell, pos, species.astype(np.int32), chi, J, np.asarray(sigma_s, np.float64), float(q_tot))
 
 
+def _place_with_min_distance(n: int, cell: np.ndarray, min_dist: float, rng: np.random.Generator) -> np.ndarray:
+    """Uniform random fractional positions, redrawing one atom of every pair closer than
+    min_dist (periodic images included) until none is left."""
+    from scipy.spatial import cKDTree
+    u = rng.random((n, 3))
+    V = abs(np.linalg.det(cell))
+    wd = np.array([V / np.linalg.norm(np.cross(cell[(d + 1) % 3], cell[(d + 2) % 3])) for d in range(3)])
+    delta = min_dist / wd                      # fractional distance to a face that matters
+    shifts = np.stack(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing="ij"), -1).reshape(-1, 3)
+    shifts = shifts[np.any(shifts != 0, axis=1)]
+    for _ in range(1000):
+        # the cell plus the periodic images of atoms near the faces they are shifted across
+        ids, pts = [np.arange(n)], [u]
+        for sh in shifts:
+            m = np.ones(n, bool)
+            for d in range(3):
+                if sh[d] == 1:
+                    m &= u[:, d] < delta[d]
+                elif sh[d] == -1:
+                    m &= u[:, d] > 1.0 - delta[d]
+            if m.any():
+                ids.append(np.nonzero(m)[0])
+                pts.append(u[m] + sh)
+        ids = np.concatenate(ids)
+        X = np.concatenate(pts) @ cell
+        pairs = cKDTree(X).query_pairs(min_dist, output_type="ndarray")
+        if len(pairs):
+            pairs = pairs[(pairs[:, 0] < n) | (pairs[:, 1] < n)]
+        if not len(pairs):
+            return u
+        idx = np.unique(np.maximum(ids[pairs[:, 0]], ids[pairs[:, 1]]))
+        u[idx] = rng.random((len(idx), 3))
+    raise RuntimeError("random placement with minimum distance failed")
+
+
 def random_ionic(n_atoms: int, rng: np.random.Generator, *, density: float = 0.045,
                  min_dist: float = 1.5, triclinic: bool = False, max_tilt_deg: float = 20.0,
                  n_species: int = 2, chi_std_atom: float = 0.3) -> Structure:
-    """Random cell at ``density`` atoms/A^3 with random sequential placement."""
+    """Random cell at ``density`` atoms/A^3, atoms at least ``min_dist`` apart."""
     V = n_atoms / density
     ratios = rng.uniform(0.75, 1.33, size=3)
     ratios = ratios / np.prod(ratios) ** (1.0 / 3.0)
     lengths = ratios * V ** (1.0 / 3.0)
     cell = sheared_cell(lengths, max_tilt_deg if triclinic else 0.0, rng)
-    # random sequential placement in fractional coordinates, checked with minimum-image distances
-    hinv = np.linalg.inv(cell)
-    frac = np.empty((n_atoms, 3))
-    placed = 0
-    ng = np.maximum(1, np.floor(lengths / 3.0).astype(int))
-    grid: dict = {}
-    tries = 0
-    while placed < n_atoms:
-        tries += 1
-        if tries > 200 * n_atoms:
-            raise RuntimeError("random sequential placement failed")
-        u = rng.random(3)
-        c = tuple((u * ng).astype(int) % ng)
-        ok = True
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dz in (-1, 0, 1):
-                    cc = ((c[0] + dx) % ng[0], (c[1] + dy) % ng[1], (c[2] + dz) % ng[2])
-                    for k in grid.get(cc, ()):
-                        d = u - frac[k]
-                        d -= np.round(d)
-                        if np.linalg.norm(d @ cell) < min_dist:
-                            ok = False
-                            break
-                    if not ok:
-                        break
-                if not ok:
-                    break
-            if not ok:
-                break
-        if ok:
-            frac[placed] = u
-            grid.setdefault(c, []).append(placed)
-            placed += 1
-    del hinv
+    frac = _place_with_min_distance(n_atoms, cell, min_dist, rng)
     species = rng.integers(0, n_species, size=n_atoms).astype(np.int32)
     chi_s = rng.normal(0.0, 1.5, size=n_species)
     J_s = rng.uniform(1.0, 3.0, size=n_species)

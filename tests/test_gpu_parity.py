@@ -181,3 +181,23 @@ def test_iteration_cap_reports_noconv():
     plan = _plan([st], max_iter=2)
     res = plan.solve(*qeq.pack([st]), raise_on_noconv=False)
     assert res.info[0]["status"] == qeq.QEQ_ERR_NOCONV
+
+
+def test_config4_batch_subset_against_dense_oracle():
+    """Uneven training-set batch (config-4 recipe, sizes capped for the dense oracle), one batched solve."""
+    from paper_2607_17978_b300 import qeq
+    structs = synth.batch_workload(20, n_min=64, n_max=1024)
+    for precision in ("mixed", "fp64"):
+        plan = _plan(structs, precision=precision)
+        pos, spc, chi, J, qt = qeq.pack(structs)
+        res = plan.solve(pos, spc, chi, J, qt)
+        qg = res.q.cpu().numpy()
+        mu = res.mu.cpu().numpy()
+        off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+        for i, st in enumerate(structs):
+            _, q, mu_ref, _, _ = _oracle(st)
+            assert np.abs(qg[off[i]:off[i + 1]] - q).max() < 1e-5, (precision, i)
+            assert abs(qg[off[i]:off[i + 1]].sum() - st.q_tot) < 1e-9
+            assert abs(mu[i] - mu_ref) < 1e-4
+            assert res.info[i]["status"] == 0
+        plan.close()
