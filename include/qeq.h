@@ -144,8 +144,8 @@ qeq_status qeq_plan_query(qeq_plan plan, int32_t s, qeq_plan_info* out);
  *   d_J        N hardnesses [eV/e^2], all > 0 (else QEQ_ERR_NOT_PD)
  *   h_qtot     n_struct total charges [e]
  *   warm       QEQ_WARM_COLD: start from q_tot/N; QEQ_WARM_USER: start from
- *              d_q (projected onto the constraint); QEQ_WARM_MLP: reserved
- *              (currently treated as cold)
+ *              d_q (projected onto the constraint); QEQ_WARM_MLP: start from
+ *              the network attached with qeq_plan_set_warm_start (projected)
  *   d_q        N charges [e]: input for QEQ_WARM_USER, output always
  *   d_mu       n_struct Lagrange multipliers mu with (A + J) q + chi = mu 1
  *              (the bordered lambda of eq. 4G_qeq_prime is -mu); may be NULL
@@ -177,6 +177,65 @@ qeq_status qeq_matvec(qeq_plan plan, const double* d_pos, const int32_t* d_speci
  * inverse FFT z, gather + real space + local terms. */
 #define QEQ_N_STAGES 8
 qeq_status qeq_profile_matvec(qeq_plan plan, int32_t n_rep, float* h_ms);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (the paper's atomic neural networks, SI "Feed-Forward
+ * Neural Networks", applied here to predict starting charges for the solve).
+ *
+ * Descriptors of atom i (radial functions of Sec. 2.2 eq. g2 with the cosine
+ * cutoff of SI "Cutoff Functions", cutoff QEQ_MLP_RCUT; the element-embracing
+ * prefactor of SI "Element-Embracing ACSFs" with H_ij = chi_j), float32 x 32:
+ *   [0..11]  sum_j exp(-2 (r_ij - R_mu)^2) f_c(r_ij),  R_mu = 0.5 + 0.5 mu A
+ *   [12..23] the same weighted by chi_j
+ *   [24..26] chi_i, J_i, sigma_i ; [27..31] zero
+ * Network per species: 32 -> 64 -> 64 -> 1, tanh, tanh, linear, evaluated on
+ * BF16 tensor cores with FP32 accumulation; inputs scaled per species as
+ * (G - mean) * inv_range (SI "Feature Scaling").
+ * Parameter block of one species (float32, QEQ_MLP_NPARAM entries):
+ *   W1[64][32], b1[64], W2[64][64], b2[64], W3[64], b3, then padding.
+ * Scaling block of one species: mean[32], inv_range[32].
+ * Training minimises 1/(2n) sum (y_i - target_i)^2 with Adam (beta 0.9/0.999,
+ * eps 1e-8, SI "Adam") on FP32 master weights. */
+#define QEQ_MLP_NFEAT 32
+#define QEQ_MLP_NHIDDEN 64
+#define QEQ_MLP_NPARAM 6400
+#define QEQ_MLP_RCUT 6.0f
+typedef struct qeq_mlp_s* qeq_mlp;
+
+/* Network for n_species species, zero-initialised (set parameters with
+ * qeq_mlp_set_params), training batches of at most max_batch atoms; device
+ * memory on the current device. */
+qeq_status qeq_mlp_create(int32_t n_species, int64_t max_batch, qeq_mlp* out);
+void qeq_mlp_destroy(qeq_mlp mlp);
+/* h_params: n_species * QEQ_MLP_NPARAM floats (NULL = keep), h_scale:
+ * n_species * 2 * QEQ_MLP_NFEAT floats (NULL = keep); new parameters reset Adam. */
+qeq_status qeq_mlp_set_params(qeq_mlp mlp, const float* h_params, const float* h_scale);
+/* Copies out parameters, scaling, Adam moments and step count (any may be NULL). */
+qeq_status qeq_mlp_get_params(qeq_mlp mlp, float* h_params, float* h_scale, float* h_adam_m, float* h_adam_v,
+                              int64_t* h_step);
+/* Restores Adam moments and step count (checkpoint resume). */
+qeq_status qeq_mlp_set_adam_state(qeq_mlp mlp, const float* h_adam_m, const float* h_adam_v, int64_t step);
+/* d_out[i] = network output for atom i (d_feat n x 32 unscaled descriptors). */
+qeq_status qeq_mlp_forward(qeq_mlp mlp, const float* d_feat, const int32_t* d_species, int64_t n, float* d_out,
+                           void* cuda_stream);
+/* One training step on a batch of n <= max_batch atoms: forward, backward, and,
+ * when apply_update, an Adam update with learning rate lr.  d_grad_out (may be
+ * NULL): the batch gradient, n_species * QEQ_MLP_NPARAM floats; h_loss (may be
+ * NULL): the batch loss.  Gradients are summed per 64-atom tile and then over
+ * tiles in a fixed order (deterministic). */
+qeq_status qeq_mlp_train_step(qeq_mlp mlp, const float* d_feat, const int32_t* d_species, const float* d_target,
+                              int64_t n, float lr, int32_t apply_update, float* d_grad_out, float* h_loss,
+                              void* cuda_stream);
+/* Descriptors (n_atoms x 32, the caller's atom order) of the plan's cells. */
+qeq_status qeq_features(qeq_plan plan, const double* d_pos, const int32_t* d_species, const double* d_chi,
+                        const double* d_J, float* d_feat);
+/* Attach a network for QEQ_WARM_MLP solves (NULL detaches; the plan does not
+ * own it).  The plan's first QEQ_WARM_MLP solve needs this call first; it
+ * allocates the descriptor buffers.  In the solve the network's charges are
+ * projected onto the charge constraint; if their projected residual exceeds
+ * that of the uniform start, or is not finite, the solve restarts cold and
+ * reports warm_used = 0. */
+qeq_status qeq_plan_set_warm_start(qeq_plan plan, qeq_mlp mlp);
 
 /* ------------------------------------------------------------------------
  * qeq_matvec_static -- the FP64 matvec of qeq_matvec for ONE small cell,

@@ -215,6 +215,8 @@ static void free_plan(qeq_plan_s* P) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
+  if (P->d_feat) cudaFree(P->d_feat);
+  if (P->d_pred) cudaFree(P->d_pred);
   if (P->ev_done) cudaEventDestroy(P->ev_done);
   if (P->graph_iter) cudaGraphExecDestroy(P->graph_iter);
 }
@@ -421,6 +423,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
       double g = sqrt(2.0) * sig[a];
       double w = (g < 0.999 * omega) ? omega : g;
       T.self_s[a] = D.coulomb_k * sqrt(2.0 / kPi) * (1.0 / g - 1.0 / w);
+      T.sigma_s[a] = sig[a];
       T.diag_s[a] = D.coulomb_k / (sig[a] * sqrt(kPi));
     }
     T.any_narrow = any;
@@ -441,6 +444,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
       double l = rc / wd[d] * K / QEQ_BIN;
       int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
       T.rs_range[d] = std::max(1, R);
+      double lf = QEQ_MLP_RCUT / wd[d] * K / QEQ_BIN;
+      T.feat_range[d] = std::max(1, (int)ceil(lf + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0));
     }
     T.M = (int64_t)T.K[0] * T.K[1] * T.K[2];
     T.mesh_off = mesh_off;

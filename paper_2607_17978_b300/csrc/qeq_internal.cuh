@@ -50,6 +50,9 @@ struct StructDev {
   double self_s[QEQ_MAX_SPECIES];                   // k_e sqrt(2/pi)(1/gamma_ss - 1/w_ss)
   double diag_s[QEQ_MAX_SPECIES];                   // k_e/(sigma_s sqrt pi): Jacobi diagonal part
   uint32_t narrow[QEQ_MAX_SPECIES];                 // bit t set: pair (s,t) has a real-space term
+  double sigma_s[QEQ_MAX_SPECIES];                  // Gaussian width per species
+  int feat_range[3];                                // bins searched for descriptor neighbours
+  int pad3_;
 };
 
 // Division by a runtime-invariant divisor d with a multiply and a shift
@@ -237,6 +240,9 @@ inline int fft_tile_lines(int maxK) {
   int* d_done = nullptr;           // all-structures-inactive flag
   int* h_done = nullptr;           // pinned mirror
   cudaEvent_t ev_done = nullptr;
+  struct qeq_mlp_s* mlp = nullptr; // warm-start network (not owned)
+  float* d_feat = nullptr;         // descriptors, sorted order
+  float* d_pred = nullptr;         // network output, sorted order
   int64_t launches = 0;            // kernels launched by this plan (graph replays count their kernels)
   int64_t graph_kernels = 0;       // kernels inside the captured iteration graph
   bool capturing = false;
@@ -306,6 +312,8 @@ cudaError_t launch_prepare_atoms(qeq_plan_s* P, const double* pos, const int32_t
 cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, int with_J,
                           int use_active, int fuse_pAp, cudaEvent_t* ev /* QEQ_N_STAGES+1 or NULL */);
 cudaError_t matvec_set_attributes();
+// launchers (mlp.cu)
+cudaError_t launch_mlp_warm_start(qeq_plan_s* P, double* d_q_sorted);
 
 // Deterministic block-wide sum of part[(first + i) * stride + k], i < count:
 // thread t adds the entries i = t, t + blockDim, ... in order, then thread 0

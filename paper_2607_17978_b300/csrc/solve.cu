@@ -99,7 +99,7 @@ __global__ void k_init(const Chunk* __restrict__ chunks, const int* __restrict__
   double v[6] = {0, 0, 0, 0, 1e300, 0};
   const int op[6] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM, RED_MIN, RED_SUM};
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
-    double qa = (warm == QEQ_WARM_USER) ? q_user[perm[a]] : 0.0;
+    double qa = (warm == QEQ_WARM_USER) ? q_user[perm[a]] : (warm == QEQ_WARM_MLP ? q[a] : 0.0);
     if (!isfinite(qa)) qa = 0.0;
     q[a] = qa;
     v[0] += qa;
@@ -458,22 +458,47 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
   const int prec = P->precision;
   const int max_iter = P->desc.max_iter;
   int wm = (warm == QEQ_WARM_USER) ? QEQ_WARM_USER : QEQ_WARM_COLD;
-  count_launch(P);
-  k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q, wm, P->d_dinv, P->d_chi, P->d_J, P->d_q, P->d_sc,
-                            red_part(P), red_counter(P));
-  count_launch(P);
-  k_project<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_sc);
-  count_launch(P);
-  k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol);
-  TRY(cudaGetLastError());
-  // first residual with the iteration's matvec
-  TRY(launch_matvec(P, prec, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
-  count_launch(P);
-  k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
-                             red_counter(P), max_iter);
-  count_launch(P);
+  if (warm == QEQ_WARM_MLP) {
+    if (!P->mlp) {
+      P->last_error = "QEQ_WARM_MLP needs a network attached with qeq_plan_set_warm_start";
+      return QEQ_ERR_INVALID;
+    }
+    TRY(launch_mlp_warm_start(P, P->d_q));
+    wm = QEQ_WARM_MLP;
+  }
+  int warm_kept = (wm != QEQ_WARM_COLD) ? 1 : 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    count_launch(P, 3);
+    k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q, wm, P->d_dinv, P->d_chi, P->d_J, P->d_q, P->d_sc,
+                              red_part(P), red_counter(P));
+    k_project<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_sc);
+    k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol);
+    TRY(cudaGetLastError());
+    // first residual with the iteration's matvec
+    TRY(launch_matvec(P, prec, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
+    count_launch(P);
+    k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
+                               red_counter(P), max_iter);
+    TRY(cudaGetLastError());
+    if (wm != QEQ_WARM_MLP) break;
+    // the plain method judges the network's start: a projected residual larger than that
+    // of the uniform start (||P chi||_2 for q_tot = 0), or a non-finite one, means a cold restart
+    std::vector<PcgScalars> h(ns);
+    TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    bool bad = false;
+    for (int i = 0; i < ns; ++i) {
+      double n = (double)h[i].n, mean = h[i].r_sum / n;
+      double pl2 = sqrt(fmax(h[i].r_sq - h[i].r_sum * mean, 0.0));
+      if (!std::isfinite(pl2) || pl2 > sqrt(h[i].chi_p2) + fabs(h[i].q_tot) * 1e3) bad = true;
+    }
+    if (!bad) break;
+    wm = QEQ_WARM_COLD;
+    warm_kept = 0;
+    TRY(init_scalars(P, h_qtot) == QEQ_OK ? cudaSuccess : cudaErrorUnknown);
+  }
+  count_launch(P, 2);
   k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 1, red_part(P), red_counter(P));
-  count_launch(P);
   k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
   TRY(cudaGetLastError());
   const int max_restarts = 4;
@@ -523,7 +548,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
       h_info[i].status = c.status;
       h_info[i].iterations = c.iters;
       h_info[i].restarts = c.restarts;
-      h_info[i].warm_used = (wm == QEQ_WARM_USER) ? 1 : 0;
+      h_info[i].warm_used = warm_kept;
       h_info[i].residual_inf = pinf;
       h_info[i].residual_l2 = pl2;
       h_info[i].error_bound_l2 = pl2 / c.j_min;

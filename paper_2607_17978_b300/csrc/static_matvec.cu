@@ -240,6 +240,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     double g = sqrt(2.0) * h_sigma[a];
     double w = (g < 0.999 * omega) ? omega : g;
     T.self_s[a] = coulomb_k * sqrt(2.0 / kPiS) * (1.0 / g - 1.0 / w);
+    T.sigma_s[a] = h_sigma[a];
     T.diag_s[a] = coulomb_k / (h_sigma[a] * sqrt(kPiS));
   }
   T.any_narrow = any;

@@ -26,7 +26,10 @@ QEQ_N_STAGES = 8
 STAGE_NAMES = ["species_sums", "spread", "fft_z", "fft_y", "fft_x_green", "ifft_y", "ifft_z", "gather"]
 
 EXPORTED = ["qeq_plan_create", "qeq_plan_destroy", "qeq_plan_query", "qeq_solve", "qeq_energy", "qeq_matvec",
-            "qeq_profile_matvec", "qeq_status_str", "qeq_last_error", "qeq_matvec_static"]
+            "qeq_profile_matvec", "qeq_status_str", "qeq_last_error", "qeq_matvec_static", "qeq_mlp_create",
+            "qeq_mlp_destroy", "qeq_mlp_set_params", "qeq_mlp_get_params", "qeq_mlp_set_adam_state",
+            "qeq_mlp_forward", "qeq_mlp_train_step", "qeq_features", "qeq_plan_set_warm_start"]
+MLP_NFEAT, MLP_NHIDDEN, MLP_NPARAM, MLP_RCUT = 32, 64, 6400, 6.0
 
 
 class PlanDesc(ctypes.Structure):
@@ -110,6 +113,25 @@ def load_library(path: str = LIB_PATH):
     lib.qeq_matvec_static.argtypes = [dp, dp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, vp]
     lib.qeq_matvec_static.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.qeq_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(vp)]
+    lib.qeq_mlp_create.restype = ctypes.c_int
+    lib.qeq_mlp_destroy.argtypes = [vp]
+    lib.qeq_mlp_destroy.restype = None
+    lib.qeq_mlp_set_params.argtypes = [vp, fp, fp]
+    lib.qeq_mlp_set_params.restype = ctypes.c_int
+    lib.qeq_mlp_get_params.argtypes = [vp, fp, fp, fp, fp, ctypes.POINTER(ctypes.c_int64)]
+    lib.qeq_mlp_get_params.restype = ctypes.c_int
+    lib.qeq_mlp_set_adam_state.argtypes = [vp, fp, fp, ctypes.c_int64]
+    lib.qeq_mlp_set_adam_state.restype = ctypes.c_int
+    lib.qeq_mlp_forward.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    lib.qeq_mlp_forward.restype = ctypes.c_int
+    lib.qeq_mlp_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, vp, fp, vp]
+    lib.qeq_mlp_train_step.restype = ctypes.c_int
+    lib.qeq_features.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.qeq_features.restype = ctypes.c_int
+    lib.qeq_plan_set_warm_start.argtypes = [vp, vp]
+    lib.qeq_plan_set_warm_start.restype = ctypes.c_int
     del ip
     if path == LIB_PATH:
         _lib = lib
@@ -198,7 +220,25 @@ class Plan:
     def _sync_in(self):
         self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
 
-    def solve(self, pos, species, chi, J, q_tot=None, q0=None, raise_on_noconv=True, out=None):
+    def features(self, pos, species, chi, J):
+        """Descriptors (n_atoms x 32 float32, the caller's atom order)."""
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        chi = self._dev(chi, torch.float64)
+        J = self._dev(J, torch.float64)
+        f = torch.empty(self.n_atoms, MLP_NFEAT, dtype=torch.float32, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_features(self.h, _ptr(pos), _ptr(species), _ptr(chi), _ptr(J), _ptr(f)),
+                    "qeq_features")
+        return f
+
+    def set_warm_start(self, mlp):
+        self._mlp = mlp
+        self._check(self.lib.qeq_plan_set_warm_start(self.h, mlp.h if mlp is not None else None),
+                    "qeq_plan_set_warm_start")
+
+    def solve(self, pos, species, chi, J, q_tot=None, q0=None, raise_on_noconv=True, out=None, warm=None):
         torch = self.torch
         pos = self._dev(pos, torch.float64).reshape(-1, 3)
         species = self._dev(species, torch.int32)
@@ -207,11 +247,14 @@ class Plan:
         if q_tot is None:
             q_tot = np.zeros(self.n_struct)
         qt = np.ascontiguousarray(np.broadcast_to(np.asarray(q_tot, np.float64), (self.n_struct,)))
-        warm = QEQ_WARM_COLD
         q = out if out is not None else torch.empty(self.n_atoms, dtype=torch.float64, device=self.device)
-        if q0 is not None:
+        if warm == "mlp":
+            warm = QEQ_WARM_MLP
+        elif q0 is not None:
             q.copy_(self._dev(q0, torch.float64))
             warm = QEQ_WARM_USER
+        else:
+            warm = QEQ_WARM_COLD
         mu = torch.empty(self.n_struct, dtype=torch.float64, device=self.device)
         info = (Info * self.n_struct)()
         self._sync_in()
@@ -252,6 +295,93 @@ class Plan:
         ms = (ctypes.c_float * QEQ_N_STAGES)()
         self._check(self.lib.qeq_profile_matvec(self.h, n_rep, ms), "qeq_profile_matvec")
         return dict(zip(STAGE_NAMES, [float(v) for v in ms]))
+
+
+class Mlp:
+    """Warm-start network (qeq_mlp): per-species 32 -> 64 -> 64 -> 1 on the GPU."""
+
+    def __init__(self, n_species, max_batch=65536, device=None):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda")
+        self.n_species = int(n_species)
+        self.max_batch = int(max_batch)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(device=self.device)
+            st = self.lib.qeq_mlp_create(self.n_species, self.max_batch, ctypes.byref(h))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_mlp_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qeq_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f(self, a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if a is not None else None
+
+    def set_params(self, params=None, scale=None):
+        p = None if params is None else np.ascontiguousarray(params, np.float32).reshape(-1)
+        sc = None if scale is None else np.ascontiguousarray(scale, np.float32).reshape(-1)
+        if p is not None and p.size != self.n_species * MLP_NPARAM:
+            raise ValueError("params size")
+        if sc is not None and sc.size != self.n_species * 2 * MLP_NFEAT:
+            raise ValueError("scale size")
+        st = self.lib.qeq_mlp_set_params(self.h, self._f(p), self._f(sc))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_mlp_set_params")
+
+    def get_state(self):
+        npar = self.n_species * MLP_NPARAM
+        p = np.zeros(npar, np.float32)
+        sc = np.zeros(self.n_species * 2 * MLP_NFEAT, np.float32)
+        m = np.zeros(npar, np.float32)
+        v = np.zeros(npar, np.float32)
+        step = ctypes.c_int64(0)
+        st = self.lib.qeq_mlp_get_params(self.h, self._f(p), self._f(sc), self._f(m), self._f(v), ctypes.byref(step))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_mlp_get_params")
+        return {"params": p, "scale": sc, "adam_m": m, "adam_v": v, "step": int(step.value)}
+
+    def set_adam_state(self, m, v, step):
+        m = np.ascontiguousarray(m, np.float32)
+        v = np.ascontiguousarray(v, np.float32)
+        st = self.lib.qeq_mlp_set_adam_state(self.h, self._f(m), self._f(v), int(step))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_mlp_set_adam_state")
+
+    def forward(self, feat, species):
+        torch = self.torch
+        feat = torch.as_tensor(feat, dtype=torch.float32, device=self.device).contiguous()
+        species = torch.as_tensor(species, dtype=torch.int32, device=self.device).contiguous()
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        st = self.lib.qeq_mlp_forward(self.h, _ptr(feat), _ptr(species), feat.shape[0], _ptr(out),
+                                      ctypes.c_void_p(self.stream.cuda_stream))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_mlp_forward")
+        return out
+
+    def train_step(self, feat, species, target, lr=1e-3, apply=True, want_grad=False):
+        torch = self.torch
+        grad = torch.empty(self.n_species * MLP_NPARAM, dtype=torch.float32, device=self.device) if want_grad else None
+        loss = ctypes.c_float(0.0)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        st = self.lib.qeq_mlp_train_step(self.h, _ptr(feat), _ptr(species), _ptr(target), feat.shape[0], float(lr),
+                                         1 if apply else 0, _ptr(grad), ctypes.byref(loss),
+                                         ctypes.c_void_p(self.stream.cuda_stream))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_mlp_train_step")
+        return float(loss.value), grad
 
 
 def matvec_static(cell, sigma_s, pos, species, x, J=None, *, coulomb_k=14.3996454784, ewald_tol=1e-6,

@@ -1,0 +1,135 @@
+"""GPU warm start: descriptors, BF16 tensor-core network and its training against the CPU oracle,
+and what the trained network gains over the cold start."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from oracle import qeq_oracle as O
+from paper_2607_17978_b300 import synth
+
+pytestmark = pytest.mark.gpu
+KE = synth.COULOMB_K_EV_A
+
+
+def _structs():
+    return [synth.rocksalt(2, 5.64, 0.2, synth.rng_for(50, 0), vacancy_frac=0.05, shear_deg=10.0),
+            synth.batch_workload(1, cfg_id=51, n_min=150, n_max=300, first=1)[0]]
+
+
+def test_features_match_oracle():
+    import torch
+    from paper_2607_17978_b300 import build, qeq
+    build.build()
+    structs = _structs()
+    plan = qeq.plan_for_structures(structs)
+    pos, spc, chi, J, qt = qeq.pack(structs)
+    f = plan.features(pos, spc, chi, J).cpu().numpy()
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+    for i, st in enumerate(structs):
+        ref = M.features(st.cell, st.pos, st.species, st.chi, st.J, st.sigma_s)
+        got = f[off[i]:off[i + 1]]
+        assert np.abs(got - ref).max() < 2e-5 * max(1.0, np.abs(ref).max())
+
+
+def _random_net(n_species, seed, feat, species):
+    rng = np.random.default_rng(seed)
+    params = M.xavier(n_species, rng)
+    for s in range(n_species):
+        params[s, M.P_B1:M.P_W2] = rng.normal(size=M.NH) * 0.2
+        params[s, M.P_B2:M.P_W3] = rng.normal(size=M.NH) * 0.2
+        params[s, M.P_B3] = 0.1
+    scale = M.scale_from_features(feat, species, n_species)
+    return params, scale
+
+
+def _bf16_net(params, scale, feat):
+    """CPU inputs as the GPU sees them: BF16 weights (biases FP32) and BF16 scaled features."""
+    pr = params.copy()
+    for s in range(len(pr)):
+        pr[s, M.P_W1:M.P_B1] = M.bf16_round(pr[s, M.P_W1:M.P_B1])
+        pr[s, M.P_W2:M.P_B2] = M.bf16_round(pr[s, M.P_W2:M.P_B2])
+    return pr
+
+
+def test_forward_and_gradient_match_oracle():
+    import torch
+    from paper_2607_17978_b300 import qeq
+    rng = np.random.default_rng(3)
+    n, S = 300, 2
+    feat = rng.normal(size=(n, M.NF)) * 2 + 1
+    feat[:, 27:] = 0
+    sp = rng.integers(0, S, n)
+    tgt = rng.normal(size=n) * 0.5
+    params, scale = _random_net(S, 4, feat, sp)
+    mlp = qeq.Mlp(S, max_batch=1024)
+    mlp.set_params(params.astype(np.float32), scale.astype(np.float32))
+    dev = torch.device("cuda")
+    f_t = torch.tensor(feat, dtype=torch.float32, device=dev)
+    s_t = torch.tensor(sp, dtype=torch.int32, device=dev)
+    t_t = torch.tensor(tgt, dtype=torch.float32, device=dev)
+    y = mlp.forward(f_t, s_t).cpu().numpy()
+    # CPU oracle on the GPU's BF16-rounded weights and inputs
+    p32 = params.astype(np.float32).astype(np.float64)
+    pr = _bf16_net(p32, scale, feat)
+    # scaled inputs rounded to BF16: fold the rounding into features with identity scaling
+    Xs = np.zeros_like(feat)
+    for s in range(S):
+        m = sp == s
+        Xs[m] = M.bf16_round((feat[m].astype(np.float32) - scale[s, 0].astype(np.float32)) * scale[s, 1].astype(np.float32))
+    ident = np.zeros_like(scale)
+    ident[:, 1] = 1.0
+    y_ref, _ = M.forward(Xs, sp, pr, ident)
+    assert np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref) < 2e-2
+    loss, g = mlp.train_step(f_t, s_t, t_t, apply=False, want_grad=True)
+    L_ref, g_ref = M.loss_and_grad(Xs, sp, tgt, pr, ident)
+    g = g.cpu().numpy().reshape(S, -1)
+    assert abs(loss - L_ref) < 2e-2 * L_ref
+    for s in range(S):
+        rel = np.linalg.norm(g[s] - g_ref[s]) / np.linalg.norm(g_ref[s])
+        assert rel < 1e-2, (s, rel)
+    # one Adam step equals the CPU update applied to the GPU's gradient
+    before = mlp.get_state()["params"].reshape(S, -1).astype(np.float64)
+    mlp.train_step(f_t, s_t, t_t, lr=1e-3, apply=True, want_grad=False)
+    after = mlp.get_state()["params"].reshape(S, -1).astype(np.float64)
+    exp, _, _ = M.adam_step(before, g.astype(np.float64), 0 * before, 0 * before, 1, 1e-3)
+    assert np.abs(after - exp).max() < 1e-6
+    mlp.close()
+
+
+def test_warm_start_gain_and_fallback():
+    import torch
+    from paper_2607_17978_b300 import qeq, warmstart
+    train_structs = synth.training_structures(240, cfg_id=6, n_min=64, n_max=600)
+    feat, spc, tgt, it_cold_train = warmstart.solve_targets(train_structs)
+    mlp = qeq.Mlp(2, max_batch=4096)
+    mlp.set_params(warmstart.xavier_params(2, 0), warmstart.fit_scale(feat, spc, 2))
+    losses = warmstart.train(mlp, feat, spc, tgt, epochs=40, batch=2048, lr=3e-3)
+    assert losses[-1] < 0.2 * losses[0]
+    held = synth.training_structures(6, cfg_id=6, first=100000, n_min=200, n_max=600)
+    plan = qeq.plan_for_structures(held)
+    pos, sp, chi, J, qt = qeq.pack(held)
+    cold = plan.solve(pos, sp, chi, J, qt)
+    plan.set_warm_start(mlp)
+    warm = plan.solve(pos, sp, chi, J, qt, warm="mlp")
+    ic = np.array([i["iterations"] for i in cold.info])
+    iw = np.array([i["iterations"] for i in warm.info])
+    assert all(i["warm_used"] == 1 for i in warm.info)
+    assert iw.mean() < ic.mean(), (iw, ic)
+    qc, qw = cold.q.cpu().numpy(), warm.q.cpu().numpy()
+    assert np.abs(qc - qw).max() < 1e-5
+    st = held[0]
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=KE)
+    q_ref, _ = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+    assert np.abs(qw[:st.n] - q_ref).max() < 1e-5
+    # a network that predicts nonsense per atom (a constant offset would be removed by the
+    # projection): the solve falls back to the cold start and still converges
+    bad = mlp.get_state()
+    p = bad["params"].reshape(2, -1).copy()
+    w3 = qeq.MLP_NHIDDEN * qeq.MLP_NFEAT + qeq.MLP_NHIDDEN + qeq.MLP_NHIDDEN * qeq.MLP_NHIDDEN + qeq.MLP_NHIDDEN
+    p[:, w3:w3 + qeq.MLP_NHIDDEN] *= 1e4
+    mlp.set_params(p, bad["scale"])
+    fb = plan.solve(pos, sp, chi, J, qt, warm="mlp")
+    assert all(i["warm_used"] == 0 and i["status"] == 0 for i in fb.info)
+    assert np.abs(fb.q.cpu().numpy() - qc).max() < 1e-5
+    plan.close()
+    mlp.close()
