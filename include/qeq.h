@@ -232,9 +232,10 @@ qeq_status qeq_features(qeq_plan plan, const double* d_pos, const int32_t* d_spe
 /* Attach a network for QEQ_WARM_MLP solves (NULL detaches; the plan does not
  * own it).  The plan's first QEQ_WARM_MLP solve needs this call first; it
  * allocates the descriptor buffers.  In the solve the network's charges are
- * projected onto the charge constraint; if their projected residual exceeds
- * that of the uniform start, or is not finite, the solve restarts cold and
- * reports warm_used = 0. */
+ * projected onto the charge constraint and kept only if their QEq energy is
+ * below that of the uniform start q_tot/N (on the constraint plane
+ * E(q) - E(q*) = 1/2 ||q - q*||_A^2, the error norm CG reduces); otherwise, or
+ * if it is not finite, the solve restarts cold and reports warm_used = 0. */
 qeq_status qeq_plan_set_warm_start(qeq_plan plan, qeq_mlp mlp);
 
 /* ------------------------------------------------------------------------

@@ -100,6 +100,7 @@ struct PcgScalars {
   double j_min;
   double q_tot;
   double chi_p2;      // ||P chi||_2^2
+  double chi_sum;     // sum chi
   double E_lin, E_quad, E_J;  // chi.q, q.Aq, q.Jq
   double xsum[QEQ_MAX_SPECIES];       // per-species sums of the matvec input
   int active;         // 1 while iterating

@@ -115,6 +115,7 @@ __global__ void k_init(const Chunk* __restrict__ chunks, const int* __restrict__
     c.qsum = tot[0];
     c.s0 = tot[1];
     c.chi_p2 = fmax(tot[3] - tot[2] * tot[2] / n, 0.0);
+    c.chi_sum = tot[2];
     c.j_min = tot[4];
   }
 }
@@ -282,6 +283,37 @@ __global__ void k_energy(const Chunk* __restrict__ chunks, const double* __restr
     c.E_quad = tot[1];
     c.E_J = tot[2];
   }
+}
+
+// E(q) = chi.q + 1/2 q.A q with A q = -chi - r:  E = 1/2 chi.q - 1/2 q.r  (per structure, into E_lin)
+__global__ void k_start_energy(const Chunk* __restrict__ chunks, const double* __restrict__ q,
+                               const double* __restrict__ r, const double* __restrict__ chi,
+                               PcgScalars* __restrict__ sc, double* part, int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  double v[2] = {0, 0};
+  const int op[2] = {RED_SUM, RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    v[0] += chi[a] * q[a];
+    v[1] += q[a] * r[a];
+  }
+  double tot[2];
+  if (chunk_reduce<2>(v, op, ch, part, counter, tot)) sc[ch.s].E_lin = 0.5 * tot[0] - 0.5 * tot[1];
+}
+
+// per-structure sums of a vector (into E_quad): used for 1^T A 1 of the uniform start
+__global__ void k_vec_sum(const Chunk* __restrict__ chunks, const double* __restrict__ y, PcgScalars* __restrict__ sc,
+                          double* part, int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  double v[1] = {0};
+  const int op[1] = {RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) v[0] += y[a];
+  double tot[1];
+  if (chunk_reduce<1>(v, op, ch, part, counter, tot)) sc[ch.s].E_quad = tot[0];
+}
+
+__global__ void k_fill(double* __restrict__ x, int64_t n, double v) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) x[a] = v;
 }
 
 __global__ void k_unsort(const int* __restrict__ perm, int64_t n, const double* __restrict__ src, double* __restrict__ dst) {
@@ -481,16 +513,31 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
                                red_counter(P), max_iter);
     TRY(cudaGetLastError());
     if (wm != QEQ_WARM_MLP) break;
-    // the plain method judges the network's start: a projected residual larger than that
-    // of the uniform start (||P chi||_2 for q_tot = 0), or a non-finite one, means a cold restart
+    // The plain method judges the network's start by the quantity CG minimises: on the
+    // constraint plane E(q) - E(q*) = 1/2 ||q - q*||_A^2, so the start is kept iff its
+    // energy is below that of the uniform start q_tot/N (E = 0 when q_tot = 0; otherwise
+    // (q_tot/N) sum chi + 1/2 (q_tot/N)^2 1^T A 1, with one extra matvec of the ones vector).
+    count_launch(P);
+    k_start_energy<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_r, P->d_chi, P->d_sc, red_part(P), red_counter(P));
+    TRY(cudaGetLastError());
+    bool charged = false;
+    for (int i = 0; i < ns; ++i) charged |= (h_qtot[i] != 0.0);
+    if (charged) {
+      count_launch(P, 2);
+      k_fill<<<(int)((P->n_atoms + 255) / 256), 256, 0, s>>>(P->d_x, P->n_atoms, 1.0);
+      TRY(launch_matvec(P, prec, P->d_x, P->d_z, 1, 0, 0, nullptr));
+      k_vec_sum<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_sc, red_part(P), red_counter(P));
+      TRY(cudaGetLastError());
+    }
     std::vector<PcgScalars> h(ns);
     TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     bool bad = false;
     for (int i = 0; i < ns; ++i) {
-      double n = (double)h[i].n, mean = h[i].r_sum / n;
-      double pl2 = sqrt(fmax(h[i].r_sq - h[i].r_sum * mean, 0.0));
-      if (!std::isfinite(pl2) || pl2 > sqrt(h[i].chi_p2) + fabs(h[i].q_tot) * 1e3) bad = true;
+      double n = (double)h[i].n, qu = h_qtot[i] / n;
+      double e_cold = 0.0;
+      if (h_qtot[i] != 0.0) e_cold = qu * h[i].chi_sum + 0.5 * qu * qu * h[i].E_quad;
+      if (!std::isfinite(h[i].E_lin) || !(h[i].E_lin < e_cold)) bad = true;
     }
     if (!bad) break;
     wm = QEQ_WARM_COLD;
