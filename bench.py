@@ -268,7 +268,7 @@ def run_ours(args):
     d_spc = torch.tensor(spc, device=dev)
     d_chi = torch.tensor(chi, device=dev)
     d_J = torch.tensor(J, device=dev)
-    plan = qeq.plan_for_structures(structs, precision=args.precision, device=dev, **opts)
+    plan = qeq.plan_for_structures(structs, precision=args.precision, device=dev, preconditioner=args.precond, **opts)
     q_out = torch.empty(n_atoms, dtype=torch.float64, device=dev)
     # learned warm start for the rock-salt workloads (the network was trained on that recipe)
     warm = args.warm
@@ -417,7 +417,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": n_atoms, "structures": n_struct,
                    "mesh": list(qi["mesh"]) if n_struct == 1 else "per structure (autotuned)",
                    "spline_order": qi["spline_order"], "omega_A": round(qi["omega"], 4), "precision": args.precision,
-                   "graph": True, "warm_start": warm, "charge_tol_e": 1e-5, "l2": "flushed between timed steps (256 MB write)",
+                   "graph": True, "warm_start": warm, "preconditioner": args.precond, "charge_tol_e": 1e-5, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "atoms_iters_per_s": world * atoms_iters / (ms * 1e-3),
         "pcg_iterations": it_mean, "status": status,
@@ -455,6 +455,8 @@ def main():
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precond", default="fourier", choices=["fourier", "jacobi"],
+                    help="preconditioner of the chosen form (the plain FP64 leg always uses Jacobi)")
     ap.add_argument("--warm", default="auto", choices=["auto", "mlp", "cold"],
                     help="learned warm start (auto: on for the rock-salt workloads when the model file exists)")
     ap.add_argument("--profile-cells", dest="cells", type=int, default=0,

@@ -69,6 +69,18 @@ typedef enum {
 enum { QEQ_FP64 = 0, QEQ_MIXED = 1 };
 enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
 enum { QEQ_FLAG_NO_GRAPH = 1 };
+/* Preconditioners of the PCG.  JACOBI: D^-1, D_i = J_i + k_e/(sigma_i sqrt pi).
+ * FOURIER: D^-1 - D^-1 T^T F^-1[h F(T D^-1 r)], the Woodbury inverse of D plus the
+ * long-range Coulomb operator with the mesh operator T D^-1 T^T replaced by its
+ * translation-invariant mean (T: cubic B-spline spreading on a coarse FP32 mesh,
+ * h(m) = beta |b(m)|^2 g0 / (1 + s0 g0), g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2,
+ * s0 = sum_i 1/D_i).  beta < 1 keeps the preconditioner positive definite when the
+ * mean differs from the real operator by less than 1 - beta; smooth charge waves
+ * then have eigenvalues up to 1 + (1 - beta) x instead of 1 + x (x = g0 s0 grows
+ * with the cell size squared).  If r.z of a preconditioned residual is not positive
+ * the structure continues with Jacobi.  It changes no result, only the iteration
+ * count. */
+enum { QEQ_PRECOND_JACOBI = 0, QEQ_PRECOND_FOURIER = 1 };
 
 typedef struct qeq_plan_s* qeq_plan;
 
@@ -94,6 +106,10 @@ typedef struct {
   int32_t max_iter;             /* PCG iterations per structure; default 1000                 */
   double residual_tol;          /* optional extra stop: ||P r||_2 <= residual_tol*||P chi||_2 */
   int32_t flags;                /* QEQ_FLAG_*                                                 */
+  int32_t preconditioner;       /* QEQ_PRECOND_JACOBI (default) or QEQ_PRECOND_FOURIER        */
+  double precond_spacing;       /* FOURIER: coarse mesh spacing [A]; <= 0: 1.4                */
+  double precond_width;         /* FOURIER: Gaussian width w [A]; <= 0: 4.5                   */
+  double precond_scale;         /* FOURIER: safety factor beta on h, 0 < beta <= 1; <= 0: 0.98 */
 } qeq_plan_desc;
 
 /* Per-structure result of qeq_solve. */

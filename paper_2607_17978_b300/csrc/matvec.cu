@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(const StructDev* __restrict__ 
 // Works in place on layout L2 [z][y][x], where every x line is contiguous.
 // An item holds pairs of lines (z, y) and (-z, -y): the reciprocal multiply
 // needs Z(m) and Z(-m) of every complex mesh to separate its two species.
-template <typename T>
+template <typename T, bool PRE>
 __global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                               const int4* __restrict__ items, const int2* __restrict__ xpairs,
                               const T* __restrict__ bmod, const double2* __restrict__ tw64,
@@ -345,7 +345,16 @@ __global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict
     for (int c = 0; c < QEQ_MAX_SPECIES / 2; ++c) {
       if (c >= ncm) break;
       V p0 = {(T)0, (T)0}, p1 = {(T)0, (T)0};
-      if (pref != (T)0) {
+      if (PRE) {
+        // Fourier preconditioner: h(m) = |b(m)|^2 g0 / (1 + s0 g0), g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2
+        if (pref != (T)0) {
+          T e = exp(-G2 * (T)(0.5 * S.w2[0]));
+          T g0 = gpref * e / G2;
+          T hm = (T)S.omega * pref * e / ((T)1 + (T)sc[it.x].s0 * g0);  // S.omega holds beta
+          p0.x = hm * Qh[0].x;
+          p0.y = hm * Qh[0].y;
+        }
+      } else if (pref != (T)0) {
         for (int t = 0; t < S.S; ++t) {
           T g0 = pref * exp(-G2 * (T)(0.5 * S.w2[(2 * c) * QEQ_MAX_SPECIES + t]));
           p0.x += g0 * Qh[t].x;
@@ -676,6 +685,128 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
   }
 }
 
+// ------------------------------------------------------------------ Fourier preconditioner
+// Cubic B-spline (order 4) weights of every atom on its structure's coarse mesh,
+// once per solve: M_4(w + j), j = 0..3, for stencil points f - j.
+__global__ void k_pre_weights(const StructDev* __restrict__ stp, const int* __restrict__ sorted_struct,
+                              const double* __restrict__ posc, int64_t n, int* __restrict__ pbase,
+                              float* __restrict__ pw) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const StructDev& S = stp[sorted_struct[a]];
+  int f[3];
+  for (int d = 0; d < 3; ++d) {
+    double u = posc[3 * a] * S.hinv[d] + posc[3 * a + 1] * S.hinv[3 + d] + posc[3 * a + 2] * S.hinv[6 + d];
+    u -= floor(u);
+    double x = u * S.K[d];
+    int fi = (int)floor(x);
+    if (fi >= S.K[d]) fi = S.K[d] - 1;
+    if (fi < 0) fi = 0;
+    double w = x - fi;
+    f[d] = fi;
+    double w2 = w * w, w3 = w2 * w;
+    pw[a * 12 + d * 4 + 0] = (float)(w3 / 6.0);
+    pw[a * 12 + d * 4 + 1] = (float)((-3.0 * w3 + 3.0 * w2 + 3.0 * w + 1.0) / 6.0);
+    pw[a * 12 + d * 4 + 2] = (float)((3.0 * w3 - 6.0 * w2 + 4.0) / 6.0);
+    pw[a * 12 + d * 4 + 3] = (float)((1.0 - w) * (1.0 - w) * (1.0 - w) / 6.0);
+  }
+  pbase[a] = f[0] | (f[1] << 10) | (f[2] << 20);
+}
+
+// v = D^-1 r spread on the coarse mesh (real part); the mesh is small and L2 resident
+__global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __restrict__ sorted_struct,
+                             const int* __restrict__ pbase, const float* __restrict__ pw,
+                             const double* __restrict__ dinv, const double* __restrict__ r, int64_t n,
+                             const PcgScalars* __restrict__ sc, int use_active, float2* __restrict__ mesh) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const int s = sorted_struct[a];
+  if (use_active && !sc[s].active) return;
+  const StructDev& S = stp[s];
+  const int bs = pbase[a];
+  const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
+  const float* w = pw + a * 12;
+  const float v = (float)(dinv[a] * r[a]);
+  float2* m = mesh + S.mesh_off;
+  for (int jx = 0; jx < 4; ++jx) {
+    int kx = f[0] - jx;
+    if (kx < 0) kx += S.K[0];
+    for (int jy = 0; jy < 4; ++jy) {
+      int ky = f[1] - jy;
+      if (ky < 0) ky += S.K[1];
+      const float wxy = v * w[jx] * w[4 + jy];
+      float2* row = m + ((int64_t)kx * S.K[1] + ky) * S.K[2];
+      for (int jz = 0; jz < 4; ++jz) {
+        int kz = f[2] - jz;
+        if (kz < 0) kz += S.K[2];
+        atomicAdd(&row[kz].x, wxy * w[8 + jz]);
+      }
+    }
+  }
+}
+
+// u = D^-1 (r - phi), phi the interpolated coarse potential; per-structure sum of u
+__global__ void k_pre_gather(const Chunk* __restrict__ chunks, const StructDev* __restrict__ stp,
+                             const int* __restrict__ pbase, const float* __restrict__ pw,
+                             const double* __restrict__ dinv, const double* __restrict__ r,
+                             const float2* __restrict__ mesh, PcgScalars* __restrict__ sc, int use_active,
+                             int slot, double* __restrict__ u, double* __restrict__ part, int* __restrict__ counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  if (use_active && !sc[ch.s].active) return;
+  const StructDev& S = stp[ch.s];
+  const float2* m = mesh + S.mesh_off;
+  double acc = 0.0;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    const int bs = pbase[a];
+    const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
+    const float* w = pw + a * 12;
+    float phi = 0.f;
+    for (int jx = 0; jx < 4; ++jx) {
+      int kx = f[0] - jx;
+      if (kx < 0) kx += S.K[0];
+      for (int jy = 0; jy < 4; ++jy) {
+        int ky = f[1] - jy;
+        if (ky < 0) ky += S.K[1];
+        const float2* row = m + ((int64_t)kx * S.K[1] + ky) * S.K[2];
+        float rs = 0.f;
+        for (int jz = 0; jz < 4; ++jz) {
+          int kz = f[2] - jz;
+          if (kz < 0) kz += S.K[2];
+          rs += w[8 + jz] * row[kz].x;
+        }
+        phi += w[jx] * w[4 + jy] * rs;
+      }
+    }
+    double ua = dinv[a] * (r[a] - (double)phi);
+    u[a] = ua;
+    acc += ua;
+  }
+  __shared__ double red[256];
+  __shared__ bool last;
+  acc = warp_sum<double>(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
+    part[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(&counter[ch.s], 1) == ch.count - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double tot = ordered_block_sum(part, ch.first, ch.count, 1, 0, red);
+    if (threadIdx.x == 0) {
+      if (slot == 0)
+        sc[ch.s].usum = tot;
+      else
+        sc[ch.s].w1sum = tot;
+      counter[ch.s] = 0;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host side
 template <typename T, int P>
 cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, int use_active, int fuse_pAp,
@@ -716,7 +847,7 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
                                                         Pl->d_sc, use_active, mesh2, mesh, Pl->tl);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
-  k_fft_x_green<T><<<Pl->n_xitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_xitems, Pl->d_xpairs, bmod,
+  k_fft_x_green<T, false><<<Pl->n_xitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_xitems, Pl->d_xpairs, bmod,
                                                    Pl->d_tw64, Pl->d_tw32, Pl->d_sc, use_active, mesh);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
@@ -753,7 +884,8 @@ cudaError_t set_smem_attrs() {
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_ZI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return cudaSuccess;
 }
 
@@ -780,4 +912,35 @@ cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, i
   if (p == 4) return matvec_impl<double, 4>(P, x, y, with_J, use_active, fuse_pAp, ev);
   if (p == 6) return matvec_impl<double, 6>(P, x, y, with_J, use_active, fuse_pAp, ev);
   return matvec_impl<double, 8>(P, x, y, with_J, use_active, fuse_pAp, ev);
+}
+
+cudaError_t launch_precond_setup(qeq_plan_s* P) {
+  count_launch(P);
+  k_pre_weights<<<(int)((P->n_atoms + 255) / 256), 256, 0, P->stream>>>(P->d_stp, P->d_key, P->d_posc, P->n_atoms,
+                                                                        P->d_pbase, P->d_pw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, int use_active) {
+  cudaStream_t s = P->stream;
+  const size_t smf = sizeof(float2) * (size_t)P->fft_smem_elems;
+  const float* bmod = P->d_bmod32;
+  count_launch(P, 7);
+  QEQ_CUDA_TRY(cudaMemsetAsync(P->d_pmesh, 0, sizeof(float2) * (size_t)P->total_pmesh, s));
+  k_pre_spread<<<(int)((P->n_atoms + 255) / 256), 256, 0, s>>>(P->d_stp, P->d_key, P->d_pbase, P->d_pw, P->d_dinv, r,
+                                                               P->n_atoms, P->d_sc, use_active, P->d_pmesh);
+  k_fft_pass<float, PASS_ZF><<<P->n_pz, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pzitems, P->d_tw64, P->d_tw32, P->d_sc,
+                                                       use_active, P->d_pmesh, P->d_pmesh2, P->tlp);
+  k_fft_pass<float, PASS_YF><<<P->n_py, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pyitems, P->d_tw64, P->d_tw32, P->d_sc,
+                                                       use_active, P->d_pmesh2, P->d_pmesh, P->tlp);
+  k_fft_x_green<float, true><<<P->n_px, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pxitems, P->d_xpairs, bmod, P->d_tw64,
+                                                       P->d_tw32, P->d_sc, use_active, P->d_pmesh);
+  k_fft_pass<float, PASS_YI><<<P->n_py, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pyitems, P->d_tw64, P->d_tw32, P->d_sc,
+                                                       use_active, P->d_pmesh, P->d_pmesh2, P->tlp);
+  k_fft_pass<float, PASS_ZI><<<P->n_pz, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pzitems, P->d_tw64, P->d_tw32, P->d_sc,
+                                                       use_active, P->d_pmesh2, P->d_pmesh, P->tlp);
+  k_pre_gather<<<P->n_chunks, 256, 0, s>>>(P->d_chunks, P->d_stp, P->d_pbase, P->d_pw, P->d_dinv, r, P->d_pmesh, P->d_sc,
+                                           use_active, slot, u, P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES,
+                                           P->d_counter + 3 * P->n_struct);
+  return cudaGetLastError();
 }

@@ -211,7 +211,8 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_chi,    P->d_dinv,    P->d_posc,    P->d_row,      P->d_row_cnt, P->d_col,
                   P->d_val64,  P->d_val32,   P->d_q,       P->d_r,        P->d_z,       P->d_p,
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
-                  P->d_err,    P->d_done};
+                  P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems,
+                  P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -493,6 +494,59 @@ static qeq_status build_plan(qeq_plan_s* P) {
       chunks.push_back(ch);
     }
   }
+  // --- Fourier preconditioner: a coarse mesh per structure (spacing ~2 A, cubic B-splines)
+  std::vector<StructDev> hsp;
+  std::vector<int4> pzit, pyit, pxit;
+  int64_t pmesh_off = 0;
+  if (D.preconditioner == QEQ_PRECOND_FOURIER) {
+    const double kPreSpacing = D.precond_spacing, kPreWidth = D.precond_width;
+    int maxKp = 8;
+    for (int s = 0; s < ns; ++s) {
+      StructDev Tp = hs[s];
+      double wd[3];
+      plane_widths(Tp.h, Tp.V, wd);
+      for (int d = 0; d < 3; ++d) {
+        Tp.K[d] = next_smooth(std::max(8, (int)ceil(wd[d] / kPreSpacing - 1e-9)));
+        maxKp = std::max(maxKp, Tp.K[d]);
+      }
+      hsp.push_back(Tp);
+    }
+    const int tlp = fft_tile_lines(maxKp);
+    P->tlp = tlp;
+    for (int s = 0; s < ns; ++s) {
+      StructDev& Tp = hsp[s];
+      Tp.S = 1;
+      Tp.ncm = 1;
+      Tp.p = 4;
+      Tp.M = (int64_t)Tp.K[0] * Tp.K[1] * Tp.K[2];
+      Tp.mesh_off = pmesh_off;
+      pmesh_off += Tp.M;
+      for (int k = 0; k < QEQ_MAX_SPECIES * QEQ_MAX_SPECIES; ++k) Tp.w2[k] = kPreWidth * kPreWidth;
+      Tp.green_pref = hs[s].green_pref;
+      Tp.omega = D.precond_scale;  // the coarse mesh carries beta in the otherwise unused split width
+      for (int d = 0; d < 3; ++d) {
+        Tp.fft_plan[d] = fft_plan_for(Tp.K[d]);
+        Tp.bmod_off[d] = (int)bmod.size();
+        std::vector<double> bm(Tp.K[d]);
+        bspline_moduli(Tp.K[d], 4, bm.data());
+        for (double v : bm) {
+          bmod.push_back(v);
+          bmod32.push_back((float)v);
+        }
+      }
+      Tp.xpair_off = (int)xpairs.size();
+      smem_elems = std::max<int64_t>(
+          smem_elems, fft_work_lists(Tp, s, tlp, Tp.xpair_off, [&](int4 v) { pzit.push_back(v); },
+                                     [&](int4 v) { pyit.push_back(v); }, [&](int2 v) { xpairs.push_back(v); },
+                                     [&](int4 v) { pxit.push_back(v); }));
+    }
+  }
+  P->precond = D.preconditioner;
+  P->hsp = hsp;
+  P->n_pz = (int)pzit.size();
+  P->n_py = (int)pyit.size();
+  P->n_px = (int)pxit.size();
+  P->total_pmesh = pmesh_off;
   P->hs = hs;
   P->hfft = fplans;
   P->total_bins = bin_off;
@@ -567,6 +621,18 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(dalloc(P, &P->d_done, 4));
   ALLOC(cudaHostAlloc((void**)&P->h_done, sizeof(int) * 8, cudaHostAllocDefault));
   ALLOC(cudaEventCreateWithFlags(&P->ev_done, cudaEventDisableTiming));
+  if (P->precond == QEQ_PRECOND_FOURIER) {
+    ALLOC(upload(P, &P->d_stp, hsp));
+    ALLOC(upload(P, &P->d_pzitems, pzit));
+    ALLOC(upload(P, &P->d_pyitems, pyit));
+    ALLOC(upload(P, &P->d_pxitems, pxit));
+    ALLOC(dalloc(P, &P->d_pmesh, (size_t)P->total_pmesh));
+    ALLOC(dalloc(P, &P->d_pmesh2, (size_t)P->total_pmesh));
+    ALLOC(dalloc(P, &P->d_w1, N));
+    ALLOC(dalloc(P, &P->d_u, N));
+    ALLOC(dalloc(P, &P->d_pbase, N));
+    ALLOC(dalloc(P, &P->d_pw, (size_t)N * 12));
+  }
   ALLOC(matvec_set_attributes());
 #undef ALLOC
   return QEQ_OK;
@@ -589,7 +655,14 @@ extern "C" qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stre
   if (!(D.ewald_tol > 0)) D.ewald_tol = 1e-6;
   if (!(D.r_cut > 0)) D.r_cut = 8.0;
   if (D.max_iter <= 0) D.max_iter = 1000;
+  if (!(D.precond_spacing > 0)) D.precond_spacing = 1.4;
+  if (!(D.precond_width > 0)) D.precond_width = 4.5;
+  if (!(D.precond_scale > 0) || D.precond_scale > 1.0) D.precond_scale = 0.98;
   if (D.spline_order != 0 && D.spline_order != 4 && D.spline_order != 6 && D.spline_order != 8) {
+    delete P;
+    return QEQ_ERR_INVALID;
+  }
+  if (D.preconditioner != QEQ_PRECOND_JACOBI && D.preconditioner != QEQ_PRECOND_FOURIER) {
     delete P;
     return QEQ_ERR_INVALID;
   }

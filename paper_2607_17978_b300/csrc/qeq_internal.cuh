@@ -101,6 +101,8 @@ struct PcgScalars {
   double q_tot;
   double chi_p2;      // ||P chi||_2^2
   double chi_sum;     // sum chi
+  double usum;        // sum of the last preconditioned residual (Fourier preconditioner)
+  double w1sum;       // sum of M^-1 1
   double E_lin, E_quad, E_J;  // chi.q, q.Aq, q.Jq
   double xsum[QEQ_MAX_SPECIES];       // per-species sums of the matvec input
   int active;         // 1 while iterating
@@ -109,7 +111,8 @@ struct PcgScalars {
   int restarts;
   int status;
   int n;
-  int pad_[2];
+  int jacobi;         // 1: the Fourier preconditioner was dropped for Jacobi
+  int pad_;
 };
 
 // Atom-chunk for reductions: one CTA, atoms [begin, end) of one structure.
@@ -241,6 +244,17 @@ inline int fft_tile_lines(int maxK) {
   int* d_done = nullptr;           // all-structures-inactive flag
   int* h_done = nullptr;           // pinned mirror
   cudaEvent_t ev_done = nullptr;
+  // Fourier preconditioner (coarse mesh per structure)
+  int precond = QEQ_PRECOND_JACOBI;
+  std::vector<StructDev> hsp;
+  StructDev* d_stp = nullptr;
+  int4 *d_pzitems = nullptr, *d_pyitems = nullptr, *d_pxitems = nullptr;
+  int n_pz = 0, n_py = 0, n_px = 0, tlp = 8;
+  int64_t total_pmesh = 0;
+  float2 *d_pmesh = nullptr, *d_pmesh2 = nullptr;
+  double *d_w1 = nullptr, *d_u = nullptr;
+  int* d_pbase = nullptr;
+  float* d_pw = nullptr;
   struct qeq_mlp_s* mlp = nullptr; // warm-start network (not owned)
   float* d_feat = nullptr;         // descriptors, sorted order
   float* d_pred = nullptr;         // network output, sorted order
@@ -313,6 +327,9 @@ cudaError_t launch_prepare_atoms(qeq_plan_s* P, const double* pos, const int32_t
 cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, int with_J,
                           int use_active, int fuse_pAp, cudaEvent_t* ev /* QEQ_N_STAGES+1 or NULL */);
 cudaError_t matvec_set_attributes();
+cudaError_t launch_precond_setup(qeq_plan_s* P);
+// u = M^-1 r for the Fourier preconditioner; sum of u per structure into usum (slot 0) or w1sum (slot 1)
+cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, int use_active);
 // launchers (mlp.cu)
 cudaError_t launch_mlp_warm_start(qeq_plan_s* P, double* d_q_sorted);
 

@@ -222,13 +222,49 @@ __global__ void k_precond(const Chunk* __restrict__ chunks, const double* __rest
   }
 }
 
-// p = z + beta p
-__global__ void k_direction(const Chunk* __restrict__ chunks, const double* __restrict__ z, double* __restrict__ p,
-                            const PcgScalars* __restrict__ sc) {
+// Fourier preconditioner: z = u - w1 (sum u / sum w1) (so that 1^T z = 0); rz_new = r.z; beta.
+// The Jacobi direction zj = D^-1 (r - shift) is formed beside it: if r.z of the
+// Fourier direction is not positive (the preconditioner lost definiteness) the
+// structure continues with Jacobi for the rest of the solve.
+__global__ void k_proj_rz(const Chunk* __restrict__ chunks, const double* __restrict__ r, const double* __restrict__ u,
+                          const double* __restrict__ w1, const double* __restrict__ dinv, double* __restrict__ z,
+                          double* __restrict__ zj, PcgScalars* __restrict__ sc, int restart, double* part,
+                          int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  if (!sc[ch.s].active) return;
+  const double f = sc[ch.s].usum / sc[ch.s].w1sum;
+  const double sh = sc[ch.s].shift;
+  double v[2] = {0, 0};
+  const int op[2] = {RED_SUM, RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    double za = u[a] - f * w1[a];
+    double zja = dinv[a] * (r[a] - sh);
+    z[a] = za;
+    zj[a] = zja;
+    v[0] += r[a] * za;
+    v[1] += r[a] * zja;
+  }
+  double tot[2];
+  if (chunk_reduce<2>(v, op, ch, part, counter, tot)) {
+    PcgScalars& c = sc[ch.s];
+    if (!c.jacobi && !(tot[0] > 0.0 && isfinite(tot[0]))) {
+      c.jacobi = 1;
+      restart = 1;
+    }
+    double rz = c.jacobi ? tot[1] : tot[0];
+    c.beta = (restart || c.rz == 0.0) ? 0.0 : rz / c.rz;
+    c.rz = rz;
+  }
+}
+
+// p = z + beta p  (zj instead of z for a structure that fell back to Jacobi)
+__global__ void k_direction(const Chunk* __restrict__ chunks, const double* __restrict__ z,
+                            const double* __restrict__ zj, double* __restrict__ p, const PcgScalars* __restrict__ sc) {
   const Chunk ch = chunks[blockIdx.x];
   if (!sc[ch.s].active) return;
   const double beta = sc[ch.s].beta;
-  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) p[a] = z[a] + beta * p[a];
+  const double* zz = (zj && sc[ch.s].jacobi) ? zj : z;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) p[a] = zz[a] + beta * p[a];
 }
 
 // all structures inactive?
@@ -351,6 +387,25 @@ qeq_status cuda_fail(qeq_plan_s* P, cudaError_t e, const char* where) {
 int* red_counter(qeq_plan_s* P) { return P->d_counter + 2 * P->n_struct; }
 double* red_part(qeq_plan_s* P) { return P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES + P->total_bins + 8; }
 
+const double* dir_alt(qeq_plan_s* P) { return P->precond == QEQ_PRECOND_FOURIER ? P->d_x : nullptr; }
+
+// z = preconditioned, projected residual; beta and rz (restart: beta = 0)
+cudaError_t precondition(qeq_plan_s* P, int restart, int use_active) {
+  cudaStream_t s = P->stream;
+  int nc = P->n_chunks;
+  if (P->precond == QEQ_PRECOND_FOURIER) {
+    QEQ_CUDA_TRY(launch_precond(P, P->d_r, P->d_u, 0, use_active));
+    count_launch(P);
+    k_proj_rz<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_u, P->d_w1, P->d_dinv, P->d_z, P->d_x, P->d_sc, restart,
+                                 red_part(P), red_counter(P));
+  } else {
+    count_launch(P);
+    k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, restart, red_part(P),
+                                 red_counter(P));
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t one_iteration(qeq_plan_s* P, int prec) {
   cudaStream_t s = P->stream;
   int nc = P->n_chunks;
@@ -359,10 +414,9 @@ cudaError_t one_iteration(qeq_plan_s* P, int prec) {
   count_launch(P);
   k_update<<<nc, 256, 0, s>>>(P->d_chunks, P->d_p, P->d_Ap, P->d_dinv, P->d_q, P->d_r, P->d_sc, red_part(P),
                               red_counter(P), max_iter);
+  QEQ_CUDA_TRY(precondition(P, 0, 1));
   count_launch(P);
-  k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 0, red_part(P), red_counter(P));
-  count_launch(P);
-  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
+  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
   return cudaGetLastError();
 }
 
@@ -499,6 +553,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     wm = QEQ_WARM_MLP;
   }
   int warm_kept = (wm != QEQ_WARM_COLD) ? 1 : 0;
+  if (P->precond == QEQ_PRECOND_FOURIER) TRY(launch_precond_setup(P));
   for (int attempt = 0; attempt < 2; ++attempt) {
     count_launch(P, 3);
     k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q, wm, P->d_dinv, P->d_chi, P->d_J, P->d_q, P->d_sc,
@@ -506,6 +561,12 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     k_project<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_sc);
     k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol);
     TRY(cudaGetLastError());
+    if (P->precond == QEQ_PRECOND_FOURIER) {
+      // w1 = M^-1 1 and its sums, for projecting preconditioned residuals onto 1^T z = 0
+      count_launch(P);
+      k_fill<<<(int)((P->n_atoms + 255) / 256), 256, 0, s>>>(P->d_x, P->n_atoms, 1.0);
+      TRY(launch_precond(P, P->d_x, P->d_w1, 1, 0));
+    }
     // first residual with the iteration's matvec
     TRY(launch_matvec(P, prec, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
     count_launch(P);
@@ -544,9 +605,9 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     warm_kept = 0;
     TRY(init_scalars(P, h_qtot) == QEQ_OK ? cudaSuccess : cudaErrorUnknown);
   }
-  count_launch(P, 2);
-  k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 1, red_part(P), red_counter(P));
-  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
+  TRY(precondition(P, 1, 1));
+  count_launch(P);
+  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
   TRY(cudaGetLastError());
   const int max_restarts = 4;
   for (int outer = 0; outer <= max_restarts + 1; ++outer) {
@@ -564,10 +625,9 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
                                red_counter(P), max_iter);
     count_launch(P);
     k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_done);
+    TRY(precondition(P, 1, 1));
     count_launch(P);
-    k_precond<<<nc, 256, 0, s>>>(P->d_chunks, P->d_r, P->d_dinv, P->d_z, P->d_sc, 1, red_part(P), red_counter(P));
-    count_launch(P);
-    k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, P->d_p, P->d_sc);
+    k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
     TRY(cudaGetLastError());
     TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));

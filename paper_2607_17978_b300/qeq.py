@@ -49,6 +49,10 @@ class PlanDesc(ctypes.Structure):
         ("max_iter", ctypes.c_int32),
         ("residual_tol", ctypes.c_double),
         ("flags", ctypes.c_int32),
+        ("preconditioner", ctypes.c_int32),
+        ("precond_spacing", ctypes.c_double),
+        ("precond_width", ctypes.c_double),
+        ("precond_scale", ctypes.c_double),
     ]
 
 
@@ -160,7 +164,8 @@ class Plan:
 
     def __init__(self, cells, atom_offsets, sigma, *, coulomb_k=14.3996454784, charge_tol=1e-5,
                  ewald_tol=1e-6, r_cut=8.0, spline_order=0, mesh_spacing=0.0, precision="fp64",
-                 max_iter=1000, residual_tol=0.0, graph=True, device=None):
+                 max_iter=1000, residual_tol=0.0, graph=True, device=None, preconditioner="jacobi",
+                 precond_spacing=0.0, precond_width=0.0, precond_scale=0.0):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -180,7 +185,8 @@ class Plan:
                      cells.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.n_species,
                      sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), coulomb_k, charge_tol, ewald_tol,
                      r_cut, spline_order, mesh_spacing, prec, max_iter, residual_tol,
-                     0 if graph else QEQ_FLAG_NO_GRAPH)
+                     0 if graph else QEQ_FLAG_NO_GRAPH, {"jacobi": 0, "fourier": 1}[preconditioner],
+                     precond_spacing, precond_width, precond_scale)
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.Stream(device=self.device)
             h = ctypes.c_void_p()

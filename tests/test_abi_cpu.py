@@ -54,13 +54,13 @@ def test_invalid_descriptions_are_rejected_before_any_device_work(lib):
     def desc(**kw):
         d = qeq.PlanDesc(1, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                          cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 2,
-                         sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
+                         sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
         for k, v in kw.items():
             setattr(d, k, v)
         return d
 
     for bad in (dict(n_struct=0), dict(n_species=0), dict(n_species=9), dict(spline_order=5),
-                dict(precision=7)):
+                dict(precision=7), dict(preconditioner=3)):
         assert lib.qeq_plan_create(ctypes.byref(desc(**bad)), None, ctypes.byref(h)) == qeq.QEQ_ERR_INVALID
     assert lib.qeq_plan_create(None, None, ctypes.byref(h)) == qeq.QEQ_ERR_INVALID
     assert lib.qeq_last_error(None) == b"null plan"
