@@ -505,117 +505,71 @@ __device__ __forceinline__ const double* pair_vals<double>(const double* v64, co
   return v64;
 }
 
-// One CTA per 16^3 brick: the brick plus its (P-1)-point low-side halo of the
-// potential mesh is staged in shared memory (one complex mesh at a time); a warp
-// takes one of the brick's atoms, lanes own stencil rows and run along z, and a
-// warp reduction gives the mesh part of y_i.  The same warp adds the real-space
-// pair row and the local terms, and the CTA contributes x.y to a per-structure
-// sum when fuse_pAp is set.
+// Gathering without shared-memory staging: a warp takes one atom (atoms in sorted
+// order, so neighbouring warps touch the same mesh rows through L1), lanes own 4
+// stencil rows x 8 z points and read the potential straight from the mesh; the
+// same warp adds the real-space pair row and the local terms.  CTAs are atom
+// chunks of one structure, so x.y is reduced per structure deterministically.
 template <typename T, int P>
-__global__ void __launch_bounds__(256) k_gather(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
-                         const int* __restrict__ bin_start, const int* __restrict__ base,
-                         const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ J,
-                         const double* __restrict__ x, const int64_t* __restrict__ row, const int* __restrict__ col,
-                         const double* __restrict__ v64, const float* __restrict__ v32, int with_J, int with_pairs,
-                         PcgScalars* __restrict__ sc, int use_active, int fuse_pAp, double* __restrict__ part,
-                         int* __restrict__ counter, const typename C2<T>::t* __restrict__ mesh,
-                         double* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_gather_direct(
+    const Chunk* __restrict__ chunks, const StructDev* __restrict__ st, const int* __restrict__ base,
+    const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ J,
+    const double* __restrict__ x, const int64_t* __restrict__ row, const int* __restrict__ col,
+    const double* __restrict__ v64, const float* __restrict__ v32, int with_J, int with_pairs,
+    PcgScalars* __restrict__ sc, int use_active, int fuse_pAp, double* __restrict__ part, int* __restrict__ counter,
+    const typename C2<T>::t* __restrict__ mesh, double* __restrict__ y, int split) {
   using V = typename C2<T>::t;
-  const int g = blockIdx.x;
-  const int s = brick_struct[g];
-  const StructDev& S = st[s];
-  if (use_active && !sc[s].active) return;
+  const Chunk ch = chunks[blockIdx.x / split];
+  const int sub = blockIdx.x - (blockIdx.x / split) * split;
+  if (use_active && !sc[ch.s].active) return;
+  const StructDev& S = st[ch.s];
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Brick B = brick_of(S, g);
-  int len[3];
-  for (int d = 0; d < 3; ++d) len[d] = B.ext[d] + P - 1;
-  // the brick plus its low-side halo, complex, rows (lx, ly) padded to QEQ_RS elements
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* reg = reinterpret_cast<V*>(smem_raw);
-  // the brick's atoms: its (up to) 2 x 2 x 2 bins
-  __shared__ int bstart[8], bcount[8], nbin;
-  if (threadIdx.x == 0) {
-    int n = 0;
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b)
-        for (int c = 0; c < 2; ++c) {
-          int i0 = B.x0[0] / QEQ_BIN + a, i1 = B.x0[1] / QEQ_BIN + b, i2 = B.x0[2] / QEQ_BIN + c;
-          if (i0 >= S.nb[0] || i1 >= S.nb[1] || i2 >= S.nb[2]) continue;
-          int gb = S.bin_off + (i0 * S.nb[1] + i1) * S.nb[2] + i2;
-          bstart[n] = bin_start[gb];
-          bcount[n] = bin_start[gb + 1] - bin_start[gb];
-          ++n;
-        }
-    nbin = n;
-  }
-  const T* vals = pair_vals<T>(v64, v32);
   const int jz = lane & 7, rsub = lane >> 3;
+  const T* vals = pair_vals<T>(v64, v32);
   double blk = 0.0;
-  for (int cm = 0; cm < S.ncm; ++cm) {
-    __syncthreads();
-    const V* mg = mesh + S.mesh_off + (int64_t)cm * S.M;
-    // rows (lx, ly) over warps, z over lanes; every index wraps at most once
-    // because the region is shorter than twice the mesh in each direction
-    for (int rrow = w; rrow < len[0] * len[1]; rrow += nw) {
-      const int lx = rrow / len[1], ly = rrow - (rrow / len[1]) * len[1];
-      int kx = B.x0[0] - (P - 1) + lx, ky = B.x0[1] - (P - 1) + ly;
-      if (kx < 0) kx += S.K[0];
-      if (kx >= S.K[0]) kx -= S.K[0];
-      if (ky < 0) ky += S.K[1];
-      if (ky >= S.K[1]) ky -= S.K[1];
-      const V* src = mg + ((int64_t)kx * S.K[1] + ky) * S.K[2];
-      V* dre = reg + rrow * QEQ_RS;
-      for (int lz = lane; lz < len[2]; lz += 32) {
-        int kz = B.x0[2] - (P - 1) + lz;
-        if (kz < 0) kz += S.K[2];
-        if (kz >= S.K[2]) kz -= S.K[2];
-        cp_async_elem(dre + lz, src + kz);
+  // this CTA's share of the chunk: atoms begin + sub*nw + w, stepping split*nw
+  for (int64_t t = ch.begin + (int64_t)sub * nw + w; t < ch.end; t += (int64_t)split * nw) {
+    const int sp = spec[t];
+    const int part_ = sp & 1;
+    const V* mg = mesh + S.mesh_off + (int64_t)(sp >> 1) * S.M;
+    const int bs = base[t];
+    const int f0 = bs & 1023, f1 = (bs >> 10) & 1023, f2 = (bs >> 20) & 1023;
+    const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
+    T acc = (T)0;
+    if (jz < P) {
+      int kz = f2 - (P - 1) + jz;
+      if (kz < 0) kz += S.K[2];
+      const T wzj = wt[2 * QEQ_MAXP + P - 1 - jz];
+      T racc = (T)0;
+#pragma unroll
+      for (int r = rsub; r < P * P; r += 4) {
+        const int jx = r / P, jy = r - (r / P) * P;
+        int kx = f0 - (P - 1) + jx;
+        if (kx < 0) kx += S.K[0];
+        int ky = f1 - (P - 1) + jy;
+        if (ky < 0) ky += S.K[1];
+        const V v = __ldg(mg + ((int64_t)kx * S.K[1] + ky) * S.K[2] + kz);
+        racc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
       }
+      acc = racc * wzj;
     }
-    cp_async_wait_all();
-    __syncthreads();
-    int total = 0;
-    for (int b = 0; b < nbin; ++b) total += bcount[b];
-    for (int idx = w; idx < total; idx += nw) {
-      int b = 0, off = idx;
-      while (off >= bcount[b]) off -= bcount[b++];
-      const int t = bstart[b] + off;
-      const int sp = spec[t];
-      if ((sp >> 1) != cm) continue;
-      const int bs = base[t];
-      const int o0 = (bs & 1023) - B.x0[0], o1 = ((bs >> 10) & 1023) - B.x0[1], o2 = ((bs >> 20) & 1023) - B.x0[2];
-      const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
-      const int part_ = sp & 1;
-      // stencil point f - (P-1) + j is at local index f - x0 + j, weight M_p(w + P-1-j)
-      T acc = (T)0;
-      if (jz < P) {
-        const T wzj = wt[2 * QEQ_MAXP + P - 1 - jz];
-        for (int r = rsub; r < P * P; r += 4) {
-          const int jx = r / P, jy = r - (r / P) * P;
-          const V v = reg[((o0 + jx) * len[1] + (o1 + jy)) * QEQ_RS + o2 + jz];
-          acc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
-        }
-        acc *= wzj;
-      }
-      if (with_pairs) {
-        int64_t r0 = row[t], r1 = row[t + 1];
-        for (int64_t k = r0 + lane; k < r1; k += 32) acc += vals[k] * (T)x[col[k]];
-      }
-      acc = warp_sum<T>(acc);
-      if (lane == 0) {
-        double xi = x[t];
-        double loc = S.self_s[sp] * xi;
-        if (with_J) loc += J[t] * xi;
-        const PcgScalars& c = sc[s];
-        for (int tt = 0; tt < S.S; ++tt) loc -= S.corr[sp * QEQ_MAX_SPECIES + tt] * c.xsum[tt];
-        double yi = (double)acc + loc;
-        y[t] = yi;
-        blk += xi * yi;
-      }
+    if (with_pairs) {
+      int64_t r0 = row[t], r1 = row[t + 1];
+      for (int64_t k = r0 + lane; k < r1; k += 32) acc += vals[k] * (T)x[col[k]];
+    }
+    acc = warp_sum<T>(acc);
+    if (lane == 0) {
+      double xi = x[t];
+      double loc = S.self_s[sp] * xi;
+      if (with_J) loc += J[t] * xi;
+      const PcgScalars& c = sc[ch.s];
+      for (int tt = 0; tt < S.S; ++tt) loc -= S.corr[sp * QEQ_MAX_SPECIES + tt] * c.xsum[tt];
+      double yi = (double)acc + loc;
+      y[t] = yi;
+      blk += xi * yi;
     }
   }
   if (fuse_pAp) {
-    // deterministic per-structure reduction of x.y over the structure's bricks
     __shared__ double wsum[32];
     __shared__ double red[256];
     __shared__ bool last;
@@ -624,20 +578,19 @@ __global__ void __launch_bounds__(256) k_gather(const StructDev* __restrict__ st
     if (threadIdx.x == 0) {
       double b = 0.0;
       for (int i = 0; i < nw; ++i) b += wsum[i];
-      part[g] = b;
+      part[blockIdx.x] = b;
       __threadfence();
-      int prev = atomicAdd(&counter[s], 1);
-      last = (prev == S.nbr[0] * S.nbr[1] * S.nbr[2] - 1);
+      last = (atomicAdd(&counter[ch.s], 1) == ch.count * split - 1);
     }
     __syncthreads();
     if (last) {
       __threadfence();
-      double tot = ordered_block_sum(part, S.brick_off, S.nbr[0] * S.nbr[1] * S.nbr[2], 1, 0, red);
+      double tot = ordered_block_sum(part, ch.first * split, ch.count * split, 1, 0, red);
       if (threadIdx.x == 0) {
-        PcgScalars& c = sc[s];
+        PcgScalars& c = sc[ch.s];
         c.pAp = tot;
         c.alpha = (tot != 0.0) ? c.rz / tot : 0.0;
-        counter[s] = 0;
+        counter[ch.s] = 0;
       }
     }
   }
@@ -652,8 +605,14 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
   if (use_active && !sc[ch.s].active) return;
   __shared__ double red[QEQ_MAX_SPECIES][33];
   double loc[QEQ_MAX_SPECIES];
+#pragma unroll
   for (int k = 0; k < QEQ_MAX_SPECIES; ++k) loc[k] = 0.0;
-  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) loc[spec[a]] += x[a];
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    const int sp = spec[a];
+    const double xa = x[a];
+#pragma unroll
+    for (int k = 0; k < QEQ_MAX_SPECIES; ++k) loc[k] += (sp == k) ? xa : 0.0;
+  }
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = 0; k < QEQ_MAX_SPECIES; ++k) {
     double v = warp_sum<double>(loc[k]);
@@ -861,14 +820,11 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   QEQ_CUDA_TRY(mark());
   // stage 7: gathering + real-space pairs + local terms (+ x.y per structure)
   {
-    int reg = QEQ_BRICK + P - 1;
-    size_t sm = (size_t)reg * reg * QEQ_RS * sizeof(V);
     int with_pairs = Pl->pair_cap > 0;
-    k_gather<T, P><<<Pl->total_bricks, 256, sm, s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
-                                                   Pl->d_spec, Pl->d_J, x, Pl->d_row, Pl->d_col, Pl->d_val64,
-                                                   Pl->d_val32, with_J, with_pairs, Pl->d_sc, use_active, fuse_pAp,
-                                                   Pl->d_part + (size_t)Pl->n_chunks * QEQ_MAX_SPECIES,
-                                                   Pl->d_counter + Pl->n_struct, mesh, y);
+    k_gather_direct<T, P><<<Pl->n_chunks * Pl->gather_split, 256, 0, s>>>(
+        Pl->d_chunks, Pl->d_st, Pl->d_base, wts, Pl->d_spec, Pl->d_J, x, Pl->d_row, Pl->d_col, Pl->d_val64,
+        Pl->d_val32, with_J, with_pairs, Pl->d_sc, use_active, fuse_pAp,
+        Pl->d_part + (size_t)Pl->n_chunks * QEQ_MAX_SPECIES, Pl->d_counter + Pl->n_struct, mesh, y, Pl->gather_split);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   QEQ_CUDA_TRY(mark());
@@ -879,7 +835,6 @@ template <typename T, int P>
 cudaError_t set_smem_attrs() {
   const int big = 200 * 1024;
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_gather<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));

@@ -554,6 +554,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->total_mesh = mesh_off;
   P->pair_cap = pair_cap;
   P->n_chunks = (int)chunks.size();
+  // enough gather CTAs to fill the GPU (about 4 per SM of a 148-SM part) when chunks are few
+  P->gather_split = std::max(1, std::min(16, (592 + P->n_chunks - 1) / std::max(1, P->n_chunks)));
   P->n_zitems = (int)zit.size();
   P->n_yitems = (int)yit.size();
   P->n_xitems = (int)xit.size();
@@ -611,7 +613,9 @@ static qeq_status build_plan(qeq_plan_s* P) {
   for (double** v : {&P->d_q, &P->d_r, &P->d_z, &P->d_p, &P->d_Ap, &P->d_x}) ALLOC(dalloc(P, v, N));
   ALLOC(dalloc(P, &P->d_mesh, (size_t)P->total_mesh));
   ALLOC(dalloc(P, &P->d_mesh2, (size_t)P->total_mesh));
-  ALLOC(dalloc(P, &P->d_part, (size_t)P->n_chunks * QEQ_MAX_SPECIES * 2 + P->total_bins + 64));
+  // partials: species sums (8 per chunk), gather x.y (split per chunk, or bins), PCG reductions (8 per chunk)
+  ALLOC(dalloc(P, &P->d_part, (size_t)P->n_chunks * QEQ_MAX_SPECIES * 2 +
+                                  std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * 16) + 64));
   ALLOC(dalloc(P, &P->d_counter, (size_t)ns * 4));
   ALLOC(cudaMemset(P->d_counter, 0, sizeof(int) * ns * 4));
   ALLOC(dalloc(P, &P->d_sc, ns));

@@ -251,6 +251,7 @@ inline int fft_tile_lines(int maxK) {
   int4 *d_pzitems = nullptr, *d_pyitems = nullptr, *d_pxitems = nullptr;
   int n_pz = 0, n_py = 0, n_px = 0, tlp = 8;
   int64_t total_pmesh = 0;
+  int gather_split = 1;            // CTAs per reduction chunk in the gather
   float2 *d_pmesh = nullptr, *d_pmesh2 = nullptr;
   double *d_w1 = nullptr, *d_u = nullptr;
   int* d_pbase = nullptr;
@@ -334,18 +335,21 @@ cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, 
 cudaError_t launch_mlp_warm_start(qeq_plan_s* P, double* d_q_sorted);
 
 // Deterministic block-wide sum of part[(first + i) * stride + k], i < count:
-// thread t adds the entries i = t, t + blockDim, ... in order, then thread 0
-// adds the per-thread sums in thread order.  Every thread must call it; the
-// result is valid in thread 0.  red: blockDim.x doubles of shared memory.
+// thread t adds the entries i = t, t + blockDim, ... in order, each warp combines
+// its lanes with a fixed shuffle tree and thread 0 adds the warp sums in order.
+// Every thread must call it; the result is valid in thread 0.  red: blockDim.x/32
+// doubles of shared memory.
 __device__ __forceinline__ double ordered_block_sum(const double* part, int first, int count, int stride, int k,
                                                     double* red) {
   double a = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) a += ((const volatile double*)part)[(size_t)(first + i) * stride + k];
-  red[threadIdx.x] = a;
+  // fixed shuffle tree inside each warp, then the warp sums in warp order
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
   __syncthreads();
   double tot = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < (int)blockDim.x; ++i) tot += red[i];
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
   __syncthreads();
   return tot;
 }

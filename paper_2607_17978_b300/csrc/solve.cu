@@ -76,11 +76,12 @@ __device__ bool chunk_reduce(double (&v)[NV], const int (&op)[NV], const Chunk& 
       double y = ((volatile double*)part)[(size_t)(ch.first + i) * 8 + k];
       a = op[k] == RED_SUM ? a + y : (op[k] == RED_MAX ? fmax(a, y) : fmin(a, y));
     }
-    red2[threadIdx.x] = a;
+    a = op[k] == RED_SUM ? wsum(a) : (op[k] == RED_MAX ? wmax(a) : wmin(a));
+    if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
       double x = red2[0];
-      for (int i = 1; i < (int)blockDim.x; ++i)
+      for (int i = 1; i < nw; ++i)
         x = op[k] == RED_SUM ? x + red2[i] : (op[k] == RED_MAX ? fmax(x, red2[i]) : fmin(x, red2[i]));
       tot[k] = x;
     }
@@ -385,7 +386,9 @@ qeq_status cuda_fail(qeq_plan_s* P, cudaError_t e, const char* where) {
   } while (0)
 
 int* red_counter(qeq_plan_s* P) { return P->d_counter + 2 * P->n_struct; }
-double* red_part(qeq_plan_s* P) { return P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES + P->total_bins + 8; }
+double* red_part(qeq_plan_s* P) {
+  return P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES + std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * 16) + 8;
+}
 
 const double* dir_alt(qeq_plan_s* P) { return P->precond == QEQ_PRECOND_FOURIER ? P->d_x : nullptr; }
 
@@ -725,18 +728,19 @@ extern "C" qeq_status qeq_profile_matvec(qeq_plan P, int32_t n_rep, float* h_ms)
     P->last_error = "no atoms prepared: call qeq_solve or qeq_matvec first";
     return QEQ_ERR_INVALID;
   }
-  cudaEvent_t ev[QEQ_N_STAGES + 1];
+  // all repetitions back to back on the plan's stream (no host gaps between them)
+  std::vector<cudaEvent_t> ev((size_t)n_rep * (QEQ_N_STAGES + 1));
   for (auto& e : ev) TRY(cudaEventCreate(&e));
   std::vector<double> acc(QEQ_N_STAGES, 0.0);
-  for (int r = 0; r < n_rep; ++r) {
-    TRY(launch_matvec(P, P->precision, P->d_x, P->d_Ap, 1, 0, 0, ev));
-    TRY(cudaEventSynchronize(ev[QEQ_N_STAGES]));
+  for (int r = 0; r < n_rep; ++r)
+    TRY(launch_matvec(P, P->precision, P->d_x, P->d_Ap, 1, 0, 0, ev.data() + (size_t)r * (QEQ_N_STAGES + 1)));
+  TRY(cudaEventSynchronize(ev.back()));
+  for (int r = 0; r < n_rep; ++r)
     for (int k = 0; k < QEQ_N_STAGES; ++k) {
       float ms = 0.f;
-      TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      TRY(cudaEventElapsedTime(&ms, ev[(size_t)r * (QEQ_N_STAGES + 1) + k], ev[(size_t)r * (QEQ_N_STAGES + 1) + k + 1]));
       acc[k] += ms;
     }
-  }
   for (int k = 0; k < QEQ_N_STAGES; ++k) h_ms[k] = (float)(acc[k] / n_rep);
   for (auto& e : ev) cudaEventDestroy(e);
   return QEQ_OK;
