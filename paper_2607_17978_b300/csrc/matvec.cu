@@ -403,11 +403,39 @@ __device__ __forceinline__ Brick brick_of(const StructDev& S, int g) {
 }
 
 // ------------------------------------------------------------------ spreading
-// One CTA per 16^3 brick and complex mesh.  Candidate atoms: the bins whose
-// stencils can reach the brick.  A warp takes one atom at a time; its lanes
-// own stencil rows (jx, jy) and run along z, adding into the brick in shared
-// memory (shared atomics; each mesh point is then written to global memory
-// exactly once, so the mesh needs no clearing and global memory sees no atomics).
+// One CTA per 16^3 brick and complex mesh, no atomics: thread (lx, ly) owns the
+// brick's z-row at (x0 + lx, y0 + ly) and keeps its 16 points (both species
+// parts) in registers.  The candidate atoms (those of the bins whose stencils
+// can reach the brick) are staged in batches of QEQ_SPB as compact records in
+// shared memory: stencil offsets relative to the brick, 16-bit masks of the
+// brick rows the stencil covers in x and y, the x / y weights (x pre-multiplied
+// by the charge) and the z weights at the brick's 16 z positions.  Every thread
+// then adds, atom after atom in a fixed order, its row's contribution: the
+// spread is deterministic and each mesh point is written to global memory once.
+#define QEQ_SPB 256  // candidate records per batch (one per thread)
+
+// Bits l in [0, ext) of brick rows covered by a stencil of P rows that starts
+// o rows into the brick (o in [0, K), periodic with period K >= P).
+template <int P>
+__device__ __forceinline__ unsigned stencil_rows(int o, int K, int ext) {
+  const unsigned win = (1u << P) - 1u;
+  unsigned m = 0;
+  if (o < 16) m |= win << o;                     // the stencil itself
+  if (K - o < P) m |= win >> (K - o);            // its image one period down
+  if (o + K < 16) m |= win << (o + K);           // ... and one period up (K < 16)
+  if (2 * K - o < P) m |= win >> (2 * K - o);    // two periods down (K < P + 16)
+  return m & ((1u << ext) - 1u);
+}
+
+template <typename T, int P>
+struct SpreadRecs {
+  T wz[QEQ_SPB][QEQ_BRICK];  // z weights at the brick's z positions (0 outside the stencil)
+  T wx[QEQ_SPB][P];          // q * x weights, by stencil index
+  T wy[QEQ_SPB][P];
+  unsigned mask[QEQ_SPB];    // x rows (bits 0-15) and y rows (bits 16-31) the stencil covers
+  int off[QEQ_SPB];          // ox | oy << 10 | species part << 20
+};
+
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
                          const int* __restrict__ bin_start, const int* __restrict__ base,
@@ -418,16 +446,15 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
   const int s = brick_struct[g];
   const StructDev& S = st[s];
   if (use_active && !sc[s].active) return;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, lx = tid >> 4, ly = tid & 15;
   const Brick B = brick_of(S, g);
-  // re and im planes [16][16][QEQ_RS]: a z row padded to 24 elements so that the
-  // 4 rows x 8 z points a warp touches at once fall in distinct banks
-  const int psz = QEQ_BRICK * QEQ_BRICK * QEQ_RS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* acc = reinterpret_cast<T*>(smem_raw);
+  const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
   __shared__ int cand[3][8], ncand[3];
-  if (threadIdx.x < 3) {
-    int d = threadIdx.x, nc = 0;
+  __shared__ int bin_beg[512], bin_pre[513];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SpreadRecs<T, P>& R = *reinterpret_cast<SpreadRecs<T, P>*>(smem_raw);
+  if (tid < 3) {
+    int d = tid, nc = 0;
     int span = min(B.ext[d] + P - 1, S.K[d]);
     for (int k = 0; k < span; ++k) {
       int bn = ((B.x0[d] + k) % S.K[d]) / QEQ_BIN;
@@ -437,53 +464,128 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
     }
     ncand[d] = nc;
   }
-  const int jz = lane & 7, rsub = lane >> 3;
+  __syncthreads();
+  // candidate bins (at most 8 x 8 x 8) in (i0, i1, i2) order and the prefix of their sizes
+  const int nc1 = ncand[1], nc2 = ncand[2], nbins = ncand[0] * nc1 * nc2;
+  for (int k = tid; k < nbins; k += blockDim.x) {
+    const int i2 = k % nc2, i1 = (k / nc2) % nc1, i0 = k / (nc2 * nc1);
+    const int gb = S.bin_off + (cand[0][i0] * S.nb[1] + cand[1][i1]) * S.nb[2] + cand[2][i2];
+    bin_beg[k] = bin_start[gb];
+    bin_pre[k + 1] = bin_start[gb + 1] - bin_start[gb];
+  }
+  __syncthreads();
+  if (tid < 32) {  // inclusive scan of the sizes in chunks of 32
+    int carry = 0;
+    for (int k0 = 0; k0 < nbins; k0 += 32) {
+      int v = (k0 + tid < nbins) ? bin_pre[k0 + tid + 1] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (tid >= o) v += u;
+      }
+      if (k0 + tid < nbins) bin_pre[k0 + tid + 1] = v + carry;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (tid == 0) bin_pre[0] = 0;
+  }
+  __syncthreads();
+  const int total = bin_pre[nbins];
   for (int cm = 0; cm < S.ncm; ++cm) {
-    for (int i = threadIdx.x; i < 2 * psz; i += blockDim.x) acc[i] = (T)0;
-    __syncthreads();
-    int order = 0;
-    for (int i0 = 0; i0 < ncand[0]; ++i0)
-      for (int i1 = 0; i1 < ncand[1]; ++i1)
-        for (int i2 = 0; i2 < ncand[2]; ++i2) {
-          int gb = S.bin_off + (cand[0][i0] * S.nb[1] + cand[1][i1]) * S.nb[2] + cand[2][i2];
-          int t0 = bin_start[gb], t1 = bin_start[gb + 1];
-          for (int t = t0; t < t1; ++t, ++order) {
-            if ((order & 7) != w) continue;  // 8 warps
-            int sp = spec[t];
-            if ((sp >> 1) != cm) continue;
-            const int bs = base[t];
-            const int f0 = bs & 1023, f1 = (bs >> 10) & 1023, f2 = (bs >> 20) & 1023;
-            const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
-            int kz = f2 - (P - 1) + jz;
-            if (kz < 0) kz += S.K[2];
-            const int lz = kz - B.x0[2];
-            const bool zok = (jz < P) && lz >= 0 && lz < B.ext[2];
-            const T wzq = zok ? (T)x[t] * wt[2 * QEQ_MAXP + P - 1 - jz] : (T)0;
-            T* plane = acc + (sp & 1) * psz;
-            for (int r = rsub; r < P * P; r += 4) {
-              const int jx = r / P, jy = r - (r / P) * P;
-              int kx = f0 - (P - 1) + jx;
-              if (kx < 0) kx += S.K[0];
-              const int lx = kx - B.x0[0];
-              int ky = f1 - (P - 1) + jy;
-              if (ky < 0) ky += S.K[1];
-              const int ly = ky - B.x0[1];
-              if (!zok || lx < 0 || lx >= B.ext[0] || ly < 0 || ly >= B.ext[1]) continue;
-              atomicAdd(plane + (lx * QEQ_BRICK + ly) * QEQ_RS + lz, wzq * wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy]);
+    T re[QEQ_BRICK], im[QEQ_BRICK];
+#pragma unroll
+    for (int z = 0; z < QEQ_BRICK; ++z) re[z] = im[z] = (T)0;
+    for (int c0 = 0; c0 < total; c0 += QEQ_SPB) {
+      const int nbat = min(QEQ_SPB, total - c0);
+      if (c0 > 0) __syncthreads();  // the previous batch is consumed
+      if (tid < nbat) {
+        const int c = c0 + tid;
+        int lo = 0, hi = nbins - 1;  // last bin whose first candidate is <= c
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (bin_pre[mid] <= c) lo = mid;
+          else hi = mid - 1;
+        }
+        const int t = bin_beg[lo] + (c - bin_pre[lo]);
+        const int sp = spec[t];
+        unsigned mask = 0;
+        if ((sp >> 1) == cm) {
+          const int bs = base[t];
+          const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
+          int o[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {  // stencil start relative to the brick, in [0, K)
+            int v = f[d] - (P - 1) - B.x0[d];
+            if (v < 0) v += S.K[d];
+            if (v < 0) v += S.K[d];
+            o[d] = v;
+          }
+          const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
+          const unsigned xm = stencil_rows<P>(o[0], K0, B.ext[0]);
+          const unsigned ym = stencil_rows<P>(o[1], K1, B.ext[1]);
+          const unsigned zm = stencil_rows<P>(o[2], K2, B.ext[2]);
+#pragma unroll
+          for (int l = 0; l < QEQ_BRICK; ++l) {
+            int j = l - o[2];
+            if (j < 0) j += K2;
+            if (j >= K2) j -= K2;
+            R.wz[tid][l] = ((zm >> l) & 1u) ? wt[2 * QEQ_MAXP + P - 1 - j] : (T)0;
+          }
+          const T q = (T)x[t];
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            R.wx[tid][j] = q * wt[P - 1 - j];
+            R.wy[tid][j] = wt[QEQ_MAXP + P - 1 - j];
+          }
+          if (zm) mask = xm | (ym << 16);
+          R.off[tid] = o[0] | (o[1] << 10) | ((sp & 1) << 20);
+        }
+        R.mask[tid] = mask;
+      }
+      __syncthreads();
+      // every thread adds its row's share, atom after atom (two at a time)
+      for (int i = 0; i < nbat; i += 2) {
+        T r[2] = {(T)0, (T)0};
+        int part[2] = {0, 0};
+        bool act[2] = {false, false};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = i + u;
+          if (k < nbat) {
+            const unsigned m = R.mask[k];
+            act[u] = ((m >> lx) & 1u) && ((m >> (16 + ly)) & 1u);
+            if (act[u]) {
+              const int off = R.off[k];
+              int jx = lx - (off & 1023);
+              if (jx < 0) jx += K0;
+              int jy = ly - ((off >> 10) & 1023);
+              if (jy < 0) jy += K1;
+              r[u] = R.wx[k][jx] * R.wy[k][jy];
+              part[u] = (off >> 20) & 1;
             }
           }
         }
-    __syncthreads();
-    V* mg = mesh + S.mesh_off + (int64_t)cm * S.M;
-    const int bsz = QEQ_BRICK * QEQ_BRICK * QEQ_BRICK;
-    for (int i = threadIdx.x; i < bsz; i += blockDim.x) {
-      int lz = i % QEQ_BRICK, ly = (i / QEQ_BRICK) % QEQ_BRICK, lx = i / (QEQ_BRICK * QEQ_BRICK);
-      if (lx >= B.ext[0] || ly >= B.ext[1] || lz >= B.ext[2]) continue;
-      int o = (lx * QEQ_BRICK + ly) * QEQ_RS + lz;
-      V v = {acc[o], acc[psz + o]};
-      mg[((int64_t)(B.x0[0] + lx) * S.K[1] + (B.x0[1] + ly)) * S.K[2] + (B.x0[2] + lz)] = v;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (!act[u]) continue;
+          const T* wz = R.wz[i + u];
+          if (part[u]) {
+#pragma unroll
+            for (int z = 0; z < QEQ_BRICK; ++z) im[z] += r[u] * wz[z];
+          } else {
+#pragma unroll
+            for (int z = 0; z < QEQ_BRICK; ++z) re[z] += r[u] * wz[z];
+          }
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    if (lx < B.ext[0] && ly < B.ext[1]) {
+      V* mg = mesh + S.mesh_off + (int64_t)cm * S.M +
+              ((int64_t)(B.x0[0] + lx) * K1 + (B.x0[1] + ly)) * K2 + B.x0[2];
+#pragma unroll
+      for (int z = 0; z < QEQ_BRICK; ++z)
+        if (z < B.ext[2]) mg[z] = V{re[z], im[z]};
+    }
   }
 }
 
@@ -527,8 +629,12 @@ __global__ void __launch_bounds__(256) k_gather_direct(
   const int jz = lane & 7, rsub = lane >> 3;
   const T* vals = pair_vals<T>(v64, v32);
   double blk = 0.0;
-  // this CTA's share of the chunk: atoms begin + sub*nw + w, stepping split*nw
-  for (int64_t t = ch.begin + (int64_t)sub * nw + w; t < ch.end; t += (int64_t)split * nw) {
+  // this CTA's share of the chunk: a contiguous run of atoms, so that the CTAs in
+  // flight (launched in order) read a compact part of the mesh and the stencil
+  // halos shared by neighbouring runs are still in L2
+  const int64_t len = (ch.end - ch.begin + split - 1) / split;
+  const int64_t lo = ch.begin + (int64_t)sub * len, hi = min(ch.end, lo + len);
+  for (int64_t t = lo + w; t < hi; t += nw) {
     const int sp = spec[t];
     const int part_ = sp & 1;
     const V* mg = mesh + S.mesh_off + (int64_t)(sp >> 1) * S.M;
@@ -788,8 +894,7 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   QEQ_CUDA_TRY(mark());
   // stage 1: spreading
   {
-    size_t sm = (size_t)2 * QEQ_BRICK * QEQ_BRICK * QEQ_RS * sizeof(T);
-    k_spread<T, P><<<Pl->total_bricks, 256, sm, s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
+    k_spread<T, P><<<Pl->total_bricks, 256, sizeof(SpreadRecs<T, P>), s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
                                                       Pl->d_spec, x, Pl->d_sc, use_active, mesh);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
@@ -834,7 +939,8 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
 template <typename T, int P>
 cudaError_t set_smem_attrs() {
   const int big = 200 * 1024;
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(SpreadRecs<T, P>)));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));

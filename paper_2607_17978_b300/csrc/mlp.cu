@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "neighbors.cuh"
 #include "qeq_internal.cuh"
 
 namespace {
@@ -64,70 +65,60 @@ __device__ __forceinline__ void mma_16x8(float* c, const __nv_bfloat16* A, int s
 }
 
 // ---------------------------------------------------------------- descriptors
+// One warp per atom: the lanes take the candidate neighbours of the walk, each
+// accumulates its share of the 24 radial sums, and a fixed shuffle tree adds the
+// lanes' shares (deterministic).
 template <bool SORTED>
-__global__ void k_features(const StructDev* __restrict__ st, const int* __restrict__ sorted_struct,
-                           const int* __restrict__ bin_start, const int* __restrict__ base,
-                           const int* __restrict__ spec, const double* __restrict__ posc,
-                           const double* __restrict__ chis, const double* __restrict__ Js,
-                           const int* __restrict__ perm, int64_t n, float* __restrict__ feat) {
-  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n) return;
+__global__ void __launch_bounds__(256) k_features(const StructDev* __restrict__ st,
+                                                  const int* __restrict__ sorted_struct,
+                                                  const int* __restrict__ bin_start, const int* __restrict__ base,
+                                                  const int* __restrict__ spec, const double* __restrict__ posc,
+                                                  const double* __restrict__ chis, const double* __restrict__ Js,
+                                                  const int* __restrict__ perm, int64_t n, float* __restrict__ feat) {
+  __shared__ NbrWarpSmem ws[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t a = (int64_t)blockIdx.x * 8 + w;
+  if (a >= n) return;  // whole warp
   const StructDev& S = st[sorted_struct[a]];
   const float RC = QEQ_MLP_RCUT, ETA = 2.0f;
   float G[24];
 #pragma unroll
   for (int k = 0; k < 24; ++k) G[k] = 0.f;
-  int bs = base[a];
-  int bb[3] = {(bs & 1023) / QEQ_BIN, ((bs >> 10) & 1023) / QEQ_BIN, ((bs >> 20) & 1023) / QEQ_BIN};
-  double ra[3] = {posc[3 * a], posc[3 * a + 1], posc[3 * a + 2]};
+  const int bs = base[a];
+  const int bb[3] = {(bs & 1023) / QEQ_BIN, ((bs >> 10) & 1023) / QEQ_BIN, ((bs >> 20) & 1023) / QEQ_BIN};
+  const double ra0 = posc[3 * a], ra1 = posc[3 * a + 1], ra2 = posc[3 * a + 2];
   const double rc2 = (double)RC * RC;
-  const int R[3] = {S.feat_range[0], S.feat_range[1], S.feat_range[2]};  // bins reaching R_C
-  for (int d0 = -R[0]; d0 <= R[0]; ++d0) {
-    int c0 = bb[0] + d0;
-    int s0 = (int)floor((double)c0 / S.nb[0]);
-    c0 -= s0 * S.nb[0];
-    for (int d1 = -R[1]; d1 <= R[1]; ++d1) {
-      int c1 = bb[1] + d1;
-      int s1 = (int)floor((double)c1 / S.nb[1]);
-      c1 -= s1 * S.nb[1];
-      for (int d2 = -R[2]; d2 <= R[2]; ++d2) {
-        int c2 = bb[2] + d2;
-        int s2 = (int)floor((double)c2 / S.nb[2]);
-        c2 -= s2 * S.nb[2];
-        int gbin = S.bin_off + (c0 * S.nb[1] + c1) * S.nb[2] + c2;
-        double sh[3];
-        for (int d = 0; d < 3; ++d) sh[d] = s0 * S.h[d] + s1 * S.h[3 + d] + s2 * S.h[6 + d];
-        bool zero_shift = (s0 == 0 && s1 == 0 && s2 == 0);
-        for (int t = bin_start[gbin]; t < bin_start[gbin + 1]; ++t) {
-          if (zero_shift && t == a) continue;
-          double dx = posc[3 * t] + sh[0] - ra[0], dy = posc[3 * t + 1] + sh[1] - ra[1],
-                 dz = posc[3 * t + 2] + sh[2] - ra[2];
-          double r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 >= rc2) continue;
-          float r = (float)sqrt(r2);
-          float fc = 0.5f * (cospif(r / RC) + 1.0f);
-          float cj = (float)chis[t];
+  warp_neighbour_walk(S, bb, S.feat_range, bin_start, ws[w], [&](bool valid, int t, const double* sh, bool zero) {
+    if (!valid || (zero && t == a)) return;
+    const double dx = posc[3 * t] + sh[0] - ra0, dy = posc[3 * t + 1] + sh[1] - ra1,
+                 dz = posc[3 * t + 2] + sh[2] - ra2;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) return;
+    const float r = (float)sqrt(r2);
+    const float fc = 0.5f * (cospif(r / RC) + 1.0f);
+    const float cj = (float)chis[t];
 #pragma unroll
-          for (int mu = 0; mu < 12; ++mu) {
-            float dr = r - (0.5f + 0.5f * mu);
-            float g = __expf(-ETA * dr * dr) * fc;
-            G[mu] += g;
-            G[12 + mu] += cj * g;
-          }
-        }
-      }
+    for (int mu = 0; mu < 12; ++mu) {
+      const float dr = r - (0.5f + 0.5f * mu);
+      const float g = __expf(-ETA * dr * dr) * fc;
+      G[mu] += g;
+      G[12 + mu] += cj * g;
     }
-  }
-  int64_t o = SORTED ? a : perm[a];
+  });
+#pragma unroll
+  for (int k = 0; k < 24; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) G[k] += __shfl_xor_sync(0xffffffffu, G[k], o);
+  const int64_t o = SORTED ? a : perm[a];
   float* f = feat + o * NF;
+  float v = 0.f;
 #pragma unroll
-  for (int k = 0; k < 24; ++k) f[k] = G[k];
-  int sp = spec[a];
-  f[24] = (float)chis[a];
-  f[25] = (float)Js[a];
-  f[26] = (float)S.sigma_s[sp];
-#pragma unroll
-  for (int k = 27; k < NF; ++k) f[k] = 0.f;
+  for (int k = 0; k < 24; ++k)
+    if (lane == k) v = G[k];
+  if (lane == 24) v = (float)chis[a];
+  if (lane == 25) v = (float)Js[a];
+  if (lane == 26) v = (float)S.sigma_s[spec[a]];
+  if (lane < NF) f[lane] = v;
 }
 
 // ---------------------------------------------------------------- network
@@ -509,9 +500,9 @@ extern "C" qeq_status qeq_features(qeq_plan P, const double* d_pos, const int32_
   if (!P || !d_pos || !d_species || !d_chi || !d_J || !d_feat) return QEQ_ERR_INVALID;
   if (cudaSetDevice(P->device) != cudaSuccess) return QEQ_ERR_CUDA;
   if (launch_prepare_atoms(P, d_pos, d_species, d_chi, d_J, 0) != cudaSuccess) return QEQ_ERR_CUDA;
-  int nb = (int)((P->n_atoms + 127) / 128);
+  int nb = (int)((P->n_atoms + 7) / 8);  // one warp per atom
   count_launch(P);
-  k_features<false><<<nb, 128, 0, P->stream>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc,
+  k_features<false><<<nb, 256, 0, P->stream>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc,
                                                 P->d_chi, P->d_J, P->d_perm, P->n_atoms, d_feat);
   if (cudaGetLastError() != cudaSuccess) return QEQ_ERR_CUDA;
   if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEQ_ERR_CUDA;
@@ -543,9 +534,9 @@ extern "C" qeq_status qeq_plan_set_warm_start(qeq_plan P, qeq_mlp m) {
 cudaError_t launch_mlp_warm_start(qeq_plan_s* P, double* d_q_sorted) {
   qeq_mlp_s* m = P->mlp;
   cudaStream_t s = P->stream;
-  int nb = (int)((P->n_atoms + 127) / 128);
+  int nb = (int)((P->n_atoms + 7) / 8);  // one warp per atom
   count_launch(P, 3);
-  k_features<true><<<nb, 128, 0, s>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc, P->d_chi,
+  k_features<true><<<nb, 256, 0, s>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc, P->d_chi,
                                        P->d_J, P->d_perm, P->n_atoms, P->d_feat);
   int ntiles = (int)((P->n_atoms + TILE - 1) / TILE);
   k_mlp<false><<<ntiles, 128, mlp_smem(), s>>>(P->d_feat, P->d_spec, P->n_atoms, m->n_species, m->d_params,

@@ -554,8 +554,9 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->total_mesh = mesh_off;
   P->pair_cap = pair_cap;
   P->n_chunks = (int)chunks.size();
-  // enough gather CTAs to fill the GPU (about 4 per SM of a 148-SM part) when chunks are few
-  P->gather_split = std::max(1, std::min(16, (592 + P->n_chunks - 1) / std::max(1, P->n_chunks)));
+  // gather CTAs: runs of at most 64 atoms (8 per chunk), more when chunks are too
+  // few to fill the GPU (about 4 CTAs per SM of a 148-SM part)
+  P->gather_split = std::max(8, std::min(16, (592 + P->n_chunks - 1) / std::max(1, P->n_chunks)));
   P->n_zitems = (int)zit.size();
   P->n_yitems = (int)yit.size();
   P->n_xitems = (int)xit.size();

@@ -5,6 +5,7 @@
 // the real-space pair list of the Ewald split (SI "Ewald Summation").
 #include <math.h>
 
+#include "neighbors.cuh"
 #include "qeq_internal.cuh"
 
 namespace {
@@ -205,80 +206,71 @@ __global__ void k_gather_sorted(const StructDev* __restrict__ st, const int* __r
 }
 
 // ---------------------------------------------------------------- real-space pairs
-// Visit every (j, image) with |r_j + n h - r_a| < r_cut over the bins within
-// rs_range of atom a's bin; count (fill == 0) or write the CSR row (fill == 1).
+// Real-space pairs of atom a (one warp per atom): every (j, image) with
+// |r_j + n h - r_a| < r_cut whose species pair has a real-space term; count
+// (FILL == 0) or write the CSR row (FILL == 1) in the walk's candidate order.
 template <int FILL>
-__global__ void k_pairs(const StructDev* __restrict__ st, const int* __restrict__ bin_struct,
-                        const int* __restrict__ bin_start, const int* __restrict__ perm_unused, int64_t n,
-                        const int* __restrict__ base, const int* __restrict__ spec,
-                        const double* __restrict__ posc, const int* __restrict__ sorted_bin_of_atom_unused,
-                        int* __restrict__ row_cnt, const int64_t* __restrict__ row, int64_t cap,
-                        int* __restrict__ col, double* __restrict__ val64, float* __restrict__ val32,
-                        const int* __restrict__ atom_struct_sorted_unused, int* __restrict__ err, double k_e,
-                        const int* __restrict__ sorted_struct) {
-  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n) return;
+__global__ void __launch_bounds__(256) k_pairs(const StructDev* __restrict__ st, const int* __restrict__ bin_start,
+                                               int64_t n, const int* __restrict__ base, const int* __restrict__ spec,
+                                               const double* __restrict__ posc, int* __restrict__ row_cnt,
+                                               const int64_t* __restrict__ row, int64_t cap, int* __restrict__ col,
+                                               double* __restrict__ val64, float* __restrict__ val32,
+                                               int* __restrict__ err, double k_e,
+                                               const int* __restrict__ sorted_struct) {
+  __shared__ NbrWarpSmem ws[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t a = (int64_t)blockIdx.x * 8 + w;
+  if (a >= n) return;  // whole warp
   const StructDev& S = st[sorted_struct[a]];
-  int sa = spec[a];
-  uint32_t mask = S.narrow[sa];
+  const int sa = spec[a];
+  const uint32_t mask = S.narrow[sa];
   if (!S.any_narrow || mask == 0) {
-    if (!FILL) row_cnt[a] = 0;
+    if (!FILL && lane == 0) row_cnt[a] = 0;
     return;
   }
-  int bs = base[a];
-  int bb[3] = {(bs & 1023) / QEQ_BIN, ((bs >> 10) & 1023) / QEQ_BIN, ((bs >> 20) & 1023) / QEQ_BIN};
-  double ra[3] = {posc[3 * a], posc[3 * a + 1], posc[3 * a + 2]};
-  double rc2 = S.r_cut * S.r_cut;
+  const int bs = base[a];
+  const int bb[3] = {(bs & 1023) / QEQ_BIN, ((bs >> 10) & 1023) / QEQ_BIN, ((bs >> 20) & 1023) / QEQ_BIN};
+  const double ra0 = posc[3 * a], ra1 = posc[3 * a + 1], ra2 = posc[3 * a + 2];
+  const double rc2 = S.r_cut * S.r_cut;
+  const int64_t out = FILL ? row[a] : 0;
   int cnt = 0;
-  int64_t out = FILL ? row[a] : 0;
-  for (int d0 = -S.rs_range[0]; d0 <= S.rs_range[0]; ++d0) {
-    int c0 = bb[0] + d0;
-    int s0 = (int)floor((double)c0 / S.nb[0]);
-    c0 -= s0 * S.nb[0];
-    for (int d1 = -S.rs_range[1]; d1 <= S.rs_range[1]; ++d1) {
-      int c1 = bb[1] + d1;
-      int s1 = (int)floor((double)c1 / S.nb[1]);
-      c1 -= s1 * S.nb[1];
-      for (int d2 = -S.rs_range[2]; d2 <= S.rs_range[2]; ++d2) {
-        int c2 = bb[2] + d2;
-        int s2 = (int)floor((double)c2 / S.nb[2]);
-        c2 -= s2 * S.nb[2];
-        int g = S.bin_off + (c0 * S.nb[1] + c1) * S.nb[2] + c2;
-        double sh[3];
-        for (int d = 0; d < 3; ++d) sh[d] = s0 * S.h[d] + s1 * S.h[3 + d] + s2 * S.h[6 + d];
-        bool zero_shift = (s0 == 0 && s1 == 0 && s2 == 0);
-        int t1 = bin_start[g + 1];
-        for (int t = bin_start[g]; t < t1; ++t) {
-          int sj = spec[t];
-          if (!((mask >> sj) & 1u)) continue;
-          if (zero_shift && t == a) continue;
-          double dx = posc[3 * t] + sh[0] - ra[0];
-          double dy = posc[3 * t + 1] + sh[1] - ra[1];
-          double dz = posc[3 * t + 2] + sh[2] - ra[2];
-          double r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 >= rc2) continue;
-          if (FILL) {
-            if (out + cnt < cap) {
-              double r = sqrt(r2);
-              int k = sa * QEQ_MAX_SPECIES + sj;
-              double v;
-              if (r > 1e-12)
-                v = (erfc(r * S.inv_sw[k]) - erfc(r * S.inv_sg[k])) / r;
-              else  // coincident atoms: the r -> 0 limit
-                v = (2.0 / sqrt(M_PI)) * (S.inv_sg[k] - S.inv_sw[k]);
-              v *= k_e;
-              col[out + cnt] = t;
-              val64[out + cnt] = v;
-              val32[out + cnt] = (float)v;
-            }
-          }
-          ++cnt;
-        }
+  warp_neighbour_walk(S, bb, S.rs_range, bin_start, ws[w], [&](bool valid, int t, const double* sh, bool zero) {
+    bool acc = false;
+    double r2 = 0.0;
+    int sj = 0;
+    if (valid) {
+      sj = spec[t];
+      if (((mask >> sj) & 1u) && !(zero && t == a)) {
+        const double dx = posc[3 * t] + sh[0] - ra0;
+        const double dy = posc[3 * t + 1] + sh[1] - ra1;
+        const double dz = posc[3 * t + 2] + sh[2] - ra2;
+        r2 = dx * dx + dy * dy + dz * dz;
+        acc = r2 < rc2;
       }
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, acc);
+    if (FILL && acc) {
+      const int64_t o = out + cnt + __popc(bal & ((1u << lane) - 1u));
+      if (o < cap) {
+        const double r = sqrt(r2);
+        const int k = sa * QEQ_MAX_SPECIES + sj;
+        double v;
+        if (r > 1e-12)
+          v = (erfc(r * S.inv_sw[k]) - erfc(r * S.inv_sg[k])) / r;
+        else  // coincident atoms: the r -> 0 limit
+          v = (2.0 / sqrt(M_PI)) * (S.inv_sg[k] - S.inv_sw[k]);
+        v *= k_e;
+        col[o] = t;
+        val64[o] = v;
+        val32[o] = (float)v;
+      }
+    }
+    cnt += __popc(bal);
+  });
+  if (lane == 0) {
+    if (!FILL) row_cnt[a] = cnt;
+    if (FILL && out + cnt > cap) atomicOr(err, ERRBIT_PAIRCAP);
   }
-  if (!FILL) row_cnt[a] = cnt;
-  if (FILL && out + cnt > cap) atomicOr(err, ERRBIT_PAIRCAP);
 }
 
 __global__ void k_sorted_struct(const int* __restrict__ atom_struct, const int* __restrict__ perm, int64_t n,
@@ -310,14 +302,14 @@ cudaError_t launch_prepare_atoms(qeq_plan_s* P, const double* pos, const int32_t
                                       P->d_posc);
   QEQ_CUDA_TRY(cudaGetLastError());
   if (need_pairs) {
-    k_pairs<0><<<nb, 256, 0, s>>>(P->d_st, P->d_bin_struct, P->d_bin_start, nullptr, n, P->d_base, P->d_spec,
-                                   P->d_posc, nullptr, P->d_row_cnt, nullptr, 0, nullptr, nullptr, nullptr,
-                                   nullptr, P->d_err, P->desc.coulomb_k, P->d_key);
+    const int nbw = (int)((n + 7) / 8);  // one warp per atom
+    k_pairs<0><<<nbw, 256, 0, s>>>(P->d_st, P->d_bin_start, n, P->d_base, P->d_spec, P->d_posc, P->d_row_cnt,
+                                    nullptr, 0, nullptr, nullptr, nullptr, P->d_err, P->desc.coulomb_k, P->d_key);
     QEQ_CUDA_TRY(cudaGetLastError());
     QEQ_CUDA_TRY(exclusive_scan<int64_t>(P->d_row_cnt, n, P->d_row, (int64_t*)P->d_scan_tmp, s));
-    k_pairs<1><<<nb, 256, 0, s>>>(P->d_st, P->d_bin_struct, P->d_bin_start, nullptr, n, P->d_base, P->d_spec,
-                                   P->d_posc, nullptr, nullptr, P->d_row, P->pair_cap, P->d_col, P->d_val64,
-                                   P->d_val32, nullptr, P->d_err, P->desc.coulomb_k, P->d_key);
+    k_pairs<1><<<nbw, 256, 0, s>>>(P->d_st, P->d_bin_start, n, P->d_base, P->d_spec, P->d_posc, nullptr,
+                                    P->d_row, P->pair_cap, P->d_col, P->d_val64, P->d_val32, P->d_err,
+                                    P->desc.coulomb_k, P->d_key);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   P->have_atoms = true;

@@ -12,7 +12,6 @@
 #define QEQ_MAX_SPECIES 8
 #define QEQ_BIN 8          // mesh points per edge of an atom bin (sorting, real-space search)
 #define QEQ_BRICK 16       // mesh points per edge of a spread / gather brick (2 x 2 x 2 bins)
-#define QEQ_RS 24          // shared-memory z-row stride of a brick (conflict-free for 4 rows x 8 z)
 #define QEQ_MAXP 8         // largest supported B-spline order
 #define QEQ_MAX_STAGES 16  // radix stages of one FFT length
 #define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
@@ -97,6 +96,7 @@ struct PcgScalars {
   double r_sum, r_sq, r_max, r_min;   // residual statistics of the current r
   double tol_inf;     // stop threshold on max |P r|
   double tol_l2;      // optional stop threshold on ||P r||_2 (0 = off)
+  double inner;       // factor on both thresholds for the iteration's own (recurrence) residual
   double j_min;
   double q_tot;
   double chi_p2;      // ||P chi||_2^2

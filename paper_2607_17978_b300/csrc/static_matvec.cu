@@ -405,7 +405,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.d_Ap = cv.take<double>(N);
   P.d_mesh = cv.take<double2>((size_t)P.total_mesh);
   P.d_mesh2 = cv.take<double2>((size_t)P.total_mesh);
-  P.gather_split = std::max(1, std::min(16, (592 + nchunks - 1) / nchunks));
+  P.gather_split = std::max(8, std::min(16, (592 + nchunks - 1) / nchunks));
   P.d_part = cv.take<double>((size_t)nchunks * QEQ_MAX_SPECIES * 2 + std::max(nbins, nchunks * 16) + 64);
   P.d_counter = cv.take<int>(4);
   P.d_sc = cv.take<PcgScalars>(1);
