@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "qeq_internal.cuh"
 
@@ -128,7 +129,125 @@ __device__ __forceinline__ void dft5(V* v, T sgn) {
   v[3] = csub(r2, i2);
 }
 
-// One Stockham radix-R stage over all lines in shared memory.
+// ------------------------------------------------------------------ composite register butterflies
+// cos and sin of 2 pi m / R at compile time (quadrant reduction, Taylor series
+// on [0, pi/2]), for the internal twiddles of the composite radices.
+__host__ __device__ constexpr double cx_poly_cos(double x) {
+  double x2 = x * x, t = 1.0, s = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    t *= -x2 / ((2.0 * k - 1.0) * (2.0 * k));
+    s += t;
+  }
+  return s;
+}
+__host__ __device__ constexpr double cx_poly_sin(double x) {
+  double x2 = x * x, t = x, s = x;
+  for (int k = 1; k < 14; ++k) {
+    t *= -x2 / ((2.0 * k) * (2.0 * k + 1.0));
+    s += t;
+  }
+  return s;
+}
+__host__ __device__ constexpr double cx_cos2pi(int m, int R) {
+  const int q = (4 * m) / R, rem = 4 * m - q * R;  // 2 pi m / R = q pi/2 + phi
+  const double phi = 1.57079632679489661923 * rem / R;
+  const double c = cx_poly_cos(phi), s = cx_poly_sin(phi);
+  return q == 0 ? c : (q == 1 ? -s : (q == 2 ? -c : s));
+}
+__host__ __device__ constexpr double cx_sin2pi(int m, int R) {
+  const int q = (4 * m) / R, rem = 4 * m - q * R;
+  const double phi = 1.57079632679489661923 * rem / R;
+  const double c = cx_poly_cos(phi), s = cx_poly_sin(phi);
+  return q == 0 ? s : (q == 1 ? c : (q == 2 ? -s : -c));
+}
+
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// a * exp(sgn * 2 pi i M / R) with the constant folded in
+template <typename T, typename V, int M, int R>
+__device__ __forceinline__ V tw_const(V a, T sgn) {
+  constexpr int m = M % R;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (4 * m == R) {
+    return cmul_i<V, T>(a, sgn);
+  } else if constexpr (2 * m == R) {
+    return V{-a.x, -a.y};
+  } else if constexpr (4 * m == 3 * R) {
+    return cmul_i<V, T>(a, -sgn);
+  } else {
+    constexpr double c = cx_cos2pi(m, R), sn = cx_sin2pi(m, R);
+    const T ss = sgn * (T)sn;
+    return V{a.x * (T)c - a.y * ss, a.x * ss + a.y * (T)c};
+  }
+}
+
+template <typename T, typename V, int R>
+struct DftR;
+template <typename T, typename V>
+struct DftR<T, V, 2> {
+  static __device__ __forceinline__ void run(V* v, T) { dft2<T, V>(v); }
+};
+template <typename T, typename V>
+struct DftR<T, V, 3> {
+  static __device__ __forceinline__ void run(V* v, T sgn) { dft3<T, V>(v, sgn); }
+};
+template <typename T, typename V>
+struct DftR<T, V, 4> {
+  static __device__ __forceinline__ void run(V* v, T sgn) { dft4<T, V>(v, sgn); }
+};
+template <typename T, typename V>
+struct DftR<T, V, 5> {
+  static __device__ __forceinline__ void run(V* v, T sgn) { dft5<T, V>(v, sgn); }
+};
+
+// R = A*B point DFT in registers (Cooley-Tukey): inputs n = B n1 + n2, outputs
+// k = k1 + A k2; A-point DFTs over n1, internal twiddles W_R^(n2 k1), B-point
+// DFTs over n2.
+template <typename T, typename V, int A, int B>
+__device__ __forceinline__ void dft_ab(V* v, T sgn) {
+  constexpr int R = A * B;
+  V y[R];
+  static_for<B>([&](auto n2c) {
+    constexpr int n2 = decltype(n2c)::value;
+    V t[A];
+    static_for<A>([&](auto n1c) { t[decltype(n1c)::value] = v[B * decltype(n1c)::value + n2]; });
+    DftR<T, V, A>::run(t, sgn);
+    static_for<A>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      y[n2 * A + k1] = tw_const<T, V, n2 * k1, R>(t[k1], sgn);
+    });
+  });
+  static_for<A>([&](auto k1c) {
+    constexpr int k1 = decltype(k1c)::value;
+    V u[B];
+    static_for<B>([&](auto n2c) { u[decltype(n2c)::value] = y[decltype(n2c)::value * A + k1]; });
+    DftR<T, V, B>::run(u, sgn);
+    static_for<B>([&](auto k2c) { v[k1 + A * decltype(k2c)::value] = u[decltype(k2c)::value]; });
+  });
+}
+#define QEQ_COMPOSITE_DFT(R, A, B)                                                        \
+  template <typename T, typename V>                                                       \
+  struct DftR<T, V, R> {                                                                  \
+    static __device__ __forceinline__ void run(V* v, T sgn) { dft_ab<T, V, A, B>(v, sgn); } \
+  };
+QEQ_COMPOSITE_DFT(6, 2, 3)
+QEQ_COMPOSITE_DFT(8, 2, 4)
+QEQ_COMPOSITE_DFT(9, 3, 3)
+QEQ_COMPOSITE_DFT(10, 2, 5)
+QEQ_COMPOSITE_DFT(12, 3, 4)
+QEQ_COMPOSITE_DFT(15, 3, 5)
+QEQ_COMPOSITE_DFT(16, 4, 4)
+#undef QEQ_COMPOSITE_DFT
+
+// One Stockham radix-R stage over all lines in shared memory (padded layout).
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(const typename C2<T>::t* __restrict__ src,
                                                typename C2<T>::t* __restrict__ dst, int nlines, int K, int ld, int Ns,
@@ -147,20 +266,19 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t* __restri
     V* d = dst + line * ld;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
+    for (int r = 0; r < R; ++r) v[r] = s[fft_pidx(j + r * nbf)];
+    if (Ns > 1) {  // the first stage has k = 0: all its twiddles are 1
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      V t = tw[r * k * tws];
-      t.y *= -sgn;  // table holds exp(-2 pi i m/K); sgn = -1 keeps it, +1 conjugates
-      v[r] = cmul(v[r], t);
+      for (int r = 1; r < R; ++r) {
+        V t = tw[r * k * tws];
+        t.y *= -sgn;  // table holds exp(-2 pi i m/K); sgn = -1 keeps it, +1 conjugates
+        v[r] = cmul(v[r], t);
+      }
     }
-    if (R == 2) dft2<T, V>(v);
-    if (R == 3) dft3<T, V>(v, sgn);
-    if (R == 4) dft4<T, V>(v, sgn);
-    if (R == 5) dft5<T, V>(v, sgn);
+    DftR<T, V, R>::run(v, sgn);
     const int o = jq * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) d[fft_pidx(o + r * Ns)] = v[r];
   }
 }
 
@@ -170,15 +288,27 @@ __device__ typename C2<T>::t* fft_lines(typename C2<T>::t* a, typename C2<T>::t*
                                         const FftPlanDev& fp, const typename C2<T>::t* tw, T sgn) {
   int Ns = 1;
   for (int st = 0; st < fp.nst; ++st) {
-    int R = fp.radix[st];
-    if (R == 4)
-      stockham_stage<T, 4>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
-    else if (R == 2)
-      stockham_stage<T, 2>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
-    else if (R == 3)
-      stockham_stage<T, 3>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
-    else
-      stockham_stage<T, 5>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]);
+    const int R = fp.radix[st];
+    switch (R) {
+#define QEQ_STAGE(RR) \
+  case RR:            \
+    stockham_stage<T, RR>(a, b, nlines, K, ld, Ns, tw, sgn, fp.nbf[st], fp.ns[st]); \
+    break;
+      QEQ_STAGE(2)
+      QEQ_STAGE(3)
+      QEQ_STAGE(4)
+      QEQ_STAGE(5)
+      QEQ_STAGE(6)
+      QEQ_STAGE(8)
+      QEQ_STAGE(9)
+      QEQ_STAGE(10)
+      QEQ_STAGE(12)
+      QEQ_STAGE(15)
+      QEQ_STAGE(16)
+#undef QEQ_STAGE
+      default:
+        break;
+    }
     __syncthreads();
     typename C2<T>::t* t = a;
     a = b;
@@ -238,7 +368,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(const StructDev* __restrict__ 
     ib = (int64_t)it.z * K1 * K0 + it.w; ils = 1; ies = K0;
     ob = ((int64_t)it.w * K2 + it.z) * K1; ols = (int64_t)K2 * K1; oes = 1;
   }
-  const int ld = K + 1;  // padded shared line stride: transposed accesses spread over the banks
+  const int ld = fft_ld(K);  // padded shared lines: transposed accesses spread over the banks
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw_s = reinterpret_cast<V*>(smem_raw);
   V* a = tw_s + K;
@@ -249,12 +379,12 @@ __global__ void __launch_bounds__(256) k_fft_pass(const StructDev* __restrict__ 
   if (ies == 1) {
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
       int l = (int)fdiv((uint32_t)idx, fp.k), e = idx - l * K;
-      cp_async_elem(a + l * ld + e, g + l * ils + e);
+      cp_async_elem(a + l * ld + fft_pidx(e), g + l * ils + e);
     }
   } else {
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
       int e = (int)fdiv((uint32_t)idx, fnl), l = idx - e * nl;
-      cp_async_elem(a + l * ld + e, g + e * ies + l);
+      cp_async_elem(a + l * ld + fft_pidx(e), g + e * ies + l);
     }
   }
   cp_async_wait_all();
@@ -264,22 +394,51 @@ __global__ void __launch_bounds__(256) k_fft_pass(const StructDev* __restrict__ 
   if (oes == 1) {
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
       int l = (int)fdiv((uint32_t)idx, fp.k), e = idx - l * K;
-      o[l * ols + e] = res[l * ld + e];
+      o[l * ols + e] = res[l * ld + fft_pidx(e)];
     }
   } else {
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
       int e = (int)fdiv((uint32_t)idx, fnl), l = idx - e * nl;
-      o[e * oes + l] = res[l * ld + e];
+      o[e * oes + l] = res[l * ld + fft_pidx(e)];
     }
   }
+}
+
+// exp2 and 1/x in the mesh precision: the FP32 path uses the hardware
+// approximations (ex2.approx: relative error ~2^-22 plus the argument's own
+// rounding, which only matters where the Gaussian is already below ~1e-8 of its
+// peak; rcp with round-to-nearest), the FP64 path the exact library calls.
+template <typename T>
+__device__ __forceinline__ T exp2_mesh(T x);
+template <>
+__device__ __forceinline__ float exp2_mesh<float>(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+template <>
+__device__ __forceinline__ double exp2_mesh<double>(double x) {
+  return exp2(x);
+}
+template <typename T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ float recip<float>(float x) {
+  return __frcp_rn(x);
+}
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  return 1.0 / x;
 }
 
 // ------------------------------------------------------------------ x: FFT, reciprocal multiply, inverse FFT
 // Works in place on layout L2 [z][y][x], where every x line is contiguous.
 // An item holds pairs of lines (z, y) and (-z, -y): the reciprocal multiply
 // needs Z(m) and Z(-m) of every complex mesh to separate its two species.
-template <typename T, bool PRE>
-__global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
+// MAXS: most species of any structure of the plan (2: one complex mesh, the
+// common case, with small register use; 8: any).
+template <typename T, bool PRE, int MAXS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                               const int4* __restrict__ items, const int2* __restrict__ xpairs,
                               const T* __restrict__ bmod, const double2* __restrict__ tw64,
                               const float2* __restrict__ tw32, const PcgScalars* __restrict__ sc,
@@ -292,7 +451,7 @@ __global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict
   const int K = S.K[0], K1 = S.K[1], K2 = S.K[2];
   const int ncm = S.ncm, np = it.z;
   const int nslot = 2 * np * ncm;
-  const int ld = K + 1;
+  const int ld = fft_ld(K);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw_s = reinterpret_cast<V*>(smem_raw);
   V* a = tw_s + K;
@@ -305,70 +464,86 @@ __global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict
     int jab = (int)fdiv((uint32_t)slot, fncm), c = slot - jab * ncm;
     int2 pr = xpairs[it.y + (jab >> 1)];
     int l = (jab & 1) ? pr.y : pr.x;
-    cp_async_elem(a + slot * ld + e, mesh + S.mesh_off + (int64_t)c * S.M + (int64_t)l * K + e);
+    cp_async_elem(a + slot * ld + fft_pidx(e), mesh + S.mesh_off + (int64_t)c * S.M + (int64_t)l * K + e);
   }
   cp_async_wait_all();
   __syncthreads();
   V* R = fft_lines<T>(a, b, nslot, K, ld, fp, tw_s, (T)-1);
   V* other = (R == a) ? b : a;
-  // reciprocal multiply
+  // reciprocal multiply.  Per pair of lines the constant parts (the G(m) share of
+  // m1 b1 + m2 b2, and k_e 4 pi/V |b1(m1) b2(m2)|^2) are staged in shared memory;
+  // exponent factors are -w_st^2/2 log2(e), so each Gaussian is one exp2.
   const T* bm0 = bmod + S.bmod_off[0];
   const T* bm1 = bmod + S.bmod_off[1];
   const T* bm2 = bmod + S.bmod_off[2];
-  const T B0 = (T)S.B[0], B1 = (T)S.B[1], B2 = (T)S.B[2], B3 = (T)S.B[3], B4 = (T)S.B[4], B5 = (T)S.B[5],
-          B6 = (T)S.B[6], B7 = (T)S.B[7], B8 = (T)S.B[8];
+  const T B0 = (T)S.B[0], B1 = (T)S.B[1], B2 = (T)S.B[2];
   const T gpref = (T)S.green_pref;
+  __shared__ T hw2[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];
+  __shared__ T lineg[QEQ_XPAIRS_MAX][4];
+  for (int i = threadIdx.x; i < QEQ_MAX_SPECIES * QEQ_MAX_SPECIES; i += blockDim.x)
+    hw2[i] = (T)(-0.5 * 1.44269504088896340736 * S.w2[i]);
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    const int2 pr = xpairs[it.y + j];
+    const int mz = (int)fdiv((uint32_t)pr.x, fK1), my = pr.x - mz * K1;
+    const int c1 = (my <= K1 / 2) ? my : my - K1;
+    const int c2 = (mz <= K2 / 2) ? mz : mz - K2;
+    lineg[j][0] = (T)(c1 * S.B[3] + c2 * S.B[6]);
+    lineg[j][1] = (T)(c1 * S.B[4] + c2 * S.B[7]);
+    lineg[j][2] = (T)(c1 * S.B[5] + c2 * S.B[8]);
+    lineg[j][3] = gpref * bm1[my] * bm2[mz];
+  }
+  const T pre_beta = PRE ? (T)S.omega : (T)0;  // S.omega holds beta for the preconditioner
+  const T pre_s0 = PRE ? (T)sc[it.x].s0 : (T)0;
+  const int nspec = S.S;
+  __syncthreads();
   for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) {
-    int j = (int)fdiv((uint32_t)idx, fp.k), mx = idx - j * K;
-    int mmx = (mx == 0) ? 0 : K - mx;
-    int2 pr = xpairs[it.y + j];
-    int mz = (int)fdiv((uint32_t)pr.x, fK1), my = pr.x - mz * K1;
-    int c0 = (mx <= K / 2) ? mx : mx - K;
-    int c1 = (my <= K1 / 2) ? my : my - K1;
-    int c2 = (mz <= K2 / 2) ? mz : mz - K2;
-    T Gx = (T)c0 * B0 + (T)c1 * B3 + (T)c2 * B6;
-    T Gy = (T)c0 * B1 + (T)c1 * B4 + (T)c2 * B7;
-    T Gz = (T)c0 * B2 + (T)c1 * B5 + (T)c2 * B8;
-    T G2 = Gx * Gx + Gy * Gy + Gz * Gz;
-    T pref = (G2 > (T)0) ? gpref * bm0[mx] * bm1[my] * bm2[mz] / G2 : (T)0;
-    V Qh[QEQ_MAX_SPECIES];
+    const int j = (int)fdiv((uint32_t)idx, fp.k), mx = idx - j * K;
+    const int mmx = (mx == 0) ? 0 : K - mx;
+    const int c0 = (mx <= K / 2) ? mx : mx - K;
+    const T Gx = (T)c0 * B0 + lineg[j][0];
+    const T Gy = (T)c0 * B1 + lineg[j][1];
+    const T Gz = (T)c0 * B2 + lineg[j][2];
+    const T G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+    const T rG2 = (G2 > (T)0) ? recip<T>(G2) : (T)0;
+    const T pref = lineg[j][3] * bm0[mx] * rG2;  // G = 0 term dropped
+    V Qh[MAXS];
 #pragma unroll
-    for (int c = 0; c < QEQ_MAX_SPECIES / 2; ++c) {
+    for (int c = 0; c < MAXS / 2; ++c) {
       if (c >= ncm) break;
-      V za = R[((j * 2 + 0) * ncm + c) * ld + mx];
-      V zb = R[((j * 2 + 1) * ncm + c) * ld + mmx];
+      V za = R[((j * 2 + 0) * ncm + c) * ld + fft_pidx(mx)];
+      V zb = R[((j * 2 + 1) * ncm + c) * ld + fft_pidx(mmx)];
       // F[Q_2c] = (Z(m) + conj Z(-m))/2,  F[Q_2c+1] = (Z(m) - conj Z(-m))/(2i)
       Qh[2 * c] = {(T)0.5 * (za.x + zb.x), (T)0.5 * (za.y - zb.y)};
       Qh[2 * c + 1] = {(T)0.5 * (za.y + zb.y), (T)-0.5 * (za.x - zb.x)};
     }
 #pragma unroll
-    for (int c = 0; c < QEQ_MAX_SPECIES / 2; ++c) {
+    for (int c = 0; c < MAXS / 2; ++c) {
       if (c >= ncm) break;
       V p0 = {(T)0, (T)0}, p1 = {(T)0, (T)0};
       if (PRE) {
-        // Fourier preconditioner: h(m) = |b(m)|^2 g0 / (1 + s0 g0), g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2
-        if (pref != (T)0) {
-          T e = exp(-G2 * (T)(0.5 * S.w2[0]));
-          T g0 = gpref * e / G2;
-          T hm = (T)S.omega * pref * e / ((T)1 + (T)sc[it.x].s0 * g0);  // S.omega holds beta
-          p0.x = hm * Qh[0].x;
-          p0.y = hm * Qh[0].y;
-        }
-      } else if (pref != (T)0) {
-        for (int t = 0; t < S.S; ++t) {
-          T g0 = pref * exp(-G2 * (T)(0.5 * S.w2[(2 * c) * QEQ_MAX_SPECIES + t]));
+        // Fourier preconditioner: h(m) = beta |b(m)|^2 g0 / (1 + s0 g0), g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2
+        const T e = exp2_mesh<T>(G2 * hw2[0]);
+        const T g0 = gpref * e * rG2;
+        const T hm = pre_beta * pref * e * recip<T>((T)1 + pre_s0 * g0);
+        p0.x = hm * Qh[0].x;
+        p0.y = hm * Qh[0].y;
+      } else {
+#pragma unroll
+        for (int t = 0; t < MAXS; ++t) {
+          if (t >= nspec) break;
+          const T g0 = pref * exp2_mesh<T>(G2 * hw2[(2 * c) * QEQ_MAX_SPECIES + t]);
           p0.x += g0 * Qh[t].x;
           p0.y += g0 * Qh[t].y;
-          if (2 * c + 1 < S.S) {
-            T g1 = pref * exp(-G2 * (T)(0.5 * S.w2[(2 * c + 1) * QEQ_MAX_SPECIES + t]));
+          if (2 * c + 1 < nspec) {
+            const T g1 = pref * exp2_mesh<T>(G2 * hw2[(2 * c + 1) * QEQ_MAX_SPECIES + t]);
             p1.x += g1 * Qh[t].x;
             p1.y += g1 * Qh[t].y;
           }
         }
       }
       // W(m) = P_2c + i P_2c+1 ; W(-m) = conj(P_2c) + i conj(P_2c+1)
-      R[((j * 2 + 0) * ncm + c) * ld + mx] = {p0.x - p1.y, p0.y + p1.x};
-      R[((j * 2 + 1) * ncm + c) * ld + mmx] = {p0.x + p1.y, -p0.y + p1.x};
+      R[((j * 2 + 0) * ncm + c) * ld + fft_pidx(mx)] = {p0.x - p1.y, p0.y + p1.x};
+      R[((j * 2 + 1) * ncm + c) * ld + fft_pidx(mmx)] = {p0.x + p1.y, -p0.y + p1.x};
     }
   }
   __syncthreads();
@@ -379,7 +554,7 @@ __global__ void __launch_bounds__(256) k_fft_x_green(const StructDev* __restrict
     int2 pr = xpairs[it.y + (jab >> 1)];
     if ((jab & 1) && pr.y == pr.x) continue;  // self-paired line: written from its A copy
     int l = (jab & 1) ? pr.y : pr.x;
-    mesh[S.mesh_off + (int64_t)c * S.M + (int64_t)l * K + e] = res[slot * ld + e];
+    mesh[S.mesh_off + (int64_t)c * S.M + (int64_t)l * K + e] = res[slot * ld + fft_pidx(e)];
   }
 }
 
@@ -400,6 +575,18 @@ __device__ __forceinline__ Brick brick_of(const StructDev& S, int g) {
     B.ext[d] = min(QEQ_BRICK, S.K[d] - B.x0[d]);
   }
   return B;
+}
+
+// the matvec input in the mesh precision: the FP32 copy in mixed precision
+template <typename T>
+__device__ __forceinline__ T xval(const double* __restrict__ x, const float* __restrict__ x32, int64_t i);
+template <>
+__device__ __forceinline__ float xval<float>(const double*, const float* __restrict__ x32, int64_t i) {
+  return x32[i];
+}
+template <>
+__device__ __forceinline__ double xval<double>(const double* __restrict__ x, const float*, int64_t i) {
+  return x[i];
 }
 
 // ------------------------------------------------------------------ spreading
@@ -440,7 +627,8 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
                          const int* __restrict__ bin_start, const int* __restrict__ base,
                          const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ x,
-                         const PcgScalars* __restrict__ sc, int use_active, typename C2<T>::t* __restrict__ mesh) {
+                         const float* __restrict__ x32, const PcgScalars* __restrict__ sc, int use_active,
+                         typename C2<T>::t* __restrict__ mesh) {
   using V = typename C2<T>::t;
   const int g = blockIdx.x;
   const int s = brick_struct[g];
@@ -530,7 +718,7 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
             if (j >= K2) j -= K2;
             R.wz[tid][l] = ((zm >> l) & 1u) ? wt[2 * QEQ_MAXP + P - 1 - j] : (T)0;
           }
-          const T q = (T)x[t];
+          const T q = xval<T>(x, x32, t);
 #pragma unroll
           for (int j = 0; j < P; ++j) {
             R.wx[tid][j] = q * wt[P - 1 - j];
@@ -616,7 +804,8 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256) k_gather_direct(
     const Chunk* __restrict__ chunks, const StructDev* __restrict__ st, const int* __restrict__ base,
     const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ J,
-    const double* __restrict__ x, const int64_t* __restrict__ row, const int* __restrict__ col,
+    const double* __restrict__ x, const float* __restrict__ x32, const int64_t* __restrict__ row,
+    const int* __restrict__ col,
     const double* __restrict__ v64, const float* __restrict__ v32, int with_J, int with_pairs,
     PcgScalars* __restrict__ sc, int use_active, int fuse_pAp, double* __restrict__ part, int* __restrict__ counter,
     const typename C2<T>::t* __restrict__ mesh, double* __restrict__ y, int split) {
@@ -634,43 +823,55 @@ __global__ void __launch_bounds__(256) k_gather_direct(
   // halos shared by neighbouring runs are still in L2
   const int64_t len = (ch.end - ch.begin + split - 1) / split;
   const int64_t lo = ch.begin + (int64_t)sub * len, hi = min(ch.end, lo + len);
-  for (int64_t t = lo + w; t < hi; t += nw) {
-    const int sp = spec[t];
-    const int part_ = sp & 1;
-    const V* mg = mesh + S.mesh_off + (int64_t)(sp >> 1) * S.M;
-    const int bs = base[t];
-    const int f0 = bs & 1023, f1 = (bs >> 10) & 1023, f2 = (bs >> 20) & 1023;
-    const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
-    T acc = (T)0;
-    if (jz < P) {
-      int kz = f2 - (P - 1) + jz;
-      if (kz < 0) kz += S.K[2];
-      const T wzj = wt[2 * QEQ_MAXP + P - 1 - jz];
-      T racc = (T)0;
+  // a warp takes G <= 8 consecutive atoms: their stencils one after another (all
+  // lanes), each atom's sum parked in lane g, then the FP64 local terms for the G
+  // atoms on lanes 0..G-1 at once (FP64 issue slots are scarce)
+  const int G = (int)max((int64_t)1, min((int64_t)8, (len + nw - 1) / nw));
+  for (int64_t tb = lo + (int64_t)G * w; tb < hi; tb += (int64_t)G * nw) {
+    T mine = (T)0;
+    for (int g = 0; g < G; ++g) {
+      const int64_t t = tb + g;
+      if (t >= hi) break;
+      const int sp = spec[t];
+      const int part_ = sp & 1;
+      const V* mg = mesh + S.mesh_off + (int64_t)(sp >> 1) * S.M;
+      const int bs = base[t];
+      const int f0 = bs & 1023, f1 = (bs >> 10) & 1023, f2 = (bs >> 20) & 1023;
+      const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
+      T acc = (T)0;
+      if (jz < P) {
+        int kz = f2 - (P - 1) + jz;
+        if (kz < 0) kz += S.K[2];
+        const T wzj = wt[2 * QEQ_MAXP + P - 1 - jz];
+        T racc = (T)0;
 #pragma unroll
-      for (int r = rsub; r < P * P; r += 4) {
-        const int jx = r / P, jy = r - (r / P) * P;
-        int kx = f0 - (P - 1) + jx;
-        if (kx < 0) kx += S.K[0];
-        int ky = f1 - (P - 1) + jy;
-        if (ky < 0) ky += S.K[1];
-        const V v = __ldg(mg + ((int64_t)kx * S.K[1] + ky) * S.K[2] + kz);
-        racc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
+        for (int r = rsub; r < P * P; r += 4) {
+          const int jx = r / P, jy = r - (r / P) * P;
+          int kx = f0 - (P - 1) + jx;
+          if (kx < 0) kx += S.K[0];
+          int ky = f1 - (P - 1) + jy;
+          if (ky < 0) ky += S.K[1];
+          const V v = __ldg(mg + ((int64_t)kx * S.K[1] + ky) * S.K[2] + kz);
+          racc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
+        }
+        acc = racc * wzj;
       }
-      acc = racc * wzj;
+      if (with_pairs) {
+        int64_t r0 = row[t], r1 = row[t + 1];
+        for (int64_t k = r0 + lane; k < r1; k += 32) acc += vals[k] * xval<T>(x, x32, col[k]);
+      }
+      acc = warp_sum<T>(acc);
+      if (lane == g) mine = acc;
     }
-    if (with_pairs) {
-      int64_t r0 = row[t], r1 = row[t + 1];
-      for (int64_t k = r0 + lane; k < r1; k += 32) acc += vals[k] * (T)x[col[k]];
-    }
-    acc = warp_sum<T>(acc);
-    if (lane == 0) {
-      double xi = x[t];
+    const int64_t t = tb + lane;
+    if (lane < G && t < hi) {
+      const int sp = spec[t];
+      const double xi = x[t];
       double loc = S.self_s[sp] * xi;
       if (with_J) loc += J[t] * xi;
       const PcgScalars& c = sc[ch.s];
       for (int tt = 0; tt < S.S; ++tt) loc -= S.corr[sp * QEQ_MAX_SPECIES + tt] * c.xsum[tt];
-      double yi = (double)acc + loc;
+      const double yi = (double)mine + loc;
       y[t] = yi;
       blk += xi * yi;
     }
@@ -679,6 +880,7 @@ __global__ void __launch_bounds__(256) k_gather_direct(
     __shared__ double wsum[32];
     __shared__ double red[256];
     __shared__ bool last;
+    blk = warp_sum<double>(blk);  // lanes 0..G-1 hold the warp's atoms (fixed order)
     if (lane == 0) wsum[w] = blk;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -706,7 +908,7 @@ __global__ void __launch_bounds__(256) k_gather_direct(
 __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev* __restrict__ st,
                                const int* __restrict__ spec, const double* __restrict__ x,
                                PcgScalars* __restrict__ sc, int use_active, double* __restrict__ part,
-                               int* __restrict__ counter) {
+                               int* __restrict__ counter, float* __restrict__ x32) {
   const Chunk ch = chunks[blockIdx.x];
   if (use_active && !sc[ch.s].active) return;
   __shared__ double red[QEQ_MAX_SPECIES][33];
@@ -716,6 +918,7 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
     const int sp = spec[a];
     const double xa = x[a];
+    if (x32) x32[a] = (float)xa;
 #pragma unroll
     for (int k = 0; k < QEQ_MAX_SPECIES; ++k) loc[k] += (sp == k) ? xa : 0.0;
   }
@@ -888,14 +1091,15 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   count_launch(Pl, 8);
   QEQ_CUDA_TRY(mark());
   // stage 0: per-species sums of x (width-correction terms)
+  float* x32 = std::is_same<T, float>::value ? Pl->d_x32 : nullptr;
   k_species_sums<<<Pl->n_chunks, 256, 0, s>>>(Pl->d_chunks, Pl->d_st, Pl->d_spec, x, Pl->d_sc, use_active,
-                                               Pl->d_part, Pl->d_counter);
+                                               Pl->d_part, Pl->d_counter, x32);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
   // stage 1: spreading
   {
     k_spread<T, P><<<Pl->total_bricks, 256, sizeof(SpreadRecs<T, P>), s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
-                                                      Pl->d_spec, x, Pl->d_sc, use_active, mesh);
+                                                      Pl->d_spec, x, x32, Pl->d_sc, use_active, mesh);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   QEQ_CUDA_TRY(mark());
@@ -911,7 +1115,11 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
                                                         Pl->d_sc, use_active, mesh2, mesh, Pl->tl);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
-  k_fft_x_green<T, false><<<Pl->n_xitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_xitems, Pl->d_xpairs, bmod,
+  if (Pl->max_species <= 2)
+    k_fft_x_green<T, false, 2><<<Pl->n_xitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_xitems, Pl->d_xpairs, bmod,
+                                                   Pl->d_tw64, Pl->d_tw32, Pl->d_sc, use_active, mesh);
+  else
+    k_fft_x_green<T, false, QEQ_MAX_SPECIES><<<Pl->n_xitems, 256, smf, s>>>(Pl->d_st, Pl->d_fft, Pl->d_xitems, Pl->d_xpairs, bmod,
                                                    Pl->d_tw64, Pl->d_tw32, Pl->d_sc, use_active, mesh);
   QEQ_CUDA_TRY(cudaGetLastError());
   QEQ_CUDA_TRY(mark());
@@ -927,7 +1135,7 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   {
     int with_pairs = Pl->pair_cap > 0;
     k_gather_direct<T, P><<<Pl->n_chunks * Pl->gather_split, 256, 0, s>>>(
-        Pl->d_chunks, Pl->d_st, Pl->d_base, wts, Pl->d_spec, Pl->d_J, x, Pl->d_row, Pl->d_col, Pl->d_val64,
+        Pl->d_chunks, Pl->d_st, Pl->d_base, wts, Pl->d_spec, Pl->d_J, x, x32, Pl->d_row, Pl->d_col, Pl->d_val64,
         Pl->d_val32, with_J, with_pairs, Pl->d_sc, use_active, fuse_pAp,
         Pl->d_part + (size_t)Pl->n_chunks * QEQ_MAX_SPECIES, Pl->d_counter + Pl->n_struct, mesh, y, Pl->gather_split);
     QEQ_CUDA_TRY(cudaGetLastError());
@@ -945,8 +1153,10 @@ cudaError_t set_smem_attrs() {
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, PASS_ZI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, false, QEQ_MAX_SPECIES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<T, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return cudaSuccess;
 }
 
@@ -994,7 +1204,7 @@ cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, 
                                                        use_active, P->d_pmesh, P->d_pmesh2, P->tlp);
   k_fft_pass<float, PASS_YF><<<P->n_py, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pyitems, P->d_tw64, P->d_tw32, P->d_sc,
                                                        use_active, P->d_pmesh2, P->d_pmesh, P->tlp);
-  k_fft_x_green<float, true><<<P->n_px, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pxitems, P->d_xpairs, bmod, P->d_tw64,
+  k_fft_x_green<float, true, 2><<<P->n_px, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pxitems, P->d_xpairs, bmod, P->d_tw64,
                                                        P->d_tw32, P->d_sc, use_active, P->d_pmesh);
   k_fft_pass<float, PASS_YI><<<P->n_py, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pyitems, P->d_tw64, P->d_tw32, P->d_sc,
                                                        use_active, P->d_pmesh, P->d_pmesh2, P->tlp);

@@ -60,28 +60,6 @@ int next_smooth(int n) {
   return n;
 }
 
-std::vector<int> radices(int K) {
-  std::vector<int> r;
-  int n = K;
-  while (n % 4 == 0) {
-    r.push_back(4);
-    n /= 4;
-  }
-  while (n % 2 == 0) {
-    r.push_back(2);
-    n /= 2;
-  }
-  while (n % 3 == 0) {
-    r.push_back(3);
-    n /= 3;
-  }
-  while (n % 5 == 0) {
-    r.push_back(5);
-    n /= 5;
-  }
-  return r;
-}
-
 // cardinal B-spline M_p at the integers 0..p-1 (same order recursion as prep.cu, at w = 0)
 void bspline_at_integers(int p, double* out) {
   double a[QEQ_MAXP + 1] = {0};
@@ -212,7 +190,8 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_val64,  P->d_val32,   P->d_q,       P->d_r,        P->d_z,       P->d_p,
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems,
-                  P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw};
+                  P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
+                  P->d_x32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -325,6 +304,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->max_p = pbest;
   // lines per tile of the transposing FFT passes: from the largest mesh of the plan
   int maxK = 12;
+  int max_s = 1;
   {
     const double omega = split_width(D);
     for (int s = 0; s < ns; ++s) {
@@ -346,9 +326,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
     FftPlanDev f;
     memset(&f, 0, sizeof(f));
     f.K = K;
-    std::vector<int> r = radices(K);
-    f.nst = (int)r.size();
-    for (size_t i = 0; i < r.size(); ++i) f.radix[i] = r[i];
+    f.nst = fft_radices(K, f.radix);
     for (int i = 0, ns = 1; i < f.nst; ns *= f.radix[i], ++i) {
       f.nbf[i] = make_fastdiv(K / f.radix[i]);
       f.ns[i] = make_fastdiv(ns);
@@ -386,6 +364,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
     while (Ss > 1 && !(D.sigma[(size_t)S * s + Ss - 1] > 0.0)) --Ss;
     T.S = Ss;
     T.ncm = (Ss + 1) / 2;
+    max_s = std::max(max_s, Ss);
     T.p = pbest;
     T.atom_begin = P->offsets[s];
     T.atom_end = P->offsets[s + 1];
@@ -554,9 +533,10 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->total_mesh = mesh_off;
   P->pair_cap = pair_cap;
   P->n_chunks = (int)chunks.size();
-  // gather CTAs: runs of at most 64 atoms (8 per chunk), more when chunks are too
-  // few to fill the GPU (about 4 CTAs per SM of a 148-SM part)
-  P->gather_split = std::max(8, std::min(16, (592 + P->n_chunks - 1) / std::max(1, P->n_chunks)));
+  P->max_species = max_s;
+  // gather CTAs: runs of at most 64 atoms (8 per chunk), shorter runs when chunks
+  // are too few to fill the GPU (about 16 CTAs per SM of a 148-SM part)
+  P->gather_split = std::max(8, std::min(QEQ_GATHER_SPLIT_MAX, (2368 + P->n_chunks - 1) / std::max(1, P->n_chunks)));
   P->n_zitems = (int)zit.size();
   P->n_yitems = (int)yit.size();
   P->n_xitems = (int)xit.size();
@@ -612,11 +592,12 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(dalloc(P, &P->d_val64, pair_cap));
   ALLOC(dalloc(P, &P->d_val32, pair_cap));
   for (double** v : {&P->d_q, &P->d_r, &P->d_z, &P->d_p, &P->d_Ap, &P->d_x}) ALLOC(dalloc(P, v, N));
+  ALLOC(dalloc(P, &P->d_x32, N));
   ALLOC(dalloc(P, &P->d_mesh, (size_t)P->total_mesh));
   ALLOC(dalloc(P, &P->d_mesh2, (size_t)P->total_mesh));
   // partials: species sums (8 per chunk), gather x.y (split per chunk, or bins), PCG reductions (8 per chunk)
   ALLOC(dalloc(P, &P->d_part, (size_t)P->n_chunks * QEQ_MAX_SPECIES * 2 +
-                                  std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * 16) + 64));
+                                  std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * QEQ_GATHER_SPLIT_MAX) + 64));
   ALLOC(dalloc(P, &P->d_counter, (size_t)ns * 4));
   ALLOC(cudaMemset(P->d_counter, 0, sizeof(int) * ns * 4));
   ALLOC(dalloc(P, &P->d_sc, ns));

@@ -15,6 +15,8 @@
 #define QEQ_MAXP 8         // largest supported B-spline order
 #define QEQ_MAX_STAGES 16  // radix stages of one FFT length
 #define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
+#define QEQ_XPAIRS_MAX 256 // line pairs per x-pass CTA (shared per-line constants)
+#define QEQ_GATHER_SPLIT_MAX 64  // gather CTAs per reduction chunk
 
 // ---------------------------------------------------------------------------
 // Per-structure constants, built on the host by qeq_plan_create.
@@ -188,59 +190,16 @@ struct qeq_plan_s {
   float* d_val32 = nullptr;
   // vectors (sorted order)
   double *d_q = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_x = nullptr;
+  float* d_x32 = nullptr;          // FP32 copy of the matvec input (mixed precision), written by the species sums
   // mesh (reinterpreted as float2 in mixed precision)
   double2* d_mesh = nullptr;       // layouts L0 / L2 (see matvec.cu)
   double2* d_mesh2 = nullptr;      // layout L1
   int tl = 8;                      // lines per tile of the transposing FFT passes
   // reductions
-  double* d_part = nullptr;        // n_chunks * 16 partials
+  double* d_part = nullptr;        // partials: species sums, gather x.y, PCG reductions
   int* d_counter = nullptr;        // n_struct counters for last-block reductions
   PcgScalars* d_sc = nullptr;
-  int* d_err = nullptr;            // Work lists of the FFT passes of one structure (shared by qeq_plan_create and
-// the allocation-free entry point).  Z items {s, c, x, y0} and Y items
-// {s, c, z, x0} cover tiles of tl lines; X items {s, first pair, npairs, 0}
-// cover pairs of x lines (z, y) and (-z, -y), lines indexed l = z*K1 + y.
-// Returns the shared-memory size (complex elements) the passes need.
-template <class AddZ, class AddY, class AddPair, class AddX>
-inline int64_t fft_work_lists(const StructDev& T, int s, int tl, int pair_base, AddZ addz, AddY addy,
-                              AddPair addpair, AddX addx) {
-  const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
-  for (int c = 0; c < T.ncm; ++c)
-    for (int x = 0; x < K0; ++x)
-      for (int y0 = 0; y0 < K1; y0 += tl) addz(make_int4(s, c, x, y0));
-  for (int c = 0; c < T.ncm; ++c)
-    for (int z = 0; z < K2; ++z)
-      for (int x0 = 0; x0 < K0; x0 += tl) addy(make_int4(s, c, z, x0));
-  int npairs = 0;
-  for (int z = 0; z < K2; ++z)
-    for (int y = 0; y < K1; ++y) {
-      int l = z * K1 + y;
-      int lm = ((K2 - z) % K2) * K1 + (K1 - y) % K1;
-      if (l <= lm) {
-        addpair(make_int2(l, lm));
-        ++npairs;
-      }
-    }
-  int np = 4096 / (2 * T.ncm * K0);
-  if (np < 1) np = 1;
-  for (int j = 0; j < npairs; j += np) addx(make_int4(s, pair_base + j, (npairs - j < np) ? npairs - j : np, 0));
-  int64_t e = 0;
-  auto mx = [&](int64_t v) { e = v > e ? v : e; };
-  mx(K2 + 2 * (int64_t)tl * (K2 + 1));
-  mx(K1 + 2 * (int64_t)tl * (K1 + 1));
-  int nsl = 2 * (np < npairs ? np : npairs) * T.ncm;
-  mx(K0 + 2 * (int64_t)nsl * (K0 + 1));
-  return e;
-}
-
-// lines per tile: a power of two, at most 16 and at most 4096 / K elements per buffer
-inline int fft_tile_lines(int maxK) {
-  int tl = 16;
-  while (tl > 1 && tl * maxK > 4096) tl >>= 1;
-  return tl;
-}
-
-// device error bits
+  int* d_err = nullptr;            // device error bits
   int* d_done = nullptr;           // all-structures-inactive flag
   int* h_done = nullptr;           // pinned mirror
   cudaEvent_t ev_done = nullptr;
@@ -252,6 +211,7 @@ inline int fft_tile_lines(int maxK) {
   int n_pz = 0, n_py = 0, n_px = 0, tlp = 8;
   int64_t total_pmesh = 0;
   int gather_split = 1;            // CTAs per reduction chunk in the gather
+  int max_species = QEQ_MAX_SPECIES;  // most species of any structure
   float2 *d_pmesh = nullptr, *d_pmesh2 = nullptr;
   double *d_w1 = nullptr, *d_u = nullptr;
   int* d_pbase = nullptr;
@@ -266,6 +226,31 @@ inline int fft_tile_lines(int maxK) {
   int graph_iter_prec = -1;
   int graph_iter_k = 0;
 };
+
+// Shared-memory layout of FFT lines: element i of a line sits at fft_pidx(i)
+// (one pad element per 16, so strided butterfly accesses spread over the
+// banks), lines fft_ld(K) elements apart (odd, for transposed accesses).
+__host__ __device__ inline int fft_pidx(int i) { return i + (i >> 4); }
+__host__ __device__ inline int fft_ld(int K) { return (fft_pidx(K - 1) + 1) | 1; }
+
+// Radices of the FFT stages of length K (K = 2^a 3^b 5^c): greedily the largest
+// register butterfly that divides what is left.  Returns the number of stages.
+inline int fft_radices(int K, int* out) {
+  static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  int n = K, ns = 0;
+  while (n > 1 && ns < QEQ_MAX_STAGES) {
+    int r = 0;
+    for (int c : kRadix)
+      if (n % c == 0) {
+        r = c;
+        break;
+      }
+    if (r == 0) return -1;
+    out[ns++] = r;
+    n /= r;
+  }
+  return n == 1 ? ns : -1;
+}
 
 // Work lists of the FFT passes of one structure (shared by qeq_plan_create and
 // the allocation-free entry point).  Z items {s, c, x, y0} and Y items
@@ -294,13 +279,14 @@ inline int64_t fft_work_lists(const StructDev& T, int s, int tl, int pair_base, 
     }
   int np = 4096 / (2 * T.ncm * K0);
   if (np < 1) np = 1;
+  if (np > QEQ_XPAIRS_MAX) np = QEQ_XPAIRS_MAX;
   for (int j = 0; j < npairs; j += np) addx(make_int4(s, pair_base + j, (npairs - j < np) ? npairs - j : np, 0));
   int64_t e = 0;
   auto mx = [&](int64_t v) { e = v > e ? v : e; };
-  mx(K2 + 2 * (int64_t)tl * (K2 + 1));
-  mx(K1 + 2 * (int64_t)tl * (K1 + 1));
+  mx(K2 + 2 * (int64_t)tl * fft_ld(K2));
+  mx(K1 + 2 * (int64_t)tl * fft_ld(K1));
   int nsl = 2 * (np < npairs ? np : npairs) * T.ncm;
-  mx(K0 + 2 * (int64_t)nsl * (K0 + 1));
+  mx(K0 + 2 * (int64_t)nsl * fft_ld(K0));
   return e;
 }
 

@@ -390,7 +390,8 @@ qeq_status cuda_fail(qeq_plan_s* P, cudaError_t e, const char* where) {
 
 int* red_counter(qeq_plan_s* P) { return P->d_counter + 2 * P->n_struct; }
 double* red_part(qeq_plan_s* P) {
-  return P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES + std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * 16) + 8;
+  return P->d_part + (size_t)P->n_chunks * QEQ_MAX_SPECIES +
+         std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * QEQ_GATHER_SPLIT_MAX) + 8;
 }
 
 const double* dir_alt(qeq_plan_s* P) { return P->precond == QEQ_PRECOND_FOURIER ? P->d_x : nullptr; }

@@ -289,13 +289,8 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     FftPlanDev& f = G.fft[d];
     memset(&f, 0, sizeof(f));
     f.K = K;
-    int n = K, ns = 0;
-    for (int r : {4, 2, 3, 5})
-      while (n % r == 0) {
-        f.radix[ns++] = r;
-        n /= r;
-      }
-    f.nst = ns;
+    f.nst = fft_radices(K, f.radix);
+    if (f.nst < 1) return QEQ_ERR_INVALID;
     for (int i = 0, prod = 1; i < f.nst; prod *= f.radix[i], ++i) {
       f.nbf[i] = make_fastdiv(K / f.radix[i]);
       f.ns[i] = make_fastdiv(prod);
@@ -362,6 +357,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.total_mesh = T.M * T.ncm;
   P.pair_cap = pair_cap;
   P.n_chunks = nchunks;
+  P.max_species = S;
   P.n_zitems = nz;
   P.n_yitems = ny;
   P.n_xitems = nx;
@@ -405,8 +401,8 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.d_Ap = cv.take<double>(N);
   P.d_mesh = cv.take<double2>((size_t)P.total_mesh);
   P.d_mesh2 = cv.take<double2>((size_t)P.total_mesh);
-  P.gather_split = std::max(8, std::min(16, (592 + nchunks - 1) / nchunks));
-  P.d_part = cv.take<double>((size_t)nchunks * QEQ_MAX_SPECIES * 2 + std::max(nbins, nchunks * 16) + 64);
+  P.gather_split = std::max(8, std::min(QEQ_GATHER_SPLIT_MAX, (2368 + nchunks - 1) / nchunks));
+  P.d_part = cv.take<double>((size_t)nchunks * QEQ_MAX_SPECIES * 2 + std::max(nbins, nchunks * QEQ_GATHER_SPLIT_MAX) + 64);
   P.d_counter = cv.take<int>(4);
   P.d_sc = cv.take<PcgScalars>(1);
   P.d_err = cv.take<int>(4);
