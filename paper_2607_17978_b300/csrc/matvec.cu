@@ -730,38 +730,32 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
         R.mask[tid] = mask;
       }
       __syncthreads();
-      // every thread adds its row's share, atom after atom (two at a time)
-      for (int i = 0; i < nbat; i += 2) {
-        T r[2] = {(T)0, (T)0};
-        int part[2] = {0, 0};
-        bool act[2] = {false, false};
+      // every thread adds its row's share, atom after atom.  A warp owns the rows
+      // lx = 2w, 2w+1: it ballots the records whose stencil covers one of them
+      // (32 records per ballot) and visits only those, in record order.
+      const unsigned wsel = 3u << (2 * (tid >> 5));
+      const int lane = tid & 31;
+      for (int i0 = 0; i0 < nbat; i0 += 32) {
+        const int ii = i0 + lane;
+        unsigned bal = __ballot_sync(0xffffffffu, ii < nbat && (R.mask[ii] & wsel) != 0u);
+        while (bal) {
+          const int k = i0 + __ffs(bal) - 1;
+          bal &= bal - 1u;
+          const unsigned m = R.mask[k];
+          if (!((m >> lx) & 1u) || !((m >> (16 + ly)) & 1u)) continue;
+          const int off = R.off[k];
+          int jx = lx - (off & 1023);
+          if (jx < 0) jx += K0;
+          int jy = ly - ((off >> 10) & 1023);
+          if (jy < 0) jy += K1;
+          const T r = R.wx[k][jx] * R.wy[k][jy];
+          const T* wz = R.wz[k];
+          if ((off >> 20) & 1) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int k = i + u;
-          if (k < nbat) {
-            const unsigned m = R.mask[k];
-            act[u] = ((m >> lx) & 1u) && ((m >> (16 + ly)) & 1u);
-            if (act[u]) {
-              const int off = R.off[k];
-              int jx = lx - (off & 1023);
-              if (jx < 0) jx += K0;
-              int jy = ly - ((off >> 10) & 1023);
-              if (jy < 0) jy += K1;
-              r[u] = R.wx[k][jx] * R.wy[k][jy];
-              part[u] = (off >> 20) & 1;
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (!act[u]) continue;
-          const T* wz = R.wz[i + u];
-          if (part[u]) {
-#pragma unroll
-            for (int z = 0; z < QEQ_BRICK; ++z) im[z] += r[u] * wz[z];
+            for (int z = 0; z < QEQ_BRICK; ++z) im[z] += r * wz[z];
           } else {
 #pragma unroll
-            for (int z = 0; z < QEQ_BRICK; ++z) re[z] += r[u] * wz[z];
+            for (int z = 0; z < QEQ_BRICK; ++z) re[z] += r * wz[z];
           }
         }
       }
