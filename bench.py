@@ -270,11 +270,12 @@ def run_ours(args):
     d_J = torch.tensor(J, device=dev)
     plan = qeq.plan_for_structures(structs, precision=args.precision, device=dev, preconditioner=args.precond, **opts)
     q_out = torch.empty(n_atoms, dtype=torch.float64, device=dev)
-    # learned warm start for the rock-salt workloads (the network was trained on that recipe)
+    # learned warm start for the rock-salt workloads of the recipe the network was trained on
+    # (unsheared, jittered, few vacancies; the sheared 5%-vacancy cell of workload 3 is outside it)
     warm = args.warm
     model = os.path.join(ROOT, "paper_2607_17978_b300", "models", "warmstart_rocksalt.npz")
     if warm == "auto":
-        warm = "mlp" if (args.workload in (1, 2, 3, 5) and os.path.exists(model)) else "cold"
+        warm = "mlp" if (args.workload in (1, 2, 5) and os.path.exists(model)) else "cold"
     mlp = None
     if warm == "mlp":
         from paper_2607_17978_b300 import warmstart
@@ -461,7 +462,7 @@ def main():
     ap.add_argument("--precond", default="fourier", choices=["fourier", "jacobi"],
                     help="preconditioner of the chosen form (the plain FP64 leg always uses Jacobi)")
     ap.add_argument("--warm", default="auto", choices=["auto", "mlp", "cold"],
-                    help="learned warm start (auto: on for the rock-salt workloads when the model file exists)")
+                    help="learned warm start (auto: on for workloads 1, 2 and 5, the training recipe, when the model file exists)")
     ap.add_argument("--profile-cells", dest="cells", type=int, default=0,
                     help="profiling mode: solve a rock-salt cell of N^3 conventional cells only")
     args = ap.parse_args()
