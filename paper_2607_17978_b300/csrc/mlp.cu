@@ -72,7 +72,7 @@ template <bool SORTED>
 __global__ void __launch_bounds__(256) k_features(const StructDev* __restrict__ st,
                                                   const int* __restrict__ sorted_struct,
                                                   const int* __restrict__ bin_start, const int* __restrict__ base,
-                                                  const int* __restrict__ spec, const double* __restrict__ posc,
+                                                  const int* __restrict__ spec, const float4* __restrict__ posc32,
                                                   const double* __restrict__ chis, const double* __restrict__ Js,
                                                   const int* __restrict__ perm, int64_t n, float* __restrict__ feat) {
   __shared__ NbrWarpSmem ws[8];
@@ -86,15 +86,17 @@ __global__ void __launch_bounds__(256) k_features(const StructDev* __restrict__ 
   for (int k = 0; k < 24; ++k) G[k] = 0.f;
   const int bs = base[a];
   const int bb[3] = {(bs & 1023) / QEQ_BIN, ((bs >> 10) & 1023) / QEQ_BIN, ((bs >> 20) & 1023) / QEQ_BIN};
-  const double ra0 = posc[3 * a], ra1 = posc[3 * a + 1], ra2 = posc[3 * a + 2];
-  const double rc2 = (double)RC * RC;
-  warp_neighbour_walk(S, bb, S.feat_range, bin_start, ws[w], [&](bool valid, int t, const double* sh, bool zero) {
+  // FP32 distances: the descriptors are FP32 and vanish smoothly at the cutoff
+  const float4 pa = posc32[a];
+  const float rc2 = RC * RC;
+  warp_neighbour_walk(S, bb, S.feat_range, bin_start, ws[w],
+                      [&](bool valid, int t, const double*, const float* sh, bool zero, int) {
     if (!valid || (zero && t == a)) return;
-    const double dx = posc[3 * t] + sh[0] - ra0, dy = posc[3 * t + 1] + sh[1] - ra1,
-                 dz = posc[3 * t + 2] + sh[2] - ra2;
-    const double r2 = dx * dx + dy * dy + dz * dz;
+    const float4 pt = posc32[t];
+    const float dx = pt.x + sh[0] - pa.x, dy = pt.y + sh[1] - pa.y, dz = pt.z + sh[2] - pa.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rc2) return;
-    const float r = (float)sqrt(r2);
+    const float r = sqrtf(r2);
     const float fc = 0.5f * (cospif(r / RC) + 1.0f);
     const float cj = (float)chis[t];
 #pragma unroll
@@ -502,7 +504,7 @@ extern "C" qeq_status qeq_features(qeq_plan P, const double* d_pos, const int32_
   if (launch_prepare_atoms(P, d_pos, d_species, d_chi, d_J, 0) != cudaSuccess) return QEQ_ERR_CUDA;
   int nb = (int)((P->n_atoms + 7) / 8);  // one warp per atom
   count_launch(P);
-  k_features<false><<<nb, 256, 0, P->stream>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc,
+  k_features<false><<<nb, 256, 0, P->stream>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc32,
                                                 P->d_chi, P->d_J, P->d_perm, P->n_atoms, d_feat);
   if (cudaGetLastError() != cudaSuccess) return QEQ_ERR_CUDA;
   if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEQ_ERR_CUDA;
@@ -536,7 +538,7 @@ cudaError_t launch_mlp_warm_start(qeq_plan_s* P, double* d_q_sorted) {
   cudaStream_t s = P->stream;
   int nb = (int)((P->n_atoms + 7) / 8);  // one warp per atom
   count_launch(P, 3);
-  k_features<true><<<nb, 256, 0, s>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc, P->d_chi,
+  k_features<true><<<nb, 256, 0, s>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc32, P->d_chi,
                                        P->d_J, P->d_perm, P->n_atoms, P->d_feat);
   int ntiles = (int)((P->n_atoms + TILE - 1) / TILE);
   k_mlp<false><<<ntiles, 128, mlp_smem(), s>>>(P->d_feat, P->d_spec, P->n_atoms, m->n_species, m->d_params,

@@ -20,15 +20,28 @@ struct NbrWarpSmem {
   int beg[32];       // first sorted atom of the run
   int zero[32];      // run lies in the unshifted image
   double sh[32][3];  // Cartesian image shift of the run
+  float sh32[32][3]; // the same in FP32
+  int code[32];      // image indices (s0, s1, s2) + 128, 8 bits each
 };
+
+// image indices of a periodic shift, |s_d| < 128, packed into one int and back
+__device__ __forceinline__ int pack_image(int s0, int s1, int s2) {
+  return (s0 + 128) | ((s1 + 128) << 8) | ((s2 + 128) << 16);
+}
+__device__ __forceinline__ void unpack_image(int c, int* s) {
+  s[0] = (c & 255) - 128;
+  s[1] = ((c >> 8) & 255) - 128;
+  s[2] = ((c >> 16) & 255) - 128;
+}
 
 __device__ __forceinline__ int floordiv_i(int a, int b) {
   int q = a / b;
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
-// visit(valid, t, sh, zero_shift): t = sorted index of the candidate atom,
-// sh = image shift added to its position.  Every lane of the warp must call this.
+// visit(valid, t, sh, sh32, zero_shift, code): t = sorted index of the candidate
+// atom, sh (FP64) / sh32 (FP32) = image shift added to its position, code = the
+// image indices packed by pack_image.  Every lane of the warp must call this.
 template <class Visit>
 __device__ __forceinline__ void warp_neighbour_walk(const StructDev& S, const int bb[3], const int R[3],
                                                     const int* __restrict__ bin_start, NbrWarpSmem& W,
@@ -42,7 +55,7 @@ __device__ __forceinline__ void warp_neighbour_walk(const StructDev& S, const in
   const int nruns = n0 * n1 * nseg;
   for (int r0 = 0; r0 < nruns; r0 += 32) {
     const int r = r0 + lane;
-    int beg = 0, len = 0, zero = 0;
+    int beg = 0, len = 0, zero = 0, code = 0;
     double sh0 = 0.0, sh1 = 0.0, sh2 = 0.0;
     if (r < nruns) {
       const int seg = r % nseg, col = r / nseg;
@@ -57,6 +70,7 @@ __device__ __forceinline__ void warp_neighbour_walk(const StructDev& S, const in
       beg = bin_start[g + z0];
       len = bin_start[g + z1 + 1] - beg;
       zero = (s0 == 0 && s1 == 0 && s2 == 0);
+      code = pack_image(s0, s1, s2);
       sh0 = s0 * S.h[0] + s1 * S.h[3] + s2 * S.h[6];
       sh1 = s0 * S.h[1] + s1 * S.h[4] + s2 * S.h[7];
       sh2 = s0 * S.h[2] + s1 * S.h[5] + s2 * S.h[8];
@@ -75,6 +89,10 @@ __device__ __forceinline__ void warp_neighbour_walk(const StructDev& S, const in
     W.sh[lane][0] = sh0;
     W.sh[lane][1] = sh1;
     W.sh[lane][2] = sh2;
+    W.sh32[lane][0] = (float)sh0;
+    W.sh32[lane][1] = (float)sh1;
+    W.sh32[lane][2] = (float)sh2;
+    W.code[lane] = code;
     __syncwarp();
     for (int c0 = 0; c0 < total; c0 += 32) {
       const int c = c0 + lane;
@@ -91,7 +109,7 @@ __device__ __forceinline__ void warp_neighbour_walk(const StructDev& S, const in
         j = lo;
       }
       const int t = valid ? W.beg[j] + (c - W.off[j]) : 0;
-      visit(valid, t, W.sh[j], W.zero[j] != 0);
+      visit(valid, t, W.sh[j], W.sh32[j], W.zero[j] != 0, W.code[j]);
     }
     __syncwarp();
   }

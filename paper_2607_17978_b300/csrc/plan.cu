@@ -191,7 +191,7 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems,
                   P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
-                  P->d_x32};
+                  P->d_x32,    P->d_posc32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -410,6 +410,9 @@ static qeq_status build_plan(qeq_plan_s* P) {
     // --- mesh for the plan's B-spline order
     double wd[3];
     plane_widths(h, V, wd);
+    for (int d = 0; d < 3; ++d)  // periodic images are indexed with 8 bits
+      if (std::max(rc, (double)QEQ_MLP_RCUT) > 100.0 * wd[d])
+        return fail(P, QEQ_ERR_INVALID, "cell narrower than 1/100 of the real-space cutoff");
     int Kbest[3];
     double cst;
     if (!choose_mesh(h, V, wmin, (double)(T.atom_end - T.atom_begin), pbest, D, Kbest, &cst))
@@ -586,6 +589,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(dalloc(P, &P->d_chi, N));
   ALLOC(dalloc(P, &P->d_dinv, N));
   ALLOC(dalloc(P, &P->d_posc, (size_t)N * 3));
+  ALLOC(dalloc(P, &P->d_posc32, (size_t)N));
   ALLOC(dalloc(P, &P->d_row, N + 1));
   ALLOC(dalloc(P, &P->d_row_cnt, N));
   ALLOC(dalloc(P, &P->d_col, pair_cap));

@@ -168,7 +168,7 @@ __global__ void k_gather_sorted(const StructDev* __restrict__ st, const int* __r
                                 const double* __restrict__ J, int maxp, int* __restrict__ base,
                                 double* __restrict__ wts, float* __restrict__ wts32, int* __restrict__ spec,
                                 double* __restrict__ Js, double* __restrict__ chis, double* __restrict__ dinv,
-                                double* __restrict__ posc) {
+                                double* __restrict__ posc, float4* __restrict__ posc32) {
   int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n) return;
   int i = perm[a];
@@ -202,20 +202,29 @@ __global__ void k_gather_sorted(const StructDev* __restrict__ st, const int* __r
   Js[a] = Ji;
   chis[a] = ci;
   dinv[a] = 1.0 / (fmax(Ji, 0.0) + S.diag_s[sp]);
-  for (int d = 0; d < 3; ++d) posc[3 * a + d] = u[0] * S.h[d] + u[1] * S.h[3 + d] + u[2] * S.h[6 + d];
+  double c[3];
+  for (int d = 0; d < 3; ++d) {
+    c[d] = u[0] * S.h[d] + u[1] * S.h[3 + d] + u[2] * S.h[6 + d];
+    posc[3 * a + d] = c[d];
+  }
+  posc32[a] = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);
 }
 
 // ---------------------------------------------------------------- real-space pairs
 // Real-space pairs of atom a (one warp per atom): every (j, image) with
 // |r_j + n h - r_a| < r_cut whose species pair has a real-space term; count
 // (FILL == 0) or write the CSR row (FILL == 1) in the walk's candidate order.
+// Distances are tested in FP32 with a margin well above FP32 position rounding;
+// only candidates inside the margin band are decided in FP64, so the cutoff is
+// the exact FP64 test.  FILL first records (column, image) per pair, then the
+// warp computes the FP64 values over its finished row with every lane busy.
 template <int FILL>
 __global__ void __launch_bounds__(256) k_pairs(const StructDev* __restrict__ st, const int* __restrict__ bin_start,
                                                int64_t n, const int* __restrict__ base, const int* __restrict__ spec,
-                                               const double* __restrict__ posc, int* __restrict__ row_cnt,
-                                               const int64_t* __restrict__ row, int64_t cap, int* __restrict__ col,
-                                               double* __restrict__ val64, float* __restrict__ val32,
-                                               int* __restrict__ err, double k_e,
+                                               const double* __restrict__ posc, const float4* __restrict__ posc32,
+                                               int* __restrict__ row_cnt, const int64_t* __restrict__ row, int64_t cap,
+                                               int* __restrict__ col, double* __restrict__ val64,
+                                               float* __restrict__ val32, int* __restrict__ err, double k_e,
                                                const int* __restrict__ sorted_struct) {
   __shared__ NbrWarpSmem ws[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -231,42 +240,66 @@ __global__ void __launch_bounds__(256) k_pairs(const StructDev* __restrict__ st,
   const int bs = base[a];
   const int bb[3] = {(bs & 1023) / QEQ_BIN, ((bs >> 10) & 1023) / QEQ_BIN, ((bs >> 20) & 1023) / QEQ_BIN};
   const double ra0 = posc[3 * a], ra1 = posc[3 * a + 1], ra2 = posc[3 * a + 2];
-  const double rc2 = S.r_cut * S.r_cut;
+  const float4 pa = posc32[a];
+  const double rc = S.r_cut, rc2 = rc * rc;
+  // FP32 rounding of |r| is below ~1e-7 of the cell's extent: 1e-6 of it plus 1e-3 A is safe
+  const double ext = norm3d(S.h[0], S.h[1], S.h[2]) + norm3d(S.h[3], S.h[4], S.h[5]) + norm3d(S.h[6], S.h[7], S.h[8]);
+  const double marg = 1e-3 + 1e-6 * ext;
+  const float in2 = (float)((rc - marg) * (rc - marg)), out2 = (float)((rc + marg) * (rc + marg));
   const int64_t out = FILL ? row[a] : 0;
   int cnt = 0;
-  warp_neighbour_walk(S, bb, S.rs_range, bin_start, ws[w], [&](bool valid, int t, const double* sh, bool zero) {
-    bool acc = false;
-    double r2 = 0.0;
-    int sj = 0;
-    if (valid) {
-      sj = spec[t];
-      if (((mask >> sj) & 1u) && !(zero && t == a)) {
-        const double dx = posc[3 * t] + sh[0] - ra0;
-        const double dy = posc[3 * t + 1] + sh[1] - ra1;
-        const double dz = posc[3 * t + 2] + sh[2] - ra2;
-        r2 = dx * dx + dy * dy + dz * dz;
-        acc = r2 < rc2;
-      }
+  warp_neighbour_walk(S, bb, S.rs_range, bin_start, ws[w],
+                      [&](bool valid, int t, const double* sh, const float* sh32, bool zero, int code) {
+    bool acc = false, band = false;
+    if (valid && ((mask >> spec[t]) & 1u) && !(zero && t == a)) {
+      const float4 pt = posc32[t];
+      const float dx = pt.x + sh32[0] - pa.x, dy = pt.y + sh32[1] - pa.y, dz = pt.z + sh32[2] - pa.z;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      acc = r2 < in2;
+      band = !acc && r2 <= out2;
+    }
+    if (__any_sync(0xffffffffu, band) && band) {  // rare: the exact FP64 test
+      const double dx = posc[3 * t] + sh[0] - ra0, dy = posc[3 * t + 1] + sh[1] - ra1,
+                   dz = posc[3 * t + 2] + sh[2] - ra2;
+      acc = dx * dx + dy * dy + dz * dz < rc2;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, acc);
     if (FILL && acc) {
       const int64_t o = out + cnt + __popc(bal & ((1u << lane) - 1u));
       if (o < cap) {
-        const double r = sqrt(r2);
-        const int k = sa * QEQ_MAX_SPECIES + sj;
-        double v;
-        if (r > 1e-12)
-          v = (erfc(r * S.inv_sw[k]) - erfc(r * S.inv_sg[k])) / r;
-        else  // coincident atoms: the r -> 0 limit
-          v = (2.0 / sqrt(M_PI)) * (S.inv_sg[k] - S.inv_sw[k]);
-        v *= k_e;
         col[o] = t;
-        val64[o] = v;
-        val32[o] = (float)v;
+        val64[o] = (double)code;  // replaced by the pair value below
       }
     }
     cnt += __popc(bal);
   });
+  if (FILL) {
+    __syncwarp();
+    const int64_t m = min((int64_t)cnt, cap - out);
+    for (int64_t k = lane; k < m; k += 32) {
+      const int64_t o = out + k;
+      const int t = col[o];
+      int s[3];
+      unpack_image((int)val64[o], s);
+      double d2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double dd = posc[3 * t + d] + (s[0] * S.h[d] + s[1] * S.h[3 + d] + s[2] * S.h[6 + d]) -
+                          (d == 0 ? ra0 : (d == 1 ? ra1 : ra2));
+        d2 += dd * dd;
+      }
+      const double r = sqrt(d2);
+      const int kk = sa * QEQ_MAX_SPECIES + spec[t];
+      double v;
+      if (r > 1e-12)
+        v = (erfc(r * S.inv_sw[kk]) - erfc(r * S.inv_sg[kk])) / r;
+      else  // coincident atoms: the r -> 0 limit
+        v = (2.0 / sqrt(M_PI)) * (S.inv_sg[kk] - S.inv_sw[kk]);
+      v *= k_e;
+      val64[o] = v;
+      val32[o] = (float)v;
+    }
+  }
   if (lane == 0) {
     if (!FILL) row_cnt[a] = cnt;
     if (FILL && out + cnt > cap) atomicOr(err, ERRBIT_PAIRCAP);
@@ -299,15 +332,17 @@ cudaError_t launch_prepare_atoms(qeq_plan_s* P, const double* pos, const int32_t
   k_sorted_struct<<<nb, 256, 0, s>>>(P->d_atom_struct, P->d_perm, n, P->d_key);
   k_gather_sorted<<<nb, 256, 0, s>>>(P->d_st, P->d_atom_struct, P->d_perm, n, pos, species, chi, J, QEQ_MAXP,
                                       P->d_base, P->d_wts, P->d_wts32, P->d_spec, P->d_J, P->d_chi, P->d_dinv,
-                                      P->d_posc);
+                                      P->d_posc, P->d_posc32);
   QEQ_CUDA_TRY(cudaGetLastError());
   if (need_pairs) {
     const int nbw = (int)((n + 7) / 8);  // one warp per atom
-    k_pairs<0><<<nbw, 256, 0, s>>>(P->d_st, P->d_bin_start, n, P->d_base, P->d_spec, P->d_posc, P->d_row_cnt,
+    k_pairs<0><<<nbw, 256, 0, s>>>(P->d_st, P->d_bin_start, n, P->d_base, P->d_spec, P->d_posc, P->d_posc32,
+                                    P->d_row_cnt,
                                     nullptr, 0, nullptr, nullptr, nullptr, P->d_err, P->desc.coulomb_k, P->d_key);
     QEQ_CUDA_TRY(cudaGetLastError());
     QEQ_CUDA_TRY(exclusive_scan<int64_t>(P->d_row_cnt, n, P->d_row, (int64_t*)P->d_scan_tmp, s));
-    k_pairs<1><<<nbw, 256, 0, s>>>(P->d_st, P->d_bin_start, n, P->d_base, P->d_spec, P->d_posc, nullptr,
+    k_pairs<1><<<nbw, 256, 0, s>>>(P->d_st, P->d_bin_start, n, P->d_base, P->d_spec, P->d_posc, P->d_posc32,
+                                    nullptr,
                                     P->d_row, P->pair_cap, P->d_col, P->d_val64, P->d_val32, P->d_err,
                                     P->desc.coulomb_k, P->d_key);
     QEQ_CUDA_TRY(cudaGetLastError());

@@ -182,6 +182,7 @@ struct qeq_plan_s {
   double* d_chi = nullptr;
   double* d_dinv = nullptr;        // 1/D_i
   double* d_posc = nullptr;        // Cartesian, wrapped, sorted, 3 per atom
+  float4* d_posc32 = nullptr;      // the same in FP32 (x, y, z, 0), for the neighbour-walk distance tests
   // real-space pair list (CSR over sorted atoms)
   int64_t* d_row = nullptr;        // N+1
   int* d_row_cnt = nullptr;        // N

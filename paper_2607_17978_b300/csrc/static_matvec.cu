@@ -392,6 +392,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.d_chi = cv.take<double>(N);
   P.d_dinv = cv.take<double>(N);
   P.d_posc = cv.take<double>((size_t)N * 3);
+  P.d_posc32 = cv.take<float4>(N);
   P.d_row = cv.take<int64_t>(N + 1);
   P.d_row_cnt = cv.take<int>(N);
   P.d_col = cv.take<int>(pair_cap);
