@@ -191,7 +191,7 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems,
                   P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
-                  P->d_x32,    P->d_posc32};
+                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -595,7 +595,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(dalloc(P, &P->d_col, pair_cap));
   ALLOC(dalloc(P, &P->d_val64, pair_cap));
   ALLOC(dalloc(P, &P->d_val32, pair_cap));
-  for (double** v : {&P->d_q, &P->d_r, &P->d_z, &P->d_p, &P->d_Ap, &P->d_x}) ALLOC(dalloc(P, v, N));
+  for (double** v : {&P->d_q, &P->d_r, &P->d_z, &P->d_p, &P->d_Ap, &P->d_x, &P->d_q1, &P->d_r1})
+    ALLOC(dalloc(P, v, N));
   ALLOC(dalloc(P, &P->d_x32, N));
   ALLOC(dalloc(P, &P->d_mesh, (size_t)P->total_mesh));
   ALLOC(dalloc(P, &P->d_mesh2, (size_t)P->total_mesh));

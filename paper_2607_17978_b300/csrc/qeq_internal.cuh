@@ -107,6 +107,8 @@ struct PcgScalars {
   double w1sum;       // sum of M^-1 1
   double E_lin, E_quad, E_J;  // chi.q, q.Aq, q.Jq
   double xsum[QEQ_MAX_SPECIES];       // per-species sums of the matvec input
+  double slack;       // bound on the error of the checked residual (0 for an FP64 check)
+  double dmax, dmaxD; // max |q - q1| and max D_i since the last FP64 check
   int active;         // 1 while iterating
   int converged;      // 1 when the recursive residual meets the tolerance
   int iters;
@@ -191,6 +193,7 @@ struct qeq_plan_s {
   float* d_val32 = nullptr;
   // vectors (sorted order)
   double *d_q = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_x = nullptr;
+  double *d_q1 = nullptr, *d_r1 = nullptr;  // charges and FP64 residual at the last FP64 check
   float* d_x32 = nullptr;          // FP32 copy of the matvec input (mixed precision), written by the species sums
   // mesh (reinterpreted as float2 in mixed precision)
   double2* d_mesh = nullptr;       // layouts L0 / L2 (see matvec.cu)

@@ -227,3 +227,26 @@ def test_fourier_preconditioner_same_charges_fewer_iterations(precision):
         assert np.abs(qb[off[i]:off[i + 1]] - qi).max() < 1e-5, i
     r2 = pf.solve(*args, q0=rf.q)
     assert r2.info[0]["iterations"] <= 4
+
+
+def test_mixed_final_check_bounds_the_fp64_residual():
+    """After an FP64 check, the mixed path certifies the final charges from the FP64
+    residual of that check plus the FP32 product of the later change, with an error
+    bound. The true FP64 residual must still meet the check's threshold, and the
+    charges must agree with the plain FP64 solve."""
+    import torch
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(2)
+    args = qeq.pack([st])
+    pm = _plan([st], precision="mixed", preconditioner="fourier", ewald_tol=1e-6, r_cut=8.0)
+    pd = _plan([st], precision="fp64", ewald_tol=1e-6, r_cut=8.0)
+    rm = pm.solve(*args)
+    rd = pd.solve(*args)
+    assert rm.info[0]["restarts"] >= 1  # the change-based check was the one that accepted
+    q = rm.q
+    y = pd.matvec(torch.tensor(st.pos, device=q.device), torch.tensor(st.species, device=q.device), q,
+                  J=torch.tensor(st.J, device=q.device), fp64=True).cpu().numpy()
+    r = -st.chi - y
+    pinf = np.abs(r - r.mean()).max()
+    assert pinf <= 0.5 * 1e-5 * st.J.min(), pinf
+    assert np.abs(q.cpu().numpy() - rd.q.cpu().numpy()).max() < 1e-5
