@@ -344,10 +344,6 @@ static qeq_status build_plan(qeq_plan_s* P) {
     return idx;
   };
 
-  // atoms per reduction chunk (one CTA of the vector kernels): 512, halved down to
-  // 64 while the plan would have fewer chunks than ~4 per SM of a 148-SM GPU
-  int chunk_atoms = QEQ_CHUNK;
-  while (chunk_atoms > 64 && (P->offsets[ns] + chunk_atoms - 1) / chunk_atoms < 592) chunk_atoms >>= 1;
   for (int s = 0; s < ns; ++s) {
     StructDev& T = hs[s];
     memset(&T, 0, sizeof(T));
@@ -468,12 +464,12 @@ static qeq_status build_plan(qeq_plan_s* P) {
     // --- reduction chunks
     int first = (int)chunks.size();
     int64_t nat = T.atom_end - T.atom_begin;
-    int cnt = (int)((nat + chunk_atoms - 1) / chunk_atoms);
+    int cnt = (int)((nat + QEQ_CHUNK - 1) / QEQ_CHUNK);
     for (int c = 0; c < cnt; ++c) {
       Chunk ch;
       ch.s = s;
-      ch.begin = T.atom_begin + (int64_t)c * chunk_atoms;
-      ch.end = std::min<int64_t>(T.atom_end, ch.begin + chunk_atoms);
+      ch.begin = T.atom_begin + (int64_t)c * QEQ_CHUNK;
+      ch.end = std::min<int64_t>(T.atom_end, ch.begin + QEQ_CHUNK);
       ch.first = first;
       ch.count = cnt;
       ch.last = (c == cnt - 1);
