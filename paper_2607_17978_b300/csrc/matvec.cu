@@ -521,10 +521,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_green(con
       if (c >= ncm) break;
       V p0 = {(T)0, (T)0}, p1 = {(T)0, (T)0};
       if (PRE) {
-        // Fourier preconditioner: h(m) = beta |b(m)|^2 g0 / (1 + s0 g0), g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2
+        // Fourier preconditioner: h(m) = |b(m)|^2 g0 min(1/(1 + x), beta/x), x = s0 g0,
+        // g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2: the Woodbury factor 1/(1 + x), capped at
+        // beta/x for the smoothest modes of large cells (x > beta/(1 - beta)), where the
+        // correction nearly cancels D^-1 and the circulant approximation's error would
+        // otherwise make M indefinite
         const T e = exp2_mesh<T>(G2 * hw2[0]);
         const T g0 = gpref * e * rG2;
-        const T hm = pre_beta * pref * e * recip<T>((T)1 + pre_s0 * g0);
+        const T x = pre_s0 * g0;
+        const T fac = (x > (T)0) ? fmin(recip<T>((T)1 + x), pre_beta * recip<T>(x)) : (T)1;
+        const T hm = pref * e * fac;
         p0.x = hm * Qh[0].x;
         p0.y = hm * Qh[0].y;
       } else {

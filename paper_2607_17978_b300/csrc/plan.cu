@@ -647,8 +647,8 @@ extern "C" qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stre
   if (!(D.r_cut > 0)) D.r_cut = 8.0;
   if (D.max_iter <= 0) D.max_iter = 1000;
   if (!(D.precond_spacing > 0)) D.precond_spacing = 1.4;
-  if (!(D.precond_width > 0)) D.precond_width = 4.5;
-  if (!(D.precond_scale > 0) || D.precond_scale > 1.0) D.precond_scale = 0.98;
+  if (!(D.precond_width > 0)) D.precond_width = 3.0;
+  if (!(D.precond_scale > 0) || D.precond_scale > 1.0) D.precond_scale = 0.99;
   if (D.spline_order != 0 && D.spline_order != 4 && D.spline_order != 6 && D.spline_order != 8) {
     delete P;
     return QEQ_ERR_INVALID;
