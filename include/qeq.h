@@ -73,12 +73,12 @@ enum { QEQ_FLAG_NO_GRAPH = 1 };
  * FOURIER: D^-1 - D^-1 T^T F^-1[h F(T D^-1 r)], the Woodbury inverse of D plus the
  * long-range Coulomb operator with the mesh operator T D^-1 T^T replaced by its
  * translation-invariant mean (T: cubic B-spline spreading on a coarse FP32 mesh,
- * h(m) = |b(m)|^2 g0 min(1/(1 + x), beta/x), x = s0 g0, g0 = k_e (4 pi/V)
- * exp(-G^2 w^2/2)/G^2, s0 = sum_i 1/D_i).  The cap beta/x acts only on the smoothest
- * modes of large cells (x > beta/(1 - beta); x grows with the cell size squared), where
- * the correction nearly cancels D^-1: it keeps the preconditioner positive definite
- * when the mean differs from the real operator by less than 1 - beta, at the price of
- * eigenvalues up to 1 + (1 - beta) x for those modes.  If r.z of a preconditioned residual is not positive
+ * h(m) = beta |b(m)|^2 g0 / (1 + s0 g0), g0 = k_e (4 pi/V) exp(-G^2 w^2/2)/G^2,
+ * s0 = sum_i 1/D_i).  beta = 1 while x = s0 g0 of the smoothest mode is at most 150;
+ * larger cells (x grows with the cell size squared) use precond_scale: beta < 1 keeps
+ * the preconditioner positive definite when the mean differs from the real operator
+ * by less than 1 - beta, where the correction nearly cancels D^-1 for smooth modes,
+ * at the price of eigenvalues up to 1 + (1 - beta) x.  If r.z of a preconditioned residual is not positive
  * the structure continues with Jacobi.  It changes no result, only the iteration
  * count. */
 enum { QEQ_PRECOND_JACOBI = 0, QEQ_PRECOND_FOURIER = 1 };
@@ -110,8 +110,8 @@ typedef struct {
   int32_t preconditioner;       /* QEQ_PRECOND_JACOBI (default) or QEQ_PRECOND_FOURIER        */
   double precond_spacing;       /* FOURIER: coarse mesh spacing [A]; <= 0: 1.4                */
   double precond_width;         /* FOURIER: Gaussian width w [A]; <= 0: 3.0                   */
-  double precond_scale;         /* FOURIER: cap beta/x on the Woodbury factor 1/(1+x) of the   */
-                                /* smoothest modes, 0 < beta <= 1; <= 0: 0.99                 */
+  double precond_scale;         /* FOURIER: safety factor beta of large cells, 0 < beta <= 1;  */
+                                /* <= 0: 0.98                                                 */
 } qeq_plan_desc;
 
 /* Per-structure result of qeq_solve. */

@@ -506,6 +506,21 @@ static qeq_status build_plan(qeq_plan_s* P) {
       for (int k = 0; k < QEQ_MAX_SPECIES * QEQ_MAX_SPECIES; ++k) Tp.w2[k] = kPreWidth * kPreWidth;
       Tp.green_pref = hs[s].green_pref;
       Tp.omega = D.precond_scale;  // the coarse mesh carries beta in the otherwise unused split width
+      {  // g0 at the smallest nonzero reciprocal vector (small integer combinations of the basis)
+        double g2min = 1e300;
+        for (int m0 = -2; m0 <= 2; ++m0)
+          for (int m1 = -2; m1 <= 2; ++m1)
+            for (int m2 = -2; m2 <= 2; ++m2) {
+              if (!m0 && !m1 && !m2) continue;
+              double g2 = 0.0;
+              for (int c = 0; c < 3; ++c) {
+                double gc = m0 * Tp.B[c] + m1 * Tp.B[3 + c] + m2 * Tp.B[6 + c];
+                g2 += gc * gc;
+              }
+              g2min = std::min(g2min, g2);
+            }
+        Tp.pre_g0max = Tp.green_pref * exp(-0.5 * g2min * kPreWidth * kPreWidth) / g2min;
+      }
       for (int d = 0; d < 3; ++d) {
         Tp.fft_plan[d] = fft_plan_for(Tp.K[d]);
         Tp.bmod_off[d] = (int)bmod.size();
@@ -648,7 +663,7 @@ extern "C" qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stre
   if (D.max_iter <= 0) D.max_iter = 1000;
   if (!(D.precond_spacing > 0)) D.precond_spacing = 1.4;
   if (!(D.precond_width > 0)) D.precond_width = 3.0;
-  if (!(D.precond_scale > 0) || D.precond_scale > 1.0) D.precond_scale = 0.99;
+  if (!(D.precond_scale > 0) || D.precond_scale > 1.0) D.precond_scale = 0.98;
   if (D.spline_order != 0 && D.spline_order != 4 && D.spline_order != 6 && D.spline_order != 8) {
     delete P;
     return QEQ_ERR_INVALID;

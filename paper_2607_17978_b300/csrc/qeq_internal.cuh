@@ -21,6 +21,7 @@
 // ---------------------------------------------------------------------------
 // Per-structure constants, built on the host by qeq_plan_create.
 struct StructDev {
+  double pre_g0max;       // preconditioner mesh: largest g0(m), at the smallest nonzero |G|
   double h[9];            // cell rows a1 a2 a3
   double hinv[9];         // h^{-1}: fractional u = r h^{-1}
   double B[9];            // rows 2 pi b_k: G(m) = m0 B[0..2] + m1 B[3..5] + m2 B[6..8]
