@@ -1,7 +1,7 @@
 """Pins of the FP64 oracle against textbook physics, closed forms and invariants.
 
 The paper prints no worked QEq example, so the oracle is pinned by what the
-mathematics fixes (SURVEY-style pins P1-P7):
+mathematics fixes (pins P1-P7):
   * the rock-salt Madelung constant (point-charge limit of the Ewald machinery);
   * the Ewald split equals the plain reciprocal-sum definition for any omega;
   * the single-Gaussian self term in a cubic box against the simple-cubic
