@@ -668,7 +668,7 @@ extern "C" qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stre
   if (!(D.ewald_tol > 0)) D.ewald_tol = 1e-6;
   if (!(D.r_cut > 0)) D.r_cut = 8.0;
   if (D.max_iter <= 0) D.max_iter = 1000;
-  if (!(D.precond_spacing > 0)) D.precond_spacing = 1.4;
+  if (!(D.precond_spacing > 0)) D.precond_spacing = 2.0;
   if (!(D.precond_width > 0)) D.precond_width = 0.0;  // 0: chosen per cell size
   if (!(D.precond_scale > 0) || D.precond_scale > 1.0) D.precond_scale = 0.98;
   if (D.spline_order != 0 && D.spline_order != 4 && D.spline_order != 6 && D.spline_order != 8) {
