@@ -1,16 +1,20 @@
 """Benchmark of the periodic QEq solve on one B300 (or N replicas).
 
-One step = one complete cold-start QEq solve of the workload cell through the
-C ABI (charges to 1e-5 e, final FP64 residual check included), inputs resident
-on the device.  The default workload is the 13,824-atom rock-salt cell
-(12x12x12 conventional cells, jitter 0.15 A, r_cut 8 A, ewald_tol 1e-6); the
-chosen form is mixed precision (FP32 mesh, FP64 reductions) with the PCG
-iterations captured in a CUDA graph.  Beside it: the plain FP64 GPU PCG (no
-graph), the roofline of the dominant matvec kernel (CUDA events on the plan's
-stream), an end-to-end number through the public API with host buffers, and
-the FP64 CPU oracle timed on the host cores.
+One step = one complete cold- or warm-start QEq solve of the workload through
+the C ABI (charges to 1e-5 e, final FP64 residual check included), inputs
+resident on the device.  The default workload is the largest single-GPU cell,
+the 980,000-atom rock-salt cell (50x50x50 conventional cells, 2% vacancies,
+jitter 0.2 A, r_cut 8 A, ewald_tol 1e-6); the chosen form is mixed precision
+(FP32 mesh, FP64 reductions), the Fourier-Woodbury preconditioner, the learned
+warm start (rock-salt recipe) and the PCG iterations captured in CUDA graphs.
+Beside it: the plain FP64 GPU PCG (Jacobi, no graph), the roofline of the
+dominant matvec kernel (CUDA events on the plan's stream), the whole matvec
+against the algorithmic byte model 24 S M + 28 N, the error of the chosen
+form against the FP64 oracle (dense solve, or the oracle's residual on sampled
+rows where a dense solve is infeasible), an end-to-end number through the
+public API with host buffers, and the FP64 CPU oracle timed on the host cores.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2|1|3|5]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 5|1|2|3|4]
 
 --gpus N > 1 runs under torch.distributed.run with no collective on the data
 path: a single cell runs as one replica per rank ("scaling": "weak"); the
@@ -37,11 +41,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QEq solves/s and atoms*CG-iters/s at 1e-5 e vs plain FP64 GPU PCG; % HBM roofline"
 UNIT = "solves/s"
-# Jacobi-PCG iterations of a full solve of the default workload at 1e-5 e (about 100 on
-# this 13,824-atom cell), used to
-# extrapolate the CPU oracle's matvec time to a solve (the oracle's own solve is
-# a dense LU that does not fit the time budget at this size).
-PCG_ITERS_REFERENCE = 100
+# Jacobi-PCG iterations of the plain FP64 solve at 1e-5 e, measured on the GPU with the
+# current code (bench line "plain_fp64.iterations"), used by the reference arm to scale
+# the CPU oracle's measured matvec time to a solve where the dense solve does not fit
+# the time budget; the arm of ours uses the count measured in the same run.
+PLAIN_PCG_ITERS = {1: 21, 2: 94, 3: 234, 5: 409}
 WORKLOAD_OPTS = {
     1: dict(ewald_tol=1e-7, r_cut=9.0),
     2: dict(ewald_tol=1e-6, r_cut=8.0),
@@ -119,27 +123,45 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- byte model
-def stage_bytes(plan, prec: str, n_atoms: int, pairs: int):
-    """Algorithmic DRAM bytes per launch of each matvec stage (all structures of the plan)."""
-    cs = 8 if prec == "mixed" else 16          # complex element
-    rs = 4 if prec == "mixed" else 8           # real element
-    mesh = 0
+def mesh_points(plan):
+    """Sum over structures of S * M (species x mesh points): the real meshes of the byte model."""
+    sm = 0
     for s in range(plan.n_struct):
         qi = plan.query(s)
         K = qi["mesh"]
-        mesh += K[0] * K[1] * K[2] * ((qi["n_species"] + 1) // 2)
-    p = plan.query(0)["spline_order"]
-    atom_in = n_atoms * (3 * p * rs + 4 + 4 + 8)  # spline weights, stencil base, species, x
+        sm += K[0] * K[1] * K[2] * qi["n_species"]
+    return sm
+
+
+def stage_bytes(plan, prec: str, n_atoms: int):
+    """Algorithmic DRAM bytes per launch of each matvec stage (all structures of the plan).
+
+    The algorithmic model of one matvec is B = S M (4 spread write + 4 + 4 forward FFT
+    + 4 + 4 inverse FFT + 4 gather read) + N (8 q + 12 pos + 8 y) = 24 S M + 28 N bytes
+    in FP32 (mesh bytes doubled in FP64).  Per stage: the spread writes the mesh once and
+    reads positions and charges (4 S M + 20 N), every FFT pass reads and writes the mesh
+    once (8 S M; the passes beyond one per direction count against the matvec's
+    efficiency, not against its budget), the gather reads the mesh once and writes y
+    (4 S M + 8 N).  Real-space pair bytes are not part of the model.
+    """
+    rs = 4 if prec == "mixed" else 8           # one real mesh value
+    SM = mesh_points(plan)
     return {
         "species_sums": n_atoms * (8 + 4),
-        "spread": mesh * cs + atom_in,
-        "fft_z": 2 * mesh * cs,
-        "fft_y": 2 * mesh * cs,
-        "fft_x_green": 2 * mesh * cs,
-        "ifft_y": 2 * mesh * cs,
-        "ifft_z": 2 * mesh * cs,
-        "gather": mesh * cs + atom_in + n_atoms * (8 + 8 + 8) + pairs * (rs + 4),
+        "spread": SM * rs + n_atoms * 20,
+        "fft_z": 2 * SM * rs,
+        "fft_y": 2 * SM * rs,
+        "fft_x_green": 2 * SM * rs,
+        "ifft_y": 2 * SM * rs,
+        "ifft_z": 2 * SM * rs,
+        "gather": SM * rs + n_atoms * 8,
     }
+
+
+def matvec_model_bytes(plan, prec: str, n_atoms: int):
+    """24 S M + 28 N (FP32; 48 S M + 28 N in FP64): the bytes one matvec must move."""
+    rs = 4 if prec == "mixed" else 8
+    return 6 * rs * mesh_points(plan) + 28 * n_atoms
 
 
 def load_traffic():
@@ -152,38 +174,95 @@ def load_traffic():
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_matvec_time(st, budget_s: float = 20.0):
-    from oracle import qeq_oracle as O
-    from paper_2607_17978_b300 import synth
+def _cores():
     cores = len(os.sched_getaffinity(0))
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    O.build_c()
-    q = np.random.default_rng(0).normal(size=st.n)
-    times = []
-    t_start = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > budget_s * 0.5 or len(times) >= 5:
-            break
-    return min(times), cores, len(times)
+    return cores
 
 
-def cpu_oracle_dense_batch(structs, every: int = 64):
-    """Dense bordered oracle solves of a stratified sample of a batch: solves/s."""
+def oracle_matvec_seconds(st, reps: int = 1):
+    """Best wall time of the oracle's full FP64 Ewald matvec of ``st`` over ``reps`` calls."""
     from oracle import qeq_oracle as O
     from paper_2607_17978_b300 import synth
-    cores = len(os.sched_getaffinity(0))
     O.build_c()
+    q = np.random.default_rng(0).normal(size=st.n)
+    best = math.inf
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+# full oracle matvecs above this many atoms do not fit the bench's CPU budget (minutes each):
+# their time is extrapolated from two smaller cells of the same recipe
+FULL_MATVEC_MAX_ATOMS = 200_000
+SUBCELLS = (16, 24)          # conventional cells per edge of the two timed sub-cells
+
+
+def oracle_matvec_estimate(workload: int, st, reps: int = 1):
+    """Oracle FP64 matvec time of the workload cell: measured, or extrapolated by the power
+    law t = a N^b through two timed sub-cells of the same recipe.  Returns (seconds, text)."""
+    from paper_2607_17978_b300 import synth
+    if st.n <= FULL_MATVEC_MAX_ATOMS:
+        t = oracle_matvec_seconds(st, reps)
+        return t, f"FP64 oracle Ewald matvec of the full {st.n}-atom cell: {t:.2f} s (measured)"
+    sub = [synth.workload(workload, scale=k) for k in SUBCELLS]
+    ts = [oracle_matvec_seconds(x, reps) for x in sub]
+    b = math.log(ts[1] / ts[0]) / math.log(sub[1].n / sub[0].n)
+    t = ts[1] * (st.n / sub[1].n) ** b
+    return t, (f"FP64 oracle Ewald matvec measured on {sub[0].n} and {sub[1].n}-atom cells of the same recipe "
+               f"({ts[0]:.2f} s, {ts[1]:.2f} s), extrapolated to {st.n} atoms by t ~ N^{b:.2f}: {t:.1f} s")
+
+
+def oracle_error_single(workload: int, st, q, mu, n_rows: int = 64):
+    """Error of GPU charges q (input order) against the FP64 oracle.
+
+    Dense bordered solve up to 2,000 atoms (max |q - q*|); the oracle's full matvec up to
+    FULL_MATVEC_MAX_ATOMS (projected residual P(A q + chi) on every atom and the certified
+    bound ||q - q*||_2 <= ||P(A q + chi)||_2 / J_min); above, the residual on n_rows seeded
+    sampled rows.  Returns (dict, seconds spent)."""
+    from oracle import qeq_oracle as O
+    from paper_2607_17978_b300 import synth
+    O.build_c()
+    KE = synth.COULOMB_K_EV_A
+    t0 = time.perf_counter()
+    if st.n <= 2000:
+        sol = O.solve_structure(st, k_e=KE)
+        out = {"kind": "dense bordered oracle solve, every atom", "max_dq_e": float(np.abs(q - sol.q).max()),
+               "dmu_eV": float(abs(mu - sol.mu))}
+    elif st.n <= FULL_MATVEC_MAX_ATOMS:
+        y = O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=KE)
+        Pr, mu_o = O.projected_residual(y, st.J, st.chi, q)
+        out = {"kind": "oracle FP64 matvec of the chosen charges, every atom",
+               "residual_inf_eV": float(np.abs(Pr).max()), "bound_l2_e": O.certified_bound(Pr, st.J),
+               "dmu_eV": float(abs(mu - mu_o)), "stop_threshold_eV": 0.5 * 1e-5 * float(st.J.min())}
+    else:
+        rows = np.sort(np.random.default_rng(workload).choice(st.n, n_rows, replace=False))
+        omega = 11.0
+        y = O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=KE, omega=omega, rows=rows)
+        r = y + st.J[rows] * q[rows] + st.chi[rows] - mu
+        out = {"kind": f"oracle FP64 residual (A q + chi - mu) of the chosen charges on {n_rows} seeded sampled rows",
+               "residual_inf_eV": float(np.abs(r).max()), "stop_threshold_eV": 0.5 * 1e-5 * float(st.J.min())}
+    return out, time.perf_counter() - t0
+
+
+def oracle_error_batch(structs, q, mu, every: int = 64):
+    """Dense oracle solves of every ``every``-th structure of a batch: max |q - q*|, and their time."""
+    from oracle import qeq_oracle as O
+    from paper_2607_17978_b300 import synth
+    O.build_c()
+    off = np.concatenate([[0], np.cumsum([x.n for x in structs])])
     sample = list(range(0, len(structs), every))
+    worst, dmu = 0.0, 0.0
     t0 = time.perf_counter()
     for k in sample:
-        O.solve_structure(structs[k], k_e=synth.COULOMB_K_EV_A)
+        sol = O.solve_structure(structs[k], k_e=synth.COULOMB_K_EV_A)
+        worst = max(worst, float(np.abs(q[off[k]:off[k + 1]] - sol.q).max()))
+        dmu = max(dmu, float(abs(mu[k] - sol.mu)))
     t = time.perf_counter() - t0
-    return (len(sample) / t, cores,
-            f"dense FP64 oracle solves (Ewald assembly + bordered LU) of {len(sample)} of {len(structs)} structures "
-            f"(every {every}th), {t:.1f} s")
+    return ({"kind": f"dense bordered oracle solves of {len(sample)} of {len(structs)} structures (every {every}th)",
+             "max_dq_e": worst, "dmu_eV": dmu}, len(sample) / t, t)
 
 
 def run_reference(args):
@@ -194,8 +273,9 @@ def run_reference(args):
     from oracle import qeq_oracle as O
     from paper_2607_17978_b300 import synth
     structs = workload_structs(args.workload)
-    cores = len(os.sched_getaffinity(0))
+    cores = _cores()
     O.build_c()
+    extra = {}
     if len(structs) > 1:
         # one dense bordered solve per step, cycling through every 64th structure
         sample = list(range(0, len(structs), 64))
@@ -204,29 +284,57 @@ def run_reference(args):
         t0 = time.perf_counter()
         for k in range(args.steps):
             O.solve_structure(structs[sample[k % len(sample)]], k_e=synth.COULOMB_K_EV_A)
-        solve_s = (time.perf_counter() - t0) / args.steps
+        step_s = (time.perf_counter() - t0) / args.steps
+        solve_s = step_s
         desc = (f"dense FP64 oracle solve (Ewald assembly + bordered LU) of one structure per step, cycling through "
                 f"every 64th of the {len(structs)} structures")
         atoms = sum(x.n for x in structs)
-    else:
+    elif structs[0].n <= 2000:
         st = structs[0]
-        q = np.random.default_rng(0).normal(size=st.n)
         for _ in range(args.warmup):
-            O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
+            O.solve_structure(st, k_e=synth.COULOMB_K_EV_A)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            O.ewald_matvec(st.cell, st.pos, st.sigma, q, k_e=synth.COULOMB_K_EV_A)
-        solve_s = (time.perf_counter() - t0) / args.steps * PCG_ITERS_REFERENCE
-        desc = (f"one FP64 Ewald matvec of the full {st.n}-atom cell per step by the CPU oracle, "
-                f"x {PCG_ITERS_REFERENCE} PCG iterations (extrapolated to a solve)")
+            O.solve_structure(st, k_e=synth.COULOMB_K_EV_A)
+        step_s = solve_s = (time.perf_counter() - t0) / args.steps
+        desc = f"dense FP64 oracle solve (Ewald assembly + bordered LU) of the {st.n}-atom cell per step"
+        atoms = st.n
+    else:
+        # one oracle FP64 matvec per step (of the cell itself when it fits, else of a sub-cell of
+        # the same recipe, alternating the two sizes of the extrapolation); a solve is that
+        # matvec time x the plain-PCG iteration count of this workload
+        st = structs[0]
+        iters = PLAIN_PCG_ITERS[args.workload]
+        cells = [st] if st.n <= FULL_MATVEC_MAX_ATOMS else [synth.workload(args.workload, scale=k) for k in SUBCELLS]
+        for k in range(args.warmup):
+            oracle_matvec_seconds(cells[k % len(cells)])
+        ts = [[] for _ in cells]
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ts[k % len(cells)].append(oracle_matvec_seconds(cells[k % len(cells)]))
+        step_s = (time.perf_counter() - t0) / args.steps
+        if len(cells) == 1:
+            t_mv = float(np.mean(ts[0]))
+            how = f"measured, mean of {len(ts[0])}"
+        else:
+            m = [float(np.mean(x)) for x in ts]
+            b = math.log(m[1] / m[0]) / math.log(cells[1].n / cells[0].n)
+            t_mv = m[1] * (st.n / cells[1].n) ** b
+            how = (f"steps alternate {cells[0].n}- and {cells[1].n}-atom cells of the same recipe "
+                   f"({m[0]:.2f} s, {m[1]:.2f} s), extrapolated to {st.n} atoms by t ~ N^{b:.2f}")
+        solve_s = t_mv * iters
+        desc = (f"one FP64 oracle Ewald matvec per step ({how}); solve = matvec {t_mv:.2f} s x {iters} plain "
+                f"Jacobi-PCG iterations (measured on the GPU for this workload)")
+        extra = {"solve_seconds_extrapolated": solve_s, "matvec_seconds": t_mv}
         atoms = st.n
     value = 1.0 / solve_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": atoms, "structures": len(structs)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -348,8 +456,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (per-stage CUDA events on the plan's stream)
     prof = plan.profile_matvec(20)
-    pairs_est = 0
-    sb = stage_bytes(plan, args.precision, n_atoms, pairs_est)
+    sb = stage_bytes(plan, args.precision, n_atoms)
     dom = max(prof, key=prof.get)
     pk = peaks()
     hbm = pk.get("hbm_gbs")
@@ -358,7 +465,7 @@ def run_ours(args):
     achieved = sb[dom] / (prof[dom] * 1e-3) / 1e9
     traffic = load_traffic().get(f"{dom}:{args.workload}:{args.precision}")
     matvec_ms = sum(prof.values())
-    matvec_bytes = sum(sb.values())
+    matvec_bytes = matvec_model_bytes(plan, args.precision, n_atoms)
 
     # ---- plain FP64 GPU PCG (one structure per launch, no graph): the comparison denominator
     sample = list(range(0, n_struct, 16)) if n_struct > 1 else [0]
@@ -371,7 +478,7 @@ def run_ours(args):
         q1 = np.array([s1.q_tot])
         plain.solve(*a1, q1)
         torch.cuda.synchronize()
-        n_plain = max(1, min(3, args.steps)) if n_struct == 1 else 1
+        n_plain = max(1, min(3, args.steps)) if (n_struct == 1 and s1.n < 100_000) else 1
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.fill_(0.0)
         plain.stream.wait_stream(torch.cuda.current_stream(dev))
@@ -411,17 +518,29 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    # ---- error of the chosen form against the FP64 oracle, and the oracle timed on the host cores
+    cpu, oracle_err = None, None
+    if not args.no_oracle:
+        cores = _cores()
+        q_np = q_out.cpu().numpy()
+        mu_np = res.mu.cpu().numpy()
         if n_struct > 1:
-            v, cores, smp = cpu_oracle_dense_batch(structs)
-            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp}
+            oracle_err, v, t_or = oracle_error_batch(structs, q_np, mu_np)
+            if world == 1:
+                cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                       "sample": f"{oracle_err['kind']}: {t_or:.1f} s (the same solves that give the oracle error)"}
         else:
-            t_mv, cores, reps = cpu_oracle_matvec_time(st)
-            v = 1.0 / (t_mv * PCG_ITERS_REFERENCE)
-            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": (f"FP64 Ewald matvec of the full {st.n}-atom cell by the CPU oracle (best of {reps}), "
-                              f"x {PCG_ITERS_REFERENCE} PCG iterations: extrapolated to one solve")}
+            oracle_err, t_or = oracle_error_single(args.workload, st, q_np, float(mu_np[0]))
+            if world == 1:
+                if st.n <= 2000:
+                    t_solve = t_or
+                    cpu = {"value": 1.0 / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"dense FP64 oracle solve (Ewald assembly + bordered LU) of the cell: {t_solve:.3f} s"}
+                else:
+                    it_p = float(np.mean(plain_iters))
+                    t_mv, how = oracle_matvec_estimate(args.workload, st)
+                    cpu = {"value": 1.0 / (t_mv * it_p), "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"{how}; x {it_p:.0f} plain Jacobi-PCG iterations measured in this run = one solve"}
     value = n_total * 1000.0 / ms
     qi = plan.query(0)
     line = {
@@ -444,10 +563,12 @@ def run_ours(args):
                        "sample": ("every structure" if n_struct == 1 else
                                   f"{len(sample)} of {n_struct} structures (every 16th) solved one at a time, "
                                   f"time scaled by {n_struct}/{len(sample)}")},
-        "matvec": {"ms": matvec_ms, "algorithmic_bytes": matvec_bytes,
+        "matvec": {"ms": matvec_ms, "model": "24 S M + 28 N bytes (FP32 mesh; 48 S M + 28 N in FP64)",
+                   "algorithmic_bytes": matvec_bytes,
                    "GBps": matvec_bytes / (matvec_ms * 1e-3) / 1e9,
                    "frac_hbm": matvec_bytes / (matvec_ms * 1e-3) / 1e9 / hbm,
-                   "stages_ms": {k: round(v, 5) for k, v in prof.items()}},
+                   "stages_ms": {k: round(v, 5) for k, v in prof.items()},
+                   "stage_frac_hbm": {k: round(sb[k] / (prof[k] * 1e-3) / 1e9 / hbm, 4) for k in prof if prof[k] > 0}},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "algorithmic_bytes_per_launch": sb[dom], "launch_ms": prof[dom]},
@@ -455,6 +576,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if oracle_err:
+        line["oracle_error"] = oracle_err
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -467,9 +590,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle error and the CPU oracle baseline (host work after the GPU legs)")
     ap.add_argument("--precond", default="fourier", choices=["fourier", "jacobi"],
                     help="preconditioner of the chosen form (the plain FP64 leg always uses Jacobi)")
     ap.add_argument("--warm", default="auto", choices=["auto", "mlp", "cold"],

@@ -958,6 +958,18 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
 }
 
 // ------------------------------------------------------------------ Fourier preconditioner
+// Power-of-two scale of the fixed-point coarse spread: max |D^-1 r| is at most
+// max|r| max D^-1 (max D^-1 alone for the ones vector), mapped to 2^48; a mesh
+// point sums the B-spline weights (each at most 2/3 per direction) of the atoms
+// around it, far below the 2^15 headroom of a signed 64-bit integer.
+__device__ __forceinline__ double pre_fixed_scale(const PcgScalars& c, int ones_input) {
+  double b = c.dinv_max * (ones_input ? 1.0 : fmax(fabs(c.r_max), fabs(c.r_min)));
+  if (!(b > 0.0) || !isfinite(b)) b = 1.0;
+  int e;
+  frexp(b, &e);                    // b < 2^e
+  return ldexp(1.0, 48 - e);
+}
+
 // Cubic B-spline (order 4) weights of every atom on its structure's coarse mesh,
 // once per solve: M_4(w + j), j = 0..3, for stencil points f - j.
 __global__ void k_pre_weights(const StructDev* __restrict__ stp, const int* __restrict__ sorted_struct,
@@ -985,11 +997,17 @@ __global__ void k_pre_weights(const StructDev* __restrict__ stp, const int* __re
   pbase[a] = f[0] | (f[1] << 10) | (f[2] << 20);
 }
 
-// v = D^-1 r spread on the coarse mesh (real part); the mesh is small and L2 resident
+// v = D^-1 r spread on the coarse mesh in 64-bit fixed point: every contribution
+// is rounded to an integer multiple of 2^-e (e per structure, from a bound on
+// max |v|) and added with an integer atomic.  Integer addition does not depend
+// on the order of the atomics, so the coarse mesh, and with it every
+// preconditioned solve, is bitwise reproducible.  k_pre_fixed_to_float turns the
+// sums back into the FP32 mesh.
 __global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __restrict__ sorted_struct,
                              const int* __restrict__ pbase, const float* __restrict__ pw,
                              const double* __restrict__ dinv, const double* __restrict__ r, int64_t n,
-                             const PcgScalars* __restrict__ sc, int use_active, float2* __restrict__ mesh) {
+                             const PcgScalars* __restrict__ sc, int use_active, int ones_input,
+                             unsigned long long* __restrict__ imesh) {
   int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n) return;
   const int s = sorted_struct[a];
@@ -999,7 +1017,8 @@ __global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __res
   const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
   const float* w = pw + a * 12;
   const float v = (float)(dinv[a] * r[a]);
-  float2* m = mesh + S.mesh_off;
+  const double scale = pre_fixed_scale(sc[s], ones_input);
+  unsigned long long* m = imesh + S.mesh_off;
   for (int jx = 0; jx < 4; ++jx) {
     int kx = f[0] - jx;
     if (kx < 0) kx += S.K[0];
@@ -1007,13 +1026,30 @@ __global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __res
       int ky = f[1] - jy;
       if (ky < 0) ky += S.K[1];
       const float wxy = v * w[jx] * w[4 + jy];
-      float2* row = m + ((int64_t)kx * S.K[1] + ky) * S.K[2];
+      unsigned long long* row = m + ((int64_t)kx * S.K[1] + ky) * S.K[2];
       for (int jz = 0; jz < 4; ++jz) {
         int kz = f[2] - jz;
         if (kz < 0) kz += S.K[2];
-        atomicAdd(&row[kz].x, wxy * w[8 + jz]);
+        const long long c = __double2ll_rn((double)(wxy * w[8 + jz]) * scale);
+        atomicAdd(&row[kz], (unsigned long long)c);
       }
     }
+  }
+}
+
+// fixed-point coarse mesh -> FP32 complex mesh (real part), structure found by bisection
+__global__ void k_pre_fixed_to_float(const StructDev* __restrict__ stp, int ns, int64_t total,
+                                     const PcgScalars* __restrict__ sc, int ones_input,
+                                     const unsigned long long* __restrict__ imesh, float2* __restrict__ mesh) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (stp[mid].mesh_off <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const double inv = 1.0 / pre_fixed_scale(sc[lo], ones_input);
+    mesh[i] = make_float2((float)((double)(long long)imesh[i] * inv), 0.f);
   }
 }
 
@@ -1200,10 +1236,17 @@ cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, 
   cudaStream_t s = P->stream;
   const size_t smf = sizeof(float2) * (size_t)P->fft_smem_elems;
   const float* bmod = P->d_bmod32;
-  count_launch(P, 7);
-  QEQ_CUDA_TRY(cudaMemsetAsync(P->d_pmesh, 0, sizeof(float2) * (size_t)P->total_pmesh, s));
+  count_launch(P, 8);
+  // fixed-point sums in the second coarse buffer (8 bytes per point, like the float2 mesh)
+  unsigned long long* imesh = reinterpret_cast<unsigned long long*>(P->d_pmesh2);
+  QEQ_CUDA_TRY(cudaMemsetAsync(imesh, 0, sizeof(unsigned long long) * (size_t)P->total_pmesh, s));
   k_pre_spread<<<(int)((P->n_atoms + 255) / 256), 256, 0, s>>>(P->d_stp, P->d_key, P->d_pbase, P->d_pw, P->d_dinv, r,
-                                                               P->n_atoms, P->d_sc, use_active, P->d_pmesh);
+                                                               P->n_atoms, P->d_sc, use_active, slot == 1, imesh);
+  {
+    const int nb = (int)std::min<int64_t>((P->total_pmesh + 255) / 256, 148 * 16);
+    k_pre_fixed_to_float<<<nb, 256, 0, s>>>(P->d_stp, P->n_struct, P->total_pmesh, P->d_sc, slot == 1, imesh,
+                                            P->d_pmesh);
+  }
   k_fft_pass<float, PASS_ZF><<<P->n_pz, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pzitems, P->d_tw64, P->d_tw32, P->d_sc,
                                                        use_active, P->d_pmesh, P->d_pmesh2, P->tlp);
   k_fft_pass<float, PASS_YF><<<P->n_py, 256, smf, s>>>(P->d_stp, P->d_fft, P->d_pyitems, P->d_tw64, P->d_tw32, P->d_sc,

@@ -191,7 +191,7 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems,
                   P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
-                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1};
+                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -632,6 +632,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(dalloc(P, &P->d_err, 4));
   ALLOC(cudaMemset(P->d_err, 0, sizeof(int) * 4));
   ALLOC(dalloc(P, &P->d_done, 4));
+  ALLOC(dalloc(P, &P->d_reject, ns));
+  ALLOC(cudaMemset(P->d_reject, 0, sizeof(int) * ns));
   ALLOC(cudaHostAlloc((void**)&P->h_done, sizeof(int) * 8, cudaHostAllocDefault));
   ALLOC(cudaEventCreateWithFlags(&P->ev_done, cudaEventDisableTiming));
   if (P->precond == QEQ_PRECOND_FOURIER) {

@@ -110,6 +110,7 @@ struct PcgScalars {
   double xsum[QEQ_MAX_SPECIES];       // per-species sums of the matvec input
   double slack;       // bound on the error of the checked residual (0 for an FP64 check)
   double dmax, dmaxD; // max |q - q1| and max D_i since the last FP64 check
+  double dinv_max;    // max_i 1/D_i (scale of the fixed-point coarse spread)
   int active;         // 1 while iterating
   int converged;      // 1 when the recursive residual meets the tolerance
   int iters;
@@ -206,6 +207,7 @@ struct qeq_plan_s {
   PcgScalars* d_sc = nullptr;
   int* d_err = nullptr;            // device error bits
   int* d_done = nullptr;           // all-structures-inactive flag
+  int* d_reject = nullptr;         // n_struct: 1 where the network start was rejected
   int* h_done = nullptr;           // pinned mirror
   cudaEvent_t ev_done = nullptr;
   // Fourier preconditioner (coarse mesh per structure)

@@ -92,15 +92,17 @@ __device__ bool chunk_reduce(double (&v)[NV], const int (&op)[NV], const Chunk& 
 }
 
 // q0: user charges (permuted to sorted order) or zero; sums for the projection.
+// reject (MLP start only, may be NULL): structures whose network start was rejected start cold.
 __global__ void k_init(const Chunk* __restrict__ chunks, const int* __restrict__ perm, const double* __restrict__ q_user,
-                       int warm, const double* __restrict__ dinv, const double* __restrict__ chi,
-                       const double* __restrict__ J, double* __restrict__ q, PcgScalars* __restrict__ sc,
-                       double* part, int* counter) {
+                       int warm, const int* __restrict__ reject, const double* __restrict__ dinv,
+                       const double* __restrict__ chi, const double* __restrict__ J, double* __restrict__ q,
+                       PcgScalars* __restrict__ sc, double* part, int* counter) {
   const Chunk ch = chunks[blockIdx.x];
   double v[6] = {0, 0, 0, 0, 1e300, 0};
-  const int op[6] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM, RED_MIN, RED_SUM};
+  const int op[6] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM, RED_MIN, RED_MAX};
+  const bool mlp_kept = warm == QEQ_WARM_MLP && !(reject && reject[ch.s]);
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
-    double qa = (warm == QEQ_WARM_USER) ? q_user[perm[a]] : (warm == QEQ_WARM_MLP ? q[a] : 0.0);
+    double qa = (warm == QEQ_WARM_USER) ? q_user[perm[a]] : (mlp_kept ? q[a] : 0.0);
     if (!isfinite(qa)) qa = 0.0;
     q[a] = qa;
     v[0] += qa;
@@ -108,6 +110,7 @@ __global__ void k_init(const Chunk* __restrict__ chunks, const int* __restrict__
     v[2] += chi[a];
     v[3] += chi[a] * chi[a];
     v[4] = fmin(v[4], J[a]);
+    v[5] = fmax(v[5], dinv[a]);
   }
   double tot[6];
   if (chunk_reduce<6>(v, op, ch, part, counter, tot)) {
@@ -118,6 +121,7 @@ __global__ void k_init(const Chunk* __restrict__ chunks, const int* __restrict__
     c.chi_p2 = fmax(tot[3] - tot[2] * tot[2] / n, 0.0);
     c.chi_sum = tot[2];
     c.j_min = tot[4];
+    c.dinv_max = tot[5];
   }
 }
 
@@ -418,6 +422,11 @@ __global__ void k_vec_sum(const Chunk* __restrict__ chunks, const double* __rest
   if (chunk_reduce<1>(v, op, ch, part, counter, tot)) sc[ch.s].E_quad = tot[0];
 }
 
+__global__ void k_flip(int* __restrict__ f, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = f[i] ? 0 : 1;
+}
+
 __global__ void k_fill(double* __restrict__ x, int64_t n, double v) {
   int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a < n) x[a] = v;
@@ -632,11 +641,13 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     TRY(launch_mlp_warm_start(P, P->d_q));
     wm = QEQ_WARM_MLP;
   }
-  int warm_kept = (wm != QEQ_WARM_COLD) ? 1 : 0;
+  // per structure: 1 when the solve starts from the user's or the network's charges
+  std::vector<int> warm_kept(ns, wm != QEQ_WARM_COLD ? 1 : 0);
+  const int* reject = nullptr;
   if (P->precond == QEQ_PRECOND_FOURIER) TRY(launch_precond_setup(P));
   for (int attempt = 0; attempt < 2; ++attempt) {
     count_launch(P, 3);
-    k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q, wm, P->d_dinv, P->d_chi, P->d_J, P->d_q, P->d_sc,
+    k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q, wm, reject, P->d_dinv, P->d_chi, P->d_J, P->d_q, P->d_sc,
                               red_part(P), red_counter(P));
     k_project<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_sc);
     k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol,
@@ -654,7 +665,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
                                red_counter(P), max_iter);
     TRY(cudaGetLastError());
-    if (wm != QEQ_WARM_MLP) break;
+    if (wm != QEQ_WARM_MLP || attempt == 1) break;
     // The plain method judges the network's start by the quantity CG minimises: on the
     // constraint plane E(q) - E(q*) = 1/2 ||q - q*||_A^2, so the start is kept iff its
     // energy is below that of the uniform start q_tot/N (E = 0 when q_tot = 0; otherwise
@@ -674,17 +685,24 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     std::vector<PcgScalars> h(ns);
     TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
-    bool bad = false;
+    // each structure keeps or rejects its own network start; the rejected ones restart
+    // from the uniform start (every structure's first residual is recomputed, the kept
+    // ones reproduce theirs exactly)
+    int n_bad = 0;
     for (int i = 0; i < ns; ++i) {
       double n = (double)h[i].n, qu = h_qtot[i] / n;
       double e_cold = 0.0;
       if (h_qtot[i] != 0.0) e_cold = qu * h[i].chi_sum + 0.5 * qu * qu * h[i].E_quad;
-      if (!std::isfinite(h[i].E_lin) || !(h[i].E_lin < e_cold)) bad = true;
+      const bool bad = !std::isfinite(h[i].E_lin) || !(h[i].E_lin < e_cold);
+      warm_kept[i] = bad ? 0 : 1;
+      n_bad += bad ? 1 : 0;
     }
-    if (!bad) break;
-    wm = QEQ_WARM_COLD;
-    warm_kept = 0;
-    TRY(init_scalars(P, h_qtot) == QEQ_OK ? cudaSuccess : cudaErrorUnknown);
+    if (n_bad == 0) break;
+    TRY(cudaMemcpyAsync(P->d_reject, warm_kept.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+    count_launch(P);
+    k_flip<<<(ns + 255) / 256, 256, 0, s>>>(P->d_reject, ns);  // kept -> 0, rejected -> 1
+    TRY(init_scalars(P, h_qtot) == QEQ_OK ? cudaSuccess : cudaErrorUnknown);  // synchronises the copy
+    reject = P->d_reject;
   }
   TRY(precondition(P, 1, 1));
   count_launch(P);
@@ -751,7 +769,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
       h_info[i].status = c.status;
       h_info[i].iterations = c.iters;
       h_info[i].restarts = c.restarts;
-      h_info[i].warm_used = warm_kept;
+      h_info[i].warm_used = warm_kept[i];
       h_info[i].residual_inf = pinf;
       h_info[i].residual_l2 = pl2;
       h_info[i].error_bound_l2 = pl2 / c.j_min;

@@ -391,22 +391,42 @@ class Mlp:
 
 
 def matvec_static(cell, sigma_s, pos, species, x, J=None, *, coulomb_k=14.3996454784, ewald_tol=1e-6,
-                  r_cut=8.0, stream=None):
+                  r_cut=8.0, stream=None, device=None):
     """FP64 matvec of one small cell through qeq_matvec_static (no device allocation in the library).
 
-    Device inputs are torch CUDA tensors; the output tensor is allocated here by
-    the caller side (torch), the library itself allocates nothing.
+    Inputs are converted to contiguous float64 / int32 tensors on the target
+    device and their sizes checked against n = len(x) before the call; the
+    output tensor is allocated here (torch), the library itself allocates
+    nothing.  The call runs on ``stream`` (default: torch's current stream of
+    that device), so it is ordered after the caller's earlier work there.
     """
     import torch
     lib = load_library()
+    dev = torch.device(device) if device is not None else (x.device if isinstance(x, torch.Tensor) else
+                                                           torch.device("cuda"))
+    if dev.type != "cuda":
+        raise QEqError(QEQ_ERR_INVALID, "qeq_matvec_static needs CUDA tensors")
+
+    def _as(t, dtype):
+        return torch.as_tensor(t, dtype=dtype, device=dev).contiguous()
+
+    x = _as(x, torch.float64).reshape(-1)
+    pos = _as(pos, torch.float64).reshape(-1)
+    species = _as(species, torch.int32).reshape(-1)
+    J = _as(J, torch.float64).reshape(-1) if J is not None else None
+    n = int(x.numel())
+    if pos.numel() != 3 * n or species.numel() != n or (J is not None and J.numel() != n):
+        raise QEqError(QEQ_ERR_INVALID, f"qeq_matvec_static: pos must hold 3n, species and J n entries (n = {n})")
     cell = np.ascontiguousarray(np.asarray(cell, np.float64).reshape(9))
-    sig = np.ascontiguousarray(np.asarray(sigma_s, np.float64))
-    n = int(x.shape[0])
-    y = torch.empty(n, dtype=torch.float64, device=x.device)
-    st = lib.qeq_matvec_static(cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                               sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sig), n, _ptr(pos),
-                               _ptr(species), _ptr(J), _ptr(x), _ptr(y), coulomb_k, ewald_tol, r_cut,
-                               ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
+    sig = np.ascontiguousarray(np.asarray(sigma_s, np.float64).reshape(-1))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        st = lib.qeq_matvec_static(cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sig), n, _ptr(pos),
+                                   _ptr(species), _ptr(J), _ptr(x), _ptr(y), coulomb_k, ewald_tol, r_cut,
+                                   ctypes.c_void_p(stream.cuda_stream))
     if st != QEQ_OK:
         raise QEqError(st, "qeq_matvec_static: " + lib.qeq_status_str(st).decode())
     return y

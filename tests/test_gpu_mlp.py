@@ -133,3 +133,41 @@ def test_warm_start_gain_and_fallback():
     assert np.abs(fb.q.cpu().numpy() - qc).max() < 1e-5
     plan.close()
     mlp.close()
+
+
+def test_warm_start_acceptance_is_per_structure():
+    """A batch with a structure from the training recipe and one with the electronegativities
+    of the two sublattices swapped (the network, trained on the original sign pattern, predicts
+    charges of the wrong sign there): the first keeps its network start, the second restarts
+    from the uniform start, and both reach the oracle's charges."""
+    import os
+    import torch
+    from paper_2607_17978_b300 import qeq, warmstart
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    mlp, _ = warmstart.load(os.path.join(root, "paper_2607_17978_b300", "models", "warmstart_rocksalt.npz"))
+    good = synth.rocksalt(4, 5.64, 0.2, synth.rng_for(5, 11), vacancy_frac=0.02)
+    bad = synth.rocksalt(4, 5.64, 0.2, synth.rng_for(5, 12), vacancy_frac=0.02)
+    bad.chi = -bad.chi
+    structs = [good, bad]
+    plan = qeq.plan_for_structures(structs, precision="mixed", preconditioner="fourier")
+    plan.set_warm_start(mlp)
+    pos, sp, chi, J, qt = qeq.pack(structs)
+    d = [torch.tensor(a, device="cuda") for a in (pos, sp, chi, J)]
+    res = plan.solve(*d, qt, warm="mlp")
+    assert [i["warm_used"] for i in res.info] == [1, 0], res.info
+    assert all(i["status"] == 0 for i in res.info)
+    qg = res.q.cpu().numpy()
+    off = [0, good.n, good.n + bad.n]
+    for k, st in enumerate(structs):
+        A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=KE)
+        q_ref, _ = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+        assert np.abs(qg[off[k]:off[k + 1]] - q_ref).max() < 1e-5, k
+    # the kept structure's solve is the one it gets alone
+    p1 = qeq.plan_for_structures([good], precision="mixed", preconditioner="fourier")
+    p1.set_warm_start(mlp)
+    r1 = p1.solve(*[torch.tensor(a, device="cuda") for a in qeq.pack([good])[:4]], np.array([good.q_tot]), warm="mlp")
+    assert r1.info[0]["warm_used"] == 1
+    assert np.abs(r1.q.cpu().numpy() - qg[:good.n]).max() < 2e-6
+    plan.close()
+    p1.close()
+    mlp.close()

@@ -1,4 +1,4 @@
-"""The allocation-free matvec entry point (qeq_matvec_static) against qeq_matvec.
+"""The allocation-free matvec entry point (qeq_matvec_static) against qeq_matvec and the oracle.
 
 qeq_matvec_static serves callers that cannot call cudaMalloc: its scratch is a
 file-scope device array, so the library allocates nothing during the call.
@@ -9,6 +9,7 @@ previous call's contents, so two calls in a row are checked).
 import numpy as np
 import pytest
 
+from oracle import qeq_oracle as O
 from paper_2607_17978_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -32,6 +33,8 @@ def test_static_matvec_matches_plan_matvec_twice(case):
     d_J = torch.tensor(J, device=dev)
     tol = 1e-6
     plan = qeq.plan_for_structures([st], ewald_tol=tol, r_cut=8.0)
+    # the oracle's dense (E + diag J) of this cell: an independent check of the shared kernels
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=synth.COULOMB_K_EV_A) + np.diag(st.J)
     rng = np.random.default_rng(case)
     xs = [rng.normal(size=st.n), rng.normal(size=st.n) * 0.3 + 0.1]
     for x in xs:                                   # two calls in a row share the scratch array
@@ -42,6 +45,9 @@ def test_static_matvec_matches_plan_matvec_twice(case):
         yr, yc = y_ref.cpu().numpy(), y.cpu().numpy()
         rel = np.sqrt(np.mean((yc - yr) ** 2)) / np.sqrt(np.mean(yr ** 2))
         assert rel < tol, rel
+        yo = A @ x
+        rel_o = np.sqrt(np.mean((yc - yo) ** 2)) / np.sqrt(np.mean(yo ** 2))
+        assert rel_o < tol, rel_o
     plan.close()
 
 
