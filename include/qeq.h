@@ -68,7 +68,12 @@ typedef enum {
 
 enum { QEQ_FP64 = 0, QEQ_MIXED = 1 };
 enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
-enum { QEQ_FLAG_NO_GRAPH = 1 };
+/* Plan flags.  NO_GRAPH: launch every PCG iteration from the host instead of CUDA graphs.
+ * TEST_STALL (tests only): in the main mesh's x FFT pass, the first tile announces 16 more
+ * bytes on its copy barrier than its bulk copies deliver, so its bounded wait (0.5 s on the
+ * GPU's global timer) runs out; the kernel flags the timeout and returns, and the call
+ * returns QEQ_ERR_TIMEOUT.  It exercises the timeout path without any fault. */
+enum { QEQ_FLAG_NO_GRAPH = 1, QEQ_FLAG_TEST_STALL = 2 };
 /* Preconditioners of the PCG.  JACOBI: D^-1, D_i = J_i + k_e/(sigma_i sqrt pi).
  * FOURIER: D^-1 - D^-1 T^T F^-1[h F(T D^-1 r)], the Woodbury inverse of D plus the
  * long-range Coulomb operator with the mesh operator T D^-1 T^T replaced by its
@@ -270,24 +275,30 @@ qeq_status qeq_plan_set_warm_start(qeq_plan plan, qeq_mlp mlp);
  * n_atoms <= QEQ_STATIC_MAX_ATOMS, n_species <= QEQ_STATIC_MAX_SPECIES, at
  * most QEQ_STATIC_MAX_MESH mesh points per direction (the mesh, B-spline order
  * and Ewald split are chosen exactly as qeq_plan_create does) and at most
- * QEQ_STATIC_MAX_PAIRS real-space pair slots; larger inputs return
- * QEQ_ERR_CAPACITY without touching the GPU.
+ * QEQ_STATIC_MAX_PAIRS real-space pair slots.  The array holds every buffer
+ * for inputs at all of these limits at once (checked at compile time).  Atom,
+ * species and mesh limits are checked on the host before any GPU work and
+ * return QEQ_ERR_CAPACITY; the estimated pair-slot count is checked on the host
+ * too, and the actual pair count, known only after the neighbour search, is
+ * checked on the device: a cell with more pairs than slots also returns
+ * QEQ_ERR_CAPACITY (nothing is written past the slots).
  *   h_cell     9 doubles, rows a1 a2 a3 [A]     h_sigma  n_species widths [A]
  *   d_pos      n_atoms x 3 [A]    d_species  n_atoms indices
  *   d_J        n_atoms hardnesses or NULL (diag J left out)
  *   d_x, d_y   input / output vectors of n_atoms
  *   coulomb_k, ewald_tol, r_cut   as in qeq_plan_desc (<= 0: defaults)
  *   cuda_stream                   a cudaStream_t (NULL = legacy stream)
- * The call returns after the stream has finished.  All calls share the
- * scratch array, which keeps the last call's contents: calls that overlap on
- * the GPU, or come from several host threads at once, race.  The first call on
- * a device sets up that device (it looks up the array's device address and
- * the kernels' shared-memory limits); make it before any stream capture. */
+ * Each call reads the device's error bits back to the host and returns after
+ * the stream has finished its work.  All calls share the scratch array, which
+ * keeps the last call's contents: calls that overlap on the GPU, or come from
+ * several host threads at once, race.  The first call on a device sets up that
+ * device (it looks up the array's device address and the kernels'
+ * shared-memory limits); make that first call before any stream capture. */
 #define QEQ_STATIC_MAX_ATOMS 4096
 #define QEQ_STATIC_MAX_SPECIES 4
 #define QEQ_STATIC_MAX_MESH 64
 #define QEQ_STATIC_MAX_PAIRS 1048576
-#define QEQ_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+#define QEQ_STATIC_SCRATCH_BYTES (40u * 1024u * 1024u)
 qeq_status qeq_matvec_static(const double* h_cell, const double* h_sigma, int32_t n_species, int32_t n_atoms,
                              const double* d_pos, const int32_t* d_species, const double* d_J,
                              const double* d_x, double* d_y, double coulomb_k, double ewald_tol,

@@ -183,13 +183,13 @@ static qeq_status fail(qeq_plan_s* P, qeq_status st, const std::string& msg) {
 static void free_plan(qeq_plan_s* P) {
   if (!P) return;
   void* ptrs[] = {P->d_st,     P->d_fft,     P->d_tw64,    P->d_tw32,     P->d_bmod,    P->d_bmod32,
-                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_xpairs,   P->d_bin_struct, P->d_atom_struct, P->d_brick_struct,
+                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_yiitems,  P->d_bin_struct, P->d_atom_struct, P->d_brick_struct,
                   P->d_chunks, P->d_key,     P->d_bin_count, P->d_bin_start, P->d_bin_fill, P->d_perm,
                   P->d_scan_tmp, P->d_base,  P->d_wts,     P->d_wts32,    P->d_spec,    P->d_J,
                   P->d_chi,    P->d_dinv,    P->d_posc,    P->d_row,      P->d_row_cnt, P->d_col,
                   P->d_val64,  P->d_val32,   P->d_q,       P->d_r,        P->d_z,       P->d_p,
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
-                  P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems,
+                  P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems, P->d_pyiitems, P->d_fft_tabs,
                   P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
                   P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject};
   for (void* p : ptrs)
@@ -267,14 +267,13 @@ static qeq_status build_plan(qeq_plan_s* P) {
   std::vector<float2> tw32;
   std::vector<double> bmod;
   std::vector<float> bmod32;
-  std::vector<int4> zit, yit, xit;
-  std::vector<int2> xpairs;
+  std::vector<int> tabs;
+  std::vector<int4> zit, yit, yiit, xit;
   std::vector<int> bin_struct, brick_struct;
   std::vector<Chunk> chunks;
   int64_t mesh_off = 0;
   int bin_off = 0;
   int64_t pair_cap = 0;
-  int64_t smem_elems = 0;
 
 
   // B-spline order: one per plan (the kernels are specialised on it); when not
@@ -302,47 +301,25 @@ static qeq_status build_plan(qeq_plan_s* P) {
     if (pbest == 0) return fail(P, QEQ_ERR_INVALID, "no mesh meets ewald_tol within 1000 points per direction");
   }
   P->max_p = pbest;
-  // lines per tile of the transposing FFT passes: from the largest mesh of the plan
-  int maxK = 12;
-  int max_s = 1;
-  {
-    const double omega = split_width(D);
-    for (int s = 0; s < ns; ++s) {
-      const double* h = D.cells + 9 * s;
-      double V = fabs(det3(h)), c = 0;
-      int K[3] = {12, 12, 12};
-      if (V > 1e-9)
-        choose_mesh(h, V, narrowest_width(D.sigma + (size_t)S * s, S, omega),
-                    (double)(P->offsets[s + 1] - P->offsets[s]), pbest, D, K, &c);
-      for (int d = 0; d < 3; ++d) maxK = std::max(maxK, K[d]);
-    }
-  }
-  const int tl = fft_tile_lines(maxK);
-  P->tl = tl;
-
   auto fft_plan_for = [&](int K) {
     auto it = fft_index.find(K);
     if (it != fft_index.end()) return it->second;
     FftPlanDev f;
     memset(&f, 0, sizeof(f));
-    f.K = K;
-    f.nst = fft_radices(K, f.radix);
-    for (int i = 0, ns = 1; i < f.nst; ns *= f.radix[i], ++i) {
-      f.nbf[i] = make_fastdiv(K / f.radix[i]);
-      f.ns[i] = make_fastdiv(ns);
-    }
-    f.k = make_fastdiv(K);
     f.tw_off = (int)tw64.size();
-    for (int m = 0; m < K; ++m) {
-      double ang = -2.0 * kPi * (double)m / K;
-      tw64.push_back(make_double2(cos(ang), sin(ang)));
-      tw32.push_back(make_float2((float)cos(ang), (float)sin(ang)));
-    }
+    f.tab_off = (int)tabs.size();
+    const int padK = K + (K & 1);  // keeps every twiddle table 16-byte aligned
+    tw64.resize(tw64.size() + padK);
+    tw32.resize(tw32.size() + padK);
+    tabs.resize(tabs.size() + 3 * (size_t)K);
+    if (!fft_plan_fill(K, f, tw64.data() + f.tw_off, tw32.data() + f.tw_off, tabs.data() + f.tab_off)) return -1;
     int idx = (int)fplans.size();
     fplans.push_back(f);
     fft_index[K] = idx;
     return idx;
   };
+  int maxK[3] = {1, 1, 1};
+  int max_s = 1;
 
   for (int s = 0; s < ns; ++s) {
     StructDev& T = hs[s];
@@ -430,9 +407,10 @@ static qeq_status build_plan(qeq_plan_s* P) {
       double lf = QEQ_MLP_RCUT / wd[d] * K / QEQ_BIN;
       T.feat_range[d] = std::max(1, (int)ceil(lf + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0));
     }
-    T.M = (int64_t)T.K[0] * T.K[1] * T.K[2];
+    mesh_layout(T);
     T.mesh_off = mesh_off;
-    mesh_off += T.M * T.ncm;
+    mesh_off += T.Mp * T.ncm;
+    for (int d = 0; d < 3; ++d) maxK[d] = std::max(maxK[d], T.K[d]);
     T.bin_off = bin_off;
     int nbins = T.nb[0] * T.nb[1] * T.nb[2];
     for (int b = 0; b < nbins; ++b) bin_struct.push_back(s);
@@ -441,6 +419,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
     for (int b = 0; b < T.nbr[0] * T.nbr[1] * T.nbr[2]; ++b) brick_struct.push_back(s);
     for (int d = 0; d < 3; ++d) {
       T.fft_plan[d] = fft_plan_for(T.K[d]);
+      if (T.fft_plan[d] < 0) return fail(P, QEQ_ERR_INVALID, "mesh size without an FFT plan");
       T.bmod_off[d] = (int)bmod.size();
       std::vector<double> bm(T.K[d]);
       bspline_moduli(T.K[d], T.p, bm.data());
@@ -449,12 +428,6 @@ static qeq_status build_plan(qeq_plan_s* P) {
         bmod32.push_back((float)v);
       }
     }
-    // --- FFT work lists (transposing passes)
-    T.xpair_off = (int)xpairs.size();
-    smem_elems = std::max<int64_t>(
-        smem_elems, fft_work_lists(T, s, tl, T.xpair_off, [&](int4 v) { zit.push_back(v); },
-                                   [&](int4 v) { yit.push_back(v); }, [&](int2 v) { xpairs.push_back(v); },
-                                   [&](int4 v) { xit.push_back(v); }));
     // --- real-space pair capacity: local density bound with margin
     if (any) {
       int64_t n = T.atom_end - T.atom_begin;
@@ -476,33 +449,38 @@ static qeq_status build_plan(qeq_plan_s* P) {
       chunks.push_back(ch);
     }
   }
+  // --- FFT tile sizes from the largest mesh of the plan, then the work lists
+  P->geo = fft_geometry(maxK, (max_s + 1) / 2);
+  for (int s = 0; s < ns; ++s)
+    fft_work_lists(hs[s], s, P->geo.tl, P->geo.tlx, [&](int4 v) { zit.push_back(v); },
+                   [&](int4 v) { yit.push_back(v); }, [&](int4 v) { yiit.push_back(v); },
+                   [&](int4 v) { xit.push_back(v); });
   // --- Fourier preconditioner: a coarse mesh per structure (spacing ~2 A, cubic B-splines)
   std::vector<StructDev> hsp;
-  std::vector<int4> pzit, pyit, pxit;
+  std::vector<int4> pzit, pyit, pyiit, pxit;
   int64_t pmesh_off = 0;
   if (D.preconditioner == QEQ_PRECOND_FOURIER) {
     const double kPreSpacing = D.precond_spacing;
-    int maxKp = 8;
+    int maxKp[3] = {8, 8, 8};
     for (int s = 0; s < ns; ++s) {
       StructDev Tp = hs[s];
       double wd[3];
       plane_widths(Tp.h, Tp.V, wd);
       for (int d = 0; d < 3; ++d) {
         Tp.K[d] = next_smooth(std::max(8, (int)ceil(wd[d] / kPreSpacing - 1e-9)));
-        maxKp = std::max(maxKp, Tp.K[d]);
+        maxKp[d] = std::max(maxKp[d], Tp.K[d]);
       }
       hsp.push_back(Tp);
     }
-    const int tlp = fft_tile_lines(maxKp);
-    P->tlp = tlp;
+    P->pgeo = fft_geometry(maxKp, 1);
     for (int s = 0; s < ns; ++s) {
       StructDev& Tp = hsp[s];
       Tp.S = 1;
       Tp.ncm = 1;
       Tp.p = 4;
-      Tp.M = (int64_t)Tp.K[0] * Tp.K[1] * Tp.K[2];
+      mesh_layout(Tp);
       Tp.mesh_off = pmesh_off;
-      pmesh_off += Tp.M;
+      pmesh_off += Tp.Mp;
       // Gaussian width of the long-range part it inverts: as given, else 3 A for cells up to
       // 80 A wide and 4.5 A above (measured: 17 against 21 iterations at 68 A; at 135 A,
       // sheared, 3 A left the preconditioner close to Jacobi; at 282 A both gave ~105)
@@ -530,6 +508,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
       }
       for (int d = 0; d < 3; ++d) {
         Tp.fft_plan[d] = fft_plan_for(Tp.K[d]);
+        if (Tp.fft_plan[d] < 0) return fail(P, QEQ_ERR_INVALID, "mesh size without an FFT plan");
         Tp.bmod_off[d] = (int)bmod.size();
         std::vector<double> bm(Tp.K[d]);
         bspline_moduli(Tp.K[d], 4, bm.data());
@@ -538,11 +517,9 @@ static qeq_status build_plan(qeq_plan_s* P) {
           bmod32.push_back((float)v);
         }
       }
-      Tp.xpair_off = (int)xpairs.size();
-      smem_elems = std::max<int64_t>(
-          smem_elems, fft_work_lists(Tp, s, tlp, Tp.xpair_off, [&](int4 v) { pzit.push_back(v); },
-                                     [&](int4 v) { pyit.push_back(v); }, [&](int2 v) { xpairs.push_back(v); },
-                                     [&](int4 v) { pxit.push_back(v); }));
+      fft_work_lists(Tp, s, P->pgeo.tl, P->pgeo.tlx, [&](int4 v) { pzit.push_back(v); },
+                     [&](int4 v) { pyit.push_back(v); }, [&](int4 v) { pyiit.push_back(v); },
+                     [&](int4 v) { pxit.push_back(v); });
     }
   }
   P->precond = D.preconditioner;
@@ -550,6 +527,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->n_pz = (int)pzit.size();
   P->n_py = (int)pyit.size();
   P->n_px = (int)pxit.size();
+  P->n_pyi = (int)pyiit.size();
   P->total_pmesh = pmesh_off;
   P->hs = hs;
   P->hfft = fplans;
@@ -565,9 +543,17 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->n_zitems = (int)zit.size();
   P->n_yitems = (int)yit.size();
   P->n_xitems = (int)xit.size();
-  P->fft_smem_elems = smem_elems;
-  if ((size_t)smem_elems * sizeof(double2) > 200 * 1024)
-    return fail(P, QEQ_ERR_INVALID, "FFT tile exceeds shared memory");
+  P->n_yiitems = (int)yiit.size();
+  P->max_ncm = (max_s + 1) / 2;
+  {
+    const FftGeom& g = P->geo;
+    const int hx = max_s <= 2 ? 1 : QEQ_MAX_SPECIES / 2;
+    const size_t big = std::max({fft_tile_smem(g.sub64, std::max(g.ldz64, g.ldy64), sizeof(double2)),
+                                 fft_x_smem(g.subx64, g.ldx64, sizeof(double2), hx, sizeof(double)),
+                                 fft_tile_smem(g.sub32, std::max(g.ldz32, g.ldy32), sizeof(float2)),
+                                 fft_x_smem(g.subx32, g.ldx32, sizeof(float2), hx, sizeof(float))});
+    if (big > 227 * 1024 - 1024) return fail(P, QEQ_ERR_INVALID, "FFT tile exceeds shared memory");
+  }
 
   // atom -> structure (input order)
   std::vector<int> atom_struct(P->n_atoms);
@@ -590,7 +576,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(upload(P, &P->d_zitems, zit));
   ALLOC(upload(P, &P->d_yitems, yit));
   ALLOC(upload(P, &P->d_xitems, xit));
-  ALLOC(upload(P, &P->d_xpairs, xpairs));
+  ALLOC(upload(P, &P->d_yiitems, yiit));
+  ALLOC(upload(P, &P->d_fft_tabs, tabs));
   ALLOC(upload(P, &P->d_bin_struct, bin_struct));
   ALLOC(upload(P, &P->d_brick_struct, brick_struct));
   ALLOC(upload(P, &P->d_atom_struct, atom_struct));
@@ -641,6 +628,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
     ALLOC(upload(P, &P->d_pzitems, pzit));
     ALLOC(upload(P, &P->d_pyitems, pyit));
     ALLOC(upload(P, &P->d_pxitems, pxit));
+    ALLOC(upload(P, &P->d_pyiitems, pyiit));
     ALLOC(dalloc(P, &P->d_pmesh, (size_t)P->total_pmesh));
     ALLOC(dalloc(P, &P->d_pmesh2, (size_t)P->total_pmesh));
     ALLOC(dalloc(P, &P->d_w1, N));
@@ -688,6 +676,7 @@ extern "C" qeq_status qeq_plan_create(const qeq_plan_desc* desc, void* cuda_stre
   P->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&P->device);
   P->graph_ok = (P->stream != nullptr) && !(D.flags & QEQ_FLAG_NO_GRAPH);
+  P->test_stall = (D.flags & QEQ_FLAG_TEST_STALL) ? 1 : 0;
   qeq_status st = build_plan(P);
   // the caller's description arrays are not kept
   D.atom_offsets = nullptr;

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <math.h>
+
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -13,9 +16,8 @@
 #define QEQ_BIN 8          // mesh points per edge of an atom bin (sorting, real-space search)
 #define QEQ_BRICK 16       // mesh points per edge of a spread / gather brick (2 x 2 x 2 bins)
 #define QEQ_MAXP 8         // largest supported B-spline order
-#define QEQ_MAX_STAGES 16  // radix stages of one FFT length
+#define QEQ_MAX_STAGES 12  // radix stages of one FFT length
 #define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
-#define QEQ_XPAIRS_MAX 256 // line pairs per x-pass CTA (shared per-line constants)
 #define QEQ_GATHER_SPLIT_MAX 64  // gather CTAs per reduction chunk
 
 // ---------------------------------------------------------------------------
@@ -36,15 +38,15 @@ struct StructDev {
   int p;                  // B-spline order
   int any_narrow;         // 1 if some species pair has a real-space term
   int64_t M;              // K0*K1*K2
+  int64_t Mp;             // elements per complex mesh in memory (padded layouts, even)
   int64_t mesh_off;       // complex-element offset of this structure's complex mesh 0
   int64_t atom_begin, atom_end;
   int bin_off;            // first global bin of this structure
   int fft_plan[3];        // FFT plan index per direction
   int bmod_off[3];        // offsets into the B-spline modulus table per direction
-  int xpair_off;          // first entry of this structure in the x-pass line-pair table
+  int P[3];               // padded line lengths K_d + (K_d & 1) (innermost stride of each layout)
   int brick_off;          // first global brick of this structure
   int nbr[3];             // bricks per direction (ceil(K/QEQ_BRICK))
-  int pad2_;
   double w2[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];     // reciprocal Gaussian width^2 w_st^2
   double corr[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];   // G = 0 width term over r < r_cut (narrow pairs)
   double inv_sw[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES]; // 1/(sqrt2 w_st) (narrow pairs)
@@ -78,15 +80,20 @@ __host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.s; }
 #endif
 
+// Mixed-radix plan of one FFT length K = R_0 ... R_{m-1} (see fft.cuh): stage s has
+// Q_s = R_0...R_{s-1} blocks of L_s = K/Q_s points and stride S_s = L_s/R_s.
 struct FftPlanDev {
   int K;
   int nst;
   int radix[QEQ_MAX_STAGES];
-  int tw_off;  // offset of exp(-2 pi i m / K), m < K, in the twiddle tables
-  int pad_;
-  FastDiv nbf[QEQ_MAX_STAGES];  // K / radix of each stage
-  FastDiv ns[QEQ_MAX_STAGES];   // product of the radices before each stage
-  FastDiv k;                    // K
+  int S[QEQ_MAX_STAGES];
+  int L[QEQ_MAX_STAGES];
+  int Q[QEQ_MAX_STAGES];
+  FastDiv fnb[QEQ_MAX_STAGES];  // K / R_s
+  FastDiv fS[QEQ_MAX_STAGES];   // S_s
+  FastDiv fK;                   // K
+  int tw_off;   // offset of exp(-2 pi i m / K), m < K, in the twiddle tables (even)
+  int tab_off;  // int tables: blk[K/R_{m-1}] at tab_off, freq[K] at +K, pos[K] at +2K
 };
 
 // Per-structure scalars of the PCG (device resident).
@@ -130,6 +137,16 @@ struct Chunk {
   int count;    // chunks of the structure
 };
 
+// Tile sizes of the FFT passes of one set of meshes: item lines (tl, tlx) and, per
+// precision, lines per shared-memory tile (sub, subx) with the maximal shared-line
+// lengths (ld*) the kernels' dynamic shared memory is sized for.
+struct FftGeom {
+  int tl = 1, tlx = 1;
+  int sub32 = 1, sub64 = 1, subx32 = 1, subx64 = 1;
+  int ldz32 = 0, ldz64 = 0, ldy32 = 0, ldy64 = 0, ldx32 = 0, ldx64 = 0;
+  int max_ncm = 1;
+};
+
 // ---------------------------------------------------------------------------
 struct qeq_plan_s {
   qeq_plan_desc desc;
@@ -148,10 +165,11 @@ struct qeq_plan_s {
   int64_t total_mesh = 0;          // complex elements over all structures and complex meshes
   int64_t pair_cap = 0;
   int n_chunks = 0;
-  int n_zitems = 0, n_yitems = 0, n_xitems = 0;
+  int n_zitems = 0, n_yitems = 0, n_yiitems = 0, n_xitems = 0;
   int64_t workspace_bytes = 0;
   bool have_atoms = false;         // sorted atom data valid for profiling
   bool graph_ok = true;
+  int test_stall = 0;              // QEQ_FLAG_TEST_STALL: one x-pass tile's bounded wait runs out
 
   // device tables
   StructDev* d_st = nullptr;
@@ -160,12 +178,14 @@ struct qeq_plan_s {
   float2* d_tw32 = nullptr;
   double* d_bmod = nullptr;
   float* d_bmod32 = nullptr;
+  int* d_fft_tabs = nullptr;       // per FFT length: block offsets, frequency of position, position of frequency
   int max_ncm = 1;                 // largest complex-mesh count of any structure
-  int64_t fft_smem_elems = 0;      // complex elements of shared memory per FFT CTA
-  int4* d_zitems = nullptr;
-  int4* d_yitems = nullptr;
-  int4* d_xitems = nullptr;
-  int2* d_xpairs = nullptr;
+  FftGeom geo;                     // tile sizes of the FFT passes of the matvec mesh
+  FftGeom pgeo;                    // ... of the preconditioner mesh
+  int4* d_zitems = nullptr;        // z passes {s, c, x, y0}
+  int4* d_yitems = nullptr;        // forward y pass {s, c, z, x0}
+  int4* d_yiitems = nullptr;       // inverse y pass {s, c, x, z0}
+  int4* d_xitems = nullptr;        // x pass {s, z, y0, lines}
   int* d_bin_struct = nullptr;     // structure of each global bin
   int* d_brick_struct = nullptr;   // structure of each global brick
   int total_bricks = 0;
@@ -198,9 +218,8 @@ struct qeq_plan_s {
   double *d_q1 = nullptr, *d_r1 = nullptr;  // charges and FP64 residual at the last FP64 check
   float* d_x32 = nullptr;          // FP32 copy of the matvec input (mixed precision), written by the species sums
   // mesh (reinterpreted as float2 in mixed precision)
-  double2* d_mesh = nullptr;       // layouts L0 / L2 (see matvec.cu)
-  double2* d_mesh2 = nullptr;      // layout L1
-  int tl = 8;                      // lines per tile of the transposing FFT passes
+  double2* d_mesh = nullptr;       // layouts L0 / L2 (see fft.cuh)
+  double2* d_mesh2 = nullptr;      // layouts L1 / L3
   // reductions
   double* d_part = nullptr;        // partials: species sums, gather x.y, PCG reductions
   int* d_counter = nullptr;        // n_struct counters for last-block reductions
@@ -214,8 +233,8 @@ struct qeq_plan_s {
   int precond = QEQ_PRECOND_JACOBI;
   std::vector<StructDev> hsp;
   StructDev* d_stp = nullptr;
-  int4 *d_pzitems = nullptr, *d_pyitems = nullptr, *d_pxitems = nullptr;
-  int n_pz = 0, n_py = 0, n_px = 0, tlp = 8;
+  int4 *d_pzitems = nullptr, *d_pyitems = nullptr, *d_pyiitems = nullptr, *d_pxitems = nullptr;
+  int n_pz = 0, n_py = 0, n_pyi = 0, n_px = 0;
   int64_t total_pmesh = 0;
   int gather_split = 1;            // CTAs per reduction chunk in the gather
   int max_species = QEQ_MAX_SPECIES;  // most species of any structure
@@ -234,39 +253,159 @@ struct qeq_plan_s {
   int graph_iter_k = 0;
 };
 
-// Shared-memory layout of FFT lines: element i of a line sits at fft_pidx(i)
-// (one pad element per 16, so strided butterfly accesses spread over the
-// banks), lines fft_ld(K) elements apart (odd, for transposed accesses).
-__host__ __device__ inline int fft_pidx(int i) { return i + (i >> 4); }
-__host__ __device__ inline int fft_ld(int K) { return (fft_pidx(K - 1) + 1) | 1; }
-
-// Radices of the FFT stages of length K (K = 2^a 3^b 5^c): greedily the largest
-// register butterfly that divides what is left.  Returns the number of stages.
-inline int fft_radices(int K, int* out) {
-  static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
-  int n = K, ns = 0;
-  while (n > 1 && ns < QEQ_MAX_STAGES) {
-    int r = 0;
-    for (int c : kRadix)
-      if (n % c == 0) {
-        r = c;
-        break;
-      }
-    if (r == 0) return -1;
-    out[ns++] = r;
-    n /= r;
-  }
-  return n == 1 ? ns : -1;
+inline int fft_is_radix(int r) {
+  return r == 2 || r == 3 || r == 4 || r == 5 || r == 6 || r == 8 || r == 9 || r == 10 || r == 12 || r == 15 ||
+         r == 16;
 }
 
-// Work lists of the FFT passes of one structure (shared by qeq_plan_create and
-// the allocation-free entry point).  Z items {s, c, x, y0} and Y items
-// {s, c, z, x0} cover tiles of tl lines; X items {s, first pair, npairs, 0}
-// cover pairs of x lines (z, y) and (-z, -y), lines indexed l = z*K1 + y.
-// Returns the shared-memory size (complex elements) the passes need.
-template <class AddZ, class AddY, class AddPair, class AddX>
-inline int64_t fft_work_lists(const StructDev& T, int s, int tl, int pair_base, AddZ addz, AddY addy,
-                              AddPair addpair, AddX addx) {
+// depth-first search of fft_radices: ordered factorisations of rem into register radices,
+// no deeper than the best found so far
+inline void fft_radices_search(int rem, int d, int* cur, int* best, int& nbest) {
+  static const int kR[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  if (rem == 1) {
+    if (d == 0) return;
+    bool take = nbest < 0 || d < nbest;
+    if (!take && d == nbest) {
+      const bool co = cur[d - 1] & 1, bo = best[nbest - 1] & 1;
+      if (co != bo) {
+        take = co;
+      } else {
+        for (int i = 0; i < d; ++i)
+          if (cur[i] != best[i]) {
+            take = cur[i] > best[i];
+            break;
+          }
+      }
+    }
+    if (take) {
+      for (int i = 0; i < d; ++i) best[i] = cur[i];
+      nbest = d;
+    }
+    return;
+  }
+  if (d >= QEQ_MAX_STAGES || (nbest >= 0 && d >= nbest)) return;
+  for (int r : kR)
+    if (rem % r == 0) {
+      cur[d] = r;
+      fft_radices_search(rem / r, d + 1, cur, best, nbest);
+    }
+}
+
+// Radices of the FFT stages of length K (K = 2^a 3^b 5^c): the ordered factorisation
+// into register butterflies (2-16) with the fewest stages; among those an odd last
+// radix (its contiguous shared-memory reads spread over the banks), then the
+// lexicographically largest.  Returns the number of stages, -1 if none.
+inline int fft_radices(int K, int* out) {
+  int best[QEQ_MAX_STAGES] = {0}, cur[QEQ_MAX_STAGES] = {0}, nbest = -1;
+  if (K < 2) return -1;
+  fft_radices_search(K, 0, cur, best, nbest);
+  for (int i = 0; i < nbest; ++i) out[i] = best[i];
+  return nbest;
+}
+
+// Stage constants, twiddles (K entries each, from tw_off) and the int tables (3K entries
+// from tab_off: block offset of each natural base u, frequency of each block-order
+// position, block-order position of each frequency) of one FFT length.
+inline bool fft_plan_fill(int K, FftPlanDev& f, double2* tw64, float2* tw32, int* tab) {
+  f.K = K;
+  f.nst = fft_radices(K, f.radix);
+  if (f.nst < 1) return false;
+  int Q = 1;
+  for (int s = 0; s < f.nst; ++s) {
+    f.Q[s] = Q;
+    f.L[s] = K / Q;
+    f.S[s] = f.L[s] / f.radix[s];
+    f.fnb[s] = make_fastdiv(K / f.radix[s]);
+    f.fS[s] = make_fastdiv(f.S[s]);
+    Q *= f.radix[s];
+  }
+  f.fK = make_fastdiv(K);
+  const double kTwoPi = 6.28318530717958647692;
+  for (int m = 0; m < K; ++m) {
+    const double ang = -kTwoPi * (double)m / K;
+    tw64[m] = make_double2(cos(ang), sin(ang));
+    tw32[m] = make_float2((float)cos(ang), (float)sin(ang));
+  }
+  // every digit tuple (k_0 .. k_{m-1}): position sum_s S_s k_s, frequency sum_s Q_s k_s
+  const int m = f.nst;
+  int k[QEQ_MAX_STAGES] = {0};
+  for (int t = 0; t < K; ++t) {
+    int p = 0, fq = 0;
+    for (int s = 0; s < m; ++s) {
+      p += f.S[s] * k[s];
+      fq += f.Q[s] * k[s];
+    }
+    tab[K + p] = fq;
+    tab[2 * K + fq] = p;
+    if (k[m - 1] == 0) tab[fq] = p;  // natural base u = fq (last digit 0) -> its block's offset
+    for (int s = 0; s < m; ++s) {   // next tuple, digit 0 fastest
+      if (++k[s] < f.radix[s]) break;
+      k[s] = 0;
+    }
+  }
+  return true;
+}
+
+// Padded line lengths and the per-complex-mesh size of the four layouts (fft.cuh).
+inline void mesh_layout(StructDev& T) {
+  for (int d = 0; d < 3; ++d) T.P[d] = T.K[d] + (T.K[d] & 1);
+  const int64_t K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
+  int64_t m = K0 * K1 * T.P[2];
+  m = std::max(m, K0 * K2 * (int64_t)T.P[1]);
+  m = std::max(m, K2 * K1 * (int64_t)T.P[0]);
+  T.M = K0 * K1 * K2;
+  T.Mp = m;
+}
+
+// Shared-memory line strides as the kernels compute them (fft.cuh fft_smem_ld).
+inline int fft_ld32(int K) {
+  int ld = K + (K & 1);
+  return (ld & 3) ? ld : ld + 2;
+}
+inline int fft_ld64(int K) { return K | 1; }
+
+// Tile sizes for meshes whose largest sizes per direction are maxK[3] (most complex
+// meshes max_ncm): item lines of the y/z passes (16 FP32 lines in at most ~64 KB) and of
+// the x pass (2 max_ncm lines per pair); FP64 sub-tiles hold half as many lines.
+inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
+  FftGeom g;
+  g.max_ncm = max_ncm;
+  g.ldz32 = fft_ld32(maxK[2]);
+  g.ldz64 = fft_ld64(maxK[2]);
+  g.ldy32 = fft_ld32(maxK[1]);
+  g.ldy64 = fft_ld64(maxK[1]);
+  g.ldx32 = fft_ld32(maxK[0]);
+  g.ldx64 = fft_ld64(maxK[0]);
+  const int ldyz = std::max(g.ldz32, g.ldy32);
+  const int64_t budget = 64 * 1024;
+  int tl = 16;
+  while (tl > 1 && (int64_t)tl * ldyz * 8 > budget) tl >>= 1;
+  g.tl = tl;
+  g.sub32 = tl;
+  g.sub64 = std::max(1, tl / 2);
+  int tlx = 8;
+  while (tlx > 1 && (int64_t)2 * max_ncm * tlx * g.ldx32 * 8 > budget) tlx >>= 1;
+  g.tlx = tlx;
+  g.subx32 = tlx;
+  g.subx64 = std::max(1, tlx / 2);
+  return g;
+}
+
+// Dynamic shared memory of the passes (must match the kernels' carving in fft.cuh).
+inline size_t fft_tile_smem(int sub, int ld, size_t elem) { return 128 + (size_t)sub * ld * elem; }
+inline size_t fft_x_smem(int sub, int ld, size_t elem, int maxs_half, size_t real) {
+  size_t hdr = 128 + 2 * 2 * (size_t)maxs_half * sub * sizeof(int64_t) + (size_t)sub * 4 * real;
+  hdr = (hdr + 127) & ~(size_t)127;
+  return hdr + 2 * (size_t)maxs_half * sub * ld * elem;
+}
+
+// Work lists of the FFT passes of one structure (shared by qeq_plan_create and the
+// allocation-free entry point).  Z items {s, c, x, y0} and inverse-y items {s, c, x, z0},
+// forward-y items {s, c, z, x0} cover tl lines; x items {s, z, y0, lines} cover up to
+// tlx lines (z <= K2/2, and y <= K1/2 on the planes that are their own mirror).
+template <class AddZ, class AddY, class AddYI, class AddX>
+inline void fft_work_lists(const StructDev& T, int s, int tl, int tlx, AddZ addz, AddY addy, AddYI addyi,
+                           AddX addx) {
   const int K0 = T.K[0], K1 = T.K[1], K2 = T.K[2];
   for (int c = 0; c < T.ncm; ++c)
     for (int x = 0; x < K0; ++x)
@@ -274,34 +413,14 @@ inline int64_t fft_work_lists(const StructDev& T, int s, int tl, int pair_base, 
   for (int c = 0; c < T.ncm; ++c)
     for (int z = 0; z < K2; ++z)
       for (int x0 = 0; x0 < K0; x0 += tl) addy(make_int4(s, c, z, x0));
-  int npairs = 0;
-  for (int z = 0; z < K2; ++z)
-    for (int y = 0; y < K1; ++y) {
-      int l = z * K1 + y;
-      int lm = ((K2 - z) % K2) * K1 + (K1 - y) % K1;
-      if (l <= lm) {
-        addpair(make_int2(l, lm));
-        ++npairs;
-      }
-    }
-  int np = 4096 / (2 * T.ncm * K0);
-  if (np < 1) np = 1;
-  if (np > QEQ_XPAIRS_MAX) np = QEQ_XPAIRS_MAX;
-  for (int j = 0; j < npairs; j += np) addx(make_int4(s, pair_base + j, (npairs - j < np) ? npairs - j : np, 0));
-  int64_t e = 0;
-  auto mx = [&](int64_t v) { e = v > e ? v : e; };
-  mx(K2 + 2 * (int64_t)tl * fft_ld(K2));
-  mx(K1 + 2 * (int64_t)tl * fft_ld(K1));
-  int nsl = 2 * (np < npairs ? np : npairs) * T.ncm;
-  mx(K0 + 2 * (int64_t)nsl * fft_ld(K0));
-  return e;
-}
-
-// lines per tile: a power of two, at most 16 and at most 4096 / K elements per buffer
-inline int fft_tile_lines(int maxK) {
-  int tl = 16;
-  while (tl > 1 && tl * maxK > 4096) tl >>= 1;
-  return tl;
+  for (int c = 0; c < T.ncm; ++c)
+    for (int x = 0; x < K0; ++x)
+      for (int z0 = 0; z0 < K2; z0 += tl) addyi(make_int4(s, c, x, z0));
+  for (int z = 0; 2 * z <= K2; ++z) {
+    const bool self = (z == 0) || (2 * z == K2);
+    const int ylast = self ? K1 / 2 : K1 - 1;
+    for (int y0 = 0; y0 <= ylast; y0 += tlx) addx(make_int4(s, z, y0, std::min(tlx, ylast + 1 - y0)));
+  }
 }
 
 // device error bits
@@ -311,6 +430,7 @@ enum {
   ERRBIT_J = 4,
   ERRBIT_PAIRCAP = 8,
   ERRBIT_SORT = 16,
+  ERRBIT_TIMEOUT = 32,  // a bounded device wait ran out
 };
 
 // ---------------------------------------------------------------------------

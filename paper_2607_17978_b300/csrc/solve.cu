@@ -342,25 +342,33 @@ __global__ void k_direction(const Chunk* __restrict__ chunks, const double* __re
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) p[a] = zz[a] + beta * p[a];
 }
 
-// all structures inactive?
-__global__ void k_done(const PcgScalars* __restrict__ sc, int ns, int* __restrict__ done) {
+// all structures inactive?  A timed-out device wait (ERRBIT_TIMEOUT) stops every structure.
+__global__ void k_done(PcgScalars* __restrict__ sc, int ns, const int* __restrict__ err, int* __restrict__ done) {
   __shared__ int any;
+  const bool stop = (*((volatile const int*)err) & ERRBIT_TIMEOUT) != 0;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < ns; s += blockDim.x)
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    if (stop) sc[s].active = 0;
     if (sc[s].active) any = 1;
+  }
   __syncthreads();
   if (threadIdx.x == 0) *done = any ? 0 : 1;
 }
 
 // after a final check: restart the failing structures (bounded), settle the rest
-__global__ void k_after_check(PcgScalars* __restrict__ sc, int ns, int max_restarts, int max_iter, int* __restrict__ done) {
+__global__ void k_after_check(PcgScalars* __restrict__ sc, int ns, int max_restarts, int max_iter,
+                              const int* __restrict__ err, int* __restrict__ done) {
   __shared__ int any;
+  const bool stop = (*((volatile const int*)err) & ERRBIT_TIMEOUT) != 0;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     PcgScalars& c = sc[s];
-    if (c.converged) {
+    if (stop) {
+      c.status = QEQ_ERR_TIMEOUT;
+      c.active = 0;
+    } else if (c.converged) {
       c.status = QEQ_OK;
       c.active = 0;
     } else if (c.restarts < max_restarts && c.iters < max_iter) {
@@ -526,7 +534,7 @@ cudaError_t run_iterations(qeq_plan_s* P, int prec) {
       for (int k = 0; k < kItersPerCheck && e == cudaSuccess; ++k) e = one_iteration(P, prec);
       if (e == cudaSuccess) {
         count_launch(P);
-        k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_done);
+        k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_err, P->d_done);
         e = cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s);
       }
       cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -543,7 +551,7 @@ cudaError_t run_iterations(qeq_plan_s* P, int prec) {
   } else {
     for (int k = 0; k < kItersPerCheck; ++k) QEQ_CUDA_TRY(one_iteration(P, prec));
     count_launch(P);
-    k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_done);
+    k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_err, P->d_done);
     QEQ_CUDA_TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
   }
   return cudaStreamSynchronize(s);
@@ -566,6 +574,19 @@ qeq_status check_inputs(qeq_plan_s* P) {
     }
     P->last_error = (err & ERRBIT_SPECIES) ? "species index out of range" : "non-finite input";
     return QEQ_ERR_INVALID;
+  }
+  return QEQ_OK;
+}
+
+// after a call's device work: a bounded device wait that ran out (ERRBIT_TIMEOUT)
+qeq_status check_timeout(qeq_plan_s* P) {
+  TRY(cudaMemcpyAsync(P->h_done + 5, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  TRY(cudaStreamSynchronize(P->stream));
+  if (P->h_done[5] & ERRBIT_TIMEOUT) {
+    TRY(cudaMemsetAsync(P->d_err, 0, sizeof(int), P->stream));
+    TRY(cudaStreamSynchronize(P->stream));
+    P->last_error = "a bounded device wait (bulk copy into shared memory) ran out";
+    return QEQ_ERR_TIMEOUT;
   }
   return QEQ_OK;
 }
@@ -738,7 +759,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
       }
     }
     count_launch(P);
-    k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_done);
+    k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_err, P->d_done);
     TRY(precondition(P, 1, 1));
     count_launch(P);
     k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
@@ -777,6 +798,12 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     if (c.status != QEQ_OK && worst == QEQ_OK) worst = (qeq_status)c.status;
   }
   if (worst == QEQ_ERR_NOCONV) P->last_error = "some structure did not converge within max_iter";
+  const qeq_status tst = check_timeout(P);
+  if (tst != QEQ_OK) {
+    if (h_info)
+      for (int i = 0; i < ns; ++i) h_info[i].status = QEQ_ERR_TIMEOUT;
+    return tst;
+  }
   return worst;
 }
 
@@ -803,8 +830,7 @@ extern "C" qeq_status qeq_energy(qeq_plan P, const double* d_pos, const int32_t*
   count_launch(P);
   k_write_mu<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, nullptr, d_E_qeq, d_E_elec);
   TRY(cudaGetLastError());
-  TRY(cudaStreamSynchronize(s));
-  return QEQ_OK;
+  return check_timeout(P);
 }
 
 extern "C" qeq_status qeq_matvec(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_J,
@@ -829,8 +855,7 @@ extern "C" qeq_status qeq_matvec(qeq_plan P, const double* d_pos, const int32_t*
   count_launch(P);
   k_unsort<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, P->d_Ap, d_y);
   TRY(cudaGetLastError());
-  TRY(cudaStreamSynchronize(s));
-  return QEQ_OK;
+  return check_timeout(P);
 }
 
 extern "C" qeq_status qeq_profile_matvec(qeq_plan P, int32_t n_rep, float* h_ms) {

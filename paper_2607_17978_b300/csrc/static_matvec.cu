@@ -42,22 +42,46 @@ void* g_scratch_dev[kMaxDev] = {nullptr};
 bool g_attr_done[kMaxDev] = {false};
 
 // ---------------------------------------------------------------- host staging (no heap)
+constexpr int kSM = QEQ_STATIC_MAX_MESH;
+constexpr int kSNcm = QEQ_STATIC_MAX_SPECIES / 2;
 struct Staging {
   StructDev st;
   FftPlanDev fft[3];
-  double2 tw64[3 * QEQ_STATIC_MAX_MESH];
-  float2 tw32[3 * QEQ_STATIC_MAX_MESH];
-  double bmod[3 * QEQ_STATIC_MAX_MESH];
-  float bmod32[3 * QEQ_STATIC_MAX_MESH];
-  int4 zit[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH * (QEQ_STATIC_MAX_SPECIES / 2)];
-  int4 yit[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH * (QEQ_STATIC_MAX_SPECIES / 2)];
-  int4 xit[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH];
-  int2 xpairs[QEQ_STATIC_MAX_MESH * QEQ_STATIC_MAX_MESH / 2 + 4];
-  int bin_struct[(QEQ_STATIC_MAX_MESH / QEQ_BIN) * (QEQ_STATIC_MAX_MESH / QEQ_BIN) * (QEQ_STATIC_MAX_MESH / QEQ_BIN)];
+  double2 tw64[3 * kSM];
+  float2 tw32[3 * kSM];
+  int tabs[3 * 3 * kSM];
+  double bmod[3 * kSM];
+  float bmod32[3 * kSM];
+  int4 zit[kSM * kSM * kSNcm];
+  int4 yit[kSM * kSM * kSNcm];
+  int4 yiit[kSM * kSM * kSNcm];
+  int4 xit[(kSM / 2 + 1) * kSM];
+  int bin_struct[(kSM / QEQ_BIN) * (kSM / QEQ_BIN) * (kSM / QEQ_BIN)];
   int atom_struct[QEQ_STATIC_MAX_ATOMS];
   Chunk chunks[(QEQ_STATIC_MAX_ATOMS + QEQ_CHUNK - 1) / QEQ_CHUNK];
 };
 Staging g_stage;
+
+// Worst case of the carve below at the stated limits (every piece rounded up to 256
+// bytes, as Carver does): the scratch array must hold it.
+constexpr size_t carve_bytes(size_t count, size_t elem) { return ((count ? count : 1) * elem + 255) & ~(size_t)255; }
+constexpr size_t kStaticWorstCase() {
+  const size_t N = QEQ_STATIC_MAX_ATOMS, M = (size_t)kSM * kSM * kSM, cap = QEQ_STATIC_MAX_PAIRS;
+  const size_t nbins = (kSM / QEQ_BIN) * (kSM / QEQ_BIN) * (kSM / QEQ_BIN);
+  const size_t nch = (N + QEQ_CHUNK - 1) / QEQ_CHUNK;
+  return carve_bytes(1, sizeof(StructDev)) + carve_bytes(3, sizeof(FftPlanDev)) + carve_bytes(3 * kSM, 16) +
+         carve_bytes(3 * kSM, 8) + carve_bytes(9 * kSM, 4) + carve_bytes(3 * kSM, 8) + carve_bytes(3 * kSM, 4) +
+         3 * carve_bytes((size_t)kSM * kSM * kSNcm, 16) + carve_bytes((kSM / 2 + 1) * kSM, 16) +
+         carve_bytes(nbins, 4) + carve_bytes(nbins, 4) + carve_bytes(N, 4) + carve_bytes(nch, sizeof(Chunk)) +
+         carve_bytes(N, 4) + 3 * carve_bytes(nbins + 1, 4) + carve_bytes(N, 4) + carve_bytes(N / 1024 + 8, 8) +
+         carve_bytes(N, 4) + carve_bytes(N * 3 * QEQ_MAXP, 8) + carve_bytes(N * 3 * QEQ_MAXP, 4) +
+         carve_bytes(N, 4) + 3 * carve_bytes(N, 8) + carve_bytes(3 * N, 8) + carve_bytes(N, 16) +
+         carve_bytes(N + 1, 8) + carve_bytes(N, 4) + carve_bytes(cap, 4) + carve_bytes(cap, 8) +
+         carve_bytes(cap, 4) + 2 * carve_bytes(N, 8) + 2 * carve_bytes(M * kSNcm, 16) +
+         carve_bytes(nch * QEQ_MAX_SPECIES * 2 + (nbins > nch * QEQ_GATHER_SPLIT_MAX ? nbins : nch * QEQ_GATHER_SPLIT_MAX) + 64, 8) +
+         carve_bytes(4, 4) + carve_bytes(1, sizeof(PcgScalars)) + carve_bytes(4, 4);
+}
+static_assert(kStaticWorstCase() <= QEQ_STATIC_SCRATCH_BYTES, "static scratch smaller than the worst case of the limits");
 
 double det3s(const double* h) {
   return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
@@ -275,7 +299,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
     T.rs_range[d] = std::max(1, R);
   }
-  T.M = (int64_t)T.K[0] * T.K[1] * T.K[2];
+  mesh_layout(T);
   T.mesh_off = 0;
   T.bin_off = 0;
   const int nbins = T.nb[0] * T.nb[1] * T.nb[2];
@@ -288,21 +312,12 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     const int K = T.K[d];
     FftPlanDev& f = G.fft[d];
     memset(&f, 0, sizeof(f));
-    f.K = K;
-    f.nst = fft_radices(K, f.radix);
-    if (f.nst < 1) return QEQ_ERR_INVALID;
-    for (int i = 0, prod = 1; i < f.nst; prod *= f.radix[i], ++i) {
-      f.nbf[i] = make_fastdiv(K / f.radix[i]);
-      f.ns[i] = make_fastdiv(prod);
-    }
-    f.k = make_fastdiv(K);
-    f.tw_off = d * QEQ_STATIC_MAX_MESH;
+    f.tw_off = d * kSM;
+    f.tab_off = d * 3 * kSM;
+    if (!fft_plan_fill(K, f, G.tw64 + f.tw_off, G.tw32 + f.tw_off, G.tabs + f.tab_off)) return QEQ_ERR_INVALID;
     T.fft_plan[d] = d;
-    T.bmod_off[d] = d * QEQ_STATIC_MAX_MESH;
+    T.bmod_off[d] = d * kSM;
     for (int m = 0; m < K; ++m) {
-      double ang = -2.0 * kPiS * (double)m / K;
-      G.tw64[d * QEQ_STATIC_MAX_MESH + m] = make_double2(cos(ang), sin(ang));
-      G.tw32[d * QEQ_STATIC_MAX_MESH + m] = make_float2((float)cos(ang), (float)sin(ang));
       double re = 0.0, im = 0.0;
       for (int k = 0; k <= T.p - 2; ++k) {
         double ph = 2.0 * kPiS * (double)m * k / K;
@@ -311,17 +326,16 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
       }
       double den = re * re + im * im;
       double v = den > 1e-30 ? 1.0 / den : 0.0;
-      G.bmod[d * QEQ_STATIC_MAX_MESH + m] = v;
-      G.bmod32[d * QEQ_STATIC_MAX_MESH + m] = (float)v;
+      G.bmod[d * kSM + m] = v;
+      G.bmod32[d * kSM + m] = (float)v;
     }
   }
   // FFT work lists (transposing passes)
-  int nz = 0, ny = 0, nx = 0, npairs = 0;
-  const int tl = fft_tile_lines(std::max(T.K[0], std::max(T.K[1], T.K[2])));
-  T.xpair_off = 0;
-  const int64_t smem_elems = fft_work_lists(
-      T, 0, tl, 0, [&](int4 v) { G.zit[nz++] = v; }, [&](int4 v) { G.yit[ny++] = v; },
-      [&](int2 v) { G.xpairs[npairs++] = v; }, [&](int4 v) { G.xit[nx++] = v; });
+  int nz = 0, ny = 0, nyi = 0, nx = 0;
+  const FftGeom geo = fft_geometry(T.K, T.ncm);
+  fft_work_lists(
+      T, 0, geo.tl, geo.tlx, [&](int4 v) { G.zit[nz++] = v; }, [&](int4 v) { G.yit[ny++] = v; },
+      [&](int4 v) { G.yiit[nyi++] = v; }, [&](int4 v) { G.xit[nx++] = v; });
   int64_t pair_cap = 0;
   if (any) {
     double per = (double)n_atoms / V * (4.0 / 3.0) * kPiS * r_cut * r_cut * r_cut;
@@ -350,30 +364,31 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.max_S = S;
   P.max_p = T.p;
   P.max_ncm = T.ncm;
-  P.tl = tl;
-  P.fft_smem_elems = smem_elems;
+  P.geo = geo;
   P.total_bins = nbins;
   P.total_bricks = nbricks;
-  P.total_mesh = T.M * T.ncm;
+  P.total_mesh = T.Mp * T.ncm;
   P.pair_cap = pair_cap;
   P.n_chunks = nchunks;
   P.max_species = S;
   P.n_zitems = nz;
   P.n_yitems = ny;
   P.n_xitems = nx;
+  P.n_yiitems = nyi;
   P.desc.coulomb_k = coulomb_k;
   Carver cv{reinterpret_cast<unsigned char*>(g_scratch_dev[dev]), 0, (size_t)QEQ_STATIC_SCRATCH_BYTES};
   const int N = n_atoms;
   P.d_st = cv.take<StructDev>(1);
   P.d_fft = cv.take<FftPlanDev>(3);
-  P.d_tw64 = cv.take<double2>(3 * QEQ_STATIC_MAX_MESH);
-  P.d_tw32 = cv.take<float2>(3 * QEQ_STATIC_MAX_MESH);
-  P.d_bmod = cv.take<double>(3 * QEQ_STATIC_MAX_MESH);
-  P.d_bmod32 = cv.take<float>(3 * QEQ_STATIC_MAX_MESH);
+  P.d_tw64 = cv.take<double2>(3 * kSM);
+  P.d_tw32 = cv.take<float2>(3 * kSM);
+  P.d_fft_tabs = cv.take<int>(3 * 3 * kSM);
+  P.d_bmod = cv.take<double>(3 * kSM);
+  P.d_bmod32 = cv.take<float>(3 * kSM);
   P.d_zitems = cv.take<int4>(nz);
   P.d_yitems = cv.take<int4>(ny);
+  P.d_yiitems = cv.take<int4>(nyi);
   P.d_xitems = cv.take<int4>(nx);
-  P.d_xpairs = cv.take<int2>(npairs);
   P.d_bin_struct = cv.take<int>(nbins);
   P.d_brick_struct = cv.take<int>(nbricks);
   P.d_atom_struct = cv.take<int>(N);
@@ -421,10 +436,11 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   SCOPY(P.d_tw32, G.tw32, sizeof(G.tw32));
   SCOPY(P.d_bmod, G.bmod, sizeof(G.bmod));
   SCOPY(P.d_bmod32, G.bmod32, sizeof(G.bmod32));
+  SCOPY(P.d_fft_tabs, G.tabs, sizeof(G.tabs));
   SCOPY(P.d_zitems, G.zit, sizeof(int4) * nz);
   SCOPY(P.d_yitems, G.yit, sizeof(int4) * ny);
+  SCOPY(P.d_yiitems, G.yiit, sizeof(int4) * nyi);
   SCOPY(P.d_xitems, G.xit, sizeof(int4) * nx);
-  SCOPY(P.d_xpairs, G.xpairs, sizeof(int2) * npairs);
   SCOPY(P.d_bin_struct, G.bin_struct, sizeof(int) * nbins);
   SCOPY(P.d_brick_struct, G.bin_struct, sizeof(int) * nbricks);
   SCOPY(P.d_atom_struct, G.atom_struct, sizeof(int) * N);
