@@ -219,6 +219,9 @@ QEQ_COMPOSITE_DFT(10, 2, 5)
 QEQ_COMPOSITE_DFT(12, 3, 4)
 QEQ_COMPOSITE_DFT(15, 3, 5)
 QEQ_COMPOSITE_DFT(16, 4, 4)
+QEQ_COMPOSITE_DFT(18, 2, 9)
+QEQ_COMPOSITE_DFT(20, 4, 5)
+QEQ_COMPOSITE_DFT(24, 3, 8)
 #undef QEQ_COMPOSITE_DFT
 
 
@@ -274,32 +277,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Load nl lines of `elems` complex elements (line l from src + off(l)) into the tile, lines
 // ld elements apart.  All threads call it.  Returns false on every thread if the copy did
 // not complete within the bound (after a second bounded wait for the copies in flight).
-// extra_tx > 0 (a test hook, see QEQ_FLAG_TEST_STALL) announces more bytes than the copies
-// deliver, so that this wait runs out while the copies themselves complete normally.
-template <typename V, class LineOff>
-__device__ __forceinline__ bool load_lines(V* tile, int ld, int nl, int elems, const V* src, LineOff off,
-                                           uint64_t* bar, uint32_t& phase, int* err, int extra_tx = 0) {
-  __syncthreads();  // earlier reads of the tile are finished
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(bar, (uint32_t)(nl * elems * (int)sizeof(V) + extra_tx));
-    }
-    __syncwarp();
-    for (int l = threadIdx.x; l < nl; l += 32)
-      bulk_load(tile + (size_t)l * ld, src + off(l), (uint32_t)(elems * sizeof(V)), bar);
-  }
-  bool ok = mbar_wait_bounded(bar, phase);
-  ok = __syncthreads_and(ok);
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
-    mbar_wait_bounded(bar, phase);
-    return false;
-  }
-  phase ^= 1u;
-  return true;
-}
-
 // ------------------------------------------------------------------ mixed-radix stages in shared memory
 // A line of K = R_0 ... R_{m-1} points is transformed in place, stage after stage
 // (decimation in time over blocks): stage s works on Q_s = R_0...R_{s-1} blocks of
@@ -312,7 +289,7 @@ __device__ __forceinline__ bool load_lines(V* tile, int ld, int nl, int elems, c
 
 template <typename T, typename V>
 __device__ __forceinline__ V twiddle(const V* __restrict__ tw, int idx, T sgn) {
-  V t = __ldg(tw + idx);
+  V t = tw[idx];
   t.y *= -sgn;  // table holds exp(-2 pi i m/K); sgn = -1 keeps it, +1 conjugates
   return t;
 }
@@ -394,7 +371,7 @@ __device__ __forceinline__ void stage_last(const typename C2<T>::t* tile, int nl
       l = (int)fdiv((uint32_t)w, fp.fnb[m]);
       u = w - l * nu;
     }
-    const V* b = tile + l * ld + __ldg(blk + u);
+    const V* b = tile + l * ld + blk[u];
     V v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = b[r];
@@ -435,20 +412,31 @@ __device__ __forceinline__ void stage_inv0_out(const typename C2<T>::t* tile, in
   }
 }
 
-#define QEQ_RADIX_SWITCH(R, CALL) \
-  switch (R) {                    \
-    case 2: CALL(2); break;       \
-    case 3: CALL(3); break;       \
-    case 4: CALL(4); break;       \
-    case 5: CALL(5); break;       \
-    case 6: CALL(6); break;       \
-    case 8: CALL(8); break;       \
-    case 9: CALL(9); break;       \
-    case 10: CALL(10); break;     \
-    case 12: CALL(12); break;     \
-    case 15: CALL(15); break;     \
-    case 16: CALL(16); break;     \
-    default: break;               \
+// dispatch on a stage's radix; radices above 16 exist for FP32 stages only (T is the
+// enclosing template's mesh precision)
+#define QEQ_RADIX_SWITCH(R, CALL)                  \
+  switch (R) {                                     \
+    case 2: CALL(2); break;                        \
+    case 3: CALL(3); break;                        \
+    case 4: CALL(4); break;                        \
+    case 5: CALL(5); break;                        \
+    case 6: CALL(6); break;                        \
+    case 8: CALL(8); break;                        \
+    case 9: CALL(9); break;                        \
+    case 10: CALL(10); break;                      \
+    case 12: CALL(12); break;                      \
+    case 15: CALL(15); break;                      \
+    case 16: CALL(16); break;                      \
+    default:                                       \
+      if constexpr (sizeof(T) == 4) {              \
+        switch (R) {                               \
+          case 18: CALL(18); break;                \
+          case 20: CALL(20); break;                \
+          case 24: CALL(24); break;                \
+          default: break;                          \
+        }                                          \
+      }                                            \
+      break;                                       \
   }
 
 // all stages but the last, in forward order
@@ -492,70 +480,155 @@ __host__ __device__ __forceinline__ int fft_copy_elems(int K) {
   return sizeof(T) == 4 ? K + (K & 1) : K;
 }
 
+// Issue the bulk copies of one work unit into buffer B (warp 0 only): when `tables`, the
+// unit's FFT plan, its twiddles and ntab of its int tables (from table t0); then nl mesh
+// lines.  extra_tx > 0 (a test hook, see QEQ_FLAG_TEST_STALL) announces more bytes than
+// the copies deliver.
+template <typename T, class LineSrc>
+__device__ __forceinline__ void issue_unit(unsigned char* B, const FftBuf& L, uint64_t* bar,
+                                           const FftPlanDev* __restrict__ fsrc, const typename C2<T>::t* twg,
+                                           const int* __restrict__ tabs, int t0, int ntab, int nl, int ld,
+                                           LineSrc line, int extra_tx, bool tables) {
+  using V = typename C2<T>::t;
+  const int lane = threadIdx.x & 31;
+  const int K = fsrc->K;
+  const int twn = sizeof(T) == 4 ? K + (K & 1) : K;
+  const int K4 = (K + 3) & ~3;
+  const int elems = fft_copy_elems<T>(K);
+  const size_t tab_bytes = tables ? sizeof(FftPlanDev) + twn * sizeof(V) + ntab * K4 * 4 : 0;
+  if (lane == 0) {
+    fence_proxy_async();
+    mbar_expect_tx(bar, (uint32_t)(tab_bytes + (size_t)nl * elems * sizeof(V) + extra_tx));
+  }
+  __syncwarp();
+  if (tables) {  // skipped when the buffer already holds this plan's tables
+    if (lane == 0) bulk_load(B, fsrc, sizeof(FftPlanDev), bar);
+    if (lane == 1) bulk_load(B + L.tw, twg + fsrc->tw_off, (uint32_t)(twn * sizeof(V)), bar);
+    if (lane == 2) bulk_load(B + L.tab, tabs + fsrc->tab_off + t0 * K4, (uint32_t)(ntab * K4 * 4), bar);
+  }
+  V* tile = reinterpret_cast<V*>(B + L.tile);
+  for (int l = lane; l < nl; l += 32) bulk_load(tile + (size_t)l * ld, line(l), (uint32_t)(elems * sizeof(V)), bar);
+}
+
+// A failed bounded wait: flag it, wait (bounded) for the copies of both buffers, give up.
+__device__ __forceinline__ void give_up(int* err, uint64_t* bar, const uint32_t* ph, bool next_issued, int b) {
+  if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+  mbar_wait_bounded(&bar[b], ph[b]);
+  if (next_issued) mbar_wait_bounded(&bar[b ^ 1], ph[b ^ 1]);
+}
+
+// Persistent, two-slot pipeline: CTA b takes work units b, b + G, b + 2G, ... (a unit is a
+// sub-tile of `sub` lines of an item); the bulk copies of the next unit are in flight while
+// the current one is transformed.
 template <typename T, int PASS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     k_fft_tile(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl, const int4* __restrict__ items,
-               int TL, int sub, const double2* __restrict__ tw64, const float2* __restrict__ tw32,
-               const int* __restrict__ tabs, const PcgScalars* __restrict__ sc, int use_active,
-               const typename C2<T>::t* src, typename C2<T>::t* dst, int* __restrict__ err) {
+               int nitems, int TL, int sub, int Kmax, int ldmax, const double2* __restrict__ tw64,
+               const float2* __restrict__ tw32, const int* __restrict__ tabs, const PcgScalars* __restrict__ sc,
+               int use_active, const typename C2<T>::t* src, typename C2<T>::t* dst, int* __restrict__ err) {
   // src and dst are the same buffer in the in-place inverse z pass (no __restrict__)
   using V = typename C2<T>::t;
   constexpr bool isZ = (PASS == PASS_ZF || PASS == PASS_ZI);
   constexpr bool fwd = (PASS == PASS_ZF || PASS == PASS_YF);
-  const int4 it = items[blockIdx.x];  // ZF, ZI: {s, c, x, y0}; YF: {s, c, z, x0}; YI: {s, c, x, z0}
-  const StructDev& S = st[it.x];
-  if (use_active && !sc[it.x].active) return;
-  const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
-  const int P0 = S.P[0], P1 = S.P[1], P2 = S.P[2];
-  const FftPlanDev& fp = fpl[S.fft_plan[isZ ? 2 : 1]];
-  const int K = isZ ? K2 : K1;
-  const int nitem = min(TL, (isZ ? K1 : (PASS == PASS_YF ? K0 : K2)) - it.w);
-  const int64_t mb = S.mesh_off + (int64_t)it.y * S.Mp;
-  // line l of the item starts at ib + l ils; element e of line l goes to ob + l ols + e oes
-  int64_t ib, ils, ob, ols, oes;
-  if (PASS == PASS_ZF) {
-    ib = ((int64_t)it.z * K1 + it.w) * P2; ils = P2;
-    ob = (int64_t)it.z * K2 * P1 + it.w; ols = 1; oes = P1;
-  } else if (PASS == PASS_ZI) {
-    ib = ((int64_t)it.z * K1 + it.w) * P2; ils = P2;
-    ob = ib; ols = P2; oes = 1;
-  } else if (PASS == PASS_YF) {
-    ib = ((int64_t)it.w * K2 + it.z) * P1; ils = (int64_t)K2 * P1;
-    ob = (int64_t)it.z * K1 * P0 + it.w; ols = 1; oes = P0;
-  } else {
-    ib = ((int64_t)it.w * K0 + it.z) * P1; ils = (int64_t)K0 * P1;
-    ob = (int64_t)it.z * K1 * P2 + it.w; ols = 1; oes = P2;
-  }
-  (void)P0;
-  const int ld = fft_smem_ld<T>(K);
-  const int elems = fft_copy_elems<T>(K);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  V* tile = reinterpret_cast<V*>(smem_raw + 128);
-  if (threadIdx.x == 0) mbar_init(bar);
+  const FftBuf L = fft_buf(Kmax, ldmax, sub, (int)sizeof(V), 1, 0);
+  unsigned char* bufs = smem_raw + 128;
+  __shared__ int buf_plan[2];  // FFT plan whose tables each buffer holds (read and written by warp 0)
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    buf_plan[0] = buf_plan[1] = -1;
+  }
   __syncthreads();
-  uint32_t phase = 0;
-  const V* tw = twiddles<T>(tw64, tw32) + fp.tw_off;
-  const int* blk = tabs + fp.tab_off;
+  const int nsub = (TL + sub - 1) / sub;
+  const int nunits = nitems * nsub;
+  const V* twg = twiddles<T>(tw64, tw32);
   const T sgn = fwd ? (T)-1 : (T)1;
-  const V* g = src + mb + ib;
-  V* o = dst + mb + ob;
-  for (int l0 = 0; l0 < nitem; l0 += sub) {
-    const int nl = min(sub, nitem - l0);
-    if (!load_lines(tile, ld, nl, elems, g + l0 * ils, [&](int l) { return (int64_t)l * ils; }, bar, phase, err))
-      return;
-    stages_fwd_inplace<T>(tile, nl, ld, fp, fp.nst - 1, tw, sgn);
-    int lsh = 0;
-    while ((1 << lsh) < nl) ++lsh;
-    V* ol = o + l0 * ols;
-    auto store = [&](int l, int e, V v) { ol[l * ols + e * oes] = v; };
+  // unit u: sub-tile (u mod nsub) of item u / nsub
+  struct Geo {
+    int ok, plan, K, nl;
+    int64_t in0, ils, out0, ols, oes;
+  };
+  auto geo = [&](int u) {
+    Geo g;
+    g.ok = 0;
+    if (u >= nunits) return g;
+    const int i = u / nsub, part = u - i * nsub;
+    const int4 it = items[i];  // ZF, ZI: {s, c, x, y0}; YF: {s, c, z, x0}; YI: {s, c, x, z0}
+    if (use_active && !sc[it.x].active) return g;
+    const StructDev& S = st[it.x];
+    const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
+    const int P0 = S.P[0], P1 = S.P[1], P2 = S.P[2];
+    const int nitem = min(TL, (isZ ? K1 : (PASS == PASS_YF ? K0 : K2)) - it.w);
+    g.nl = min(sub, nitem - part * sub);
+    if (g.nl <= 0) return g;
+    g.ok = 1;
+    g.plan = S.fft_plan[isZ ? 2 : 1] + (sizeof(T) == 8 ? 1 : 0);
+    g.K = isZ ? K2 : K1;
+    const int64_t mb = S.mesh_off + (int64_t)it.y * S.Mp;
+    // line l starts at in0 + l ils; element e of line l goes to out0 + l ols + e oes
+    int64_t ib, ob;
+    if (PASS == PASS_ZF) {
+      ib = ((int64_t)it.z * K1 + it.w) * P2; g.ils = P2;
+      ob = (int64_t)it.z * K2 * P1 + it.w; g.ols = 1; g.oes = P1;
+    } else if (PASS == PASS_ZI) {
+      ib = ((int64_t)it.z * K1 + it.w) * P2; g.ils = P2;
+      ob = ib; g.ols = P2; g.oes = 1;
+    } else if (PASS == PASS_YF) {
+      ib = ((int64_t)it.w * K2 + it.z) * P1; g.ils = (int64_t)K2 * P1;
+      ob = (int64_t)it.z * K1 * P0 + it.w; g.ols = 1; g.oes = P0;
+    } else {
+      ib = ((int64_t)it.w * K0 + it.z) * P1; g.ils = (int64_t)K0 * P1;
+      ob = (int64_t)it.z * K1 * P2 + it.w; g.ols = 1; g.oes = P2;
+    }
+    (void)P0;
+    g.in0 = mb + ib + (int64_t)part * sub * g.ils;
+    g.out0 = mb + ob + (int64_t)part * sub * g.ols;
+    return g;
+  };
+  auto issue = [&](const Geo& g, int b) {  // warp 0
+    issue_unit<T>(bufs + (size_t)b * L.bytes, L, &bar[b], fpl + g.plan, twg, tabs, 0, 1, g.nl,
+                  fft_smem_ld<T>(g.K), [&](int l) { return src + g.in0 + l * g.ils; }, 0, buf_plan[b] != g.plan);
+    if ((threadIdx.x & 31) == 0) buf_plan[b] = g.plan;
+  };
+  uint32_t ph[2] = {0u, 0u};
+  int u = blockIdx.x, k = 0;
+  Geo cur = geo(u);
+  if (threadIdx.x < 32 && cur.ok) issue(cur, 0);
+  for (; u < nunits; u += gridDim.x, ++k) {
+    const int b = k & 1;
+    const Geo nxt = geo(u + gridDim.x);
+    if (threadIdx.x < 32 && nxt.ok) issue(nxt, b ^ 1);  // buffer b^1 was released at the end of the last unit
+    if (cur.ok) {
+      bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], ph[b]));
+      if (!ok) {
+        give_up(err, bar, ph, nxt.ok, b);
+        return;
+      }
+      ph[b] ^= 1u;
+      unsigned char* B = bufs + (size_t)b * L.bytes;
+      const FftPlanDev& fp = *reinterpret_cast<const FftPlanDev*>(B);
+      const V* tw = reinterpret_cast<const V*>(B + L.tw);
+      const int* blk = reinterpret_cast<const int*>(B + L.tab);
+      V* tile = reinterpret_cast<V*>(B + L.tile);
+      const int ld = fft_smem_ld<T>(cur.K), nl = cur.nl;
+      stages_fwd_inplace<T>(tile, nl, ld, fp, fp.nst - 1, tw, sgn);
+      int lsh = 0;
+      while ((1 << lsh) < nl) ++lsh;
+      V* o = dst + cur.out0;
+      const int64_t ols = cur.ols, oes = cur.oes;
+      auto store = [&](int l, int e, V v) { o[l * ols + e * oes] = v; };
 #define QEQ_CALL(RR)                                                                      \
   if (PASS == PASS_ZI)                                                                    \
     stage_last<T, RR, false>(tile, nl, lsh, ld, fp, blk, sgn, store);                     \
   else                                                                                    \
     stage_last<T, RR, true>(tile, nl, lsh, ld, fp, blk, sgn, store)
-    QEQ_RADIX_SWITCH(fp.radix[fp.nst - 1], QEQ_CALL)
+      QEQ_RADIX_SWITCH(fp.radix[fp.nst - 1], QEQ_CALL)
 #undef QEQ_CALL
+      __syncthreads();  // the buffer is free for the unit after next
+    }
+    cur = nxt;
   }
 }
 
@@ -603,81 +676,139 @@ constexpr double kPreBetaOneX = 150.0;
 template <typename T, bool PRE, int MAXS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
-                  const int4* __restrict__ items, int sub, const T* __restrict__ bmod,
-                  const double2* __restrict__ tw64, const float2* __restrict__ tw32, const int* __restrict__ tabs,
-                  const PcgScalars* __restrict__ sc, int use_active, const typename C2<T>::t* __restrict__ src,
-                  typename C2<T>::t* __restrict__ dst, int* __restrict__ err, int stall) {
+                  const int4* __restrict__ items, int nitems, int TLX, int sub, int Kmax, int ldmax,
+                  const T* __restrict__ bmod, const double2* __restrict__ tw64, const float2* __restrict__ tw32,
+                  const int* __restrict__ tabs, const PcgScalars* __restrict__ sc, int use_active,
+                  const typename C2<T>::t* __restrict__ src, typename C2<T>::t* __restrict__ dst,
+                  int* __restrict__ err, int stall) {
   using V = typename C2<T>::t;
-  const int4 it = items[blockIdx.x];  // {struct, z, y0, number of lines}
-  const StructDev& S = st[it.x];
-  if (use_active && !sc[it.x].active) return;
-  const FftPlanDev& fp = fpl[S.fft_plan[0]];
-  const int K = S.K[0], K1 = S.K[1], K2 = S.K[2];
-  const int P0 = S.P[0], P1 = S.P[1];
-  const int ncm = S.ncm;
-  const int z = it.y, mz = (K2 - z) % K2;
-  const int ld = fft_smem_ld<T>(K);
-  const int elems = fft_copy_elems<T>(K);
+  constexpr int HX = MAXS / 2;  // most complex meshes
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  int64_t* slot_in = reinterpret_cast<int64_t*>(smem_raw + 128);          // 2 ncm sub
-  int64_t* slot_out = slot_in + 2 * (MAXS / 2) * sub;                      // 2 ncm sub (-1: do not write)
-  T(*lineg)[4] = reinterpret_cast<T(*)[4]>(slot_out + 2 * (MAXS / 2) * sub);  // sub
+  const FftBuf L = fft_buf(Kmax, ldmax, 2 * HX * sub, (int)sizeof(V), 2, fft_x_extra(sub, HX, (int)sizeof(T)));
+  unsigned char* bufs = smem_raw + 128;
   __shared__ T hw2[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];
-  const size_t hdr = 128 + 2 * 2 * (MAXS / 2) * sub * sizeof(int64_t) + sub * 4 * sizeof(T);
-  V* tile = reinterpret_cast<V*>(smem_raw + ((hdr + 127) & ~(size_t)127));
-  if (threadIdx.x == 0) mbar_init(bar);
-  for (int i = threadIdx.x; i < QEQ_MAX_SPECIES * QEQ_MAX_SPECIES; i += blockDim.x)
-    hw2[i] = (T)(-0.5 * 1.44269504088896340736 * S.w2[i]);
+  __shared__ int hw2_s;
+  __shared__ int buf_plan[2];  // FFT plan whose tables each buffer holds (read and written by warp 0)
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    hw2_s = -1;
+    buf_plan[0] = buf_plan[1] = -1;
+  }
   __syncthreads();
-  uint32_t phase = 0;
-  const V* tw = twiddles<T>(tw64, tw32) + fp.tw_off;
-  const int* freq = tabs + fp.tab_off + K;
-  const int* pos = tabs + fp.tab_off + 2 * K;
-  const T* bm0 = bmod + S.bmod_off[0];
-  const T* bm1 = bmod + S.bmod_off[1];
-  const T* bm2 = bmod + S.bmod_off[2];
-  const T B0 = (T)S.B[0], B1 = (T)S.B[1], B2 = (T)S.B[2];
-  const T gpref = (T)S.green_pref;
-  // beta: 1 (the plain Woodbury factor) while the smoothest mode's x = s0 g0 stays small,
-  // else the plan's safety factor (S.omega holds it for the preconditioner mesh); large
-  // cells need it because the correction nearly cancels D^-1 for their smooth modes and
-  // the circulant mean's error would then make M indefinite
-  const T pre_beta = PRE ? ((sc[it.x].s0 * S.pre_g0max <= kPreBetaOneX) ? (T)1 : (T)S.omega) : (T)0;
-  const T pre_s0 = PRE ? (T)sc[it.x].s0 : (T)0;
-  const int nspec = S.S;
-  const int c2 = (z <= K2 / 2) ? z : z - K2;
-  for (int j0 = 0; j0 < it.w; j0 += sub) {
-    const int np = min(sub, it.w - j0);
-    const int nsl = 2 * ncm * np;  // slot (ab * ncm + c) * np + l
-    __syncthreads();               // the previous sub-tile's slot tables are no longer read
-    for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
+  const int nsub = (TLX + sub - 1) / sub;
+  const int nunits = nitems * nsub;
+  const V* twg = twiddles<T>(tw64, tw32);
+  // unit u: pairs [j0, j0 + np) of item u / nsub, j0 = (u mod nsub) sub
+  struct Geo {
+    int ok, s, z, y0, np;
+  };
+  auto geo = [&](int u) {
+    Geo g;
+    g.ok = 0;
+    if (u >= nunits) return g;
+    const int i = u / nsub, part = u - i * nsub;
+    const int4 it = items[i];  // {struct, z, y0, number of lines}
+    if (use_active && !sc[it.x].active) return g;
+    g.np = min(sub, it.w - part * sub);
+    if (g.np <= 0) return g;
+    g.ok = 1;
+    g.s = it.x;
+    g.z = it.y;
+    g.y0 = it.z + part * sub;
+    return g;
+  };
+  // warp 0: slot tables and line constants of the unit in buffer b, then its copies
+  auto issue = [&](const Geo& g, int b, int extra) {
+    const StructDev& S = st[g.s];
+    const int K = S.K[0], K1 = S.K[1], K2 = S.K[2], P0 = S.P[0], P1 = S.P[1], ncm = S.ncm;
+    unsigned char* B = bufs + (size_t)b * L.bytes;
+    int64_t* slot_in = reinterpret_cast<int64_t*>(B + L.extra);
+    int64_t* slot_out = slot_in + 2 * HX * sub;
+    T(*lineg)[4] = reinterpret_cast<T(*)[4]>(slot_out + 2 * HX * sub);
+    const int np = g.np, nsl = 2 * ncm * np, z = g.z, mz = (K2 - z) % K2;
+    const int lane = threadIdx.x & 31;
+    for (int sl = lane; sl < nsl; sl += 32) {  // slot (ab * ncm + c) * np + l
       const int l = sl % np, gc = sl / np, c = gc % ncm, ab = gc / ncm;
-      const int y = it.z + j0 + l;
+      const int y = g.y0 + l;
       const int yy = ab ? (K1 - y) % K1 : y, zz = ab ? mz : z;
       const int64_t mb = S.mesh_off + (int64_t)c * S.Mp;
       slot_in[sl] = mb + ((int64_t)zz * K1 + yy) * P0;
       slot_out[sl] = (ab && zz == z && yy == y) ? -1 : mb + (int64_t)zz * K * P1 + yy;  // self-paired copy
     }
-    for (int l = threadIdx.x; l < np; l += blockDim.x) {
-      const int my = it.z + j0 + l;
+    const T* bm1 = bmod + S.bmod_off[1];
+    const T* bm2 = bmod + S.bmod_off[2];
+    const int c2 = (z <= K2 / 2) ? z : z - K2;
+    for (int l = lane; l < np; l += 32) {
+      const int my = g.y0 + l;
       const int c1 = (my <= K1 / 2) ? my : my - K1;
       lineg[l][0] = (T)(c1 * S.B[3] + c2 * S.B[6]);
       lineg[l][1] = (T)(c1 * S.B[4] + c2 * S.B[7]);
       lineg[l][2] = (T)(c1 * S.B[5] + c2 * S.B[8]);
-      lineg[l][3] = gpref * bm1[my] * bm2[z];
+      lineg[l][3] = (T)S.green_pref * bm1[my] * bm2[z];
     }
-    __syncthreads();
-    const int extra = (stall && blockIdx.x == 0 && j0 == 0) ? 16 : 0;
-    if (!load_lines(tile, ld, nsl, elems, src, [&](int sl) { return slot_in[sl]; }, bar, phase, err, extra)) return;
+    __syncwarp();
+    const int plan = S.fft_plan[0] + (sizeof(T) == 8 ? 1 : 0);
+    issue_unit<T>(B, L, &bar[b], fpl + plan, twg, tabs, 1, 2, nsl, fft_smem_ld<T>(K),
+                  [&](int sl) { return src + slot_in[sl]; }, extra, buf_plan[b] != plan);
+    if (lane == 0) buf_plan[b] = plan;
+  };
+  uint32_t ph[2] = {0u, 0u};
+  int u = blockIdx.x, k = 0;
+  Geo cur = geo(u);
+  if (threadIdx.x < 32 && cur.ok) issue(cur, 0, (stall && blockIdx.x == 0) ? 16 : 0);
+  for (; u < nunits; u += gridDim.x, ++k) {
+    const int b = k & 1;
+    const Geo nxt = geo(u + gridDim.x);
+    if (threadIdx.x < 32 && nxt.ok) issue(nxt, b ^ 1, 0);
+    if (!cur.ok) {
+      cur = nxt;
+      continue;
+    }
+    bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], ph[b]));
+    if (!ok) {
+      give_up(err, bar, ph, nxt.ok, b);
+      return;
+    }
+    ph[b] ^= 1u;
+    const StructDev& S = st[cur.s];
+    const int K = S.K[0], P1 = S.P[1], ncm = S.ncm, np = cur.np, nsl = 2 * ncm * np;
+    const int ld = fft_smem_ld<T>(K);
+    unsigned char* B = bufs + (size_t)b * L.bytes;
+    const FftPlanDev& fp = *reinterpret_cast<const FftPlanDev*>(B);
+    const V* tw = reinterpret_cast<const V*>(B + L.tw);
+    const int K4 = (K + 3) & ~3;
+    const int* freq = reinterpret_cast<const int*>(B + L.tab);
+    const int* pos = freq + K4;
+    const int64_t* slot_out = reinterpret_cast<const int64_t*>(B + L.extra) + 2 * HX * sub;
+    const T(*lineg)[4] = reinterpret_cast<const T(*)[4]>(slot_out + 2 * HX * sub);
+    V* tile = reinterpret_cast<V*>(B + L.tile);
+    if (hw2_s != cur.s) {  // exponent factors -w_st^2/2 log2(e) of this structure
+      __syncthreads();
+      for (int i = threadIdx.x; i < QEQ_MAX_SPECIES * QEQ_MAX_SPECIES; i += blockDim.x)
+        hw2[i] = (T)(-0.5 * 1.44269504088896340736 * S.w2[i]);
+      if (threadIdx.x == 0) hw2_s = cur.s;
+      __syncthreads();
+    }
+    const T* bm0 = bmod + S.bmod_off[0];
+    const T B0 = (T)S.B[0], B1 = (T)S.B[1], B2 = (T)S.B[2];
+    const T gpref = (T)S.green_pref;
+    // beta: 1 (the plain Woodbury factor) while the smoothest mode's x = s0 g0 stays small,
+    // else the plan's safety factor (S.omega holds it for the preconditioner mesh); large
+    // cells need it because the correction nearly cancels D^-1 for their smooth modes and
+    // the circulant mean's error would then make M indefinite
+    const T pre_beta = PRE ? ((sc[cur.s].s0 * S.pre_g0max <= kPreBetaOneX) ? (T)1 : (T)S.omega) : (T)0;
+    const T pre_s0 = PRE ? (T)sc[cur.s].s0 : (T)0;
+    const int nspec = S.S;
     // forward x FFT, every stage in place: block order
     stages_fwd_inplace<T>(tile, nsl, ld, fp, fp.nst, tw, (T)-1);
-    // reciprocal multiply; exponent factors are -w_st^2/2 log2(e), so each Gaussian is one exp2
+    // reciprocal multiply; each Gaussian is one exp2
     for (int w = threadIdx.x; w < np * K; w += blockDim.x) {
       const int l = (int)fdiv((uint32_t)w, fp.fK), p = w - l * K;
-      const int mx = __ldg(freq + p);
+      const int mx = freq[p];
       const int mmx = (mx == 0) ? 0 : K - mx;
-      const int p2 = __ldg(pos + mmx);
+      const int p2 = pos[mmx];
       const int c0 = (mx <= K / 2) ? mx : mx - K;
       const T Gx = (T)c0 * B0 + lineg[l][0];
       const T Gy = (T)c0 * B1 + lineg[l][1];
@@ -687,7 +818,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
       const T pref = lineg[l][3] * bm0[mx] * rG2;  // G = 0 term dropped
       V Qh[MAXS];
 #pragma unroll
-      for (int c = 0; c < MAXS / 2; ++c) {
+      for (int c = 0; c < HX; ++c) {
         if (c >= ncm) break;
         const V za = tile[(size_t)(c * np + l) * ld + p];
         const V zb = tile[(size_t)((ncm + c) * np + l) * ld + p2];
@@ -696,7 +827,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
         Qh[2 * c + 1] = {(T)0.5 * (za.y + zb.y), (T)-0.5 * (za.x - zb.x)};
       }
 #pragma unroll
-      for (int c = 0; c < MAXS / 2; ++c) {
+      for (int c = 0; c < HX; ++c) {
         if (c >= ncm) break;
         V p0 = {(T)0, (T)0}, p1 = {(T)0, (T)0};
         if (PRE) {
@@ -707,6 +838,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
           const T hm = pre_beta * pref * e * recip<T>((T)1 + pre_s0 * g0);
           p0.x = hm * Qh[0].x;
           p0.y = hm * Qh[0].y;
+        } else if (MAXS == 2) {
+          // g_st = g_ts: three Gaussians for the two species of the complex mesh
+          const T g00 = pref * exp2_mesh<T>(G2 * hw2[0]);
+          if (nspec > 1) {
+            const T g01 = pref * exp2_mesh<T>(G2 * hw2[1]);
+            const T g11 = pref * exp2_mesh<T>(G2 * hw2[QEQ_MAX_SPECIES + 1]);
+            p0.x = g00 * Qh[0].x + g01 * Qh[1].x;
+            p0.y = g00 * Qh[0].y + g01 * Qh[1].y;
+            p1.x = g01 * Qh[0].x + g11 * Qh[1].x;
+            p1.y = g01 * Qh[0].y + g11 * Qh[1].y;
+          } else {
+            p0.x = g00 * Qh[0].x;
+            p0.y = g00 * Qh[0].y;
+          }
         } else {
 #pragma unroll
           for (int t = 0; t < MAXS; ++t) {
@@ -737,12 +882,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     int lsh = 0;
     while ((1 << lsh) < np) ++lsh;
     auto store = [&](int sl, int e, V v) {
-      const int64_t b = slot_out[sl];
-      if (b >= 0) dst[b + (int64_t)e * P1] = v;
+      const int64_t bo = slot_out[sl];
+      if (bo >= 0) dst[bo + (int64_t)e * P1] = v;
     };
 #define QEQ_CALL(RR) stage_inv0_out<T, RR>(tile, 2 * ncm, np, lsh, ld, fp, tw, store)
     QEQ_RADIX_SWITCH(fp.radix[0], QEQ_CALL)
 #undef QEQ_CALL
+    __syncthreads();  // the buffer is free for the unit after next
+    cur = nxt;
   }
 }
 

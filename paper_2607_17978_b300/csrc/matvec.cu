@@ -41,8 +41,9 @@ __device__ __forceinline__ Brick brick_of(const StructDev& S, int g) {
   int bc0 = gl / (S.nbr[2] * S.nbr[1]);
   int bc[3] = {bc0, bc1, bc2};
   for (int d = 0; d < 3; ++d) {
-    B.x0[d] = bc[d] * QEQ_BRICK;
-    B.ext[d] = min(QEQ_BRICK, S.K[d] - B.x0[d]);
+    const int e = (d == 2) ? QEQ_BRICK_Z : QEQ_BRICK_XY;
+    B.x0[d] = bc[d] * e;
+    B.ext[d] = min(e, S.K[d] - B.x0[d]);
   }
   return B;
 }
@@ -86,12 +87,17 @@ __device__ __forceinline__ unsigned stencil_rows(int o, int K, int ext) {
 
 template <typename T, int P>
 struct SpreadRecs {
-  T wz[QEQ_SPB][QEQ_BRICK];  // z weights at the brick's z positions (0 outside the stencil)
+  T wz[QEQ_SPB][QEQ_BRICK_Z];  // z weights at the brick's z positions (0 outside the stencil)
   T wx[QEQ_SPB][P];          // q * x weights, by stencil index
   T wy[QEQ_SPB][P];
   unsigned mask[QEQ_SPB];    // x rows (bits 0-15) and y rows (bits 16-31) the stencil covers
   int off[QEQ_SPB];          // ox | oy << 10 | species part << 20
 };
+
+template <typename T, int P>
+constexpr size_t spread_smem() {
+  return sizeof(SpreadRecs<T, P>);
+}
 
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
@@ -149,9 +155,9 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
   __syncthreads();
   const int total = bin_pre[nbins];
   for (int cm = 0; cm < S.ncm; ++cm) {
-    T re[QEQ_BRICK], im[QEQ_BRICK];
+    T re[QEQ_BRICK_Z], im[QEQ_BRICK_Z];
 #pragma unroll
-    for (int z = 0; z < QEQ_BRICK; ++z) re[z] = im[z] = (T)0;
+    for (int z = 0; z < QEQ_BRICK_Z; ++z) re[z] = im[z] = (T)0;
     for (int c0 = 0; c0 < total; c0 += QEQ_SPB) {
       const int nbat = min(QEQ_SPB, total - c0);
       if (c0 > 0) __syncthreads();  // the previous batch is consumed
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
           const unsigned ym = stencil_rows<P>(o[1], K1, B.ext[1]);
           const unsigned zm = stencil_rows<P>(o[2], K2, B.ext[2]);
 #pragma unroll
-          for (int l = 0; l < QEQ_BRICK; ++l) {
+          for (int l = 0; l < QEQ_BRICK_Z; ++l) {
             int j = l - o[2];
             if (j < 0) j += K2;
             if (j >= K2) j -= K2;
@@ -222,10 +228,10 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
           const T* wz = R.wz[k];
           if ((off >> 20) & 1) {
 #pragma unroll
-            for (int z = 0; z < QEQ_BRICK; ++z) im[z] += r * wz[z];
+            for (int z = 0; z < QEQ_BRICK_Z; ++z) im[z] += r * wz[z];
           } else {
 #pragma unroll
-            for (int z = 0; z < QEQ_BRICK; ++z) re[z] += r * wz[z];
+            for (int z = 0; z < QEQ_BRICK_Z; ++z) re[z] += r * wz[z];
           }
         }
       }
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
       V* mg = mesh + S.mesh_off + (int64_t)cm * S.Mp +
               ((int64_t)(B.x0[0] + lx) * K1 + (B.x0[1] + ly)) * S.P[2] + B.x0[2];
 #pragma unroll
-      for (int z = 0; z < QEQ_BRICK; ++z)
+      for (int z = 0; z < QEQ_BRICK_Z; ++z)
         if (z < B.ext[2]) mg[z] = V{re[z], im[z]};
     }
   }
@@ -576,51 +582,93 @@ __global__ void k_pre_gather(const Chunk* __restrict__ chunks, const StructDev* 
 }
 
 // ------------------------------------------------------------------ host side
+// Persistent grid of an FFT pass: the resident CTAs of all SMs, at most one per unit.
+int fft_grid(qeq_plan_s* P, const void* fn, size_t smem, int nunits) {
+  int blocks = 0;
+  for (int i = 0; i < P->n_occ; ++i)
+    if (P->occ[i].fn == fn && P->occ[i].smem == smem) {
+      blocks = P->occ[i].blocks;
+      break;
+    }
+  if (blocks == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 256, smem) != cudaSuccess || blocks < 1) {
+      cudaGetLastError();
+      blocks = 1;
+    }
+    if (P->n_occ < (int)(sizeof(P->occ) / sizeof(P->occ[0]))) P->occ[P->n_occ++] = {fn, smem, blocks};
+  }
+  return std::max(1, std::min(nunits, blocks * P->num_sms));
+}
+
 // The five FFT passes (buffers a: L0 / L2, b: L1 / L3): ZF a -> b, YF b -> a, X a -> b,
 // YI b -> a, ZI a in place.  mark() records a stage event after each pass.
 template <typename T, bool PRE, class Mark>
-cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const StructDev* st, const int4* zit, int nz,
-                              const int4* yit, int ny, const int4* yiit, int nyi, const int4* xit, int nx,
-                              int use_active, typename C2<T>::t* a, typename C2<T>::t* b, int max_species,
-                              Mark mark) {
+cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax, const StructDev* st,
+                              const int4* zit, int nz, const int4* yit, int ny, const int4* yiit, int nyi,
+                              const int4* xit, int nx, int use_active, typename C2<T>::t* a, typename C2<T>::t* b,
+                              int max_species, Mark mark) {
   using V = typename C2<T>::t;
   constexpr bool F32 = std::is_same<T, float>::value;
   cudaStream_t s = Pl->stream;
   const T* bmod = F32 ? (const T*)(const void*)Pl->d_bmod32 : (const T*)(const void*)Pl->d_bmod;
   const int sub = F32 ? g.sub32 : g.sub64;
   const int subx = F32 ? g.subx32 : g.subx64;
-  const size_t smz = fft_tile_smem(sub, F32 ? g.ldz32 : g.ldz64, sizeof(V));
-  const size_t smy = fft_tile_smem(sub, F32 ? g.ldy32 : g.ldy64, sizeof(V));
+  const int nsub = (g.tl + sub - 1) / sub, nsubx = (g.tlx + subx - 1) / subx;
+  const int ldz = F32 ? g.ldz32 : g.ldz64, ldy = F32 ? g.ldy32 : g.ldy64, ldx = F32 ? g.ldx32 : g.ldx64;
+  const size_t smz = 128 + 2 * (size_t)fft_buf(kmax[2], ldz, sub, sizeof(V), 1, 0).bytes;
+  const size_t smy = 128 + 2 * (size_t)fft_buf(kmax[1], ldy, sub, sizeof(V), 1, 0).bytes;
   const int* tabs = Pl->d_fft_tabs;
   int* err = Pl->d_err;
-  k_fft_tile<T, PASS_ZF><<<nz, 256, smz, s>>>(st, Pl->d_fft, zit, g.tl, sub, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
-                                              use_active, a, b, err);
-  QEQ_CUDA_TRY(cudaGetLastError());
-  QEQ_CUDA_TRY(mark());
-  k_fft_tile<T, PASS_YF><<<ny, 256, smy, s>>>(st, Pl->d_fft, yit, g.tl, sub, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
-                                              use_active, b, a, err);
-  QEQ_CUDA_TRY(cudaGetLastError());
-  QEQ_CUDA_TRY(mark());
-  if (PRE || max_species <= 2) {
-    const size_t smx = fft_x_smem(subx, F32 ? g.ldx32 : g.ldx64, sizeof(V), 1, sizeof(T));
-    k_fft_x_green<T, PRE, 2><<<nx, 256, smx, s>>>(st, Pl->d_fft, xit, subx, bmod, Pl->d_tw64, Pl->d_tw32, tabs,
-                                                  Pl->d_sc, use_active, a, b, err, PRE ? 0 : Pl->test_stall);
-  } else {
-    const size_t smx = fft_x_smem(subx, F32 ? g.ldx32 : g.ldx64, sizeof(V), QEQ_MAX_SPECIES / 2, sizeof(T));
-    k_fft_x_green<T, false, QEQ_MAX_SPECIES><<<nx, 256, smx, s>>>(st, Pl->d_fft, xit, subx, bmod, Pl->d_tw64,
-                                                                  Pl->d_tw32, tabs, Pl->d_sc, use_active, a, b, err,
-                                                                  Pl->test_stall);
+  {
+    auto fn = k_fft_tile<T, PASS_ZF>;
+    fn<<<fft_grid(Pl, (const void*)fn, smz, nz * nsub), 256, smz, s>>>(
+        st, Pl->d_fft, zit, nz, g.tl, sub, kmax[2], ldz, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, a, b, err);
+    QEQ_CUDA_TRY(cudaGetLastError());
+    QEQ_CUDA_TRY(mark());
   }
-  QEQ_CUDA_TRY(cudaGetLastError());
-  QEQ_CUDA_TRY(mark());
-  k_fft_tile<T, PASS_YI><<<nyi, 256, smy, s>>>(st, Pl->d_fft, yiit, g.tl, sub, Pl->d_tw64, Pl->d_tw32, tabs,
-                                               Pl->d_sc, use_active, b, a, err);
-  QEQ_CUDA_TRY(cudaGetLastError());
-  QEQ_CUDA_TRY(mark());
-  k_fft_tile<T, PASS_ZI><<<nz, 256, smz, s>>>(st, Pl->d_fft, zit, g.tl, sub, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
-                                              use_active, a, a, err);
-  QEQ_CUDA_TRY(cudaGetLastError());
-  QEQ_CUDA_TRY(mark());
+  {
+    auto fn = k_fft_tile<T, PASS_YF>;
+    fn<<<fft_grid(Pl, (const void*)fn, smy, ny * nsub), 256, smy, s>>>(
+        st, Pl->d_fft, yit, ny, g.tl, sub, kmax[1], ldy, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, b, a, err);
+    QEQ_CUDA_TRY(cudaGetLastError());
+    QEQ_CUDA_TRY(mark());
+  }
+  {
+    const int stall = PRE ? 0 : Pl->test_stall;
+    if (PRE || max_species <= 2) {
+      auto fn = k_fft_x_green<T, PRE, 2>;
+      const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], ldx, 2 * subx, sizeof(V), 2,
+                                                   fft_x_extra(subx, 1, sizeof(T))).bytes;
+      fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+          st, Pl->d_fft, xit, nx, g.tlx, subx, kmax[0], ldx, bmod, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
+          use_active, a, b, err, stall);
+    } else {
+      constexpr int HX = QEQ_MAX_SPECIES / 2;
+      auto fn = k_fft_x_green<T, false, QEQ_MAX_SPECIES>;
+      const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], ldx, 2 * HX * subx, sizeof(V), 2,
+                                                   fft_x_extra(subx, HX, sizeof(T))).bytes;
+      fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+          st, Pl->d_fft, xit, nx, g.tlx, subx, kmax[0], ldx, bmod, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
+          use_active, a, b, err, stall);
+    }
+    QEQ_CUDA_TRY(cudaGetLastError());
+    QEQ_CUDA_TRY(mark());
+  }
+  {
+    auto fn = k_fft_tile<T, PASS_YI>;
+    fn<<<fft_grid(Pl, (const void*)fn, smy, nyi * nsub), 256, smy, s>>>(
+        st, Pl->d_fft, yiit, nyi, g.tl, sub, kmax[1], ldy, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, b, a,
+        err);
+    QEQ_CUDA_TRY(cudaGetLastError());
+    QEQ_CUDA_TRY(mark());
+  }
+  {
+    auto fn = k_fft_tile<T, PASS_ZI>;
+    fn<<<fft_grid(Pl, (const void*)fn, smz, nz * nsub), 256, smz, s>>>(
+        st, Pl->d_fft, zit, nz, g.tl, sub, kmax[2], ldz, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, a, a, err);
+    QEQ_CUDA_TRY(cudaGetLastError());
+    QEQ_CUDA_TRY(mark());
+  }
   return cudaSuccess;
 }
 
@@ -645,13 +693,13 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   QEQ_CUDA_TRY(mark());
   // stage 1: spreading
   {
-    k_spread<T, P><<<Pl->total_bricks, 256, sizeof(SpreadRecs<T, P>), s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
+    k_spread<T, P><<<Pl->total_bricks, 256, spread_smem<T, P>(), s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
                                                       Pl->d_spec, x, x32, Pl->d_sc, use_active, mesh);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   QEQ_CUDA_TRY(mark());
   V* mesh2 = reinterpret_cast<V*>(Pl->d_mesh2);
-  QEQ_CUDA_TRY((launch_fft_passes<T, false>(Pl, Pl->geo, Pl->d_st, Pl->d_zitems, Pl->n_zitems, Pl->d_yitems,
+  QEQ_CUDA_TRY((launch_fft_passes<T, false>(Pl, Pl->geo, Pl->fft_kmax, Pl->d_st, Pl->d_zitems, Pl->n_zitems, Pl->d_yitems,
                                             Pl->n_yitems, Pl->d_yiitems, Pl->n_yiitems, Pl->d_xitems, Pl->n_xitems,
                                             use_active, mesh, mesh2, Pl->max_species, mark)));
   // stage 7: gathering + real-space pairs + local terms (+ x.y per structure)
@@ -671,7 +719,7 @@ template <typename T, int P>
 cudaError_t set_smem_attrs() {
   const int big = 227 * 1024 - 1024;  // leaves room for the kernels' static shared arrays
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(SpreadRecs<T, P>)));
+                                    (int)spread_smem<T, P>()));
   if (P == 4) {  // the FFT kernels do not depend on the B-spline order: set them once
     QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_tile<T, PASS_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_tile<T, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -733,7 +781,7 @@ cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, 
                                             P->d_pmesh);
   }
   QEQ_CUDA_TRY(cudaGetLastError());
-  QEQ_CUDA_TRY((launch_fft_passes<float, true>(P, P->pgeo, P->d_stp, P->d_pzitems, P->n_pz, P->d_pyitems, P->n_py,
+  QEQ_CUDA_TRY((launch_fft_passes<float, true>(P, P->pgeo, P->pfft_kmax, P->d_stp, P->d_pzitems, P->n_pz, P->d_pyitems, P->n_py,
                                                P->d_pyiitems, P->n_pyi, P->d_pxitems, P->n_px, use_active,
                                                P->d_pmesh, P->d_pmesh2, 1, []() { return cudaSuccess; })));
   k_pre_gather<<<P->n_chunks, 256, 0, s>>>(P->d_chunks, P->d_stp, P->d_pbase, P->d_pw, P->d_dinv, r, P->d_pmesh, P->d_sc,

@@ -301,20 +301,24 @@ static qeq_status build_plan(qeq_plan_s* P) {
     if (pbest == 0) return fail(P, QEQ_ERR_INVALID, "no mesh meets ewald_tol within 1000 points per direction");
   }
   P->max_p = pbest;
+  // two plans per FFT length: FP32 stages (radices up to 32), then FP64 stages (up to 16)
   auto fft_plan_for = [&](int K) {
     auto it = fft_index.find(K);
     if (it != fft_index.end()) return it->second;
-    FftPlanDev f;
-    memset(&f, 0, sizeof(f));
-    f.tw_off = (int)tw64.size();
-    f.tab_off = (int)tabs.size();
-    const int padK = K + (K & 1);  // keeps every twiddle table 16-byte aligned
-    tw64.resize(tw64.size() + padK);
-    tw32.resize(tw32.size() + padK);
-    tabs.resize(tabs.size() + 3 * (size_t)K);
-    if (!fft_plan_fill(K, f, tw64.data() + f.tw_off, tw32.data() + f.tw_off, tabs.data() + f.tab_off)) return -1;
-    int idx = (int)fplans.size();
-    fplans.push_back(f);
+    const int idx = (int)fplans.size();
+    for (int maxR : {QEQ_MAXR32, QEQ_MAXR64}) {
+      FftPlanDev f;
+      memset(&f, 0, sizeof(f));
+      f.tw_off = (int)tw64.size();
+      f.tab_off = (int)tabs.size();
+      const int padK = K + (K & 1);  // keeps every twiddle table 16-byte aligned
+      tw64.resize(tw64.size() + padK);
+      tw32.resize(tw32.size() + padK);
+      tabs.resize(tabs.size() + 3 * (size_t)((K + 3) & ~3));
+      if (!fft_plan_fill(K, f, tw64.data() + f.tw_off, tw32.data() + f.tw_off, tabs.data() + f.tab_off, maxR))
+        return -1;
+      fplans.push_back(f);
+    }
     fft_index[K] = idx;
     return idx;
   };
@@ -399,7 +403,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
       T.K[d] = K;
       (void)cst;
       T.nb[d] = (K + QEQ_BIN - 1) / QEQ_BIN;
-      T.nbr[d] = (K + QEQ_BRICK - 1) / QEQ_BRICK;
+      T.nbr[d] = (K + (d == 2 ? QEQ_BRICK_Z : QEQ_BRICK_XY) - 1) / (d == 2 ? QEQ_BRICK_Z : QEQ_BRICK_XY);
       // bins that can hold an atom within r_cut (plus one for a ragged last bin)
       double l = rc / wd[d] * K / QEQ_BIN;
       int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
@@ -473,6 +477,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
       hsp.push_back(Tp);
     }
     P->pgeo = fft_geometry(maxKp, 1);
+    for (int d = 0; d < 3; ++d) P->pfft_kmax[d] = maxKp[d];
     for (int s = 0; s < ns; ++s) {
       StructDev& Tp = hsp[s];
       Tp.S = 1;
@@ -545,15 +550,22 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->n_xitems = (int)xit.size();
   P->n_yiitems = (int)yiit.size();
   P->max_ncm = (max_s + 1) / 2;
+  for (int d = 0; d < 3; ++d) P->fft_kmax[d] = maxK[d];
   {
     const FftGeom& g = P->geo;
     const int hx = max_s <= 2 ? 1 : QEQ_MAX_SPECIES / 2;
-    const size_t big = std::max({fft_tile_smem(g.sub64, std::max(g.ldz64, g.ldy64), sizeof(double2)),
-                                 fft_x_smem(g.subx64, g.ldx64, sizeof(double2), hx, sizeof(double)),
-                                 fft_tile_smem(g.sub32, std::max(g.ldz32, g.ldy32), sizeof(float2)),
-                                 fft_x_smem(g.subx32, g.ldx32, sizeof(float2), hx, sizeof(float))});
-    if (big > 227 * 1024 - 1024) return fail(P, QEQ_ERR_INVALID, "FFT tile exceeds shared memory");
+    size_t big = 0;
+    for (int e : {8, 16}) {  // FP32, FP64 complex elements
+      const int sub = e == 8 ? g.sub32 : g.sub64, subx = e == 8 ? g.subx32 : g.subx64;
+      const int ldz = e == 8 ? g.ldz32 : g.ldz64, ldy = e == 8 ? g.ldy32 : g.ldy64, ldx = e == 8 ? g.ldx32 : g.ldx64;
+      big = std::max(big, (size_t)fft_buf(maxK[2], ldz, sub, e, 1, 0).bytes);
+      big = std::max(big, (size_t)fft_buf(maxK[1], ldy, sub, e, 1, 0).bytes);
+      big = std::max(big, (size_t)fft_buf(maxK[0], ldx, 2 * hx * subx, e, 2, fft_x_extra(subx, hx, e / 2)).bytes);
+    }
+    if (128 + 2 * big > 227 * 1024 - 1024) return fail(P, QEQ_ERR_INVALID, "FFT tile exceeds shared memory");
   }
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (P->num_sms < 1) P->num_sms = 1;
 
   // atom -> structure (input order)
   std::vector<int> atom_struct(P->n_atoms);

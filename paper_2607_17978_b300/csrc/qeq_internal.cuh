@@ -14,7 +14,8 @@
 
 #define QEQ_MAX_SPECIES 8
 #define QEQ_BIN 8          // mesh points per edge of an atom bin (sorting, real-space search)
-#define QEQ_BRICK 16       // mesh points per edge of a spread / gather brick (2 x 2 x 2 bins)
+#define QEQ_BRICK_XY 16    // spread brick: mesh points in x and y (2 x 2 bins) ...
+#define QEQ_BRICK_Z 16     // ... and in z (2 bins)
 #define QEQ_MAXP 8         // largest supported B-spline order
 #define QEQ_MAX_STAGES 12  // radix stages of one FFT length
 #define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
@@ -42,11 +43,11 @@ struct StructDev {
   int64_t mesh_off;       // complex-element offset of this structure's complex mesh 0
   int64_t atom_begin, atom_end;
   int bin_off;            // first global bin of this structure
-  int fft_plan[3];        // FFT plan index per direction
+  int fft_plan[3];        // FFT plan index per direction (FP32 stages; the FP64 plan follows it)
   int bmod_off[3];        // offsets into the B-spline modulus table per direction
   int P[3];               // padded line lengths K_d + (K_d & 1) (innermost stride of each layout)
   int brick_off;          // first global brick of this structure
-  int nbr[3];             // bricks per direction (ceil(K/QEQ_BRICK))
+  int nbr[3];             // spread bricks per direction
   double w2[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];     // reciprocal Gaussian width^2 w_st^2
   double corr[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];   // G = 0 width term over r < r_cut (narrow pairs)
   double inv_sw[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES]; // 1/(sqrt2 w_st) (narrow pairs)
@@ -82,7 +83,7 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return 
 
 // Mixed-radix plan of one FFT length K = R_0 ... R_{m-1} (see fft.cuh): stage s has
 // Q_s = R_0...R_{s-1} blocks of L_s = K/Q_s points and stride S_s = L_s/R_s.
-struct FftPlanDev {
+struct alignas(16) FftPlanDev {
   int K;
   int nst;
   int radix[QEQ_MAX_STAGES];
@@ -93,8 +94,31 @@ struct FftPlanDev {
   FastDiv fS[QEQ_MAX_STAGES];   // S_s
   FastDiv fK;                   // K
   int tw_off;   // offset of exp(-2 pi i m / K), m < K, in the twiddle tables (even)
-  int tab_off;  // int tables: blk[K/R_{m-1}] at tab_off, freq[K] at +K, pos[K] at +2K
+  int tab_off;  // int tables, K4 = K rounded up to 4: blk[K/R_{m-1}] at tab_off, freq[K] at +K4, pos[K] at +2 K4
 };
+static_assert(sizeof(FftPlanDev) % 16 == 0, "FFT plans are bulk-copied");
+
+// One buffer of the FFT passes' shared-memory pipeline (fft.cuh): the unit's FFT plan,
+// its twiddles (even count), ntab int tables of K4 entries, `extra` bytes of per-unit
+// tables, and the line tile.  Offsets in bytes from the buffer start.
+struct FftBuf {
+  int tw, tab, extra, tile, bytes;
+};
+__host__ __device__ inline int fft_align(int x, int a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline FftBuf fft_buf(int Kmax, int ldmax, int lines, int elem, int ntab, int extra) {
+  FftBuf b;
+  b.tw = fft_align((int)sizeof(FftPlanDev), 16);
+  b.tab = b.tw + (Kmax + (Kmax & 1)) * elem;
+  b.extra = b.tab + ntab * ((Kmax + 3) & ~3) * 4;
+  b.tile = fft_align(b.extra + extra, 128);
+  b.bytes = fft_align(b.tile + lines * ldmax * elem, 128);
+  return b;
+}
+// per-unit tables of the x pass: input and output line offsets of 2 hx sub slots, 4 line
+// constants per pair
+__host__ __device__ inline int fft_x_extra(int sub, int hx, int real) {
+  return 2 * 2 * hx * sub * 8 + sub * 4 * real;
+}
 
 // Per-structure scalars of the PCG (device resident).
 struct PcgScalars {
@@ -182,6 +206,15 @@ struct qeq_plan_s {
   int max_ncm = 1;                 // largest complex-mesh count of any structure
   FftGeom geo;                     // tile sizes of the FFT passes of the matvec mesh
   FftGeom pgeo;                    // ... of the preconditioner mesh
+  int num_sms = 148;
+  struct OccEntry {
+    const void* fn;
+    size_t smem;
+    int blocks;
+  } occ[24];                       // resident CTAs per SM of the persistent FFT kernels (no heap)
+  int n_occ = 0;
+  int fft_kmax[3] = {1, 1, 1};     // largest mesh size per direction (matvec mesh)
+  int pfft_kmax[3] = {1, 1, 1};    // ... (preconditioner mesh)
   int4* d_zitems = nullptr;        // z passes {s, c, x, y0}
   int4* d_yitems = nullptr;        // forward y pass {s, c, z, x0}
   int4* d_yiitems = nullptr;       // inverse y pass {s, c, x, z0}
@@ -253,15 +286,15 @@ struct qeq_plan_s {
   int graph_iter_k = 0;
 };
 
-inline int fft_is_radix(int r) {
-  return r == 2 || r == 3 || r == 4 || r == 5 || r == 6 || r == 8 || r == 9 || r == 10 || r == 12 || r == 15 ||
-         r == 16;
-}
+// Register butterflies: FP32 stages use radices up to 24 (larger ones spill at the
+// 128-register budget of two 256-thread CTAs per SM), FP64 stages up to 16.
+#define QEQ_MAXR32 24
+#define QEQ_MAXR64 16
 
-// depth-first search of fft_radices: ordered factorisations of rem into register radices,
-// no deeper than the best found so far
-inline void fft_radices_search(int rem, int d, int* cur, int* best, int& nbest) {
-  static const int kR[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+// depth-first search of fft_radices: ordered factorisations of rem into register radices
+// no larger than maxR, no deeper than the best found so far
+inline void fft_radices_search(int rem, int d, int* cur, int* best, int& nbest, int maxR) {
+  static const int kR[] = {24, 20, 18, 16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
   if (rem == 1) {
     if (d == 0) return;
     bool take = nbest < 0 || d < nbest;
@@ -285,30 +318,31 @@ inline void fft_radices_search(int rem, int d, int* cur, int* best, int& nbest) 
   }
   if (d >= QEQ_MAX_STAGES || (nbest >= 0 && d >= nbest)) return;
   for (int r : kR)
-    if (rem % r == 0) {
+    if (r <= maxR && rem % r == 0) {
       cur[d] = r;
-      fft_radices_search(rem / r, d + 1, cur, best, nbest);
+      fft_radices_search(rem / r, d + 1, cur, best, nbest, maxR);
     }
 }
 
 // Radices of the FFT stages of length K (K = 2^a 3^b 5^c): the ordered factorisation
-// into register butterflies (2-16) with the fewest stages; among those an odd last
+// into register butterflies (2 ... maxR) with the fewest stages; among those an odd last
 // radix (its contiguous shared-memory reads spread over the banks), then the
 // lexicographically largest.  Returns the number of stages, -1 if none.
-inline int fft_radices(int K, int* out) {
+inline int fft_radices(int K, int* out, int maxR) {
   int best[QEQ_MAX_STAGES] = {0}, cur[QEQ_MAX_STAGES] = {0}, nbest = -1;
   if (K < 2) return -1;
-  fft_radices_search(K, 0, cur, best, nbest);
+  fft_radices_search(K, 0, cur, best, nbest, maxR);
   for (int i = 0; i < nbest; ++i) out[i] = best[i];
   return nbest;
 }
 
-// Stage constants, twiddles (K entries each, from tw_off) and the int tables (3K entries
-// from tab_off: block offset of each natural base u, frequency of each block-order
-// position, block-order position of each frequency) of one FFT length.
-inline bool fft_plan_fill(int K, FftPlanDev& f, double2* tw64, float2* tw32, int* tab) {
+// Stage constants, twiddles (K entries each, from tw_off) and the int tables (3 K4
+// entries, K4 = K rounded up to 4, from tab_off: block offset of each natural base u,
+// frequency of each block-order position, block-order position of each frequency) of
+// one FFT length.
+inline bool fft_plan_fill(int K, FftPlanDev& f, double2* tw64, float2* tw32, int* tab, int maxR) {
   f.K = K;
-  f.nst = fft_radices(K, f.radix);
+  f.nst = fft_radices(K, f.radix, maxR);
   if (f.nst < 1) return false;
   int Q = 1;
   for (int s = 0; s < f.nst; ++s) {
@@ -335,8 +369,9 @@ inline bool fft_plan_fill(int K, FftPlanDev& f, double2* tw64, float2* tw32, int
       p += f.S[s] * k[s];
       fq += f.Q[s] * k[s];
     }
-    tab[K + p] = fq;
-    tab[2 * K + fq] = p;
+    const int K4 = (K + 3) & ~3;
+    tab[K4 + p] = fq;
+    tab[2 * K4 + fq] = p;
     if (k[m - 1] == 0) tab[fq] = p;  // natural base u = fq (last digit 0) -> its block's offset
     for (int s = 0; s < m; ++s) {   // next tuple, digit 0 fastest
       if (++k[s] < f.radix[s]) break;
@@ -365,8 +400,8 @@ inline int fft_ld32(int K) {
 inline int fft_ld64(int K) { return K | 1; }
 
 // Tile sizes for meshes whose largest sizes per direction are maxK[3] (most complex
-// meshes max_ncm): item lines of the y/z passes (16 FP32 lines in at most ~64 KB) and of
-// the x pass (2 max_ncm lines per pair); FP64 sub-tiles hold half as many lines.
+// meshes max_ncm): item lines of the y/z passes and of the x pass (2 max_ncm lines per
+// pair); FP64 sub-tiles hold half as many lines (the same bytes).
 inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   FftGeom g;
   g.max_ncm = max_ncm;
@@ -376,27 +411,20 @@ inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   g.ldy64 = fft_ld64(maxK[1]);
   g.ldx32 = fft_ld32(maxK[0]);
   g.ldx64 = fft_ld64(maxK[0]);
+  // two buffers per CTA and two CTAs per SM: about 36 KB of lines per buffer
   const int ldyz = std::max(g.ldz32, g.ldy32);
-  const int64_t budget = 64 * 1024;
-  int tl = 16;
+  const int64_t budget = 36 * 1024;
+  int tl = 8;
   while (tl > 1 && (int64_t)tl * ldyz * 8 > budget) tl >>= 1;
   g.tl = tl;
   g.sub32 = tl;
   g.sub64 = std::max(1, tl / 2);
-  int tlx = 8;
+  int tlx = 4;
   while (tlx > 1 && (int64_t)2 * max_ncm * tlx * g.ldx32 * 8 > budget) tlx >>= 1;
   g.tlx = tlx;
   g.subx32 = tlx;
   g.subx64 = std::max(1, tlx / 2);
   return g;
-}
-
-// Dynamic shared memory of the passes (must match the kernels' carving in fft.cuh).
-inline size_t fft_tile_smem(int sub, int ld, size_t elem) { return 128 + (size_t)sub * ld * elem; }
-inline size_t fft_x_smem(int sub, int ld, size_t elem, int maxs_half, size_t real) {
-  size_t hdr = 128 + 2 * 2 * (size_t)maxs_half * sub * sizeof(int64_t) + (size_t)sub * 4 * real;
-  hdr = (hdr + 127) & ~(size_t)127;
-  return hdr + 2 * (size_t)maxs_half * sub * ld * elem;
 }
 
 // Work lists of the FFT passes of one structure (shared by qeq_plan_create and the

@@ -46,10 +46,10 @@ constexpr int kSM = QEQ_STATIC_MAX_MESH;
 constexpr int kSNcm = QEQ_STATIC_MAX_SPECIES / 2;
 struct Staging {
   StructDev st;
-  FftPlanDev fft[3];
-  double2 tw64[3 * kSM];
-  float2 tw32[3 * kSM];
-  int tabs[3 * 3 * kSM];
+  FftPlanDev fft[6];       // per direction: FP32 stages, then FP64 stages
+  double2 tw64[6 * kSM];
+  float2 tw32[6 * kSM];
+  int tabs[6 * 3 * kSM];
   double bmod[3 * kSM];
   float bmod32[3 * kSM];
   int4 zit[kSM * kSM * kSNcm];
@@ -69,8 +69,8 @@ constexpr size_t kStaticWorstCase() {
   const size_t N = QEQ_STATIC_MAX_ATOMS, M = (size_t)kSM * kSM * kSM, cap = QEQ_STATIC_MAX_PAIRS;
   const size_t nbins = (kSM / QEQ_BIN) * (kSM / QEQ_BIN) * (kSM / QEQ_BIN);
   const size_t nch = (N + QEQ_CHUNK - 1) / QEQ_CHUNK;
-  return carve_bytes(1, sizeof(StructDev)) + carve_bytes(3, sizeof(FftPlanDev)) + carve_bytes(3 * kSM, 16) +
-         carve_bytes(3 * kSM, 8) + carve_bytes(9 * kSM, 4) + carve_bytes(3 * kSM, 8) + carve_bytes(3 * kSM, 4) +
+  return carve_bytes(1, sizeof(StructDev)) + carve_bytes(6, sizeof(FftPlanDev)) + carve_bytes(6 * kSM, 16) +
+         carve_bytes(6 * kSM, 8) + carve_bytes(18 * kSM, 4) + carve_bytes(3 * kSM, 8) + carve_bytes(3 * kSM, 4) +
          3 * carve_bytes((size_t)kSM * kSM * kSNcm, 16) + carve_bytes((kSM / 2 + 1) * kSM, 16) +
          carve_bytes(nbins, 4) + carve_bytes(nbins, 4) + carve_bytes(N, 4) + carve_bytes(nch, sizeof(Chunk)) +
          carve_bytes(N, 4) + 3 * carve_bytes(nbins + 1, 4) + carve_bytes(N, 4) + carve_bytes(N / 1024 + 8, 8) +
@@ -294,7 +294,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     int K = Kb[d];
     T.K[d] = K;
     T.nb[d] = (K + QEQ_BIN - 1) / QEQ_BIN;
-    T.nbr[d] = (K + QEQ_BRICK - 1) / QEQ_BRICK;
+    T.nbr[d] = (K + (d == 2 ? QEQ_BRICK_Z : QEQ_BRICK_XY) - 1) / (d == 2 ? QEQ_BRICK_Z : QEQ_BRICK_XY);
     double l = r_cut / wd[d] * K / QEQ_BIN;
     int R = (int)ceil(l + 1.0 / QEQ_BIN) + ((K % QEQ_BIN) ? 1 : 0);
     T.rs_range[d] = std::max(1, R);
@@ -310,12 +310,16 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   bspline_int_s(T.p, Mp);
   for (int d = 0; d < 3; ++d) {
     const int K = T.K[d];
-    FftPlanDev& f = G.fft[d];
-    memset(&f, 0, sizeof(f));
-    f.tw_off = d * kSM;
-    f.tab_off = d * 3 * kSM;
-    if (!fft_plan_fill(K, f, G.tw64 + f.tw_off, G.tw32 + f.tw_off, G.tabs + f.tab_off)) return QEQ_ERR_INVALID;
-    T.fft_plan[d] = d;
+    for (int h = 0; h < 2; ++h) {
+      FftPlanDev& f = G.fft[2 * d + h];
+      memset(&f, 0, sizeof(f));
+      f.tw_off = (2 * d + h) * kSM;
+      f.tab_off = (2 * d + h) * 3 * kSM;
+      if (!fft_plan_fill(K, f, G.tw64 + f.tw_off, G.tw32 + f.tw_off, G.tabs + f.tab_off,
+                         h ? QEQ_MAXR64 : QEQ_MAXR32))
+        return QEQ_ERR_INVALID;
+    }
+    T.fft_plan[d] = 2 * d;
     T.bmod_off[d] = d * kSM;
     for (int m = 0; m < K; ++m) {
       double re = 0.0, im = 0.0;
@@ -365,6 +369,8 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.max_p = T.p;
   P.max_ncm = T.ncm;
   P.geo = geo;
+  for (int d = 0; d < 3; ++d) P.fft_kmax[d] = T.K[d];
+  if (cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEQ_ERR_CUDA;
   P.total_bins = nbins;
   P.total_bricks = nbricks;
   P.total_mesh = T.Mp * T.ncm;
@@ -379,10 +385,10 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   Carver cv{reinterpret_cast<unsigned char*>(g_scratch_dev[dev]), 0, (size_t)QEQ_STATIC_SCRATCH_BYTES};
   const int N = n_atoms;
   P.d_st = cv.take<StructDev>(1);
-  P.d_fft = cv.take<FftPlanDev>(3);
-  P.d_tw64 = cv.take<double2>(3 * kSM);
-  P.d_tw32 = cv.take<float2>(3 * kSM);
-  P.d_fft_tabs = cv.take<int>(3 * 3 * kSM);
+  P.d_fft = cv.take<FftPlanDev>(6);
+  P.d_tw64 = cv.take<double2>(6 * kSM);
+  P.d_tw32 = cv.take<float2>(6 * kSM);
+  P.d_fft_tabs = cv.take<int>(6 * 3 * kSM);
   P.d_bmod = cv.take<double>(3 * kSM);
   P.d_bmod32 = cv.take<float>(3 * kSM);
   P.d_zitems = cv.take<int4>(nz);

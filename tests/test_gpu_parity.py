@@ -266,3 +266,26 @@ def test_mixed_final_check_bounds_the_fp64_residual():
     pinf = np.abs(r - r.mean()).max()
     assert pinf <= 0.5 * 1e-5 * st.J.min(), pinf
     assert np.abs(q.cpu().numpy() - rd.q.cpu().numpy()).max() < 1e-5
+
+
+def test_bounded_wait_that_runs_out_returns_timeout_and_the_gpu_keeps_working():
+    """QEQ_FLAG_TEST_STALL makes the first tile of every x FFT pass announce 16 more bytes on
+    its copy barrier than its bulk copies deliver: that wait runs out after its bound (0.5 s
+    of the GPU's global timer), the kernel flags it and returns, the PCG stops, and the solve
+    reports QEQ_ERR_TIMEOUT.  No fault: the copies themselves complete, and a new plan on the
+    same GPU solves correctly afterwards."""
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(1)
+    args = qeq.pack([st])
+    bad = _plan([st], ewald_tol=1e-7, r_cut=9.0, test_stall=True)
+    with pytest.raises(qeq.QEqError) as e:
+        bad.solve(*args)
+    assert e.value.status == qeq.QEQ_ERR_TIMEOUT
+    bad.close()
+    good = _plan([st], ewald_tol=1e-7, r_cut=9.0)
+    res = good.solve(*args)
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=KE)
+    q_ref, _ = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+    assert res.info[0]["status"] == 0
+    assert np.abs(res.q.cpu().numpy() - q_ref).max() < 1e-5
+    good.close()
