@@ -198,7 +198,8 @@ static void free_plan(qeq_plan_s* P) {
   if (P->d_feat) cudaFree(P->d_feat);
   if (P->d_pred) cudaFree(P->d_pred);
   if (P->ev_done) cudaEventDestroy(P->ev_done);
-  if (P->graph_iter) cudaGraphExecDestroy(P->graph_iter);
+  if (P->graph_solve) cudaGraphExecDestroy(P->graph_solve);
+  if (P->d_ctl) cudaFree(P->d_ctl);
 }
 
 extern "C" const char* qeq_status_str(qeq_status s) {
@@ -632,6 +633,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(cudaMemset(P->d_err, 0, sizeof(int) * 4));
   ALLOC(dalloc(P, &P->d_done, 4));
   ALLOC(dalloc(P, &P->d_reject, ns));
+  ALLOC(dalloc(P, &P->d_ctl, 1));
   ALLOC(cudaMemset(P->d_reject, 0, sizeof(int) * ns));
   ALLOC(cudaHostAlloc((void**)&P->h_done, sizeof(int) * 8, cudaHostAllocDefault));
   ALLOC(cudaEventCreateWithFlags(&P->ev_done, cudaEventDisableTiming));

@@ -152,6 +152,14 @@ struct PcgScalars {
   int pad_;
 };
 
+// Loop counters of the device-paced solve graph (device resident).
+struct LoopCtl {
+  int outer;          // PCG rounds done in this solve (a round ends with a final check)
+  int replays_round;  // replays of the 4-iteration body in this round
+  int replays_total;  // ... in this solve
+  int pad_;
+};
+
 // Atom-chunk for reductions: one CTA, atoms [begin, end) of one structure.
 struct Chunk {
   int s;
@@ -279,11 +287,13 @@ struct qeq_plan_s {
   float* d_feat = nullptr;         // descriptors, sorted order
   float* d_pred = nullptr;         // network output, sorted order
   int64_t launches = 0;            // kernels launched by this plan (graph replays count their kernels)
-  int64_t graph_kernels = 0;       // kernels inside the captured iteration graph
+  int64_t graph_kernels = 0;       // kernels counted while capturing a graph segment
   bool capturing = false;
-  cudaGraphExec_t graph_iter = nullptr;
-  int graph_iter_prec = -1;
-  int graph_iter_k = 0;
+  // device-paced solve: one graph per precision holding every PCG round (see solve.cu)
+  cudaGraphExec_t graph_solve = nullptr;
+  int graph_solve_prec = -1;
+  int64_t gk_inner = 0, gk_round = 0;  // kernels per inner body replay / per round outside it
+  struct LoopCtl* d_ctl = nullptr;     // device loop counters of the solve graph
 };
 
 // Register butterflies: FP32 stages use radices up to 24 (larger ones spill at the

@@ -384,6 +384,85 @@ __global__ void k_after_check(PcgScalars* __restrict__ sc, int ns, int max_resta
   if (threadIdx.x == 0) *done = any ? 0 : 1;
 }
 
+// ---------------------------------------------------------------- device-paced solve graph
+// The conditions of the graph's WHILE / IF nodes are set on the device from the
+// per-structure state, by thread 0 only (one writer per handle).
+
+// start of a round: reset the round's replay count; iterate while some structure is active
+__global__ void k_round_begin(LoopCtl* __restrict__ ctl, const PcgScalars* __restrict__ sc, int ns,
+                              const int* __restrict__ err, cudaGraphConditionalHandle h_inner) {
+  __shared__ int any;
+  const bool stop = (*((volatile const int*)err) & ERRBIT_TIMEOUT) != 0;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < ns; s += blockDim.x)
+    if (sc[s].active) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->replays_round = 0;
+    cudaGraphSetConditional(h_inner, (any && !stop) ? 1u : 0u);
+  }
+}
+
+// end of a block of iterations: continue while some structure is active, no device wait
+// ran out, and the round has not used its replays (a second guard besides max_iter)
+__global__ void k_inner_cond(PcgScalars* __restrict__ sc, int ns, const int* __restrict__ err,
+                             LoopCtl* __restrict__ ctl, int cap, cudaGraphConditionalHandle h_inner) {
+  __shared__ int any;
+  const bool stop = (*((volatile const int*)err) & ERRBIT_TIMEOUT) != 0;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    if (stop) sc[s].active = 0;
+    if (sc[s].active) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->replays_round += 1;
+    ctl->replays_total += 1;
+    cudaGraphSetConditional(h_inner, (any && ctl->replays_round < cap) ? 1u : 0u);
+  }
+}
+
+// mixed precision: the rounds after the first FP64 check and before the last allowed
+// restart check from the FP64 residual plus the FP32 product of the change (IF branch);
+// the others run the full FP64 check (ELSE branch)
+__global__ void k_choose_check(const LoopCtl* __restrict__ ctl, int max_restarts, cudaGraphConditionalHandle h_check) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h_check, (ctl->outer > 0 && ctl->outer < max_restarts) ? 1u : 0u);
+}
+
+// after a final check: restart the failing structures (bounded), settle the rest; another
+// round while some structure restarts
+__global__ void k_round_end(PcgScalars* __restrict__ sc, int ns, int max_restarts, int max_iter,
+                            const int* __restrict__ err, LoopCtl* __restrict__ ctl, cudaGraphConditionalHandle h_outer) {
+  __shared__ int any;
+  const bool stop = (*((volatile const int*)err) & ERRBIT_TIMEOUT) != 0;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    PcgScalars& c = sc[s];
+    if (stop) {
+      c.status = QEQ_ERR_TIMEOUT;
+      c.active = 0;
+    } else if (c.converged) {
+      c.status = QEQ_OK;
+      c.active = 0;
+    } else if (c.restarts < max_restarts && c.iters < max_iter) {
+      c.restarts += 1;
+      c.active = 1;
+      any = 1;
+    } else {
+      c.status = QEQ_ERR_NOCONV;
+      c.active = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->outer += 1;
+    cudaGraphSetConditional(h_outer, (any && ctl->outer <= max_restarts + 1) ? 1u : 0u);
+  }
+}
+
 __global__ void k_energy(const Chunk* __restrict__ chunks, const double* __restrict__ q, const double* __restrict__ Aq,
                          const double* __restrict__ chi, const double* __restrict__ J, PcgScalars* __restrict__ sc,
                          double* part, int* counter) {
@@ -463,6 +542,7 @@ __global__ void k_write_mu(const PcgScalars* __restrict__ sc, int ns, double* __
 // ------------------------------------------------------------------ host orchestration
 qeq_status cuda_fail(qeq_plan_s* P, cudaError_t e, const char* where) {
   P->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // the error is reported here; do not leave it to the caller's next CUDA call
   return QEQ_ERR_CUDA;
 }
 
@@ -512,49 +592,190 @@ cudaError_t one_iteration(qeq_plan_s* P, int prec) {
 }
 
 const int kItersPerCheck = 4;
+const int kMaxRestarts = 4;  // residual replacements after a failed final check
 // mixed precision: the iterations stop at this fraction of the final check's thresholds
 const double kMixedInnerTol = 0.5;
 // bound on the relative error of the FP32 operator, against max|A x| + max D max|x|
 // (measured errors are below 1e-5 of that scale; 1e-4 leaves a margin of ten)
 const double kMixedOpErr = 1e-4;
 
+// host-paced iterations (QEQ_FLAG_NO_GRAPH or the legacy stream): a block of iterations,
+// then the host reads whether any structure is still active
 cudaError_t run_iterations(qeq_plan_s* P, int prec) {
   cudaStream_t s = P->stream;
-  if (P->graph_ok) {
-    if (!P->graph_iter || P->graph_iter_prec != prec) {
-      if (P->graph_iter) {
-        cudaGraphExecDestroy(P->graph_iter);
-        P->graph_iter = nullptr;
-      }
-      cudaGraph_t g;
-      QEQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      P->capturing = true;
-      P->graph_kernels = 0;
-      cudaError_t e = cudaSuccess;
-      for (int k = 0; k < kItersPerCheck && e == cudaSuccess; ++k) e = one_iteration(P, prec);
-      if (e == cudaSuccess) {
-        count_launch(P);
-        k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_err, P->d_done);
-        e = cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s);
-      }
-      cudaError_t e2 = cudaStreamEndCapture(s, &g);
-      P->capturing = false;
-      if (e != cudaSuccess) return e;
-      QEQ_CUDA_TRY(e2);
-      e = cudaGraphInstantiate(&P->graph_iter, g, 0);
-      cudaGraphDestroy(g);
-      QEQ_CUDA_TRY(e);
-      P->graph_iter_prec = prec;
-    }
-    QEQ_CUDA_TRY(cudaGraphLaunch(P->graph_iter, s));
-    P->launches += P->graph_kernels;
-  } else {
-    for (int k = 0; k < kItersPerCheck; ++k) QEQ_CUDA_TRY(one_iteration(P, prec));
-    count_launch(P);
-    k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_err, P->d_done);
-    QEQ_CUDA_TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
-  }
+  for (int k = 0; k < kItersPerCheck; ++k) QEQ_CUDA_TRY(one_iteration(P, prec));
+  count_launch(P);
+  k_done<<<1, 256, 0, s>>>(P->d_sc, P->n_struct, P->d_err, P->d_done);
+  QEQ_CUDA_TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
   return cudaStreamSynchronize(s);
+}
+
+// the final check of a round (full FP64 residual, or in mixed precision the change-based one)
+cudaError_t final_check(qeq_plan_s* P, int prec, bool use_delta) {
+  cudaStream_t s = P->stream;
+  const int nc = P->n_chunks, max_iter = P->desc.max_iter;
+  const int nbv = (int)((P->n_atoms + 255) / 256);
+  if (use_delta) {
+    count_launch(P, 2);
+    k_delta<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_q1, P->d_dinv, P->d_x, P->d_sc, red_part(P),
+                               red_counter(P));
+    QEQ_CUDA_TRY(launch_matvec(P, QEQ_MIXED, P->d_x, P->d_Ap, 1, 0, 0, nullptr));
+    k_resid_delta<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_r1, P->d_Ap, P->d_dinv, P->d_r, P->d_sc,
+                                     red_part(P), red_counter(P), max_iter, kMixedOpErr);
+  } else {
+    QEQ_CUDA_TRY(launch_matvec(P, QEQ_FP64, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
+    count_launch(P);
+    k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
+                               red_counter(P), max_iter);
+    if (prec == QEQ_MIXED) {
+      count_launch(P);
+      k_copy2<<<nbv, 256, 0, s>>>(P->d_q, P->d_r, P->n_atoms, P->d_q1, P->d_r1);
+    }
+  }
+  return cudaGetLastError();
+}
+
+// Capture the kernels `launch` enqueues into graph g after the nodes deps; deps becomes
+// the captured segment's last nodes.  Returns the segment's kernel count in *nk.
+template <class F>
+cudaError_t capture_segment(qeq_plan_s* P, cudaGraph_t g, std::vector<cudaGraphNode_t>& deps, int64_t* nk,
+                            F&& launch) {
+  cudaStream_t s = P->stream;
+  QEQ_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                             cudaStreamCaptureModeThreadLocal));
+  P->capturing = true;
+  P->graph_kernels = 0;
+  cudaError_t e = launch();
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* d = nullptr;
+  size_t n = 0;
+  cudaError_t e2 = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &d, nullptr, &n);
+  std::vector<cudaGraphNode_t> last(d, d + n);
+  cudaGraph_t out = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(s, &out);
+  P->capturing = false;
+  if (nk) *nk += P->graph_kernels;
+  QEQ_CUDA_TRY(e);
+  QEQ_CUDA_TRY(e2);
+  QEQ_CUDA_TRY(e3);
+  deps = last;
+  return cudaSuccess;
+}
+
+// a conditional node after deps; its body graphs in bodies[0 .. size)
+cudaError_t add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, unsigned size, cudaGraph_t* bodies) {
+  // the parameter block is a union (no default constructor): zeroed raw storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& prm = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = size;
+  cudaGraphNode_t node;
+  QEQ_CUDA_TRY(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &prm));
+  for (unsigned i = 0; i < size; ++i) bodies[i] = prm.conditional.phGraph_out[i];
+  deps.assign(1, node);
+  return cudaSuccess;
+}
+
+// The whole PCG of a solve as one graph, paced on the device:
+//   WHILE round:                       (h_outer, set by k_round_end)
+//     k_round_begin
+//     WHILE block:                     (h_inner, set by k_round_begin / k_inner_cond)
+//       4 PCG iterations, k_inner_cond
+//     mixed: IF change-based check ELSE FP64 check   (h_check, set by k_choose_check)
+//     FP64:  FP64 check
+//     k_round_end, preconditioned restart direction
+// The host launches it once and reads the per-structure results once.
+cudaError_t build_solve_graph(qeq_plan_s* P, int prec) {
+  if (P->graph_solve) {
+    cudaGraphExecDestroy(P->graph_solve);
+    P->graph_solve = nullptr;
+  }
+  cudaStream_t s = P->stream;
+  const int ns = P->n_struct, nc = P->n_chunks, max_iter = P->desc.max_iter;
+  const int max_restarts = kMaxRestarts;
+  const int cap = max_iter / kItersPerCheck + 2;
+  cudaGraph_t root = nullptr;
+  QEQ_CUDA_TRY(cudaGraphCreate(&root, 0));
+  cudaError_t e = cudaSuccess;
+  P->gk_inner = 0;
+  P->gk_round = 0;
+  do {
+    cudaGraphConditionalHandle h_outer, h_inner, h_check;
+    if ((e = cudaGraphConditionalHandleCreate(&h_outer, root, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    std::vector<cudaGraphNode_t> deps;
+    if ((e = capture_segment(P, root, deps, nullptr, [&]() {
+           return cudaMemsetAsync(P->d_ctl, 0, sizeof(LoopCtl), s);
+         })) != cudaSuccess)
+      break;
+    cudaGraph_t body_round;
+    if ((e = add_conditional(root, deps, h_outer, cudaGraphCondTypeWhile, 1, &body_round)) != cudaSuccess) break;
+    if ((e = cudaGraphConditionalHandleCreate(&h_inner, body_round, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+      break;
+    std::vector<cudaGraphNode_t> rd;
+    if ((e = capture_segment(P, body_round, rd, &P->gk_round, [&]() {
+           count_launch(P);
+           k_round_begin<<<1, 256, 0, s>>>(P->d_ctl, P->d_sc, ns, P->d_err, h_inner);
+           return cudaGetLastError();
+         })) != cudaSuccess)
+      break;
+    cudaGraph_t body_block;
+    if ((e = add_conditional(body_round, rd, h_inner, cudaGraphCondTypeWhile, 1, &body_block)) != cudaSuccess) break;
+    {
+      std::vector<cudaGraphNode_t> bd;
+      if ((e = capture_segment(P, body_block, bd, &P->gk_inner, [&]() {
+             for (int k = 0; k < kItersPerCheck; ++k) QEQ_CUDA_TRY(one_iteration(P, prec));
+             count_launch(P);
+             k_inner_cond<<<1, 256, 0, s>>>(P->d_sc, ns, P->d_err, P->d_ctl, cap, h_inner);
+             return cudaGetLastError();
+           })) != cudaSuccess)
+        break;
+    }
+    if (prec == QEQ_MIXED) {
+      // (a handle no conditional node uses makes the instantiation fail: created only here)
+      if ((e = cudaGraphConditionalHandleCreate(&h_check, body_round, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        break;
+      if ((e = capture_segment(P, body_round, rd, &P->gk_round, [&]() {
+             count_launch(P);
+             k_choose_check<<<1, 32, 0, s>>>(P->d_ctl, max_restarts, h_check);
+             return cudaGetLastError();
+           })) != cudaSuccess)
+        break;
+      cudaGraph_t branch[2];
+      if ((e = add_conditional(body_round, rd, h_check, cudaGraphCondTypeIf, 2, branch)) != cudaSuccess) break;
+      std::vector<cudaGraphNode_t> b0, b1;
+      int64_t k0 = 0, k1 = 0;
+      if ((e = capture_segment(P, branch[0], b0, &k0, [&]() { return final_check(P, prec, true); })) != cudaSuccess)
+        break;
+      if ((e = capture_segment(P, branch[1], b1, &k1, [&]() { return final_check(P, prec, false); })) != cudaSuccess)
+        break;
+      P->gk_round += std::max(k0, k1);
+    } else {
+      if ((e = capture_segment(P, body_round, rd, &P->gk_round, [&]() { return final_check(P, prec, false); })) !=
+          cudaSuccess)
+        break;
+    }
+    if ((e = capture_segment(P, body_round, rd, &P->gk_round, [&]() {
+           count_launch(P);
+           k_round_end<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_err, P->d_ctl, h_outer);
+           QEQ_CUDA_TRY(precondition(P, 1, 1));
+           count_launch(P);
+           k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
+           return cudaGetLastError();
+         })) != cudaSuccess)
+      break;
+    e = cudaGraphInstantiate(&P->graph_solve, root, 0);
+  } while (false);
+  cudaGraphDestroy(root);
+  if (e != cudaSuccess) {
+    P->graph_solve = nullptr;
+    return e;
+  }
+  P->graph_solve_prec = prec;
+  return cudaSuccess;
 }
 
 qeq_status check_inputs(qeq_plan_s* P) {
@@ -729,44 +950,31 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
   count_launch(P);
   k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
   TRY(cudaGetLastError());
-  const int max_restarts = 4;
-  for (int outer = 0; outer <= max_restarts + 1; ++outer) {
-    // inner iterations (structures drop out as they converge); the device
-    // stops every structure at max_iter, the host bound is a second guard
-    const int max_launches = max_iter / kItersPerCheck + 2;
-    for (int l = 0; l < max_launches; ++l) {
-      TRY(run_iterations(P, prec));
+  const int max_restarts = kMaxRestarts;
+  if (P->graph_ok) {
+    // device-paced: every round of the PCG in one graph launch
+    if (!P->graph_solve || P->graph_solve_prec != prec) TRY(build_solve_graph(P, prec));
+    TRY(cudaGraphLaunch(P->graph_solve, s));
+  } else {
+    for (int outer = 0; outer <= max_restarts + 1; ++outer) {
+      // inner iterations (structures drop out as they converge); the device stops every
+      // structure at max_iter, the host bound is a second guard
+      const int max_launches = max_iter / kItersPerCheck + 2;
+      for (int l = 0; l < max_launches; ++l) {
+        TRY(run_iterations(P, prec));
+        if (P->h_done[0]) break;
+      }
+      TRY(final_check(P, prec, prec == QEQ_MIXED && outer > 0 && outer < max_restarts));
+      count_launch(P);
+      k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_err, P->d_done);
+      TRY(precondition(P, 1, 1));
+      count_launch(P);
+      k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
+      TRY(cudaGetLastError());
+      TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRY(cudaStreamSynchronize(s));
       if (P->h_done[0]) break;
     }
-    const int nbv = (int)((P->n_atoms + 255) / 256);
-    if (prec == QEQ_MIXED && outer > 0 && outer < max_restarts) {
-      // check from the last FP64 residual plus the FP32 product of the change since then
-      count_launch(P, 2);
-      k_delta<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_q1, P->d_dinv, P->d_x, P->d_sc, red_part(P),
-                                 red_counter(P));
-      TRY(launch_matvec(P, QEQ_MIXED, P->d_x, P->d_Ap, 1, 0, 0, nullptr));
-      k_resid_delta<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_r1, P->d_Ap, P->d_dinv, P->d_r, P->d_sc,
-                                       red_part(P), red_counter(P), max_iter, kMixedOpErr);
-    } else {
-      // final FP64 check: true residual of every structure
-      TRY(launch_matvec(P, QEQ_FP64, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
-      count_launch(P);
-      k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
-                                 red_counter(P), max_iter);
-      if (prec == QEQ_MIXED) {
-        count_launch(P);
-        k_copy2<<<nbv, 256, 0, s>>>(P->d_q, P->d_r, P->n_atoms, P->d_q1, P->d_r1);
-      }
-    }
-    count_launch(P);
-    k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_err, P->d_done);
-    TRY(precondition(P, 1, 1));
-    count_launch(P);
-    k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
-    TRY(cudaGetLastError());
-    TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TRY(cudaStreamSynchronize(s));
-    if (P->h_done[0]) break;
   }
   // energy terms from the final check's A q, outputs in input order
   count_launch(P);
@@ -778,8 +986,11 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
   k_write_mu<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, d_mu, nullptr, nullptr);
   TRY(cudaGetLastError());
   std::vector<PcgScalars> h(ns);
+  LoopCtl ctl;
   TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
+  if (P->graph_ok) TRY(cudaMemcpyAsync(&ctl, P->d_ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
+  if (P->graph_ok) P->launches += P->gk_inner * ctl.replays_total + P->gk_round * ctl.outer;
   qeq_status worst = QEQ_OK;
   for (int i = 0; i < ns; ++i) {
     const PcgScalars& c = h[i];

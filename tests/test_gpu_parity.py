@@ -289,3 +289,27 @@ def test_bounded_wait_that_runs_out_returns_timeout_and_the_gpu_keeps_working():
     assert res.info[0]["status"] == 0
     assert np.abs(res.q.cpu().numpy() - q_ref).max() < 1e-5
     good.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_paced_solve_graph_equals_host_loop(precision):
+    """The solve graph (WHILE over rounds, WHILE over 4-iteration blocks, IF between the
+    change-based and the FP64 final check, conditions set on the device) runs the same
+    kernels in the same order as the host-paced loop: identical charges, iteration and
+    restart counts, for a batch of uneven structures."""
+    from paper_2607_17978_b300 import qeq
+    structs = synth.batch_workload(5, n_min=64, n_max=700) + [synth.rocksalt(5, 5.64, 0.2, synth.rng_for(5, 9))]
+    if precision == "mixed":  # a cell whose mixed solve restarts, so both check branches run
+        structs = [synth.workload(2)] + structs[:2]
+    args = qeq.pack(structs)
+    pg = _plan(structs, precision=precision, preconditioner="fourier", ewald_tol=1e-6, r_cut=8.0)
+    ph = _plan(structs, precision=precision, preconditioner="fourier", ewald_tol=1e-6, r_cut=8.0, graph=False)
+    rg = pg.solve(*args)
+    rh = ph.solve(*args)
+    assert np.array_equal(rg.q.cpu().numpy(), rh.q.cpu().numpy())
+    for a, b in zip(rg.info, rh.info):
+        assert (a["iterations"], a["restarts"], a["status"]) == (b["iterations"], b["restarts"], b["status"])
+    assert any(i["restarts"] >= 1 for i in rg.info) or precision == "fp64"
+    # a second solve on the same instantiated graph
+    rg2 = pg.solve(*args)
+    assert np.array_equal(rg.q.cpu().numpy(), rg2.q.cpu().numpy())
