@@ -92,16 +92,24 @@ struct SpreadRecs {
   T wy[QEQ_SPB][P];
   unsigned mask[QEQ_SPB];    // x rows (bits 0-15) and y rows (bits 16-31) the stencil covers
   int off[QEQ_SPB];          // ox | oy << 10 | species part << 20
+  int atom[QEQ_SPB];         // staging: the candidate's atom (sorted index) ...
+  int oz[QEQ_SPB];           // ... its z stencil start relative to the brick
+  unsigned zm[QEQ_SPB];      // ... and the brick z positions it covers
 };
+
+// the brick's rows as they are written out: 256 rows of 16 z (one pad element per row)
+constexpr int kSpreadStageLd = QEQ_BRICK_Z + 1;
 
 template <typename T, int P>
 constexpr size_t spread_smem() {
-  return sizeof(SpreadRecs<T, P>);
+  const size_t rec = sizeof(SpreadRecs<T, P>);
+  const size_t stage = (size_t)QEQ_BRICK_XY * QEQ_BRICK_XY * kSpreadStageLd * 2 * sizeof(T);
+  return rec > stage ? rec : stage;
 }
 
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st, const int* __restrict__ brick_struct,
-                         const int* __restrict__ bin_start, const int* __restrict__ base,
+                         const int* __restrict__ brick_cand, const int* __restrict__ bin_start, const int* __restrict__ base,
                          const T* __restrict__ wts, const int* __restrict__ spec, const double* __restrict__ x,
                          const float* __restrict__ x32, const PcgScalars* __restrict__ sc, int use_active,
                          typename C2<T>::t* __restrict__ mesh) {
@@ -110,23 +118,19 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
   const int s = brick_struct[g];
   const StructDev& S = st[s];
   if (use_active && !sc[s].active) return;
-  const int tid = threadIdx.x, lx = tid >> 4, ly = tid & 15;
+  // warp w owns the brick rows x in [4 (w mod 4), +4), y in [8 (w / 4), +8)
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int lx = (w & 3) * 4 + (lane >> 3), ly = (w >> 2) * 8 + (lane & 7);
   const Brick B = brick_of(S, g);
   const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
   __shared__ int cand[3][8], ncand[3];
   __shared__ int bin_beg[512], bin_pre[513];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SpreadRecs<T, P>& R = *reinterpret_cast<SpreadRecs<T, P>*>(smem_raw);
-  if (tid < 3) {
-    int d = tid, nc = 0;
-    int span = min(B.ext[d] + P - 1, S.K[d]);
-    for (int k = 0; k < span; ++k) {
-      int bn = ((B.x0[d] + k) % S.K[d]) / QEQ_BIN;
-      bool seen = false;
-      for (int q = 0; q < nc; ++q) seen |= (cand[d][q] == bn);
-      if (!seen && nc < 8) cand[d][nc++] = bn;
-    }
-    ncand[d] = nc;
+  if (tid < QEQ_BRICK_CAND) {  // the brick's candidate bins per direction (plan table)
+    const int v = brick_cand[(size_t)g * QEQ_BRICK_CAND + tid];
+    if (tid < 3) ncand[tid] = v;
+    else if (tid >= 4) cand[(tid - 4) >> 3][(tid - 4) & 7] = v;
   }
   __syncthreads();
   // candidate bins (at most 8 x 8 x 8) in (i0, i1, i2) order and the prefix of their sizes
@@ -161,6 +165,7 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
     for (int c0 = 0; c0 < total; c0 += QEQ_SPB) {
       const int nbat = min(QEQ_SPB, total - c0);
       if (c0 > 0) __syncthreads();  // the previous batch is consumed
+      // staging, one thread per candidate: its atom, stencil starts and covered rows
       if (tid < nbat) {
         const int c = c0 + tid;
         int lo = 0, hi = nbins - 1;  // last bin whose first candidate is <= c
@@ -183,37 +188,46 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
             if (v < 0) v += S.K[d];
             o[d] = v;
           }
-          const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
           const unsigned xm = stencil_rows<P>(o[0], K0, B.ext[0]);
           const unsigned ym = stencil_rows<P>(o[1], K1, B.ext[1]);
           const unsigned zm = stencil_rows<P>(o[2], K2, B.ext[2]);
-#pragma unroll
-          for (int l = 0; l < QEQ_BRICK_Z; ++l) {
-            int j = l - o[2];
-            if (j < 0) j += K2;
-            if (j >= K2) j -= K2;
-            R.wz[tid][l] = ((zm >> l) & 1u) ? wt[2 * QEQ_MAXP + P - 1 - j] : (T)0;
-          }
-          const T q = xval<T>(x, x32, t);
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            R.wx[tid][j] = q * wt[P - 1 - j];
-            R.wy[tid][j] = wt[QEQ_MAXP + P - 1 - j];
-          }
           if (zm) mask = xm | (ym << 16);
           R.off[tid] = o[0] | (o[1] << 10) | ((sp & 1) << 20);
+          R.oz[tid] = o[2];
+          R.zm[tid] = zm;
         }
         R.mask[tid] = mask;
+        R.atom[tid] = t;
       }
       __syncthreads();
-      // every thread adds its row's share, atom after atom.  A warp owns the rows
-      // lx = 2w, 2w+1: it ballots the records whose stencil covers one of them
-      // (32 records per ballot) and visits only those, in record order.
-      const unsigned wsel = 3u << (2 * (tid >> 5));
-      const int lane = tid & 31;
+      // ... then every thread: the weights of the kept records, 32 values per record
+      for (int idx = tid; idx < nbat * 32; idx += blockDim.x) {
+        const int r = idx >> 5, k = idx & 31;
+        if (!R.mask[r]) continue;
+        const int t = R.atom[r];
+        const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
+        if (k < QEQ_BRICK_Z) {
+          int j = k - R.oz[r];
+          if (j < 0) j += K2;
+          if (j >= K2) j -= K2;
+          R.wz[r][k] = ((R.zm[r] >> k) & 1u) ? wt[2 * QEQ_MAXP + P - 1 - j] : (T)0;
+        } else if (k < QEQ_BRICK_Z + P) {
+          const int j = k - QEQ_BRICK_Z;
+          R.wx[r][j] = xval<T>(x, x32, t) * wt[P - 1 - j];
+        } else if (k >= QEQ_BRICK_Z + 8 && k < QEQ_BRICK_Z + 8 + P) {
+          const int j = k - QEQ_BRICK_Z - 8;
+          R.wy[r][j] = wt[QEQ_MAXP + P - 1 - j];
+        }
+      }
+      __syncthreads();
+      // every thread adds its row's share, atom after atom.  A warp ballots the records
+      // whose stencil covers one of its 4 x rows and one of its 8 y rows (32 records per
+      // ballot) and visits only those, in record order.
+      const unsigned xsel = 0xFu << (4 * (w & 3)), ysel = 0xFFu << (16 + 8 * (w >> 2));
       for (int i0 = 0; i0 < nbat; i0 += 32) {
         const int ii = i0 + lane;
-        unsigned bal = __ballot_sync(0xffffffffu, ii < nbat && (R.mask[ii] & wsel) != 0u);
+        const unsigned mm = ii < nbat ? R.mask[ii] : 0u;
+        unsigned bal = __ballot_sync(0xffffffffu, (mm & xsel) != 0u && (mm & ysel) != 0u);
         while (bal) {
           const int k = i0 + __ffs(bal) - 1;
           bal &= bal - 1u;
@@ -237,12 +251,25 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
       }
       __syncthreads();
     }
-    if (lx < B.ext[0] && ly < B.ext[1]) {
-      V* mg = mesh + S.mesh_off + (int64_t)cm * S.Mp +
-              ((int64_t)(B.x0[0] + lx) * K1 + (B.x0[1] + ly)) * S.P[2] + B.x0[2];
+    // write the brick through shared memory: a warp stores four whole rows (16 z points,
+    // contiguous in layout L0) per instruction instead of one point of 32 rows
+    __syncthreads();  // the records are consumed
+    {
+      V* stage = reinterpret_cast<V*>(smem_raw);
 #pragma unroll
-      for (int z = 0; z < QEQ_BRICK_Z; ++z)
-        if (z < B.ext[2]) mg[z] = V{re[z], im[z]};
+      for (int z = 0; z < QEQ_BRICK_Z; ++z) stage[(lx * QEQ_BRICK_XY + ly) * kSpreadStageLd + z] = V{re[z], im[z]};
+      __syncthreads();
+      const int zz = (lane & 7) * 2;
+      for (int row = (tid >> 5) * 4 + (lane >> 3); row < QEQ_BRICK_XY * QEQ_BRICK_XY; row += 32) {
+        const int rx = row >> 4, ry = row & 15;
+        if (rx < B.ext[0] && ry < B.ext[1]) {
+          V* mg = mesh + S.mesh_off + (int64_t)cm * S.Mp +
+                  ((int64_t)(B.x0[0] + rx) * K1 + (B.x0[1] + ry)) * S.P[2] + B.x0[2];
+          if (zz < B.ext[2]) mg[zz] = stage[row * kSpreadStageLd + zz];
+          if (zz + 1 < B.ext[2]) mg[zz + 1] = stage[row * kSpreadStageLd + zz + 1];
+        }
+      }
+      __syncthreads();  // the staging area is reused by the next complex mesh's records
     }
   }
 }
@@ -693,7 +720,7 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
   QEQ_CUDA_TRY(mark());
   // stage 1: spreading
   {
-    k_spread<T, P><<<Pl->total_bricks, 256, spread_smem<T, P>(), s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_bin_start, Pl->d_base, wts,
+    k_spread<T, P><<<Pl->total_bricks, 256, spread_smem<T, P>(), s>>>(Pl->d_st, Pl->d_brick_struct, Pl->d_brick_cand, Pl->d_bin_start, Pl->d_base, wts,
                                                       Pl->d_spec, x, x32, Pl->d_sc, use_active, mesh);
     QEQ_CUDA_TRY(cudaGetLastError());
   }

@@ -183,7 +183,7 @@ static qeq_status fail(qeq_plan_s* P, qeq_status st, const std::string& msg) {
 static void free_plan(qeq_plan_s* P) {
   if (!P) return;
   void* ptrs[] = {P->d_st,     P->d_fft,     P->d_tw64,    P->d_tw32,     P->d_bmod,    P->d_bmod32,
-                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_yiitems,  P->d_bin_struct, P->d_atom_struct, P->d_brick_struct,
+                  P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_yiitems,  P->d_bin_struct, P->d_atom_struct, P->d_brick_struct, P->d_brick_cand,
                   P->d_chunks, P->d_key,     P->d_bin_count, P->d_bin_start, P->d_bin_fill, P->d_perm,
                   P->d_scan_tmp, P->d_base,  P->d_wts,     P->d_wts32,    P->d_spec,    P->d_J,
                   P->d_chi,    P->d_dinv,    P->d_posc,    P->d_row,      P->d_row_cnt, P->d_col,
@@ -270,7 +270,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   std::vector<float> bmod32;
   std::vector<int> tabs;
   std::vector<int4> zit, yit, yiit, xit;
-  std::vector<int> bin_struct, brick_struct;
+  std::vector<int> bin_struct, brick_struct, brick_cand;
   std::vector<Chunk> chunks;
   int64_t mesh_off = 0;
   int bin_off = 0;
@@ -421,7 +421,13 @@ static qeq_status build_plan(qeq_plan_s* P) {
     for (int b = 0; b < nbins; ++b) bin_struct.push_back(s);
     bin_off += nbins;
     T.brick_off = (int)brick_struct.size();
-    for (int b = 0; b < T.nbr[0] * T.nbr[1] * T.nbr[2]; ++b) brick_struct.push_back(s);
+    for (int b = 0; b < T.nbr[0] * T.nbr[1] * T.nbr[2]; ++b) {
+      brick_struct.push_back(s);
+      const int bc[3] = {b / (T.nbr[2] * T.nbr[1]), (b / T.nbr[2]) % T.nbr[1], b % T.nbr[2]};
+      int c[QEQ_BRICK_CAND];
+      brick_candidates(T, pbest, bc, c);
+      brick_cand.insert(brick_cand.end(), c, c + QEQ_BRICK_CAND);
+    }
     for (int d = 0; d < 3; ++d) {
       T.fft_plan[d] = fft_plan_for(T.K[d]);
       if (T.fft_plan[d] < 0) return fail(P, QEQ_ERR_INVALID, "mesh size without an FFT plan");
@@ -593,6 +599,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(upload(P, &P->d_fft_tabs, tabs));
   ALLOC(upload(P, &P->d_bin_struct, bin_struct));
   ALLOC(upload(P, &P->d_brick_struct, brick_struct));
+  ALLOC(upload(P, &P->d_brick_cand, brick_cand));
   ALLOC(upload(P, &P->d_atom_struct, atom_struct));
   ALLOC(upload(P, &P->d_chunks, chunks));
   const int64_t N = P->n_atoms;

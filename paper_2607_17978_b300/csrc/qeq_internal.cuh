@@ -16,6 +16,7 @@
 #define QEQ_BIN 8          // mesh points per edge of an atom bin (sorting, real-space search)
 #define QEQ_BRICK_XY 16    // spread brick: mesh points in x and y (2 x 2 bins) ...
 #define QEQ_BRICK_Z 16     // ... and in z (2 bins)
+#define QEQ_BRICK_CAND 28  // per brick: candidate-bin counts per direction (3, pad), bins (3 x 8)
 #define QEQ_MAXP 8         // largest supported B-spline order
 #define QEQ_MAX_STAGES 12  // radix stages of one FFT length
 #define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
@@ -229,6 +230,7 @@ struct qeq_plan_s {
   int4* d_xitems = nullptr;        // x pass {s, z, y0, lines}
   int* d_bin_struct = nullptr;     // structure of each global bin
   int* d_brick_struct = nullptr;   // structure of each global brick
+  int* d_brick_cand = nullptr;     // QEQ_BRICK_CAND ints per brick (brick_candidates)
   int total_bricks = 0;
   int* d_atom_struct = nullptr;    // structure of each atom (input order)
   Chunk* d_chunks = nullptr;
@@ -435,6 +437,27 @@ inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   g.subx32 = tlx;
   g.subx64 = std::max(1, tlx / 2);
   return g;
+}
+
+// Candidate bins of spread brick (bc0, bc1, bc2) of structure T with B-spline order p: per
+// direction the distinct bins of the positions x0 .. x0 + ext + p - 2 (mod K) in order, the
+// bins that can hold an atom whose stencil reaches the brick.  out: QEQ_BRICK_CAND ints,
+// counts at 0..2, bins of direction d at 4 + 8 d.
+inline void brick_candidates(const StructDev& T, int p, const int* bc, int* out) {
+  for (int i = 0; i < QEQ_BRICK_CAND; ++i) out[i] = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int e = (d == 2) ? QEQ_BRICK_Z : QEQ_BRICK_XY;
+    const int x0 = bc[d] * e, ext = std::min(e, T.K[d] - x0);
+    const int span = std::min(ext + p - 1, T.K[d]);
+    int nc = 0;
+    for (int k = 0; k < span; ++k) {
+      const int bn = ((x0 + k) % T.K[d]) / QEQ_BIN;
+      bool seen = false;
+      for (int q = 0; q < nc; ++q) seen |= (out[4 + 8 * d + q] == bn);
+      if (!seen && nc < 8) out[4 + 8 * d + nc++] = bn;
+    }
+    out[d] = nc;
+  }
 }
 
 // Work lists of the FFT passes of one structure (shared by qeq_plan_create and the

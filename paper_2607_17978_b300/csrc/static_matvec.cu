@@ -57,6 +57,7 @@ struct Staging {
   int4 yiit[kSM * kSM * kSNcm];
   int4 xit[(kSM / 2 + 1) * kSM];
   int bin_struct[(kSM / QEQ_BIN) * (kSM / QEQ_BIN) * (kSM / QEQ_BIN)];
+  int brick_cand[(kSM / QEQ_BRICK_XY) * (kSM / QEQ_BRICK_XY) * (kSM / QEQ_BRICK_Z) * QEQ_BRICK_CAND];
   int atom_struct[QEQ_STATIC_MAX_ATOMS];
   Chunk chunks[(QEQ_STATIC_MAX_ATOMS + QEQ_CHUNK - 1) / QEQ_CHUNK];
 };
@@ -72,7 +73,8 @@ constexpr size_t kStaticWorstCase() {
   return carve_bytes(1, sizeof(StructDev)) + carve_bytes(6, sizeof(FftPlanDev)) + carve_bytes(6 * kSM, 16) +
          carve_bytes(6 * kSM, 8) + carve_bytes(18 * kSM, 4) + carve_bytes(3 * kSM, 8) + carve_bytes(3 * kSM, 4) +
          3 * carve_bytes((size_t)kSM * kSM * kSNcm, 16) + carve_bytes((kSM / 2 + 1) * kSM, 16) +
-         carve_bytes(nbins, 4) + carve_bytes(nbins, 4) + carve_bytes(N, 4) + carve_bytes(nch, sizeof(Chunk)) +
+         carve_bytes(nbins, 4) + carve_bytes(nbins, 4) + carve_bytes(nbins * QEQ_BRICK_CAND, 4) + carve_bytes(N, 4) +
+         carve_bytes(nch, sizeof(Chunk)) +
          carve_bytes(N, 4) + 3 * carve_bytes(nbins + 1, 4) + carve_bytes(N, 4) + carve_bytes(N / 1024 + 8, 8) +
          carve_bytes(N, 4) + carve_bytes(N * 3 * QEQ_MAXP, 8) + carve_bytes(N * 3 * QEQ_MAXP, 4) +
          carve_bytes(N, 4) + 3 * carve_bytes(N, 8) + carve_bytes(3 * N, 8) + carve_bytes(N, 16) +
@@ -306,6 +308,10 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   for (int b = 0; b < nbins; ++b) G.bin_struct[b] = 0;
   T.brick_off = 0;
   const int nbricks = T.nbr[0] * T.nbr[1] * T.nbr[2];
+  for (int b = 0; b < nbricks; ++b) {
+    const int bc[3] = {b / (T.nbr[2] * T.nbr[1]), (b / T.nbr[2]) % T.nbr[1], b % T.nbr[2]};
+    brick_candidates(T, T.p, bc, G.brick_cand + (size_t)b * QEQ_BRICK_CAND);
+  }
   double Mp[QEQ_MAXP];
   bspline_int_s(T.p, Mp);
   for (int d = 0; d < 3; ++d) {
@@ -397,6 +403,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   P.d_xitems = cv.take<int4>(nx);
   P.d_bin_struct = cv.take<int>(nbins);
   P.d_brick_struct = cv.take<int>(nbricks);
+  P.d_brick_cand = cv.take<int>((size_t)nbricks * QEQ_BRICK_CAND);
   P.d_atom_struct = cv.take<int>(N);
   P.d_chunks = cv.take<Chunk>(nchunks);
   P.d_key = cv.take<int>(N);
@@ -449,6 +456,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   SCOPY(P.d_xitems, G.xit, sizeof(int4) * nx);
   SCOPY(P.d_bin_struct, G.bin_struct, sizeof(int) * nbins);
   SCOPY(P.d_brick_struct, G.bin_struct, sizeof(int) * nbricks);
+  SCOPY(P.d_brick_cand, G.brick_cand, sizeof(int) * nbricks * QEQ_BRICK_CAND);
   SCOPY(P.d_atom_struct, G.atom_struct, sizeof(int) * N);
   SCOPY(P.d_chunks, G.chunks, sizeof(Chunk) * nchunks);
 #undef SCOPY
