@@ -282,3 +282,51 @@ def projected_residual(y_elec, J, chi, q):
 def certified_bound(Pr, J) -> float:
     """||q - q*||_2 <= ||P(Aq + chi)||_2 / J_min (A - diag J is PSD on 1^perp)."""
     return float(np.linalg.norm(Pr) / np.min(J))
+
+
+# --------------------------------------------------------------------------- forces (force trick)
+
+def electrostatic_forces_fd(cell, pos, sigma, q, lam=None, k_e=1.0, h=1e-4, atoms=None, omega=None):
+    """The electrostatic terms of the force trick, SI eq. (4g_force_trick), by central
+    differences of the dense Coulomb matrix:
+
+        F_k = -d/dR_k [ 1/2 q^T A(R) q + lam^T A(R) q ] = -dE_elec/dR_k|_q - lam^T (dA/dR_k) q
+
+    with A the Gaussian-charge Coulomb matrix (the hardness diagonal does not depend on
+    the positions).  lam = None leaves the second term out.  ``atoms`` selects the atoms
+    whose force is returned (default: all), shape (len(atoms), 3).  The Ewald width is held
+    fixed over the displacements (any width gives the same matrix).
+    """
+    pos = np.asarray(pos, np.float64)
+    q = np.asarray(q, np.float64)
+    lam = np.zeros_like(q) if lam is None else np.asarray(lam, np.float64)
+    sigma = np.asarray(sigma, np.float64)
+    if omega is None:
+        omega = default_omega(cell, sigma)
+    wvec = 0.5 * q + lam  # 1/2 q^T A q + lam^T A q = (q/2 + lam)^T A q for symmetric A
+    atoms = list(range(len(pos))) if atoms is None else list(atoms)
+    F = np.zeros((len(atoms), 3))
+    for a, k in enumerate(atoms):
+        for c in range(3):
+            e = []
+            for sgn in (1.0, -1.0):
+                p = pos.copy()
+                p[k, c] += sgn * h
+                A = coulomb_matrix(cell, p, sigma, k_e=k_e, omega=omega)
+                e.append(float(wvec @ (A @ q)))
+            F[a, c] = -(e[0] - e[1]) / (2.0 * h)
+    return F
+
+
+# --------------------------------------------------------------------------- electrostatic embedding
+
+def element_potentials(A_elec, species, q, n_species):
+    """Element-resolved electrostatic potentials at every atomic site (the ee4G embedding
+    of Sec. 2.2 and Fig. 1c): Gamma[i, z] = sum_{j of element z} E_ij q_j, with E the
+    Gaussian-charge Coulomb matrix; summed over z they give E q."""
+    species = np.asarray(species)
+    G = np.zeros((len(q), n_species))
+    for z in range(n_species):
+        m = species == z
+        G[:, z] = A_elec[:, m] @ np.asarray(q, np.float64)[m]
+    return G

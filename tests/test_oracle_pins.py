@@ -232,3 +232,78 @@ def test_certified_bound_holds():
     qp = q + pert
     Pr, _ = O.projected_residual(A @ qp, st.J, st.chi, qp)
     assert np.linalg.norm(pert) <= O.certified_bound(Pr, st.J) * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- forces of the force trick (SI eq. 4g_force_trick)
+
+def test_forces_of_a_distant_gaussian_dimer_match_the_closed_form():
+    """Two Gaussian charges +q, -q in a large cubic box: the force is the derivative of
+    q1 q2 erf(r/(sqrt2 gamma))/r of eq. (elec_energy) plus the periodic sum's dipole term.
+    With the G = 0 term dropped (tin-foil boundary), E = E_pair - (2 pi / 3V)|p|^2,
+    p = q (R1 - R2), i.e. a force -4 pi q^2 r / (3V) along the bond; higher image terms
+    fall off as 1/L^5."""
+    L, r, s1, s2 = 80.0, 2.3, 1.0, 1.8
+    cell = np.eye(3) * L
+    pos = np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]])
+    q = np.array([0.8, -0.8])
+    F = O.electrostatic_forces_fd(cell, pos, np.array([s1, s2]), q, k_e=1.0, h=1e-4)
+    g = math.sqrt(s1 ** 2 + s2 ** 2)
+    a = 1.0 / (math.sqrt(2.0) * g)
+    dEdr = q[0] * q[1] * (2 * a / math.sqrt(math.pi) * math.exp(-(a * r) ** 2) / r - erf(a * r) / r ** 2)
+    dEdr -= 4 * math.pi * q[0] ** 2 * r / (3 * L ** 3)
+    # E depends on R2 - R1 = r x: F_1 = +dE/dr x, F_2 = -dE/dr x
+    assert abs(F[0, 0] - dEdr) < 1e-5 * abs(dEdr)
+    assert abs(F[1, 0] + dEdr) < 1e-5 * abs(dEdr)
+    assert np.abs(F[:, 1:]).max() < 1e-7
+
+
+def test_forces_sum_to_zero_and_follow_permutations_and_translations():
+    rng = np.random.default_rng(17)
+    cell = _tri_cell()
+    pos = rng.random((5, 3)) @ cell
+    sig = np.array([1.0, 1.8, 1.0, 1.8, 1.3])
+    q = rng.normal(size=5)
+    q -= q.mean()
+    lam = rng.normal(size=5) * 0.3
+    F = O.electrostatic_forces_fd(cell, pos, sig, q, lam)
+    assert np.abs(F.sum(axis=0)).max() < 1e-7 * np.abs(F).max()
+    perm = np.array([3, 0, 4, 1, 2])
+    Fp = O.electrostatic_forces_fd(cell, pos[perm], sig[perm], q[perm], lam[perm])
+    assert np.abs(Fp - F[perm]).max() < 1e-7 * np.abs(F).max()
+    Ft = O.electrostatic_forces_fd(cell, pos + np.array([0.4, -1.3, 2.2]), sig, q, lam)
+    assert np.abs(Ft - F).max() < 1e-7 * np.abs(F).max()
+
+
+def test_force_trick_term_is_linear_in_lambda():
+    """F(q, lam) = F(q, 0) + lam-term, the lam-term linear in lam: F(q, q/2) = 2 F(q, 0)
+    (then (q/2 + lam)^T A q = q^T A q) and F(q, lam1 + lam2) = F(q, lam1) + F(q, lam2) - F(q, 0)."""
+    rng = np.random.default_rng(21)
+    cell = np.diag([9.0, 8.5, 10.0])
+    pos = rng.random((4, 3)) @ cell
+    sig = np.array([1.0, 1.5, 1.2, 0.9])
+    q = rng.normal(size=4)
+    l1, l2 = rng.normal(size=4), rng.normal(size=4)
+    F0 = O.electrostatic_forces_fd(cell, pos, sig, q)
+    assert np.abs(O.electrostatic_forces_fd(cell, pos, sig, q, 0.5 * q) - 2 * F0).max() < 1e-7 * np.abs(F0).max()
+    F12 = O.electrostatic_forces_fd(cell, pos, sig, q, l1 + l2)
+    F1 = O.electrostatic_forces_fd(cell, pos, sig, q, l1)
+    F2 = O.electrostatic_forces_fd(cell, pos, sig, q, l2)
+    assert np.abs(F12 - (F1 + F2 - F0)).max() < 1e-7 * np.abs(F12).max()
+
+
+def test_element_potentials_sum_to_the_coulomb_potential():
+    rng = np.random.default_rng(5)
+    cell = _tri_cell()
+    pos = rng.random((6, 3)) @ cell
+    spc = np.array([0, 1, 2, 0, 1, 2])
+    sig = np.array([1.0, 1.8, 1.3])[spc]
+    q = rng.normal(size=6)
+    A = O.coulomb_matrix(cell, pos, sig)
+    G = O.element_potentials(A, spc, q, 3)
+    assert np.abs(G.sum(axis=1) - A @ q).max() < 1e-13 * np.abs(A @ q).max()
+    # a charge of element z only changes Gamma[:, z]
+    q2 = q.copy()
+    q2[1] += 0.7
+    G2 = O.element_potentials(A, spc, q2, 3)
+    assert np.abs(G2[:, [0, 2]] - G[:, [0, 2]]).max() == 0.0
+    assert np.abs(G2[:, 1] - G[:, 1] - 0.7 * A[:, 1]).max() < 1e-14
