@@ -68,6 +68,11 @@ def _clib():
         lib.oracle_ewald_matvec.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_int, ip, dp]
         lib.oracle_ewald_matvec.restype = ctypes.c_int
+        lib.oracle_ewald_potential_grad.argtypes = lib.oracle_ewald_matvec.argtypes
+        lib.oracle_ewald_potential_grad.restype = ctypes.c_int
+        lib.oracle_ewald_strain_derivative.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_double,
+                                                       ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_ewald_strain_derivative.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -243,21 +248,24 @@ def solve_structure(st, k_e=1.0, omega=None) -> QEqSolution:
 
 # --------------------------------------------------------------------------- large cells
 
-def ewald_matvec(cell, pos, sigma, q, k_e=1.0, omega=None, tol=1e-13, rows=None):
-    """y = A_elec q (no hardness) for large cells; ``rows`` selects output rows."""
+def _ewald_setup(cell, pos, sigma, q, omega, tol):
     cell = np.ascontiguousarray(cell, dtype=np.float64)
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     sigma = np.ascontiguousarray(sigma, dtype=np.float64)
     q = np.ascontiguousarray(q, dtype=np.float64)
-    n = len(pos)
     gmax = math.sqrt(2.0) * float(sigma.max())
     if omega is None:
         # balance O(n_G) structure factors against O(neighbours) real space
         V = volume(cell)
         omega = max(gmax, 0.9 * (V / 1.0e4) ** (1.0 / 6.0) * 2.0)
     omega = max(float(omega), gmax)
-    r_cut = realspace_cut(omega, tol * 1e-1)
-    g_cut = recip_cut(omega, tol)
+    return cell, pos, sigma, q, omega, realspace_cut(omega, tol * 1e-1), recip_cut(omega, tol)
+
+
+def ewald_matvec(cell, pos, sigma, q, k_e=1.0, omega=None, tol=1e-13, rows=None):
+    """y = A_elec q (no hardness) for large cells; ``rows`` selects output rows."""
+    cell, pos, sigma, q, omega, r_cut, g_cut = _ewald_setup(cell, pos, sigma, q, omega, tol)
+    n = len(pos)
     if rows is None:
         y = np.zeros(n)
         rc = _clib().oracle_ewald_matvec(n, _dp(cell), _dp(pos), _dp(sigma), _dp(q), omega, r_cut, g_cut,
@@ -270,6 +278,40 @@ def ewald_matvec(cell, pos, sigma, q, k_e=1.0, omega=None, tol=1e-13, rows=None)
     if rc != 0:
         raise RuntimeError(f"oracle_ewald_matvec failed ({rc})")
     return k_e * y
+
+
+def ewald_potential_gradient(cell, pos, sigma, x, rows, k_e=1.0, omega=None, tol=1e-13):
+    """g[o] = d/dR_i sum_j A_ij x_j at atom i = rows[o] (positions of the other atoms and x
+    fixed), shape (len(rows), 3): the position derivative of a row of the Ewald sum, term by
+    term (SI "Ewald Summation"); the self and G = 0 width terms do not depend on positions."""
+    cell, pos, sigma, x, omega, r_cut, g_cut = _ewald_setup(cell, pos, sigma, x, omega, tol)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    g = np.zeros(3 * len(rows))
+    rc = _clib().oracle_ewald_potential_grad(len(pos), _dp(cell), _dp(pos), _dp(sigma), _dp(x), omega, r_cut,
+                                             g_cut, len(rows), rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                             _dp(g))
+    if rc != 0:
+        raise RuntimeError(f"oracle_ewald_potential_grad failed ({rc})")
+    return k_e * g.reshape(-1, 3)
+
+
+def electrostatic_forces_ewald(cell, pos, sigma, q, rows, lam=None, k_e=1.0, omega=None, tol=1e-13):
+    """The electrostatic terms of the force trick, SI eq. (4g_force_trick), at atoms ``rows``
+    of a cell too large for the dense matrix:
+
+        F_k = -d/dR_k [(q/2 + lam)^T A q] = -(q_k + lam_k) grad phi_q(k) - q_k grad phi_lam(k)
+
+    (A symmetric: the R_k dependence sits in row and column k), with grad phi_x(k) from
+    ewald_potential_gradient.  lam = None leaves the lam terms out."""
+    rows = np.asarray(rows)
+    q = np.asarray(q, np.float64)
+    gq = ewald_potential_gradient(cell, pos, sigma, q, rows, k_e, omega, tol)
+    F = -q[rows, None] * gq
+    if lam is not None:
+        lam = np.asarray(lam, np.float64)
+        gl = ewald_potential_gradient(cell, pos, sigma, lam, rows, k_e, omega, tol)
+        F -= lam[rows, None] * gq + q[rows, None] * gl
+    return F
 
 
 def projected_residual(y_elec, J, chi, q):
@@ -316,6 +358,52 @@ def electrostatic_forces_fd(cell, pos, sigma, q, lam=None, k_e=1.0, h=1e-4, atom
                 e.append(float(wvec @ (A @ q)))
             F[a, c] = -(e[0] - e[1]) / (2.0 * h)
     return F
+
+
+def strained(cell, pos, eps):
+    """Cell rows and positions under the homogeneous deformation r -> (1 + eps) r."""
+    F = np.eye(3) + np.asarray(eps, np.float64)
+    return np.asarray(cell, np.float64) @ F.T, np.asarray(pos, np.float64) @ F.T
+
+
+def electrostatic_strain_derivative_fd(cell, pos, sigma, q, lam=None, k_e=1.0, h=1e-5, omega=None):
+    """D[a, b] = d/d eps_ab [(q/2 + lam)^T A q] at fixed charges, A the Gaussian-charge Coulomb
+    matrix of the deformed cell and positions (r -> (1 + eps) r), by central differences: the
+    electrostatic part of the strain derivative in the force trick (SI eq. 4g_force_trick,
+    applied to the cell instead of an atom).  The stress of the form is D / V."""
+    q = np.asarray(q, np.float64)
+    lam = np.zeros_like(q) if lam is None else np.asarray(lam, np.float64)
+    sigma = np.asarray(sigma, np.float64)
+    if omega is None:
+        omega = default_omega(cell, sigma)
+    wvec = 0.5 * q + lam
+    D = np.zeros((3, 3))
+    for a in range(3):
+        for b in range(3):
+            e = []
+            for sgn in (1.0, -1.0):
+                eps = np.zeros((3, 3))
+                eps[a, b] = sgn * h
+                c2, p2 = strained(cell, pos, eps)
+                A = coulomb_matrix(c2, p2, sigma, k_e=k_e, omega=omega)
+                e.append(float(wvec @ (A @ q)))
+            D[a, b] = (e[0] - e[1]) / (2.0 * h)
+    return D
+
+
+def electrostatic_strain_derivative_ewald(cell, pos, sigma, q, lam=None, k_e=1.0, omega=None, tol=1e-13):
+    """The same strain derivative for cells too large for the dense matrix, term by term from
+    the Ewald split (oracle_ewald_strain_derivative): D = d/d eps [(q/2 + lam)^T A q]."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    wvec = 0.5 * q + (0.0 if lam is None else np.asarray(lam, np.float64))
+    cell, pos, sigma, q, omega, r_cut, g_cut = _ewald_setup(cell, pos, sigma, q, omega, tol)
+    wvec = np.ascontiguousarray(wvec, dtype=np.float64)
+    D = np.zeros(9)
+    rc = _clib().oracle_ewald_strain_derivative(len(pos), _dp(cell), _dp(pos), _dp(sigma), _dp(wvec), _dp(q),
+                                                omega, r_cut, g_cut, _dp(D))
+    if rc != 0:
+        raise RuntimeError(f"oracle_ewald_strain_derivative failed ({rc})")
+    return k_e * D.reshape(3, 3)
 
 
 # --------------------------------------------------------------------------- electrostatic embedding

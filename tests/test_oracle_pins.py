@@ -307,3 +307,137 @@ def test_element_potentials_sum_to_the_coulomb_potential():
     G2 = O.element_potentials(A, spc, q2, 3)
     assert np.abs(G2[:, [0, 2]] - G[:, [0, 2]]).max() == 0.0
     assert np.abs(G2[:, 1] - G[:, 1] - 0.7 * A[:, 1]).max() < 1e-14
+
+
+@pytest.mark.parametrize("point", [False, True])
+def test_analytic_ewald_gradient_matches_dense_central_differences(point):
+    """The term-by-term position derivative of a row of the Ewald sum (large-cell force oracle)
+    against central differences of the dense matrix, on a triclinic cell with two widths and
+    with point charges (sigma = 0: textbook Ewald), with and without the lambda term."""
+    rng = np.random.default_rng(33)
+    cell = _tri_cell()
+    n = 9
+    pos = rng.random((n, 3)) @ cell
+    sig = np.zeros(n) if point else np.where(np.arange(n) % 2 == 0, 1.0, 1.7)
+    q = rng.normal(size=n)
+    q -= q.mean()
+    lam = rng.normal(size=n)
+    rows = [0, 3, 8]
+    for la in (None, lam):
+        Ffd = O.electrostatic_forces_fd(cell, pos, sig, q, la, atoms=rows, omega=2.0 if point else None)
+        Fan = O.electrostatic_forces_ewald(cell, pos, sig, q, rows, lam=la)
+        assert np.abs(Fan - Ffd).max() < 1e-7 * np.abs(Ffd).max()
+
+
+def test_analytic_ewald_forces_sum_to_zero():
+    """Without the lambda term the forces are minus the gradient of a translation-invariant
+    energy: they sum to zero over the cell (exactly, independent of the Ewald width)."""
+    rng = np.random.default_rng(34)
+    cell = _tri_cell()
+    pos = rng.random((12, 3)) @ cell
+    sig = rng.uniform(0.8, 1.8, size=12)
+    q = rng.normal(size=12)
+    F = O.electrostatic_forces_ewald(cell, pos, sig, q, np.arange(12))
+    assert np.abs(F.sum(axis=0)).max() < 1e-10 * np.abs(F).max()
+    F2 = O.electrostatic_forces_ewald(cell, pos, sig, q, np.arange(12), omega=3.0)
+    assert np.abs(F2 - F).max() < 1e-9 * np.abs(F).max()
+
+
+def test_force_trick_gives_the_total_derivative_through_the_solve():
+    """SI eq. (4g_force_trick): for E(R) = 1/2 q*(R)^T A(R) q*(R) with q* the QEq charges,
+    dE/dR_k = d/dR_k [(q/2 + lam)^T A q] at fixed q = q*, lam solving
+    (A + J) lam = -dE/dq + nu 1 = -A q* + nu 1, sum lam = 0.  Checked against central
+    differences of E with the charges re-solved at every displaced geometry."""
+    rng = np.random.default_rng(41)
+    cell = _tri_cell()
+    n = 6
+    pos = rng.random((n, 3)) @ cell
+    sig = np.array([1.0, 1.6, 1.0, 1.6, 1.2, 1.2])
+    J = rng.uniform(1.0, 3.0, size=n)
+    chi = rng.normal(0.0, 1.0, size=n)
+    q_tot = 1.0
+
+    def energy(p):
+        A = O.coulomb_matrix(cell, p, sig, omega=2.0)
+        q, _ = O.solve_bordered(A, J, chi, q_tot)
+        return 0.5 * q @ A @ q
+
+    A = O.coulomb_matrix(cell, pos, sig, omega=2.0)
+    q, _ = O.solve_bordered(A, J, chi, q_tot)
+    lam, _ = O.solve_bordered(A, J, A @ q, 0.0)
+    assert abs(lam.sum()) < 1e-12
+    F = O.electrostatic_forces_fd(cell, pos, sig, q, lam, omega=2.0)
+    h = 1e-4
+    Ftot = np.zeros((n, 3))
+    for k in range(n):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[k, c] += h
+            pm[k, c] -= h
+            Ftot[k, c] = -(energy(pp) - energy(pm)) / (2 * h)
+    assert np.abs(F - Ftot).max() < 1e-6 * np.abs(Ftot).max()
+    # without lam the fixed-charge derivative is a different (wrong) total force here
+    F0 = O.electrostatic_forces_fd(cell, pos, sig, q, omega=2.0)
+    assert np.abs(F0 - Ftot).max() > 1e-3 * np.abs(Ftot).max()
+
+
+@pytest.mark.parametrize("analytic", [False, True])
+def test_strain_derivative_of_the_madelung_energy(analytic):
+    """Perfect rock-salt of point charges +-1: W = 1/2 q^T A q = -(N/2) M / r0 (M the Madelung
+    constant, r0 = a/2).  The energy is homogeneous of degree -1 in the lengths and the crystal
+    is cubic, so dW/d eps = -W/3 times the identity."""
+    frac, spec = synth.rocksalt_sites(2, 2, 2)
+    a = 5.64
+    cell = np.eye(3) * 2 * a
+    pos = frac @ cell
+    q = np.where(spec == 0, 1.0, -1.0)
+    sig = np.zeros(len(q))
+    W = -(len(q) / 2) * MADELUNG / (a / 2)
+    if analytic:
+        D = O.electrostatic_strain_derivative_ewald(cell, pos, sig, q, omega=2.0)
+    else:
+        D = O.electrostatic_strain_derivative_fd(cell, pos, sig, q, omega=2.0)
+    assert np.abs(D - (-W / 3) * np.eye(3)).max() < 1e-7 * abs(W)
+
+
+def test_strain_derivative_homogeneity_with_gaussian_widths():
+    """W(s R, s h, s sigma) = W / s: trace(dW/d eps) + sum_s sigma_s dW/d sigma_s = -W, on a
+    triclinic cell with three widths; the strain derivative is also symmetric (rotations
+    leave W unchanged)."""
+    rng = np.random.default_rng(51)
+    cell = _tri_cell()
+    n = 8
+    pos = rng.random((n, 3)) @ cell
+    spc = np.arange(n) % 3
+    sig_s = np.array([1.0, 1.5, 1.9])
+    q = rng.normal(size=n)
+    lam = rng.normal(size=n)
+    w = 0.5 * q + lam
+
+    def W(s_s):
+        return float(w @ O.coulomb_matrix(cell, pos, s_s[spc], omega=2.5) @ q)
+
+    D = O.electrostatic_strain_derivative_fd(cell, pos, sig_s[spc], q, lam, omega=2.5)
+    h = 1e-5
+    dsig = 0.0
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        dsig += sig_s[k] * (W(sig_s + e) - W(sig_s - e)) / (2 * h)
+    assert abs(np.trace(D) + dsig + W(sig_s)) < 1e-7 * np.abs(D).max()
+    assert np.abs(D - D.T).max() < 1e-7 * np.abs(D).max()
+
+
+@pytest.mark.parametrize("point", [False, True])
+def test_analytic_strain_derivative_matches_dense_central_differences(point):
+    rng = np.random.default_rng(52)
+    cell = _tri_cell()
+    n = 9
+    pos = rng.random((n, 3)) @ cell
+    sig = np.zeros(n) if point else np.where(np.arange(n) % 2 == 0, 0.9, 1.6)
+    q = rng.normal(size=n)
+    lam = rng.normal(size=n)
+    for la in (None, lam):
+        Dfd = O.electrostatic_strain_derivative_fd(cell, pos, sig, q, la, omega=2.0)
+        Dan = O.electrostatic_strain_derivative_ewald(cell, pos, sig, q, la, omega=2.5)
+        assert np.abs(Dan - Dfd).max() < 1e-7 * np.abs(Dfd).max()
