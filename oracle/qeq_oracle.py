@@ -231,6 +231,38 @@ def solve_bordered(A_elec, J, chi, q_tot) -> tuple[np.ndarray, float]:
     return x[:n], -float(x[n])
 
 
+# --------------------------------------------------------------------------- 4G charge training
+
+def bordered_inverse(A_elec, J):
+    """Inverse of the bordered matrix A' = [[E + diag J, 1], [1^T, 0]] of eq. (4G_qeq_prime),
+    the object Sec. "4G-HDNNP Charge Training" caches per training structure (re-inverted
+    when the hardness J is learned)."""
+    n = len(J)
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = np.asarray(A_elec, float) + np.diag(np.asarray(J, float))
+    M[:n, n] = 1.0
+    M[n, :n] = 1.0
+    return np.linalg.inv(M)
+
+
+def charges_from_inverse(Kinv, chi, q_tot):
+    """q' = -A'^{-1} chi' with chi' = (chi, -q_tot): one matrix-vector product with the cached
+    inverse (Sec. "4G-HDNNP Charge Training").  Returns q and mu (= -lambda)."""
+    n = len(chi)
+    x = Kinv @ np.concatenate([-np.asarray(chi, float), [float(q_tot)]])
+    return x[:n], -float(x[n])
+
+
+def charges_backward(Kinv, q, gq):
+    """Gradients of a loss L(q) with respect to chi and J through the bordered solve: A' is
+    symmetric, so with (lam, nu) = A'^{-1} (dL/dq, 0),
+        dL/dchi = -lam,    dL/dJ_i = -lam_i q_i   (dA'/dJ_i = e_i e_i^T)."""
+    n = len(q)
+    x = Kinv @ np.concatenate([np.asarray(gq, float), [0.0]])
+    lam = x[:n]
+    return -lam, -lam * np.asarray(q, float)
+
+
 def energies(A_elec, J, chi, q) -> tuple[float, float]:
     """E_QEq = chi.q + 1/2 q.(E + diag J) q (eq. qeq_energy) and E_elec = 1/2 q.E q (eq. elec_energy)."""
     Eq = A_elec @ q

@@ -441,3 +441,55 @@ def test_analytic_strain_derivative_matches_dense_central_differences(point):
         Dfd = O.electrostatic_strain_derivative_fd(cell, pos, sig, q, la, omega=2.0)
         Dan = O.electrostatic_strain_derivative_ewald(cell, pos, sig, q, la, omega=2.5)
         assert np.abs(Dan - Dfd).max() < 1e-7 * np.abs(Dfd).max()
+
+
+# --------------------------------------------------------------------------- 4G charge training
+
+def _train_case(n=7, seed=61):
+    rng = np.random.default_rng(seed)
+    cell = _tri_cell()
+    pos = rng.random((n, 3)) @ cell
+    sig = np.where(np.arange(n) % 2 == 0, 1.0, 1.6)
+    A = O.coulomb_matrix(cell, pos, sig, omega=2.0)
+    J = rng.uniform(1.0, 3.0, size=n)
+    chi = rng.normal(size=n)
+    return A, J, chi
+
+
+def test_charges_from_the_cached_inverse_two_atoms_by_hand():
+    """N = 2: q1 = (chi2 - chi1 + Q (a22 - a12)) / (a11 + a22 - 2 a12) with a = A + J, from
+    eliminating q2 = Q - q1 in (A + J) q = -chi + mu 1."""
+    a = np.array([[2.7, 0.4], [0.4, 1.9]])
+    J = np.zeros(2)
+    chi = np.array([0.3, -0.8])
+    Q = 0.5
+    Kinv = O.bordered_inverse(a, J)
+    q, mu = O.charges_from_inverse(Kinv, chi, Q)
+    q1 = (chi[1] - chi[0] + Q * (a[1, 1] - a[0, 1])) / (a[0, 0] + a[1, 1] - 2 * a[0, 1])
+    assert abs(q[0] - q1) < 1e-14 and abs(q[1] - (Q - q1)) < 1e-14
+    assert abs(a[0] @ q + chi[0] - mu) < 1e-14 and abs(a[1] @ q + chi[1] - mu) < 1e-14
+
+
+def test_charge_training_gradients_match_central_differences():
+    """dL/dchi and dL/dJ of L = 1/2 |q(chi, J) - q_ref|^2 through the re-inverted bordered
+    matrix, against central differences; dL/dchi sums to zero (a uniform shift of chi only
+    moves mu)."""
+    A, J, chi = _train_case()
+    q_ref = np.random.default_rng(3).normal(size=len(J)) * 0.2
+    Q = -1.0
+
+    def loss(c, j):
+        q, _ = O.charges_from_inverse(O.bordered_inverse(A, j), c, Q)
+        return 0.5 * float(np.sum((q - q_ref) ** 2))
+
+    Kinv = O.bordered_inverse(A, J)
+    q, _ = O.charges_from_inverse(Kinv, chi, Q)
+    gchi, gJ = O.charges_backward(Kinv, q, q - q_ref)
+    h = 1e-6
+    for i in range(len(J)):
+        e = np.zeros(len(J))
+        e[i] = h
+        assert abs((loss(chi + e, J) - loss(chi - e, J)) / (2 * h) - gchi[i]) < 1e-8
+        assert abs((loss(chi, J + e) - loss(chi, J - e)) / (2 * h) - gJ[i]) < 1e-8
+    assert abs(gchi.sum()) < 1e-12
+    assert abs(q.sum() - Q) < 1e-12
