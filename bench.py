@@ -347,14 +347,36 @@ def run_profile(args):
     from paper_2607_17978_b300 import build, qeq, synth
     build.build()
     st = synth.rocksalt(args.cells, synth.ROCKSALT_A, 0.2, synth.rng_for(5, 1), vacancy_frac=0.02)
-    plan = qeq.plan_for_structures([st], precision=args.precision, ewald_tol=1e-6, r_cut=8.0)
+    plan = qeq.plan_for_structures([st], precision=args.precision, ewald_tol=1e-6, r_cut=8.0, graph=not args.no_graph)
     pos, spc, chi, J, qt = qeq.pack([st])
     d = [torch.tensor(a, device="cuda") for a in (pos, spc, chi, J)]
+    torch.cuda.profiler.start()                     # ncu --profile-from-start off: the solves ...
     for _ in range(args.steps):
         r = plan.solve(*d, qt)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    stages = plan.profile_matvec(5)
+    # ... and, with --forces, one force-trick evaluation (lambda from a second solve, forces, stress)
+    extra = {}
+    if args.forces:
+        dEdq = plan.matvec(d[0], d[1], r.q, fp64=True)
+        lam = plan.solve(d[0], d[1], dEdq, d[3], np.zeros(1)).q
+        plan.forces(d[0], d[1], r.q, lam)
+        plan.stress(d[0], d[1], r.q, lam)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.profiler.start()
+        plan.stream.wait_stream(torch.cuda.current_stream())
+        ev[0].record(plan.stream)
+        plan.forces(d[0], d[1], r.q, lam)
+        ev[1].record(plan.stream)
+        plan.stress(d[0], d[1], r.q, lam)
+        ev[2].record(plan.stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        extra = {"forces_ms": ev[0].elapsed_time(ev[1]), "stress_ms": ev[1].elapsed_time(ev[2])}
     print(json.dumps({"profile_case": f"rocksalt {args.cells}^3", "atoms": st.n, "mesh": plan.query(0)["mesh"],
-                      "iterations": r.info[0]["iterations"], "stages_ms": plan.profile_matvec(5)}))
+                      "iterations": r.info[0]["iterations"], "stages_ms": stages, **extra}))
     return 0
 
 
@@ -388,7 +410,8 @@ def run_ours(args):
     d_spc = torch.tensor(spc, device=dev)
     d_chi = torch.tensor(chi, device=dev)
     d_J = torch.tensor(J, device=dev)
-    plan = qeq.plan_for_structures(structs, precision=args.precision, device=dev, preconditioner=args.precond, **opts)
+    plan = qeq.plan_for_structures(structs, precision=args.precision, device=dev, preconditioner=args.precond,
+                                   graph=not args.no_graph, **opts)
     q_out = torch.empty(n_atoms, dtype=torch.float64, device=dev)
     # learned warm start for the rock-salt workloads of the recipe the network was trained on
     # (unsheared, jittered, few vacancies; the sheared 5%-vacancy cell of workload 3 is outside it)
@@ -466,6 +489,42 @@ def run_ours(args):
     traffic = load_traffic().get(f"{dom}:{args.workload}:{args.precision}")
     matvec_ms = sum(prof.values())
     matvec_bytes = matvec_model_bytes(plan, args.precision, n_atoms)
+
+    # ---- force trick (SI eq. 4g_force_trick) after the solve: dE/dq = E q (FP64 matvec, no
+    # hardness), lambda from a second solve (chi := dE/dq, q_tot = 0), then qeq_forces(q, lambda)
+    zeros = np.zeros(n_struct)
+    box = {}
+
+    def trick():
+        box["dEdq"] = plan.matvec(d_pos, d_spc, q_out, fp64=True)
+        box["lam"] = plan.solve(d_pos, d_spc, box["dEdq"], d_J, zeros)
+        box["F"] = plan.forces(d_pos, d_spc, q_out, box["lam"].q)
+
+    def timed(fn, n=3):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(2.0)
+            plan.stream.wait_stream(torch.cuda.current_stream(dev))
+            a.record(plan.stream)
+            fn()
+            b.record(plan.stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / n
+
+    trick_ms = timed(trick)
+    lam_q = box["lam"].q
+    trick_parts = {
+        "dEdq_matvec_ms": timed(lambda: plan.matvec(d_pos, d_spc, q_out, fp64=True)),
+        "lambda_solve_ms": timed(lambda: plan.solve(d_pos, d_spc, box["dEdq"], d_J, zeros)),
+        "forces_ms": timed(lambda: plan.forces(d_pos, d_spc, q_out, lam_q)),
+        "forces_without_lambda_ms": timed(lambda: plan.forces(d_pos, d_spc, q_out)),
+        "stress_ms": timed(lambda: plan.stress(d_pos, d_spc, q_out, lam_q)),
+    }
+    trick_iters = float(np.mean([i["iterations"] for i in box["lam"].info]))
 
     # ---- plain FP64 GPU PCG (one structure per launch, no graph): the comparison denominator
     sample = list(range(0, n_struct, 16)) if n_struct > 1 else [0]
@@ -551,7 +610,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_NAME[args.workload], "atoms": atoms_total, "structures": len(structs_all),
                    "mesh": list(qi["mesh"]) if n_struct == 1 else "per structure (autotuned)",
                    "spline_order": qi["spline_order"], "omega_A": round(qi["omega"], 4), "precision": args.precision,
-                   "graph": True, "warm_start": warm, "preconditioner": args.precond, "charge_tol_e": 1e-5, "l2": "flushed between timed steps (256 MB write)",
+                   "graph": not args.no_graph, "warm_start": warm, "preconditioner": args.precond, "charge_tol_e": 1e-5, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"sharded x{world}" if sharded else f"replicas x{world}"},
         "atoms_iters_per_s": atoms_iters_all / (ms * 1e-3),
         "pcg_iterations": it_mean, "pcg_restarts_max": int(max(restarts)), "status": status,
@@ -576,6 +635,12 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    line["force_trick"] = {
+        "ms_per_step": trick_ms, "atoms_per_s": n_atoms / (trick_ms * 1e-3),
+        "lambda_pcg_iterations": trick_iters, "vs_charge_solve": trick_ms / ms,
+        "parts_ms": {k: round(v, 4) for k, v in trick_parts.items()},
+        "form": "FP64 potential meshes and gradients; lambda solve in the chosen form, cold start",
+    }
     if oracle_err:
         line["oracle_error"] = oracle_err
     if cpu:
@@ -598,6 +663,11 @@ def main():
                     help="preconditioner of the chosen form (the plain FP64 leg always uses Jacobi)")
     ap.add_argument("--warm", default="auto", choices=["auto", "mlp", "cold"],
                     help="learned warm start (auto: on for workloads 1, 2 and 5, the training recipe, when the model file exists)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-paced PCG rounds instead of the device-paced graph (same kernels; for ncu, which "
+                         "cannot profile the kernel nodes of a graph with conditional nodes)")
+    ap.add_argument("--forces", action="store_true",
+                    help="with --profile-cells: also one force-trick evaluation (forces and stress)")
     ap.add_argument("--profile-cells", dest="cells", type=int, default=0,
                     help="profiling mode: solve a rock-salt cell of N^3 conventional cells only")
     args = ap.parse_args()

@@ -40,7 +40,8 @@
  *                qeq_plan_create; calls return after that stream has finished
  *                the call's work (the host reads per-structure results).
  *   allocation   qeq_plan_create allocates every device buffer the plan
- *                needs; qeq_solve, qeq_energy and qeq_matvec allocate nothing.
+ *                needs; qeq_solve, qeq_energy, qeq_matvec, qeq_forces,
+ *                qeq_stress and qeq_embedding allocate nothing.
  *   errors       every call returns a qeq_status and never aborts the process;
  *                qeq_last_error gives a message.  Invalid input leaves outputs
  *                unspecified.
@@ -193,6 +194,71 @@ qeq_status qeq_energy(qeq_plan plan, const double* d_pos, const int32_t* d_speci
 qeq_status qeq_matvec(qeq_plan plan, const double* d_pos, const int32_t* d_species,
                       const double* d_J, const double* d_x, double* d_y, int32_t force_fp64);
 
+/* Electrostatic forces by the force trick (SI eq. 4g_force_trick).  For a
+ * total energy E(q, R) whose charges solve the QEq system, the force on atom
+ * k, with lambda solving (E + diag J) lambda = -dE/dq + nu 1, sum lambda = 0,
+ * is
+ *     F_k = -dE/dR_k|_q - lambda^T (dA/dR_k) q,
+ * and this call returns the electrostatic part of it:
+ *     d_F[k] = -(q_k + lambda_k) grad_k phi_q(k) - q_k grad_k phi_lambda(k),
+ * phi_x(k) = sum_j E_kj x_j the potential of the charges x at atom k and
+ * grad_k its gradient with respect to R_k at fixed x (the hardness and the
+ * self terms do not depend on positions).  With d_lambda = NULL the lambda
+ * terms are left out: d_F = -dE_elec/dR at fixed q (E_elec of eq.
+ * elec_energy), the force when the charges minimise E_QEq itself.  lambda
+ * comes from qeq_solve with chi := dE/dq and q_tot = 0.
+ *
+ * The potential gradients are taken in FP64 through the plane-wave terms of
+ * eq. (matvec): the potential meshes (spread, FFT, reciprocal multiply,
+ * inverse FFT) are interpolated with the derivative of the B-spline weights
+ * (dM_p(t)/dt = M_{p-1}(t) - M_{p-1}(t - 1)) and mapped to Cartesian
+ * derivatives through the cell; the screened real-space pair term of the
+ * Ewald split (SI "Ewald Summation") adds its analytic derivative.  The
+ * error is that of the matvec's interpolation (ewald_tol).  The cell
+ * counterpart is qeq_stress.
+ *
+ *   d_pos, d_species   as in qeq_solve (device, input order)
+ *   d_q                N charges (device), input order
+ *   d_lambda           N Lagrange multipliers (device) or NULL
+ *   d_F                N x 3 forces (device), input order, written
+ * Errors: QEQ_ERR_INVALID (null pointer, non-finite position, species out of
+ * range), QEQ_ERR_CUDA, QEQ_ERR_TIMEOUT. */
+qeq_status qeq_forces(qeq_plan plan, const double* d_pos, const int32_t* d_species,
+                      const double* d_q, const double* d_lambda, double* d_F);
+
+/* Strain derivative of the same electrostatic terms (the cell counterpart of
+ * qeq_forces, SI eq. 4g_force_trick): under the homogeneous deformation of a
+ * structure's cell and positions r -> (1 + eps) r at fixed charges,
+ *     d_D[9 s + 3 a + b] = d/d eps_ab [(q/2 + lambda)^T E q]
+ * (E of eq. elec_energy; lambda = NULL: d/d eps of E_elec).  The stress of
+ * these terms is D / V; D is symmetric.  Reciprocal part: the strain
+ * derivative of the plane-wave kernel, dG^2/d eps_ab = -2 G_a G_b and
+ * dV/d eps_ab = V delta_ab, summed over the forward-transformed charge
+ * meshes in FP64 (two mesh passes with lambda, by polarisation of the
+ * bilinear form; one without); real-space part: the pair-term derivative;
+ * the G = 0 width term scales as 1/V.
+ *
+ *   d_pos, d_species   as in qeq_solve (device, input order)
+ *   d_q                N charges (device), input order
+ *   d_lambda           N Lagrange multipliers (device) or NULL
+ *   d_D                n_struct x 9 (device), row-major 3x3 per structure, written
+ * Errors: as qeq_forces. */
+qeq_status qeq_stress(qeq_plan plan, const double* d_pos, const int32_t* d_species,
+                      const double* d_q, const double* d_lambda, double* d_D);
+
+/* Element-resolved electrostatic potentials of the ee4G embedding (Sec. 2.2,
+ * Fig. 1c): d_Gamma[i * n_species + z] = sum over atoms j of element z of
+ * E_ij q_j (E of eq. elec_energy, no hardness), the potential at atom i of
+ * the charges of element z; summed over z it is (E q)_i.  One FP64 matvec of
+ * eq. (matvec) per element; the descriptor built from it is the caller's.
+ *
+ *   d_pos, d_species   as in qeq_solve (device, input order)
+ *   d_q                N charges (device), input order
+ *   d_Gamma            N x n_species (device), input order, row-major, written
+ * Errors: as qeq_matvec. */
+qeq_status qeq_embedding(qeq_plan plan, const double* d_pos, const int32_t* d_species,
+                         const double* d_q, double* d_Gamma);
+
 /* Time each stage of the matvec with CUDA events on the plan's stream.
  * Runs n_rep matvecs of the plan's precision on the atoms of the last
  * qeq_solve / qeq_matvec call and writes the mean milliseconds per launch of
@@ -201,6 +267,68 @@ qeq_status qeq_matvec(qeq_plan plan, const double* d_pos, const int32_t* d_speci
  * inverse FFT z, gather + real space + local terms. */
 #define QEQ_N_STAGES 8
 qeq_status qeq_profile_matvec(qeq_plan plan, int32_t n_rep, float* h_ms);
+
+/* ------------------------------------------------------------------------
+ * 4G charge training on cached dense matrices (Sec. "4G-HDNNP Charge
+ * Training").  Training structures are small and their positions fixed while
+ * the networks learn chi (and possibly J), so the Coulomb matrix E of each
+ * structure (eq. elec_energy, periodic, G = 0 term dropped; no hardness) is
+ * assembled once, the bordered matrix A' = [[E + diag J, 1], [1^T, 0]] of
+ * eq. (4G_qeq_prime) is inverted whenever J changes, and the charges of a
+ * training step are one matrix-vector product
+ *     (q, lambda) = -A'^{-1} (chi, -q_tot),   mu = -lambda.
+ * The backward pass uses the same inverse (A' is symmetric): with
+ * (l, nu) = A'^{-1} (dL/dq, 0),  dL/dchi = -l  and  dL/dJ_i = -l_i q_i.
+ *
+ * E is assembled in FP64 by the Ewald split of SI "Ewald Summation" with one
+ * width omega >= every gamma_ij per structure (chosen for the least work),
+ * real-space and reciprocal sums truncated where their terms fall below
+ * ewald_tol (default 1e-12 here); the inverse is FP64 (Cholesky of
+ * E + diag J, triangular inverse, bordered by the Schur complement).
+ *
+ * Handle: qeq_dense_create takes a qeq_plan_desc (n_struct, atom_offsets,
+ * cells, n_species, sigma, coulomb_k, ewald_tol are read; the rest is
+ * ignored) and the CUDA stream every call runs on; it allocates E, A'^{-1}
+ * and a work matrix per structure (3 n^2 doubles) and nothing later.
+ * Structures have at most QEQ_DENSE_MAX_ATOMS atoms (else QEQ_ERR_CAPACITY).
+ * Atom arrays are packed by atom_offsets, device pointers, FP64 / int32.
+ * Calls of one handle are ordered on its stream; inputs must be ready there.
+ * ------------------------------------------------------------------------ */
+#define QEQ_DENSE_MAX_ATOMS 1024
+typedef struct qeq_dense_s* qeq_dense;
+
+qeq_status qeq_dense_create(const qeq_plan_desc* desc, void* cuda_stream, qeq_dense* out);
+void qeq_dense_destroy(qeq_dense dense);
+const char* qeq_dense_last_error(qeq_dense dense);
+
+/* E of every structure from the positions (N x 3) and species (N).
+ * Errors: QEQ_ERR_INVALID (non-finite position, species out of range). */
+qeq_status qeq_dense_assemble(qeq_dense dense, const double* d_pos, const int32_t* d_species);
+
+/* A'^{-1} of every structure with hardness d_J (N, > 0), cached until the
+ * next call.  Errors: QEQ_ERR_NOT_PD (E + diag J not positive definite),
+ * QEQ_ERR_INVALID (qeq_dense_assemble not called). */
+qeq_status qeq_dense_invert(qeq_dense dense, const double* d_J);
+
+/* Charges d_q (N) and multipliers d_mu (n_struct, may be NULL) for the
+ * electronegativities d_chi (N) and the total charges h_qtot (host,
+ * n_struct; NULL: neutral). */
+qeq_status qeq_dense_charges(qeq_dense dense, const double* d_chi, const double* h_qtot,
+                             double* d_q, double* d_mu);
+
+/* Backward pass of qeq_dense_charges for a loss gradient d_gq = dL/dq (N):
+ * d_gchi = dL/dchi (N); d_gJ = dL/dJ (N, may be NULL; then d_q may be NULL). */
+qeq_status qeq_dense_backward(qeq_dense dense, const double* d_q, const double* d_gq,
+                              double* d_gchi, double* d_gJ);
+
+/* Copy E (which = 0, n x n) or A'^{-1} (which = 1, (n+1) x (n+1)) of
+ * structure s, row-major, to d_out (device). */
+qeq_status qeq_dense_matrix(qeq_dense dense, int32_t s, int32_t which, double* d_out);
+
+/* The Ewald width and G-vector count chosen for structure s, and the kernels
+ * launched by the handle so far (any pointer may be NULL). */
+qeq_status qeq_dense_query(qeq_dense dense, int32_t s, double* h_omega, int32_t* h_ng,
+                           int64_t* h_launches);
 
 /* ------------------------------------------------------------------------
  * Learned warm start (the paper's atomic neural networks, SI "Feed-Forward

@@ -673,7 +673,15 @@ constexpr double kPreBetaOneX = 150.0;
 // the stages backwards and writes layout L3 [z][x][y] (np adjacent y per x).
 // MAXS: most species of any structure of the plan (2: one complex mesh, the common case;
 // 8: any).
-template <typename T, bool PRE, int MAXS>
+// VIR: instead of the multiply and the inverse FFT, the strain derivative of the
+// reciprocal energy Q(x) = sum_m sum_st conj(x_s(m)) g_st(m) x_t(m) of the charges on
+// the mesh (the quadratic form behind the matvec): g_st = (4 pi/V) b(m) exp(-G^2 w_st^2/2)/G^2
+// changes with a homogeneous strain through dG^2/d eps_ab = -2 G_a G_b and dV = V tr(eps),
+//   dQ/d eps_ab = sum_m sum_st E_st(m) [-delta_ab + G_a G_b (w_st^2 + 2/G^2)].
+// Each unit writes its 7 sums {sum E, (sum E_st (w_st^2 + 2/G^2)) G_a G_b for ab = xx, yy,
+// zz, xy, xz, yz} to vir[8 u ..] (dst reinterpreted), in a fixed order: a line that is
+// not its own mirror stands for itself and its mirror (weight 2).
+template <typename T, bool PRE, int MAXS, bool VIR = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                   const int4* __restrict__ items, int nitems, int TLX, int sub, int Kmax, int ldmax,
@@ -763,6 +771,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     const Geo nxt = geo(u + gridDim.x);
     if (threadIdx.x < 32 && nxt.ok) issue(nxt, b ^ 1, 0);
     if (!cur.ok) {
+      if constexpr (VIR) {
+        if (threadIdx.x < 8) reinterpret_cast<double*>(dst)[8 * (int64_t)u + threadIdx.x] = 0.0;
+      }
       cur = nxt;
       continue;
     }
@@ -803,6 +814,72 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     const int nspec = S.S;
     // forward x FFT, every stage in place: block order
     stages_fwd_inplace<T>(tile, nsl, ld, fp, fp.nst, tw, (T)-1);
+    if constexpr (VIR) {
+      const int K1 = S.K[1], K2 = S.K[2];
+      double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+      for (int w = threadIdx.x; w < np * K; w += blockDim.x) {
+        const int l = (int)fdiv((uint32_t)w, fp.fK), p = w - l * K;
+        const int mx = freq[p];
+        const int mmx = (mx == 0) ? 0 : K - mx;
+        const int p2 = pos[mmx];
+        const int c0 = (mx <= K / 2) ? mx : mx - K;
+        const double Gx = (double)c0 * S.B[0] + (double)lineg[l][0];
+        const double Gy = (double)c0 * S.B[1] + (double)lineg[l][1];
+        const double Gz = (double)c0 * S.B[2] + (double)lineg[l][2];
+        const double G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+        if (!(G2 > 0.0)) continue;  // G = 0 term dropped
+        const double rG2 = 1.0 / G2;
+        const int y = cur.y0 + l;
+        const double wt = ((K1 - y) % K1 == y && (K2 - cur.z) % K2 == cur.z) ? 1.0 : 2.0;
+        const double pref = wt * (double)lineg[l][3] * (double)bm0[mx] * rG2;
+        V Qh[MAXS];
+#pragma unroll
+        for (int c = 0; c < HX; ++c) {
+          if (c >= ncm) break;
+          const V za = tile[(size_t)(c * np + l) * ld + p];
+          const V zb = tile[(size_t)((ncm + c) * np + l) * ld + p2];
+          Qh[2 * c] = {(T)0.5 * (za.x + zb.x), (T)0.5 * (za.y - zb.y)};
+          Qh[2 * c + 1] = {(T)0.5 * (za.y + zb.y), (T)-0.5 * (za.x - zb.x)};
+        }
+        double e = 0.0, k = 0.0;
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+          if (s >= nspec) break;
+#pragma unroll
+          for (int t = 0; t < MAXS; ++t) {
+            if (t >= nspec) break;
+            const int st_ = s * QEQ_MAX_SPECIES + t;
+            const double E = pref * exp2_mesh<double>(G2 * (double)hw2[st_]) *
+                             ((double)Qh[s].x * Qh[t].x + (double)Qh[s].y * Qh[t].y);
+            e += E;
+            k += E * (S.w2[st_] + 2.0 * rG2);
+          }
+        }
+        acc[0] += e;
+        acc[1] += k * Gx * Gx;
+        acc[2] += k * Gy * Gy;
+        acc[3] += k * Gz * Gz;
+        acc[4] += k * Gx * Gy;
+        acc[5] += k * Gx * Gz;
+        acc[6] += k * Gy * Gz;
+      }
+      // fixed-order block sums: shuffle tree per warp, then warps in order
+      __shared__ double vred[7][8];
+#pragma unroll
+      for (int i = 0; i < 7; ++i) {
+        double a = acc[i];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) vred[i][threadIdx.x >> 5] = a;
+      }
+      __syncthreads();
+      if (threadIdx.x < 8) {
+        double a = 0.0;
+        if (threadIdx.x < 7)
+          for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += vred[threadIdx.x][i];
+        reinterpret_cast<double*>(dst)[8 * (int64_t)u + threadIdx.x] = a;
+      }
+      __syncthreads();  // the buffer is free for the unit after next
+    } else {
     // reciprocal multiply; each Gaussian is one exp2
     for (int w = threadIdx.x; w < np * K; w += blockDim.x) {
       const int l = (int)fdiv((uint32_t)w, fp.fK), p = w - l * K;
@@ -889,6 +966,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     QEQ_RADIX_SWITCH(fp.radix[0], QEQ_CALL)
 #undef QEQ_CALL
     __syncthreads();  // the buffer is free for the unit after next
+    }  // VIR
     cur = nxt;
   }
 }

@@ -758,11 +758,100 @@ cudaError_t set_smem_attrs() {
     if (std::is_same<T, float>::value)
       QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<float, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         big));
+    if (std::is_same<T, double>::value) {
+      QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<double, false, 2, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+      QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<double, false, QEQ_MAX_SPECIES, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    }
   }
   return cudaSuccess;
 }
 
+// FP64 potential meshes of x (spread and the five FFT passes; no gather): the mesh
+// buffer then holds phi_s in layout L0 for the force and embedding kernels
+template <int P>
+cudaError_t potential_impl(qeq_plan_s* Pl, const double* x) {
+  cudaStream_t s = Pl->stream;
+  double2* mesh = Pl->d_mesh;
+  count_launch(Pl, 6);
+  k_spread<double, P><<<Pl->total_bricks, 256, spread_smem<double, P>(), s>>>(
+      Pl->d_st, Pl->d_brick_struct, Pl->d_brick_cand, Pl->d_bin_start, Pl->d_base, Pl->d_wts, Pl->d_spec, x, nullptr,
+      Pl->d_sc, 0, mesh);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  return launch_fft_passes<double, false>(Pl, Pl->geo, Pl->fft_kmax, Pl->d_st, Pl->d_zitems, Pl->n_zitems,
+                                         Pl->d_yitems, Pl->n_yitems, Pl->d_yiitems, Pl->n_yiitems, Pl->d_xitems,
+                                         Pl->n_xitems, 0, mesh, Pl->d_mesh2, Pl->max_species,
+                                         []() { return cudaSuccess; });
+}
+
+// Strain derivative sums of the reciprocal quadratic form of x (FP64): spread, forward z
+// and y passes, then the x pass in its VIR mode, which leaves 8 doubles per x-pass unit
+// in d_mesh2 (units of structure s: items xitem_off[s] .. xitem_off[s+1], times *nsub_out)
+template <int P>
+cudaError_t virial_impl(qeq_plan_s* Pl, const double* x, int* nsub_out) {
+  cudaStream_t s = Pl->stream;
+  double2* a = Pl->d_mesh;
+  double2* b = Pl->d_mesh2;
+  const FftGeom& g = Pl->geo;
+  const int* kmax = Pl->fft_kmax;
+  count_launch(Pl, 4);
+  k_spread<double, P><<<Pl->total_bricks, 256, spread_smem<double, P>(), s>>>(
+      Pl->d_st, Pl->d_brick_struct, Pl->d_brick_cand, Pl->d_bin_start, Pl->d_base, Pl->d_wts, Pl->d_spec, x, nullptr,
+      Pl->d_sc, 0, a);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  const int sub = g.sub64, subx = g.subx64;
+  const int nsub = (g.tl + sub - 1) / sub, nsubx = (g.tlx + subx - 1) / subx;
+  const size_t smz = 128 + 2 * (size_t)fft_buf(kmax[2], g.ldz64, sub, sizeof(double2), 1, 0).bytes;
+  const size_t smy = 128 + 2 * (size_t)fft_buf(kmax[1], g.ldy64, sub, sizeof(double2), 1, 0).bytes;
+  {
+    auto fn = k_fft_tile<double, PASS_ZF>;
+    fn<<<fft_grid(Pl, (const void*)fn, smz, Pl->n_zitems * nsub), 256, smz, s>>>(
+        Pl->d_st, Pl->d_fft, Pl->d_zitems, Pl->n_zitems, g.tl, sub, kmax[2], g.ldz64, Pl->d_tw64, Pl->d_tw32,
+        Pl->d_fft_tabs, Pl->d_sc, 0, a, b, Pl->d_err);
+    QEQ_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    auto fn = k_fft_tile<double, PASS_YF>;
+    fn<<<fft_grid(Pl, (const void*)fn, smy, Pl->n_yitems * nsub), 256, smy, s>>>(
+        Pl->d_st, Pl->d_fft, Pl->d_yitems, Pl->n_yitems, g.tl, sub, kmax[1], g.ldy64, Pl->d_tw64, Pl->d_tw32,
+        Pl->d_fft_tabs, Pl->d_sc, 0, b, a, Pl->d_err);
+    QEQ_CUDA_TRY(cudaGetLastError());
+  }
+  const int nx = Pl->n_xitems;
+  if (Pl->max_species <= 2) {
+    auto fn = k_fft_x_green<double, false, 2, true>;
+    const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], g.ldx64, 2 * subx, sizeof(double2), 2,
+                                                 fft_x_extra(subx, 1, sizeof(double))).bytes;
+    fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+        Pl->d_st, Pl->d_fft, Pl->d_xitems, nx, g.tlx, subx, kmax[0], g.ldx64, Pl->d_bmod, Pl->d_tw64, Pl->d_tw32,
+        Pl->d_fft_tabs, Pl->d_sc, 0, a, b, Pl->d_err, 0);
+  } else {
+    constexpr int HX = QEQ_MAX_SPECIES / 2;
+    auto fn = k_fft_x_green<double, false, QEQ_MAX_SPECIES, true>;
+    const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], g.ldx64, 2 * HX * subx, sizeof(double2), 2,
+                                                 fft_x_extra(subx, HX, sizeof(double))).bytes;
+    fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+        Pl->d_st, Pl->d_fft, Pl->d_xitems, nx, g.tlx, subx, kmax[0], g.ldx64, Pl->d_bmod, Pl->d_tw64, Pl->d_tw32,
+        Pl->d_fft_tabs, Pl->d_sc, 0, a, b, Pl->d_err, 0);
+  }
+  *nsub_out = nsubx;
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_mesh_virial(qeq_plan_s* P, const double* x, int* nsub_out) {
+  if (P->max_p == 4) return virial_impl<4>(P, x, nsub_out);
+  if (P->max_p == 6) return virial_impl<6>(P, x, nsub_out);
+  return virial_impl<8>(P, x, nsub_out);
+}
+
+cudaError_t launch_mesh_potential(qeq_plan_s* P, const double* x) {
+  if (P->max_p == 4) return potential_impl<4>(P, x);
+  if (P->max_p == 6) return potential_impl<6>(P, x);
+  return potential_impl<8>(P, x);
+}
 
 cudaError_t matvec_set_attributes() {
   QEQ_CUDA_TRY((set_smem_attrs<float, 4>()));

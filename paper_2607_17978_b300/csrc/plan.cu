@@ -18,37 +18,6 @@ namespace {
 
 const double kPi = 3.14159265358979323846;
 
-double det3(const double* h) {
-  return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
-         h[2] * (h[3] * h[7] - h[4] * h[6]);
-}
-
-void inv3(const double* h, double* hi) {
-  double d = det3(h);
-  hi[0] = (h[4] * h[8] - h[5] * h[7]) / d;
-  hi[1] = (h[2] * h[7] - h[1] * h[8]) / d;
-  hi[2] = (h[1] * h[5] - h[2] * h[4]) / d;
-  hi[3] = (h[5] * h[6] - h[3] * h[8]) / d;
-  hi[4] = (h[0] * h[8] - h[2] * h[6]) / d;
-  hi[5] = (h[2] * h[3] - h[0] * h[5]) / d;
-  hi[6] = (h[3] * h[7] - h[4] * h[6]) / d;
-  hi[7] = (h[1] * h[6] - h[0] * h[7]) / d;
-  hi[8] = (h[0] * h[4] - h[1] * h[3]) / d;
-}
-
-// x with erfc(x) = y, by bisection (erfc is decreasing)
-double erfc_inv(double y) {
-  double lo = 0.0, hi = 30.0;
-  for (int i = 0; i < 200; ++i) {
-    double mid = 0.5 * (lo + hi);
-    if (erfc(mid) > y)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return 0.5 * (lo + hi);
-}
-
 bool smooth235(int n) {
   for (int f : {2, 3, 5})
     while (n % f == 0) n /= f;
@@ -111,16 +80,6 @@ cudaError_t upload(qeq_plan_s* P, T** ptr, const std::vector<T>& v) {
 double sphere_int(double a, double rc) {
   double tail = (0.25 * a * a - 0.5 * rc * rc) * erfc(rc / a) + a * rc / (2.0 * sqrt(kPi)) * exp(-rc * rc / (a * a));
   return 0.25 * a * a - tail;
-}
-
-// perpendicular distances between opposite faces of the cell
-void plane_widths(const double* h, double V, double* wd) {
-  for (int d = 0; d < 3; ++d) {
-    const double* a1 = h + 3 * ((d + 1) % 3);
-    const double* a2 = h + 3 * ((d + 2) % 3);
-    double cx = a1[1] * a2[2] - a1[2] * a2[1], cy = a1[2] * a2[0] - a1[0] * a2[2], cz = a1[0] * a2[1] - a1[1] * a2[0];
-    wd[d] = V / sqrt(cx * cx + cy * cy + cz * cz);
-  }
 }
 
 // Ewald split width from the real-space cutoff: erfc(r_cut / (sqrt2 omega)) = ewald_tol / 10
@@ -191,7 +150,7 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems, P->d_pyiitems, P->d_fft_tabs,
                   P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
-                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject};
+                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject,  P->d_xitem_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -462,10 +421,13 @@ static qeq_status build_plan(qeq_plan_s* P) {
   }
   // --- FFT tile sizes from the largest mesh of the plan, then the work lists
   P->geo = fft_geometry(maxK, (max_s + 1) / 2);
-  for (int s = 0; s < ns; ++s)
+  std::vector<int> xoff(1, 0);
+  for (int s = 0; s < ns; ++s) {
     fft_work_lists(hs[s], s, P->geo.tl, P->geo.tlx, [&](int4 v) { zit.push_back(v); },
                    [&](int4 v) { yit.push_back(v); }, [&](int4 v) { yiit.push_back(v); },
                    [&](int4 v) { xit.push_back(v); });
+    xoff.push_back((int)xit.size());
+  }
   // --- Fourier preconditioner: a coarse mesh per structure (spacing ~2 A, cubic B-splines)
   std::vector<StructDev> hsp;
   std::vector<int4> pzit, pyit, pyiit, pxit;
@@ -595,6 +557,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(upload(P, &P->d_zitems, zit));
   ALLOC(upload(P, &P->d_yitems, yit));
   ALLOC(upload(P, &P->d_xitems, xit));
+  ALLOC(upload(P, &P->d_xitem_off, xoff));
   ALLOC(upload(P, &P->d_yiitems, yiit));
   ALLOC(upload(P, &P->d_fft_tabs, tabs));
   ALLOC(upload(P, &P->d_bin_struct, bin_struct));

@@ -143,25 +143,6 @@ __global__ void k_sort_bins(const int* __restrict__ bin_start, int nbins, int* _
   }
 }
 
-// Cardinal B-spline values M_p(w + j), j = 0..p-1, w in [0,1), by the order recursion
-// M_n(x) = [x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)] / (n - 1), starting from M_2.
-__device__ __forceinline__ void bspline_weights(double w, int p, double* out) {
-  double a[QEQ_MAXP];
-  a[0] = w;
-  a[1] = 1.0 - w;
-  for (int n = 2; n < p; ++n) {  // a[j] = M_n(w + j), j < n  ->  M_{n+1}
-    double inv = 1.0 / n;
-    a[n] = 0.0;
-    for (int j = n; j >= 0; --j) {
-      double x = w + j;
-      double left = a[j];
-      double right = (j > 0) ? a[j - 1] : 0.0;
-      a[j] = (x * left + (n + 1 - x) * right) * inv;
-    }
-  }
-  for (int j = 0; j < p; ++j) out[j] = a[j];
-}
-
 __global__ void k_gather_sorted(const StructDev* __restrict__ st, const int* __restrict__ atom_struct,
                                 const int* __restrict__ perm, int64_t n, const double* __restrict__ pos,
                                 const int32_t* __restrict__ species, const double* __restrict__ chi,

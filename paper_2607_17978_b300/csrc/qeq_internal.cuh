@@ -61,6 +61,49 @@ struct StructDev {
   int pad3_;
 };
 
+// ---------------------------------------------------------------- host cell geometry
+inline double det3(const double* h) {
+  return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+         h[2] * (h[3] * h[7] - h[4] * h[6]);
+}
+
+// inverse of the row-major 3x3 matrix h
+inline void inv3(const double* h, double* hi) {
+  double d = det3(h);
+  hi[0] = (h[4] * h[8] - h[5] * h[7]) / d;
+  hi[1] = (h[2] * h[7] - h[1] * h[8]) / d;
+  hi[2] = (h[1] * h[5] - h[2] * h[4]) / d;
+  hi[3] = (h[5] * h[6] - h[3] * h[8]) / d;
+  hi[4] = (h[0] * h[8] - h[2] * h[6]) / d;
+  hi[5] = (h[2] * h[3] - h[0] * h[5]) / d;
+  hi[6] = (h[3] * h[7] - h[4] * h[6]) / d;
+  hi[7] = (h[1] * h[6] - h[0] * h[7]) / d;
+  hi[8] = (h[0] * h[4] - h[1] * h[3]) / d;
+}
+
+// x with erfc(x) = y, by bisection (erfc is decreasing)
+inline double erfc_inv(double y) {
+  double lo = 0.0, hi = 30.0;
+  for (int i = 0; i < 200; ++i) {
+    double mid = 0.5 * (lo + hi);
+    if (erfc(mid) > y)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// perpendicular distances between opposite faces of the cell
+inline void plane_widths(const double* h, double V, double* wd) {
+  for (int d = 0; d < 3; ++d) {
+    const double* a1 = h + 3 * ((d + 1) % 3);
+    const double* a2 = h + 3 * ((d + 2) % 3);
+    double cx = a1[1] * a2[2] - a1[2] * a2[1], cy = a1[2] * a2[0] - a1[0] * a2[2], cz = a1[0] * a2[1] - a1[1] * a2[0];
+    wd[d] = V / sqrt(cx * cx + cy * cy + cz * cz);
+  }
+}
+
 // Division by a runtime-invariant divisor d with a multiply and a shift
 // (round-up method of Granlund & Montgomery): n / d = (umulhi(n, m) + n) >> s
 // for 0 <= n < 2^31.
@@ -80,6 +123,25 @@ __host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
 
 #ifdef __CUDACC__
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.s; }
+
+// Cardinal B-spline values M_p(w + j), j = 0..p-1, w in [0,1), by the order recursion
+// M_n(x) = [x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)] / (n - 1), starting from M_2.
+__device__ __forceinline__ void bspline_weights(double w, int p, double* out) {
+  double a[QEQ_MAXP];
+  a[0] = w;
+  a[1] = 1.0 - w;
+  for (int n = 2; n < p; ++n) {  // a[j] = M_n(w + j), j < n  ->  M_{n+1}
+    double inv = 1.0 / n;
+    a[n] = 0.0;
+    for (int j = n; j >= 0; --j) {
+      double x = w + j;
+      double left = a[j];
+      double right = (j > 0) ? a[j - 1] : 0.0;
+      a[j] = (x * left + (n + 1 - x) * right) * inv;
+    }
+  }
+  for (int j = 0; j < p; ++j) out[j] = a[j];
+}
 #endif
 
 // Mixed-radix plan of one FFT length K = R_0 ... R_{m-1} (see fft.cuh): stage s has
@@ -128,7 +190,7 @@ struct PcgScalars {
   double shift;       // (1^T D^-1 r)/(1^T D^-1 1)
   double qsum;
   double pAp;
-  double r_sum, r_sq, r_max, r_min;   // residual statistics of the current r
+  double r_sum, r_l2, r_max, r_min;   // statistics of the current r: sum, ||P r||_2, max, min
   double tol_inf;     // stop threshold on max |P r|
   double tol_l2;      // optional stop threshold on ||P r||_2 (0 = off)
   double inner;       // factor on both thresholds for the iteration's own (recurrence) residual
@@ -228,6 +290,7 @@ struct qeq_plan_s {
   int4* d_yitems = nullptr;        // forward y pass {s, c, z, x0}
   int4* d_yiitems = nullptr;       // inverse y pass {s, c, x, z0}
   int4* d_xitems = nullptr;        // x pass {s, z, y0, lines}
+  int* d_xitem_off = nullptr;      // n_struct + 1: first x item of each structure
   int* d_bin_struct = nullptr;     // structure of each global bin
   int* d_brick_struct = nullptr;   // structure of each global brick
   int* d_brick_cand = nullptr;     // QEQ_BRICK_CAND ints per brick (brick_candidates)
@@ -502,6 +565,16 @@ cudaError_t launch_prepare_atoms(qeq_plan_s* P, const double* pos, const int32_t
 cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, int with_J,
                           int use_active, int fuse_pAp, cudaEvent_t* ev /* QEQ_N_STAGES+1 or NULL */);
 cudaError_t matvec_set_attributes();
+// FP64 potential meshes of x (sorted order) in d_mesh, layout L0 (no gather)
+cudaError_t launch_mesh_potential(qeq_plan_s* P, const double* x);
+// strain-derivative sums of the reciprocal quadratic form of x (FP64): 8 doubles per x-pass
+// unit in d_mesh2; *nsub_out = units per x item
+cudaError_t launch_mesh_virial(qeq_plan_s* P, const double* x, int* nsub_out);
+// launchers (forces.cu): force-trick forces and embedding potentials (input order in and out)
+cudaError_t launch_forces(qeq_plan_s* P, const double* q, const double* lambda, double* F);
+cudaError_t launch_embedding(qeq_plan_s* P, const double* q, double* Gamma);
+// D[9 s + 3 a + b] = d/d eps_ab [(q/2 + lambda)^T E q] per structure (lambda may be NULL)
+cudaError_t launch_stress(qeq_plan_s* P, const double* q, const double* lambda, double* D);
 cudaError_t launch_precond_setup(qeq_plan_s* P);
 // u = M^-1 r for the Fourier preconditioner; sum of u per structure into usum (slot 0) or w1sum (slot 1)
 cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, int use_active);

@@ -133,17 +133,21 @@ __global__ void k_project(const Chunk* __restrict__ chunks, double* __restrict__
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) q[a] += d;
 }
 
-// residual statistics -> convergence test (thread 0 of the last chunk)
-__device__ void residual_test(PcgScalars& c, const double* tot, int max_iter, int final_check) {
+// residual statistics -> convergence test (thread 0 of the last chunk).  tot[1], tot[2]
+// are sums of r - ref and (r - ref)^2 about a reference ref close to the mean of r (the
+// previous shift): r carries mu 1, and sums of r and r^2 themselves would lose the
+// projected part, sum (r - mean)^2 = tot[2] - tot[1]^2 / n, to cancellation.
+__device__ void residual_test(PcgScalars& c, const double* tot, double ref, int max_iter, int final_check) {
   double n = (double)c.n;
-  c.r_sum = tot[1];
-  c.r_sq = tot[2];
+  const double dmean = tot[1] / n;
+  c.r_sum = ref * n + tot[1];
   c.r_max = tot[3];
   c.r_min = tot[4];
   c.shift = tot[0] / c.s0;
-  double mean = c.r_sum / n;
+  const double mean = ref + dmean;
   double pinf = fmax(c.r_max - mean, mean - c.r_min);
-  double pl2 = sqrt(fmax(c.r_sq - c.r_sum * mean, 0.0));
+  double pl2 = sqrt(fmax(tot[2] - tot[1] * dmean, 0.0));
+  c.r_l2 = pl2;
   // the iterations stop a margin below the threshold of the final check, so that
   // the drift of the recurrence residual (FP32 matvec) rarely forces a restart
   const double f = final_check ? 1.0 : c.inner;
@@ -168,21 +172,22 @@ __global__ void k_resid(const Chunk* __restrict__ chunks, const double* __restri
                         const double* __restrict__ dinv, double* __restrict__ r, PcgScalars* __restrict__ sc,
                         int only_flagged, double* part, int* counter, int max_iter) {
   const Chunk ch = chunks[blockIdx.x];
+  const double ref = sc[ch.s].shift;
   double v[5] = {0, 0, 0, -1e300, 1e300};
   const int op[5] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX, RED_MIN};
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
     double ra = -chi[a] - Aq[a];
     r[a] = ra;
     v[0] += dinv[a] * ra;
-    v[1] += ra;
-    v[2] += ra * ra;
+    v[1] += ra - ref;
+    v[2] += (ra - ref) * (ra - ref);
     v[3] = fmax(v[3], ra);
     v[4] = fmin(v[4], ra);
   }
   double tot[5];
   if (chunk_reduce<5>(v, op, ch, part, counter, tot)) {
     sc[ch.s].slack = 0.0;
-    residual_test(sc[ch.s], tot, max_iter, 1);
+    residual_test(sc[ch.s], tot, ref, max_iter, 1);
   }
   (void)only_flagged;
 }
@@ -218,6 +223,7 @@ __global__ void k_resid_delta(const Chunk* __restrict__ chunks, const double* __
                               double* __restrict__ r, PcgScalars* __restrict__ sc, double* part, int* counter,
                               int max_iter, double op_err) {
   const Chunk ch = chunks[blockIdx.x];
+  const double ref = sc[ch.s].shift;
   double v[6] = {0, 0, 0, -1e300, 1e300, 0};
   const int op[6] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX, RED_MIN, RED_MAX};
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
@@ -226,8 +232,8 @@ __global__ void k_resid_delta(const Chunk* __restrict__ chunks, const double* __
     r[a] = ra;
     Ad[a] = -chi[a] - ra;
     v[0] += dinv[a] * ra;
-    v[1] += ra;
-    v[2] += ra * ra;
+    v[1] += ra - ref;
+    v[2] += (ra - ref) * (ra - ref);
     v[3] = fmax(v[3], ra);
     v[4] = fmin(v[4], ra);
     v[5] = fmax(v[5], fabs(ad));
@@ -236,7 +242,7 @@ __global__ void k_resid_delta(const Chunk* __restrict__ chunks, const double* __
   if (chunk_reduce<6>(v, op, ch, part, counter, tot)) {
     PcgScalars& c = sc[ch.s];
     c.slack = op_err * (tot[5] + c.dmaxD * c.dmax);
-    residual_test(c, tot, max_iter, 1);
+    residual_test(c, tot, ref, max_iter, 1);
   }
 }
 
@@ -256,6 +262,7 @@ __global__ void k_update(const Chunk* __restrict__ chunks, const double* __restr
   const Chunk ch = chunks[blockIdx.x];
   if (!sc[ch.s].active) return;
   const double alpha = sc[ch.s].alpha;
+  const double ref = sc[ch.s].shift;
   double v[5] = {0, 0, 0, -1e300, 1e300};
   const int op[5] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX, RED_MIN};
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
@@ -263,8 +270,8 @@ __global__ void k_update(const Chunk* __restrict__ chunks, const double* __restr
     double ra = r[a] - alpha * Ap[a];
     r[a] = ra;
     v[0] += dinv[a] * ra;
-    v[1] += ra;
-    v[2] += ra * ra;
+    v[1] += ra - ref;
+    v[2] += (ra - ref) * (ra - ref);
     v[3] = fmax(v[3], ra);
     v[4] = fmin(v[4], ra);
   }
@@ -272,11 +279,15 @@ __global__ void k_update(const Chunk* __restrict__ chunks, const double* __restr
   if (chunk_reduce<5>(v, op, ch, part, counter, tot)) {
     PcgScalars& c = sc[ch.s];
     c.iters += 1;
-    residual_test(c, tot, max_iter, 0);
+    residual_test(c, tot, ref, max_iter, 0);
   }
 }
 
-// z = D^-1 (r - shift); rz_new = r.z; beta
+// z = D^-1 (r - shift); rz_new = r.z; beta.  Since 1^T z = 0, r.z = (r - shift).z; the
+// second form is the one summed: r itself carries mu 1 (several eV), and near convergence
+// shift * sum z (rounding of order eps mu) would swamp the projected part of r.z, which
+// then corrupts alpha and beta and lets q wander along A^-1 1, a direction the projected
+// residual does not see.  As summed, r.z = sum D^-1 (r - shift)^2 >= 0.
 __global__ void k_precond(const Chunk* __restrict__ chunks, const double* __restrict__ r, const double* __restrict__ dinv,
                           double* __restrict__ z, PcgScalars* __restrict__ sc, int restart, double* part, int* counter) {
   const Chunk ch = chunks[blockIdx.x];
@@ -285,9 +296,10 @@ __global__ void k_precond(const Chunk* __restrict__ chunks, const double* __rest
   double v[1] = {0};
   const int op[1] = {RED_SUM};
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
-    double za = dinv[a] * (r[a] - sh);
+    const double rp = r[a] - sh;
+    double za = dinv[a] * rp;
     z[a] = za;
-    v[0] += r[a] * za;
+    v[0] += rp * za;
   }
   double tot[1];
   if (chunk_reduce<1>(v, op, ch, part, counter, tot)) {
@@ -312,12 +324,13 @@ __global__ void k_proj_rz(const Chunk* __restrict__ chunks, const double* __rest
   double v[2] = {0, 0};
   const int op[2] = {RED_SUM, RED_SUM};
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    const double rp = r[a] - sh;  // both directions sum to zero: dot with r - shift (see k_precond)
     double za = u[a] - f * w1[a];
-    double zja = dinv[a] * (r[a] - sh);
+    double zja = dinv[a] * rp;
     z[a] = za;
     zj[a] = zja;
-    v[0] += r[a] * za;
-    v[1] += r[a] * zja;
+    v[0] += rp * za;
+    v[1] += rp * zja;
   }
   double tot[2];
   if (chunk_reduce<2>(v, op, ch, part, counter, tot)) {
@@ -996,7 +1009,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     const PcgScalars& c = h[i];
     double n = (double)c.n, mean = c.r_sum / n;
     double pinf = fmax(c.r_max - mean, mean - c.r_min);
-    double pl2 = sqrt(fmax(c.r_sq - c.r_sum * mean, 0.0));
+    double pl2 = c.r_l2;
     if (h_info) {
       h_info[i].status = c.status;
       h_info[i].iterations = c.iters;
@@ -1066,6 +1079,53 @@ extern "C" qeq_status qeq_matvec(qeq_plan P, const double* d_pos, const int32_t*
   count_launch(P);
   k_unsort<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, P->d_Ap, d_y);
   TRY(cudaGetLastError());
+  return check_timeout(P);
+}
+
+extern "C" qeq_status qeq_forces(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_q,
+                                 const double* d_lambda, double* d_F) {
+  if (!P) return QEQ_ERR_INVALID;
+  if (!d_pos || !d_species || !d_q || !d_F) {
+    P->last_error = "null pointer";
+    return QEQ_ERR_INVALID;
+  }
+  TRY(cudaSetDevice(P->device));
+  TRY(launch_prepare_atoms(P, d_pos, d_species, nullptr, nullptr, 0));
+  qeq_status st = check_inputs(P);
+  if (st != QEQ_OK) return st;
+  TRY(launch_forces(P, d_q, d_lambda, d_F));
+  return check_timeout(P);
+}
+
+extern "C" qeq_status qeq_stress(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_q,
+                                 const double* d_lambda, double* d_D) {
+  if (!P) return QEQ_ERR_INVALID;
+  if (!d_pos || !d_species || !d_q || !d_D) {
+    P->last_error = "null pointer";
+    return QEQ_ERR_INVALID;
+  }
+  TRY(cudaSetDevice(P->device));
+  TRY(launch_prepare_atoms(P, d_pos, d_species, nullptr, nullptr, 0));
+  qeq_status st = check_inputs(P);
+  if (st != QEQ_OK) return st;
+  TRY(launch_stress(P, d_q, d_lambda, d_D));
+  return check_timeout(P);
+}
+
+extern "C" qeq_status qeq_embedding(qeq_plan P, const double* d_pos, const int32_t* d_species, const double* d_q,
+                                    double* d_Gamma) {
+  if (!P) return QEQ_ERR_INVALID;
+  if (!d_pos || !d_species || !d_q || !d_Gamma) {
+    P->last_error = "null pointer";
+    return QEQ_ERR_INVALID;
+  }
+  TRY(cudaSetDevice(P->device));
+  TRY(launch_prepare_atoms(P, d_pos, d_species, nullptr, nullptr, P->pair_cap > 0));
+  qeq_status st = check_inputs(P);
+  if (st != QEQ_OK) return st;
+  st = init_scalars(P, nullptr);
+  if (st != QEQ_OK) return st;
+  TRY(launch_embedding(P, d_q, d_Gamma));
   return check_timeout(P);
 }
 

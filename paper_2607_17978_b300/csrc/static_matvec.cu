@@ -85,36 +85,6 @@ constexpr size_t kStaticWorstCase() {
 }
 static_assert(kStaticWorstCase() <= QEQ_STATIC_SCRATCH_BYTES, "static scratch smaller than the worst case of the limits");
 
-double det3s(const double* h) {
-  return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
-         h[2] * (h[3] * h[7] - h[4] * h[6]);
-}
-
-void inv3s(const double* h, double* hi) {
-  double d = det3s(h);
-  hi[0] = (h[4] * h[8] - h[5] * h[7]) / d;
-  hi[1] = (h[2] * h[7] - h[1] * h[8]) / d;
-  hi[2] = (h[1] * h[5] - h[2] * h[4]) / d;
-  hi[3] = (h[5] * h[6] - h[3] * h[8]) / d;
-  hi[4] = (h[0] * h[8] - h[2] * h[6]) / d;
-  hi[5] = (h[2] * h[3] - h[0] * h[5]) / d;
-  hi[6] = (h[3] * h[7] - h[4] * h[6]) / d;
-  hi[7] = (h[1] * h[6] - h[0] * h[7]) / d;
-  hi[8] = (h[0] * h[4] - h[1] * h[3]) / d;
-}
-
-double erfc_inv_s(double y) {
-  double lo = 0.0, hi = 30.0;
-  for (int i = 0; i < 200; ++i) {
-    double mid = 0.5 * (lo + hi);
-    if (erfc(mid) > y)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return 0.5 * (lo + hi);
-}
-
 int next_smooth_s(int n) {
   for (;; ++n) {
     int m = n;
@@ -208,7 +178,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
     if (!std::isfinite(h_cell[k])) return QEQ_ERR_INVALID;
   for (int a = 0; a < n_species; ++a)
     if (!(h_sigma[a] > 0.0) || !std::isfinite(h_sigma[a])) return QEQ_ERR_NOT_PD;
-  const double V = fabs(det3s(h_cell));
+  const double V = fabs(det3(h_cell));
   if (!(V > 1e-9)) return QEQ_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
@@ -231,7 +201,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   memset(&T, 0, sizeof(T));
   const int S = n_species;
   for (int k = 0; k < 9; ++k) T.h[k] = h_cell[k];
-  inv3s(h_cell, T.hinv);
+  inv3(h_cell, T.hinv);
   T.V = V;
   for (int d = 0; d < 3; ++d)
     for (int c = 0; c < 3; ++c) T.B[3 * d + c] = 2.0 * kPiS * T.hinv[3 * c + d];
@@ -240,7 +210,7 @@ extern "C" qeq_status qeq_matvec_static(const double* h_cell, const double* h_si
   T.ncm = (S + 1) / 2;
   T.atom_begin = 0;
   T.atom_end = n_atoms;
-  const double omega = r_cut / (sqrt(2.0) * erfc_inv_s(0.1 * ewald_tol));
+  const double omega = r_cut / (sqrt(2.0) * erfc_inv(0.1 * ewald_tol));
   T.r_cut = r_cut;
   T.omega = omega;
   double wmin = 1e300;

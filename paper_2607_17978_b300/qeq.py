@@ -29,7 +29,10 @@ STAGE_NAMES = ["species_sums", "spread", "fft_z", "fft_y", "fft_x_green", "ifft_
 EXPORTED = ["qeq_plan_create", "qeq_plan_destroy", "qeq_plan_query", "qeq_solve", "qeq_energy", "qeq_matvec",
             "qeq_profile_matvec", "qeq_status_str", "qeq_last_error", "qeq_matvec_static", "qeq_mlp_create",
             "qeq_mlp_destroy", "qeq_mlp_set_params", "qeq_mlp_get_params", "qeq_mlp_set_adam_state",
-            "qeq_mlp_forward", "qeq_mlp_train_step", "qeq_features", "qeq_plan_set_warm_start"]
+            "qeq_mlp_forward", "qeq_mlp_train_step", "qeq_features", "qeq_plan_set_warm_start", "qeq_forces",
+            "qeq_embedding", "qeq_stress", "qeq_dense_create", "qeq_dense_destroy", "qeq_dense_last_error",
+            "qeq_dense_assemble", "qeq_dense_invert", "qeq_dense_charges", "qeq_dense_backward",
+            "qeq_dense_matrix", "qeq_dense_query"]
 MLP_NFEAT, MLP_NHIDDEN, MLP_NPARAM, MLP_RCUT = 32, 64, 6400, 6.0
 
 
@@ -109,6 +112,31 @@ def load_library(path: str = LIB_PATH):
     lib.qeq_energy.restype = ctypes.c_int
     lib.qeq_matvec.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int32]
     lib.qeq_matvec.restype = ctypes.c_int
+    lib.qeq_forces.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.qeq_forces.restype = ctypes.c_int
+    lib.qeq_dense_create.argtypes = [ctypes.POINTER(PlanDesc), vp, ctypes.POINTER(vp)]
+    lib.qeq_dense_create.restype = ctypes.c_int
+    lib.qeq_dense_destroy.argtypes = [vp]
+    lib.qeq_dense_destroy.restype = None
+    lib.qeq_dense_last_error.argtypes = [vp]
+    lib.qeq_dense_last_error.restype = ctypes.c_char_p
+    lib.qeq_dense_assemble.argtypes = [vp, vp, vp]
+    lib.qeq_dense_assemble.restype = ctypes.c_int
+    lib.qeq_dense_invert.argtypes = [vp, vp]
+    lib.qeq_dense_invert.restype = ctypes.c_int
+    lib.qeq_dense_charges.argtypes = [vp, vp, dp, vp, vp]
+    lib.qeq_dense_charges.restype = ctypes.c_int
+    lib.qeq_dense_backward.argtypes = [vp, vp, vp, vp, vp]
+    lib.qeq_dense_backward.restype = ctypes.c_int
+    lib.qeq_dense_matrix.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
+    lib.qeq_dense_matrix.restype = ctypes.c_int
+    lib.qeq_dense_query.argtypes = [vp, ctypes.c_int32, dp, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    lib.qeq_dense_query.restype = ctypes.c_int
+    lib.qeq_stress.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.qeq_stress.restype = ctypes.c_int
+    lib.qeq_embedding.argtypes = [vp, vp, vp, vp, vp]
+    lib.qeq_embedding.restype = ctypes.c_int
     lib.qeq_profile_matvec.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     lib.qeq_profile_matvec.restype = ctypes.c_int
     lib.qeq_status_str.argtypes = [ctypes.c_int]
@@ -299,6 +327,43 @@ class Plan:
                                         1 if fp64 else 0), "qeq_matvec")
         return y
 
+    def forces(self, pos, species, q, lam=None):
+        """Electrostatic forces of the force trick (qeq_forces): N x 3, input order."""
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        q = self._dev(q, torch.float64)
+        lt = self._dev(lam, torch.float64) if lam is not None else None
+        F = torch.empty(self.n_atoms, 3, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_forces(self.h, _ptr(pos), _ptr(species), _ptr(q), _ptr(lt), _ptr(F)),
+                    "qeq_forces")
+        return F
+
+    def stress(self, pos, species, q, lam=None):
+        """Strain derivative d/d eps [(q/2 + lam)^T E q] per structure (qeq_stress): n_struct x 3 x 3."""
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        q = self._dev(q, torch.float64)
+        lt = self._dev(lam, torch.float64) if lam is not None else None
+        D = torch.empty(self.n_struct, 3, 3, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_stress(self.h, _ptr(pos), _ptr(species), _ptr(q), _ptr(lt), _ptr(D)),
+                    "qeq_stress")
+        return D
+
+    def embedding(self, pos, species, q):
+        """Element-resolved potentials (qeq_embedding): N x n_species, input order."""
+        torch = self.torch
+        pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        species = self._dev(species, torch.int32)
+        q = self._dev(q, torch.float64)
+        G = torch.empty(self.n_atoms, self.n_species, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_embedding(self.h, _ptr(pos), _ptr(species), _ptr(q), _ptr(G)), "qeq_embedding")
+        return G
+
     def profile_matvec(self, n_rep: int = 10) -> dict:
         ms = (ctypes.c_float * QEQ_N_STAGES)()
         self._check(self.lib.qeq_profile_matvec(self.h, n_rep, ms), "qeq_profile_matvec")
@@ -432,6 +497,124 @@ def matvec_static(cell, sigma_s, pos, species, x, J=None, *, coulomb_k=14.399645
     if st != QEQ_OK:
         raise QEqError(st, "qeq_matvec_static: " + lib.qeq_status_str(st).decode())
     return y
+
+
+class Dense:
+    """4G charge training on cached dense matrices (qeq_dense_*): E per structure once, the
+    bordered inverse per hardness, charges and their backward pass as matrix-vector products."""
+
+    def __init__(self, cells, atom_offsets, sigma, *, coulomb_k=14.3996454784, ewald_tol=0.0, device=None):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda")
+        cells = np.ascontiguousarray(np.asarray(cells, np.float64).reshape(-1, 9))
+        offs = np.ascontiguousarray(np.asarray(atom_offsets, np.int64))
+        sigma = np.ascontiguousarray(np.atleast_2d(np.asarray(sigma, np.float64)))
+        self.n_struct = int(cells.shape[0])
+        if sigma.shape[0] != self.n_struct:
+            raise ValueError("sigma must have one row per structure")
+        self.n_species = int(sigma.shape[1])
+        self.n_atoms = int(offs[-1])
+        self.offsets = offs
+        self._keep = (cells, offs, sigma)
+        d = PlanDesc(self.n_struct, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                     cells.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.n_species,
+                     sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), coulomb_k, 0.0, ewald_tol,
+                     0.0, 0, 0.0, 0, 0, 0.0, 0, 0, 0.0, 0.0, 0.0)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(device=self.device)
+            h = ctypes.c_void_p()
+            st = self.lib.qeq_dense_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != QEQ_OK:
+            raise QEqError(st, "qeq_dense_create: " + self.lib.qeq_status_str(st).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.torch.cuda.synchronize(self.device)
+            self.lib.qeq_dense_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, x, dtype):
+        return self.torch.as_tensor(x, dtype=dtype, device=self.device).contiguous()
+
+    def _sync_in(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _sync_out(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _check(self, st, what):
+        if st != QEQ_OK:
+            msg = self.lib.qeq_dense_last_error(self.h).decode()
+            raise QEqError(st, f"{what}: {self.lib.qeq_status_str(st).decode()} ({msg})")
+
+    def assemble(self, pos, species):
+        torch = self.torch
+        self._pos = self._dev(pos, torch.float64).reshape(-1, 3)
+        self._spc = self._dev(species, torch.int32)
+        self._sync_in()
+        self._check(self.lib.qeq_dense_assemble(self.h, _ptr(self._pos), _ptr(self._spc)), "qeq_dense_assemble")
+
+    def invert(self, J):
+        self._J = self._dev(J, self.torch.float64)
+        self._sync_in()
+        self._check(self.lib.qeq_dense_invert(self.h, _ptr(self._J)), "qeq_dense_invert")
+
+    def charges(self, chi, q_tot=None):
+        torch = self.torch
+        chi = self._dev(chi, torch.float64)
+        qt = np.zeros(self.n_struct) if q_tot is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(q_tot, np.float64), (self.n_struct,)))
+        q = torch.empty(self.n_atoms, dtype=torch.float64, device=self.device)
+        mu = torch.empty(self.n_struct, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_dense_charges(self.h, _ptr(chi), qt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               _ptr(q), _ptr(mu)), "qeq_dense_charges")
+        self._sync_out()
+        return q, mu
+
+    def backward(self, q, gq):
+        torch = self.torch
+        q = self._dev(q, torch.float64)
+        gq = self._dev(gq, torch.float64)
+        gchi = torch.empty(self.n_atoms, dtype=torch.float64, device=self.device)
+        gJ = torch.empty(self.n_atoms, dtype=torch.float64, device=self.device)
+        self._sync_in()
+        self._check(self.lib.qeq_dense_backward(self.h, _ptr(q), _ptr(gq), _ptr(gchi), _ptr(gJ)), "qeq_dense_backward")
+        self._sync_out()
+        return gchi, gJ
+
+    def matrix(self, s, which=0):
+        n = int(self.offsets[s + 1] - self.offsets[s]) + (1 if which else 0)
+        out = self.torch.empty(n, n, dtype=self.torch.float64, device=self.device)
+        self._check(self.lib.qeq_dense_matrix(self.h, int(s), int(which), _ptr(out)), "qeq_dense_matrix")
+        self._sync_out()
+        return out
+
+    def query(self, s=0):
+        om, ng, nl = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64()
+        self._check(self.lib.qeq_dense_query(self.h, int(s), ctypes.byref(om), ctypes.byref(ng), ctypes.byref(nl)),
+                    "qeq_dense_query")
+        return {"omega": om.value, "n_g": ng.value, "kernel_launches": nl.value}
+
+
+def dense_for_structures(structs, **kw) -> Dense:
+    """Dense charge-training handle for a list of ``synth.Structure``."""
+    ns = max(s.n_species for s in structs)
+    cells = np.stack([s.cell for s in structs]).reshape(-1, 9)
+    offs = np.concatenate([[0], np.cumsum([s.n for s in structs])]).astype(np.int64)
+    sig = np.zeros((len(structs), ns))
+    for i, s in enumerate(structs):
+        sig[i, :s.n_species] = s.sigma_s
+    return Dense(cells, offs, sig, **kw)
 
 
 def plan_for_structures(structs, **kw) -> Plan:

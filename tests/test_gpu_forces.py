@@ -1,0 +1,287 @@
+"""GPU parity of the force trick's electrostatic forces (qeq_forces, SI eq. 4g_force_trick)
+and of the element-resolved embedding potentials (qeq_embedding, Sec. 2.2) against the FP64
+CPU oracle, through the C ABI.
+
+Forces are compared with the oracle's term-by-term Ewald derivative (itself pinned to central
+differences of the dense matrix on the CPU) and, on a few atoms, with those central
+differences directly.  Tolerance: the plane-wave part interpolates the potential meshes with
+the derivative of the B-spline weights, one order lower than the weights themselves, so the
+force error is a small multiple of the matvec's error budget ewald_tol: relative RMS (over
+the compared atoms, against the RMS force) within FORCE_TOL_FACTOR x ewald_tol.
+"""
+import numpy as np
+import pytest
+
+from oracle import qeq_oracle as O
+from paper_2607_17978_b300 import synth
+
+KE = synth.COULOMB_K_EV_A
+FORCE_TOL_FACTOR = 30.0
+pytestmark = pytest.mark.gpu
+
+
+def _plan(structs, **kw):
+    from paper_2607_17978_b300 import build, qeq
+    build.build()
+    return qeq.plan_for_structures(structs, **kw)
+
+
+def _rel_rms(a, b):
+    return float(np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)))
+
+
+def _charges(n, seed, neutral=True):
+    rng = np.random.default_rng(seed)
+    q = rng.normal(0.0, 0.7, size=n)
+    if neutral:
+        q -= q.mean()
+    lam = rng.normal(0.0, 0.3, size=n)
+    return q, lam - lam.mean()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_forces_parity_small_cell_every_atom(precision):
+    """216-atom rock-salt cell: every atom, with and without the lambda term (the forces are
+    FP64 in both plan precisions)."""
+    st = synth.workload(1)
+    tol = 1e-7
+    plan = _plan([st], precision=precision, ewald_tol=tol, r_cut=9.0)
+    q, lam = _charges(st.n, 1)
+    rows = np.arange(st.n)
+    for la in (None, lam):
+        F = plan.forces(st.pos, st.species, q, la).cpu().numpy()
+        ref = O.electrostatic_forces_ewald(st.cell, st.pos, st.sigma, q, rows, lam=la, k_e=KE)
+        err = _rel_rms(F, ref)
+        print(f"216 atoms {precision} lambda={la is not None}: rel RMS {err:.2e}, "
+              f"max {np.abs(F - ref).max() / np.abs(ref).max():.2e}")
+        assert err < FORCE_TOL_FACTOR * tol, err
+    # three atoms straight from central differences of the dense matrix
+    atoms = [0, 101, 215]
+    fd = O.electrostatic_forces_fd(st.cell, st.pos, st.sigma, q, lam, k_e=KE, atoms=atoms)
+    F = plan.forces(st.pos, st.species, q, lam).cpu().numpy()[atoms]
+    assert np.abs(F - fd).max() < FORCE_TOL_FACTOR * tol * np.abs(fd).max() * 3
+
+
+def test_forces_parity_uneven_batch():
+    """Uneven batch in one plan: triclinic cell with vacancies, ragged bins, random ionic
+    cells with 2-4 species and charged totals; every atom of every structure."""
+    structs = [synth.rocksalt(3, 5.64, 0.15, synth.rng_for(40, 0), vacancy_frac=0.05, shear_deg=10.0),
+               synth.rocksalt((2, 3, 2), 5.64, 0.2, synth.rng_for(40, 1))]
+    for s in range(3):
+        structs.append(synth.batch_workload(1, cfg_id=41, n_min=64, n_max=600, first=s)[0])
+    tol = 1e-6
+    plan = _plan(structs, ewald_tol=tol)
+    n = sum(s.n for s in structs)
+    q, lam = _charges(n, 2, neutral=False)
+    pos = np.concatenate([s.pos for s in structs])
+    spc = np.concatenate([s.species for s in structs]).astype(np.int32)
+    F = plan.forces(pos, spc, q, lam).cpu().numpy()
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+    for i, st in enumerate(structs):
+        sl = slice(off[i], off[i + 1])
+        ref = O.electrostatic_forces_ewald(st.cell, st.pos, st.sigma, q[sl], np.arange(st.n), lam=lam[sl], k_e=KE)
+        err = _rel_rms(F[sl], ref)
+        print(f"structure {i} ({st.n} atoms, {st.n_species} species): rel RMS {err:.2e}")
+        assert err < FORCE_TOL_FACTOR * tol, (i, err)
+
+
+def test_force_trick_end_to_end_on_the_gpu():
+    """The whole force trick on the GPU: q from qeq_solve, dE/dq = E q from qeq_matvec (FP64,
+    no hardness), lambda from a second qeq_solve with chi := E q and q_tot = 0, then
+    qeq_forces(q, lambda).  Against the oracle's dense solves and the Ewald derivative."""
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(1)
+    tol = 1e-7
+    plan = _plan([st], ewald_tol=tol, r_cut=9.0, charge_tol=1e-8)
+    pos, spc, chi, J, qt = qeq.pack([st])
+    q = plan.solve(pos, spc, chi, J, qt).q
+    dEdq = plan.matvec(pos, spc, q, fp64=True)
+    lam = plan.solve(pos, spc, dEdq, J, np.zeros(1)).q
+    assert abs(float(lam.sum())) < 1e-9
+    F = plan.forces(pos, spc, q, lam).cpu().numpy()
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=KE)
+    q_ref, _ = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+    lam_ref, _ = O.solve_bordered(A, st.J, A @ q_ref, 0.0)
+    ref = O.electrostatic_forces_ewald(st.cell, st.pos, st.sigma, q_ref, np.arange(st.n), lam=lam_ref, k_e=KE)
+    err = _rel_rms(F, ref)
+    print(f"force trick end to end: rel RMS {err:.2e}")
+    assert err < FORCE_TOL_FACTOR * tol + 1e-6, err
+
+
+def test_forces_full_size_13824_atoms_sampled():
+    """13,824-atom cell in the form the bench solves (mixed precision, Fourier preconditioner,
+    ewald_tol 1e-6, r_cut 8): 64 sampled atoms against the Ewald derivative."""
+    st = synth.workload(2)
+    tol = 1e-6
+    plan = _plan([st], precision="mixed", preconditioner="fourier", ewald_tol=tol, r_cut=8.0)
+    q, lam = _charges(st.n, 3)
+    rows = np.random.default_rng(4).choice(st.n, 64, replace=False)
+    F = plan.forces(st.pos, st.species, q, lam).cpu().numpy()[rows]
+    ref = O.electrostatic_forces_ewald(st.cell, st.pos, st.sigma, q, rows, lam=lam, k_e=KE, omega=6.0, tol=1e-12)
+    err = _rel_rms(F, ref)
+    print(f"13,824 atoms, 64 sampled: rel RMS {err:.2e}")
+    assert err < FORCE_TOL_FACTOR * tol, err
+
+
+def test_forces_full_size_980k_atoms_sampled():
+    """The 980,000-atom cell (480^3 mesh) the bench solves: 16 sampled atoms against the Ewald
+    derivative (one structure factor pass over every atom per charge vector on the host)."""
+    st = synth.workload(5)
+    tol = 1e-6
+    plan = _plan([st], precision="mixed", preconditioner="fourier", ewald_tol=tol, r_cut=8.0)
+    q, lam = _charges(st.n, 5)
+    rows = np.random.default_rng(6).choice(st.n, 16, replace=False)
+    F = plan.forces(st.pos, st.species, q, lam).cpu().numpy()[rows]
+    ref = O.electrostatic_forces_ewald(st.cell, st.pos, st.sigma, q, rows, lam=lam, k_e=KE, omega=11.0, tol=1e-12)
+    err = _rel_rms(F, ref)
+    print(f"980k atoms, 16 sampled: rel RMS {err:.2e}")
+    assert err < FORCE_TOL_FACTOR * tol, err
+
+
+def test_forces_reject_invalid_input_and_recover():
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(1)
+    plan = _plan([st])
+    q, _ = _charges(st.n, 7)
+    pb = st.pos.copy()
+    pb[4, 0] = np.inf
+    with pytest.raises(qeq.QEqError) as e:
+        plan.forces(pb, st.species, q)
+    assert e.value.status == qeq.QEQ_ERR_INVALID
+    sb = st.species.copy()
+    sb[0] = 5
+    with pytest.raises(qeq.QEqError) as e:
+        plan.forces(st.pos, sb, q)
+    assert e.value.status == qeq.QEQ_ERR_INVALID
+    F1 = plan.forces(st.pos, st.species, q).cpu().numpy()
+    F2 = plan.forces(st.pos, st.species, q).cpu().numpy()
+    assert np.array_equal(F1, F2)  # no atomics: repeated calls are bitwise equal
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_embedding_parity_small(precision):
+    """Gamma[i, z] = sum_{j of element z} E_ij q_j on the 216-atom cell and on a 4-species
+    random cell, against the dense oracle (FP64 matvecs in both plan precisions)."""
+    tol = 1e-7
+    for st in (synth.workload(1), synth.batch_workload(1, cfg_id=41, n_min=300, n_max=400, first=2)[0]):
+        plan = _plan([st], precision=precision, ewald_tol=tol)
+        q, _ = _charges(st.n, 8, neutral=False)
+        G = plan.embedding(st.pos, st.species, q).cpu().numpy()
+        A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=KE)
+        ref = O.element_potentials(A, st.species, q, plan.n_species)
+        assert G.shape == (st.n, plan.n_species)
+        err = _rel_rms(G, ref)
+        print(f"embedding {st.n} atoms, {st.n_species} species, {precision}: rel RMS {err:.2e}")
+        assert err < tol, err
+        # summed over elements: the potential E q of the plain matvec
+        y = plan.matvec(st.pos, st.species, q, fp64=True).cpu().numpy()
+        assert np.abs(G.sum(axis=1) - y).max() < 1e-9 * np.abs(y).max()
+
+
+def test_embedding_full_size_13824_atoms_sampled():
+    st = synth.workload(2)
+    tol = 1e-6
+    plan = _plan([st], precision="mixed", preconditioner="fourier", ewald_tol=tol, r_cut=8.0)
+    q, _ = _charges(st.n, 9)
+    rows = np.random.default_rng(10).choice(st.n, 64, replace=False)
+    G = plan.embedding(st.pos, st.species, q).cpu().numpy()[rows]
+    ref = np.stack([O.ewald_matvec(st.cell, st.pos, st.sigma, np.where(st.species == z, q, 0.0), k_e=KE,
+                                   omega=6.0, tol=1e-12, rows=rows) for z in range(2)], axis=1)
+    err = _rel_rms(G, ref)
+    print(f"embedding 13,824 atoms, 64 sampled: rel RMS {err:.2e}")
+    assert err < tol, err
+
+
+# ---------------------------------------------------------------- strain derivative (stress)
+# Same error budget as the forces: the reciprocal part differentiates the mesh kernel
+# (exact for the mesh energy), the real-space part the pair term; relative error of D
+# (max over components, against the largest component) within FORCE_TOL_FACTOR x ewald_tol.
+
+def _rel_max(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stress_parity_small_cell_against_dense_differences(precision):
+    """216-atom cell: D = d/d eps [(q/2 + lam)^T E q] against central differences of the dense
+    matrix under strain (the plain definition), with and without lambda."""
+    st = synth.workload(1)
+    tol = 1e-7
+    plan = _plan([st], precision=precision, ewald_tol=tol, r_cut=9.0)
+    q, lam = _charges(st.n, 12)
+    for la in (None, lam):
+        D = plan.stress(st.pos, st.species, q, la).cpu().numpy()[0]
+        ref = O.electrostatic_strain_derivative_fd(st.cell, st.pos, st.sigma, q, la, k_e=KE)
+        err = _rel_max(D, ref)
+        print(f"stress 216 atoms {precision} lambda={la is not None}: rel max {err:.2e}")
+        assert err < FORCE_TOL_FACTOR * tol, err
+        assert np.array_equal(D, D.T)
+
+
+def test_stress_parity_uneven_batch():
+    structs = [synth.rocksalt(3, 5.64, 0.15, synth.rng_for(40, 0), vacancy_frac=0.05, shear_deg=10.0),
+               synth.rocksalt((2, 3, 2), 5.64, 0.2, synth.rng_for(40, 1))]
+    for s in range(3):
+        structs.append(synth.batch_workload(1, cfg_id=41, n_min=64, n_max=600, first=s)[0])
+    tol = 1e-6
+    plan = _plan(structs, ewald_tol=tol)
+    n = sum(s.n for s in structs)
+    q, lam = _charges(n, 13, neutral=False)
+    pos = np.concatenate([s.pos for s in structs])
+    spc = np.concatenate([s.species for s in structs]).astype(np.int32)
+    D = plan.stress(pos, spc, q, lam).cpu().numpy()
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+    for i, st in enumerate(structs):
+        sl = slice(off[i], off[i + 1])
+        ref = O.electrostatic_strain_derivative_ewald(st.cell, st.pos, st.sigma, q[sl], lam[sl], k_e=KE)
+        err = _rel_max(D[i], ref)
+        print(f"stress structure {i} ({st.n} atoms, {st.n_species} species): rel max {err:.2e}")
+        assert err < FORCE_TOL_FACTOR * tol, (i, err)
+    D2 = plan.stress(pos, spc, q, lam).cpu().numpy()
+    assert np.array_equal(D, D2)  # fixed summation orders: bitwise repeatable
+
+
+def test_stress_full_size_13824_atoms():
+    st = synth.workload(2)
+    tol = 1e-6
+    plan = _plan([st], precision="mixed", preconditioner="fourier", ewald_tol=tol, r_cut=8.0)
+    q, lam = _charges(st.n, 14)
+    D = plan.stress(st.pos, st.species, q, lam).cpu().numpy()[0]
+    ref = O.electrostatic_strain_derivative_ewald(st.cell, st.pos, st.sigma, q, lam, k_e=KE, omega=6.0, tol=1e-10)
+    err = _rel_max(D, ref)
+    print(f"stress 13,824 atoms: rel max {err:.2e}")
+    assert err < FORCE_TOL_FACTOR * tol, err
+
+
+def test_stress_full_size_980k_atoms_is_the_strain_derivative_of_the_energy():
+    """980,000-atom cell: a property that holds at any size.  D must be the strain derivative
+    of W(eps) = (q/2 + lam)^T E(eps) q computed by the FP64 matvec of plans built on the
+    strained cell (same mesh; the mesh energy is differentiated exactly, so only the h^2
+    term of the central difference and pairs crossing r_cut separate the two)."""
+    from paper_2607_17978_b300 import qeq
+    st = synth.workload(5)
+    tol = 1e-6
+    kw = dict(precision="mixed", preconditioner="fourier", ewald_tol=tol, r_cut=8.0)
+    plan = _plan([st], **kw)
+    mesh = plan.query(0)["mesh"]
+    q, lam = _charges(st.n, 15)
+    w = 0.5 * q + lam
+    D = plan.stress(st.pos, st.species, q, lam).cpu().numpy()[0]
+    plan.close()
+    # h = 1e-4: pairs crossing r_cut (each worth ~ewald_tol of a pair term) average out
+    # below 1e-6 of D, the h^2 term is ~1e-8
+    h = 1e-4
+    for a, b in ((0, 0), (1, 2)):
+        Wpm = []
+        for sgn in (1.0, -1.0):
+            eps = np.zeros((3, 3))
+            eps[a, b] = sgn * h
+            c2, p2 = O.strained(st.cell, st.pos, eps)
+            p = qeq.Plan(c2.reshape(1, 9), np.array([0, st.n]), st.sigma_s[None, :], **kw)
+            assert p.query(0)["mesh"] == mesh
+            y = p.matvec(p2, st.species, q, fp64=True).cpu().numpy()
+            Wpm.append(float(w @ y))
+            p.close()
+        fd = (Wpm[0] - Wpm[1]) / (2 * h)
+        print(f"980k atoms D[{a}{b}] = {D[a, b]:.6e}, central difference {fd:.6e}")
+        assert abs(D[a, b] - fd) < 1e-5 * np.abs(D).max(), (a, b, D[a, b], fd)
