@@ -73,8 +73,15 @@ enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
  * TEST_STALL (tests only): in the main mesh's x FFT pass, the first tile announces 16 more
  * bytes on its copy barrier than its bulk copies deliver, so its bounded wait (0.5 s on the
  * GPU's global timer) runs out; the kernel flags the timeout and returns, and the call
- * returns QEQ_ERR_TIMEOUT.  It exercises the timeout path without any fault. */
-enum { QEQ_FLAG_NO_GRAPH = 1, QEQ_FLAG_TEST_STALL = 2 };
+ * returns QEQ_ERR_TIMEOUT.  It exercises the timeout path without any fault.
+ * TWO_RHS: the two-right-hand-side formulation of the iterative QEq that the paper compares
+ * against (Sec. "LAMMPS MD Performance"): plain PCG on (E + diag J) t = 1 and on
+ * (E + diag J) s = -chi without the charge constraint, then q = s + mu' t with
+ * mu' = (q_tot - sum s) / sum t.  Each sub-solve stops at a quarter of the charge
+ * threshold; the combined q gets the same FP64 projected-residual check as the default
+ * solver, and qeq_info reports the two sub-solves' iterations together.  Cold start only
+ * (another warm mode returns QEQ_ERR_INVALID). */
+enum { QEQ_FLAG_NO_GRAPH = 1, QEQ_FLAG_TEST_STALL = 2, QEQ_FLAG_TWO_RHS = 4 };
 /* Preconditioners of the PCG.  JACOBI: D^-1, D_i = J_i + k_e/(sigma_i sqrt pi).
  * FOURIER: D^-1 - D^-1 T^T F^-1[h F(T D^-1 r)], the Woodbury inverse of D plus the
  * long-range Coulomb operator with the mesh operator T D^-1 T^T replaced by its

@@ -3,6 +3,11 @@
 // the transposing passes of the 3D FFT with the reciprocal multiply of eq. (matvec)
 // fused into the x pass.  Included by matvec.cu only (its kernels live in that unit).
 #pragma once
+
+// resident CTAs per SM the FP32 FFT kernels are compiled for (register budget 65536 / (256 n))
+#ifndef QEQ_FFT_MIN_BLOCKS32
+#define QEQ_FFT_MIN_BLOCKS32 2
+#endif
 #include <math.h>
 
 #include <type_traits>
@@ -521,7 +526,7 @@ __device__ __forceinline__ void give_up(int* err, uint64_t* bar, const uint32_t*
 // sub-tile of `sub` lines of an item); the bulk copies of the next unit are in flight while
 // the current one is transformed.
 template <typename T, int PASS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
     k_fft_tile(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl, const int4* __restrict__ items,
                int nitems, int TL, int sub, int Kmax, int ldmax, const double2* __restrict__ tw64,
                const float2* __restrict__ tw32, const int* __restrict__ tabs, const PcgScalars* __restrict__ sc,
@@ -682,7 +687,7 @@ constexpr double kPreBetaOneX = 150.0;
 // zz, xy, xz, yz} to vir[8 u ..] (dst reinterpreted), in a fixed order: a line that is
 // not its own mirror stands for itself and its mirror (weight 2).
 template <typename T, bool PRE, int MAXS, bool VIR = false>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
     k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                   const int4* __restrict__ items, int nitems, int TLX, int sub, int Kmax, int ldmax,
                   const T* __restrict__ bmod, const double2* __restrict__ tw64, const float2* __restrict__ tw32,

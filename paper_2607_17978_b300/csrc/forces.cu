@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) k_force_grad(const StructDev* __restrict_
                                                     const int* __restrict__ sorted_struct, int64_t n,
                                                     const int* __restrict__ base, const double* __restrict__ wts,
                                                     const int* __restrict__ spec, const double* __restrict__ posc,
+                                                    const float4* __restrict__ posc32,
                                                     const int* __restrict__ bin_start, const double* __restrict__ x,
                                                     const double2* __restrict__ mesh, double k_e,
                                                     double* __restrict__ g0, double* __restrict__ g1,
@@ -91,9 +92,17 @@ __global__ void __launch_bounds__(256) k_force_grad(const StructDev* __restrict_
     const double rc2 = S.r_cut * S.r_cut;
     const uint32_t mask = S.narrow[sp];
     const double two_over_sqrtpi = 1.12837916709551257390;
+    // FP32 distance prefilter with a margin above FP32 position rounding (as the pair
+    // list's walk): only candidates that may lie within r_cut get the FP64 test
+    const float4 pa = posc32[a];
+    const double ext = norm3d(S.h[0], S.h[1], S.h[2]) + norm3d(S.h[3], S.h[4], S.h[5]) + norm3d(S.h[6], S.h[7], S.h[8]);
+    const float out2 = (float)((S.r_cut + 1e-3 + 1e-6 * ext) * (S.r_cut + 1e-3 + 1e-6 * ext));
     warp_neighbour_walk(S, bb, S.rs_range, bin_start, ws[w],
-                        [&](bool valid, int t, const double* sh, const float*, bool zero, int) {
+                        [&](bool valid, int t, const double* sh, const float* sh32, bool zero, int) {
       if (!valid || !((mask >> spec[t]) & 1u) || (zero && t == a)) return;
+      const float4 pt = posc32[t];
+      const float fx = pt.x + sh32[0] - pa.x, fy = pt.y + sh32[1] - pa.y, fz = pt.z + sh32[2] - pa.z;
+      if (fx * fx + fy * fy + fz * fz > out2) return;
       const double dx = posc[3 * t] + sh[0] - ra0, dy = posc[3 * t + 1] + sh[1] - ra1,
                    dz = posc[3 * t + 2] + sh[2] - ra2;
       const double d2 = dx * dx + dy * dy + dz * dz;
@@ -177,7 +186,7 @@ __global__ void k_scatter_column(const int* __restrict__ perm, int64_t n, const 
 __global__ void __launch_bounds__(256) k_virial_real(const StructDev* __restrict__ st,
                                                      const int* __restrict__ sorted_struct, int64_t n,
                                                      const int* __restrict__ base, const int* __restrict__ spec,
-                                                     const double* __restrict__ posc,
+                                                     const double* __restrict__ posc, const float4* __restrict__ posc32,
                                                      const int* __restrict__ bin_start, const double* __restrict__ w,
                                                      const double* __restrict__ q, double k_e,
                                                      double* __restrict__ o0, double* __restrict__ o1,
@@ -197,9 +206,17 @@ __global__ void __launch_bounds__(256) k_virial_real(const StructDev* __restrict
     const double rc2 = S.r_cut * S.r_cut;
     const uint32_t mask = S.narrow[sp];
     const double two_over_sqrtpi = 1.12837916709551257390;
+    // FP32 distance prefilter with a margin above FP32 position rounding (as the pair
+    // list's walk): only candidates that may lie within r_cut get the FP64 test
+    const float4 pa = posc32[a];
+    const double ext = norm3d(S.h[0], S.h[1], S.h[2]) + norm3d(S.h[3], S.h[4], S.h[5]) + norm3d(S.h[6], S.h[7], S.h[8]);
+    const float out2 = (float)((S.r_cut + 1e-3 + 1e-6 * ext) * (S.r_cut + 1e-3 + 1e-6 * ext));
     warp_neighbour_walk(S, bb, S.rs_range, bin_start, ws[wp],
-                        [&](bool valid, int t, const double* sh, const float*, bool zero, int) {
+                        [&](bool valid, int t, const double* sh, const float* sh32, bool zero, int) {
       if (!valid || !((mask >> spec[t]) & 1u) || (zero && t == a)) return;
+      const float4 pt = posc32[t];
+      const float fx = pt.x + sh32[0] - pa.x, fy = pt.y + sh32[1] - pa.y, fz = pt.z + sh32[2] - pa.z;
+      if (fx * fx + fy * fy + fz * fz > out2) return;
       const double dx = posc[3 * t] + sh[0] - ra0, dy = posc[3 * t + 1] + sh[1] - ra1,
                    dz = posc[3 * t + 2] + sh[2] - ra2;
       const double d2 = dx * dx + dy * dy + dz * dz;
@@ -259,49 +276,73 @@ __global__ void __launch_bounds__(256) k_virial_units(const int* __restrict__ xo
 
 // D[9 s + 3 a + b] = fa R_A + fb R_B (reciprocal, R = -delta sum E + the G_a G_b sums)
 //   + sum over the structure's atoms of the real-space parts
-//   + delta_ab sum_st wsum_s corr_st qsum_t (the G = 0 width term ~ 1/V)
-__global__ void __launch_bounds__(256) k_stress_finish(const StructDev* __restrict__ st,
+//   + delta_ab sum_st wsum_s corr_st qsum_t (the G = 0 width term ~ 1/V).
+// One CTA per reduction chunk: the chunk's 6 real-space sums and per-species sums of w
+// and q go to part[chunk * kStressPart ..]; the structure's last chunk to finish (counter)
+// combines the partials in chunk order and writes D.
+constexpr int kStressPart = 6 + 2 * QEQ_MAX_SPECIES;
+
+__global__ void __launch_bounds__(256) k_stress_finish(const Chunk* __restrict__ chunks,
+                                                       const StructDev* __restrict__ st,
                                                        const double* __restrict__ rA, const double* __restrict__ rB,
                                                        double fa, double fb, const double* __restrict__ o0,
                                                        const double* __restrict__ o1, const double* __restrict__ o2,
                                                        const double* __restrict__ o3, const double* __restrict__ o4,
                                                        const double* __restrict__ o5, const int* __restrict__ spec,
                                                        const double* __restrict__ w, const double* __restrict__ q,
+                                                       double* __restrict__ part, int* __restrict__ counter,
                                                        double* __restrict__ D) {
   __shared__ double red[8];
-  const int s = blockIdx.x;
-  const StructDev& S = st[s];
-  const int64_t a0 = S.atom_begin;
-  const int cnt = (int)(S.atom_end - S.atom_begin);
+  __shared__ bool last;
+  const Chunk ch = chunks[blockIdx.x];
+  const StructDev& S = st[ch.s];
   const double* parts[6] = {o0, o1, o2, o3, o4, o5};
-  double rs[6];
-  for (int k = 0; k < 6; ++k) rs[k] = ordered_block_sum(parts[k] + a0, 0, cnt, 1, 0, red);
-  double ws_[QEQ_MAX_SPECIES], qs_[QEQ_MAX_SPECIES];
-  for (int z = 0; z < S.S; ++z) {
-    double aw = 0.0, aq = 0.0;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
-      if (spec[a0 + i] == z) {
-        aw += w[a0 + i];
-        aq += q[a0 + i];
+  double v[kStressPart];
+#pragma unroll
+  for (int k = 0; k < kStressPart; ++k) v[k] = 0.0;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] += parts[k][a];
+    const int z = spec[a];
+#pragma unroll
+    for (int t = 0; t < QEQ_MAX_SPECIES; ++t)
+      if (t == z) {
+        v[6 + t] += w[a];
+        v[6 + QEQ_MAX_SPECIES + t] += q[a];
       }
-    ws_[z] = block_sum_fixed(aw, red);
-    qs_[z] = block_sum_fixed(aq, red);
   }
+#pragma unroll
+  for (int k = 0; k < kStressPart; ++k) {
+    const double tot = block_sum_fixed(v[k], red);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * kStressPart + k] = tot;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int prev = atomicAdd(counter + ch.s, 1);
+    last = (prev == ch.count - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x != 0) return;
+  double tot[kStressPart];
+  for (int k = 0; k < kStressPart; ++k) tot[k] = 0.0;
+  for (int c = 0; c < ch.count; ++c)  // chunk order: deterministic
+    for (int k = 0; k < kStressPart; ++k) tot[k] += ((volatile double*)part)[(size_t)(ch.first + c) * kStressPart + k];
+  counter[ch.s] = 0;
   double corr = 0.0;
   for (int z = 0; z < S.S; ++z)
-    for (int t = 0; t < S.S; ++t) corr += ws_[z] * S.corr[z * QEQ_MAX_SPECIES + t] * qs_[t];
-  if (threadIdx.x == 0) {
-    double R[7];
-    for (int k = 0; k < 7; ++k) R[k] = fa * rA[8 * s + k] + (rB ? fb * rB[8 * s + k] : 0.0);
-    const double diag = corr - R[0];
-    double* o = D + 9 * (size_t)s;
-    o[0] = R[1] + rs[0] + diag;
-    o[4] = R[2] + rs[1] + diag;
-    o[8] = R[3] + rs[2] + diag;
-    o[1] = o[3] = R[4] + rs[3];
-    o[2] = o[6] = R[5] + rs[4];
-    o[5] = o[7] = R[6] + rs[5];
-  }
+    for (int t = 0; t < S.S; ++t) corr += tot[6 + z] * S.corr[z * QEQ_MAX_SPECIES + t] * tot[6 + QEQ_MAX_SPECIES + t];
+  double R[7];
+  for (int k = 0; k < 7; ++k) R[k] = fa * rA[8 * ch.s + k] + (rB ? fb * rB[8 * ch.s + k] : 0.0);
+  const double diag = corr - R[0];
+  double* o = D + 9 * (size_t)ch.s;
+  o[0] = R[1] + tot[0] + diag;
+  o[4] = R[2] + tot[1] + diag;
+  o[8] = R[3] + tot[2] + diag;
+  o[1] = o[3] = R[4] + tot[3];
+  o[2] = o[6] = R[5] + tot[4];
+  o[5] = o[7] = R[6] + tot[5];
 }
 
 // w = q/2 + lambda (lambda sorted in w on entry, or NULL: w = q/2); x = w + q
@@ -324,8 +365,8 @@ cudaError_t launch_force_grad(qeq_plan_s* Pl, const double* x, double* const g[3
   count_launch(Pl);
   const int nbw = (int)((Pl->n_atoms + 7) / 8);  // one warp per atom
   k_force_grad<P><<<nbw, 256, 0, Pl->stream>>>(Pl->d_st, Pl->d_key, Pl->n_atoms, Pl->d_base, Pl->d_wts, Pl->d_spec,
-                                                Pl->d_posc, Pl->d_bin_start, x, Pl->d_mesh, Pl->desc.coulomb_k, g[0], g[1],
-                                                g[2]);
+                                                Pl->d_posc, Pl->d_posc32, Pl->d_bin_start, x, Pl->d_mesh,
+                                                Pl->desc.coulomb_k, g[0], g[1], g[2]);
   return cudaGetLastError();
 }
 
@@ -398,7 +439,7 @@ cudaError_t launch_stress(qeq_plan_s* P, const double* q, const double* lambda, 
   QEQ_CUDA_TRY(cudaGetLastError());
   count_launch(P);
   k_virial_real<<<(int)((n + 7) / 8), 256, 0, s>>>(P->d_st, P->d_key, n, P->d_base, P->d_spec, P->d_posc,
-                                                    P->d_bin_start, P->d_z, P->d_q, P->desc.coulomb_k, P->d_r,
+                                                    P->d_posc32, P->d_bin_start, P->d_z, P->d_q, P->desc.coulomb_k, P->d_r,
                                                     P->d_p, P->d_Ap, P->d_x, P->d_q1, P->d_r1);
   QEQ_CUDA_TRY(cudaGetLastError());
   double* rA = P->d_part;
@@ -420,7 +461,8 @@ cudaError_t launch_stress(qeq_plan_s* P, const double* q, const double* lambda, 
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   count_launch(P);
-  k_stress_finish<<<ns, 256, 0, s>>>(P->d_st, rA, lambda ? rB : nullptr, lambda ? 0.25 : 0.5, -0.25, P->d_r, P->d_p,
-                                     P->d_Ap, P->d_x, P->d_q1, P->d_r1, P->d_spec, P->d_z, P->d_q, D);
+  k_stress_finish<<<P->n_chunks, 256, 0, s>>>(P->d_chunks, P->d_st, rA, lambda ? rB : nullptr, lambda ? 0.25 : 0.5,
+                                              -0.25, P->d_r, P->d_p, P->d_Ap, P->d_x, P->d_q1, P->d_r1, P->d_spec,
+                                              P->d_z, P->d_q, P->d_stress_part, P->d_counter + 3 * ns, D);
   return cudaGetLastError();
 }

@@ -212,7 +212,8 @@ struct PcgScalars {
   int status;
   int n;
   int jacobi;         // 1: the Fourier preconditioner was dropped for Jacobi
-  int pad_;
+  int unconstrained;  // 1: plain PCG on (E + diag J) x = b, no charge constraint (two-RHS solver)
+  double tsum;        // two-RHS solver: sum of t (A t = 1)
 };
 
 // Loop counters of the device-paced solve graph (device resident).
@@ -291,6 +292,7 @@ struct qeq_plan_s {
   int4* d_yiitems = nullptr;       // inverse y pass {s, c, x, z0}
   int4* d_xitems = nullptr;        // x pass {s, z, y0, lines}
   int* d_xitem_off = nullptr;      // n_struct + 1: first x item of each structure
+  double* d_stress_part = nullptr; // per-chunk partial sums of the strain derivative (6 + 2 QEQ_MAX_SPECIES each)
   int* d_bin_struct = nullptr;     // structure of each global bin
   int* d_brick_struct = nullptr;   // structure of each global brick
   int* d_brick_cand = nullptr;     // QEQ_BRICK_CAND ints per brick (brick_candidates)

@@ -143,10 +143,17 @@ __device__ void residual_test(PcgScalars& c, const double* tot, double ref, int 
   c.r_sum = ref * n + tot[1];
   c.r_max = tot[3];
   c.r_min = tot[4];
-  c.shift = tot[0] / c.s0;
-  const double mean = ref + dmean;
-  double pinf = fmax(c.r_max - mean, mean - c.r_min);
-  double pl2 = sqrt(fmax(tot[2] - tot[1] * dmean, 0.0));
+  double pinf, pl2;
+  if (c.unconstrained) {  // plain residual (the shift, and so ref, stay 0)
+    c.shift = 0.0;
+    pinf = fmax(fabs(c.r_max), fabs(c.r_min));
+    pl2 = sqrt(fmax(tot[2] + ref * (2.0 * tot[1] + n * ref), 0.0));
+  } else {
+    c.shift = tot[0] / c.s0;
+    const double mean = ref + dmean;
+    pinf = fmax(c.r_max - mean, mean - c.r_min);
+    pl2 = sqrt(fmax(tot[2] - tot[1] * dmean, 0.0));
+  }
   c.r_l2 = pl2;
   // the iterations stop a margin below the threshold of the final check, so that
   // the drift of the recurrence residual (FP32 matvec) rarely forces a restart
@@ -319,7 +326,7 @@ __global__ void k_proj_rz(const Chunk* __restrict__ chunks, const double* __rest
                           int* counter) {
   const Chunk ch = chunks[blockIdx.x];
   if (!sc[ch.s].active) return;
-  const double f = sc[ch.s].usum / sc[ch.s].w1sum;
+  const double f = sc[ch.s].unconstrained ? 0.0 : sc[ch.s].usum / sc[ch.s].w1sum;  // no projection without the constraint
   const double sh = sc[ch.s].shift;
   double v[2] = {0, 0};
   const int op[2] = {RED_SUM, RED_SUM};
@@ -563,6 +570,12 @@ qeq_status cuda_fail(qeq_plan_s* P, cudaError_t e, const char* where) {
   do {                                                   \
     cudaError_t e_ = (expr);                             \
     if (e_ != cudaSuccess) return cuda_fail(P, e_, #expr); \
+  } while (0)
+
+#define TRY_ST(expr)                 \
+  do {                               \
+    qeq_status st_ = (expr);         \
+    if (st_ != QEQ_OK) return st_;   \
   } while (0)
 
 int* red_counter(qeq_plan_s* P) { return P->d_counter + 2 * P->n_struct; }
@@ -851,13 +864,164 @@ qeq_status init_scalars(qeq_plan_s* P, const double* h_qtot) {
   return QEQ_OK;
 }
 
-__global__ void k_set_tol(PcgScalars* sc, int ns, double charge_tol, double rel_tol, double inner) {
+__global__ void k_set_tol(PcgScalars* sc, int ns, double charge_tol, double rel_tol, double inner,
+                          int unconstrained, double scale) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
   PcgScalars& c = sc[s];
-  c.tol_inf = 0.5 * charge_tol * c.j_min;
-  c.tol_l2 = rel_tol > 0 ? rel_tol * sqrt(c.chi_p2) : 0.0;
+  c.tol_inf = scale * 0.5 * charge_tol * c.j_min;
+  c.tol_l2 = rel_tol > 0 ? scale * rel_tol * sqrt(c.chi_p2) : 0.0;
   c.inner = inner;
+  c.unconstrained = unconstrained;
+}
+
+// two-RHS solver: per structure sum s (sorted, in q) and sum t (t in input order, in t_in)
+__global__ void k_two_rhs_sums(const Chunk* __restrict__ chunks, const int* __restrict__ perm,
+                               const double* __restrict__ q, const double* __restrict__ t_in,
+                               PcgScalars* __restrict__ sc, double* part, int* counter) {
+  const Chunk ch = chunks[blockIdx.x];
+  double v[2] = {0.0, 0.0};
+  const int op[2] = {RED_SUM, RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    v[0] += q[a];
+    v[1] += t_in[perm[a]];
+  }
+  double tot[2];
+  if (chunk_reduce<2>(v, op, ch, part, counter, tot)) {
+    sc[ch.s].qsum = tot[0];
+    sc[ch.s].tsum = tot[1];
+  }
+}
+
+// q = s + mu' t with mu' = (q_tot - sum s) / sum t, so that sum q = q_tot; the combined
+// charges go to out (input order), from which the final check reads them
+__global__ void k_two_rhs_combine(const Chunk* __restrict__ chunks, const int* __restrict__ perm,
+                                  const double* __restrict__ q, double* __restrict__ t_out,
+                                  const PcgScalars* __restrict__ sc) {
+  const Chunk ch = chunks[blockIdx.x];
+  const PcgScalars& c = sc[ch.s];
+  const double m = (c.q_tot - c.qsum) / c.tsum;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    const int i = perm[a];
+    t_out[i] = q[a] + m * t_out[i];
+  }
+}
+
+// Every PCG round from the current q and r: the first direction, then the device-paced
+// graph (or the host loop) until every structure has stopped.
+qeq_status pcg_rounds(qeq_plan_s* P, int prec) {
+  cudaStream_t s = P->stream;
+  const int nc = P->n_chunks, ns = P->n_struct, max_iter = P->desc.max_iter;
+  TRY(precondition(P, 1, 1));
+  count_launch(P);
+  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
+  TRY(cudaGetLastError());
+  const int max_restarts = kMaxRestarts;
+  if (P->graph_ok) {
+    // device-paced: every round of the PCG in one graph launch
+    if (!P->graph_solve || P->graph_solve_prec != prec) TRY(build_solve_graph(P, prec));
+    TRY(cudaGraphLaunch(P->graph_solve, s));
+  } else {
+    for (int outer = 0; outer <= max_restarts + 1; ++outer) {
+      // inner iterations (structures drop out as they converge); the device stops every
+      // structure at max_iter, the host bound is a second guard
+      const int max_launches = max_iter / kItersPerCheck + 2;
+      for (int l = 0; l < max_launches; ++l) {
+        TRY(run_iterations(P, prec));
+        if (P->h_done[0]) break;
+      }
+      TRY(final_check(P, prec, prec == QEQ_MIXED && outer > 0 && outer < max_restarts));
+      count_launch(P);
+      k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_err, P->d_done);
+      TRY(precondition(P, 1, 1));
+      count_launch(P);
+      k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
+      TRY(cudaGetLastError());
+      TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRY(cudaStreamSynchronize(s));
+      if (P->h_done[0]) break;
+    }
+  }
+  return QEQ_OK;
+}
+
+// kernels the device-paced graph ran so far in this solve (read from its loop counters)
+qeq_status account_graph(qeq_plan_s* P) {
+  if (!P->graph_ok) return QEQ_OK;
+  LoopCtl ctl;
+  TRY(cudaMemcpyAsync(&ctl, P->d_ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, P->stream));
+  TRY(cudaStreamSynchronize(P->stream));
+  P->launches += P->gk_inner * ctl.replays_total + P->gk_round * ctl.outer;
+  return QEQ_OK;
+}
+
+// Two-RHS solver (the iterative-QEq formulation used for comparison with n2p2): plain
+// PCG on A t = 1 and A s = -chi, A = E + diag J (no charge constraint), then
+// q = s + mu' t with mu' = (q_tot - sum s)/sum t.  Each sub-solve stops at a quarter of
+// the constrained threshold; the combined charges then get the usual projected FP64
+// check.  t waits in the caller's output buffer while s is solved.  Returns the sub-solves'
+// iterations and worst status.
+qeq_status two_rhs_phase(qeq_plan_s* P, const double* d_chi_user, const double* h_qtot, double* d_q_user,
+                         int* iters, int* restarts, int* status) {
+  cudaStream_t s = P->stream;
+  const int nc = P->n_chunks, ns = P->n_struct, prec = P->precision, max_iter = P->desc.max_iter;
+  const int nb = (int)((P->n_atoms + 255) / 256);
+  std::vector<PcgScalars> h(ns);
+  for (int i = 0; i < ns; ++i) iters[i] = restarts[i] = status[i] = 0;
+  for (int rhs = 0; rhs < 2; ++rhs) {
+    if (rhs == 0) {  // chi := -1: r = 1 - A t
+      count_launch(P);
+      k_fill<<<nb, 256, 0, s>>>(P->d_chi, P->n_atoms, -1.0);
+    } else {  // the caller's chi again (prepare sorted it into d_chi)
+      count_launch(P);
+      k_sort_in<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, d_chi_user, P->d_chi);
+      TRY_ST(init_scalars(P, h_qtot));
+    }
+    count_launch(P, 2);
+    k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, nullptr, QEQ_WARM_COLD, nullptr, P->d_dinv, P->d_chi, P->d_J,
+                              P->d_q, P->d_sc, red_part(P), red_counter(P));
+    k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol,
+                                               prec == QEQ_MIXED ? kMixedInnerTol : 1.0, 1, 0.25);
+    TRY(cudaGetLastError());
+    if (P->precond == QEQ_PRECOND_FOURIER) {  // w1 is read (times 0) by the direction kernel
+      count_launch(P);
+      k_fill<<<nb, 256, 0, s>>>(P->d_x, P->n_atoms, 1.0);
+      TRY(launch_precond(P, P->d_x, P->d_w1, 1, 0));
+    }
+    TRY(launch_matvec(P, prec, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
+    count_launch(P);
+    k_resid<<<nc, 256, 0, s>>>(P->d_chunks, P->d_chi, P->d_Ap, P->d_dinv, P->d_r, P->d_sc, 0, red_part(P),
+                               red_counter(P), max_iter);
+    TRY(cudaGetLastError());
+    TRY_ST(pcg_rounds(P, prec));
+    TRY_ST(account_graph(P));
+    TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < ns; ++i) {
+      iters[i] += h[i].iters;
+      restarts[i] += h[i].restarts;
+      if (h[i].status != QEQ_OK && status[i] == QEQ_OK) status[i] = h[i].status;
+    }
+    if (rhs == 0) {  // t -> the caller's buffer (input order)
+      count_launch(P);
+      k_unsort<<<nb, 256, 0, s>>>(P->d_perm, P->n_atoms, P->d_q, d_q_user);
+      TRY(cudaGetLastError());
+    }
+  }
+  count_launch(P, 2);
+  k_two_rhs_sums<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, P->d_q, d_q_user, P->d_sc, red_part(P), red_counter(P));
+  k_two_rhs_combine<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, P->d_q, d_q_user, P->d_sc);
+  TRY(cudaGetLastError());
+  // the combined charges as the start of a constrained "solve" with no iterations: its
+  // statistics, tolerance and the FP64 check of the result
+  TRY_ST(init_scalars(P, h_qtot));
+  count_launch(P, 2);
+  k_init<<<nc, 256, 0, s>>>(P->d_chunks, P->d_perm, d_q_user, QEQ_WARM_USER, nullptr, P->d_dinv, P->d_chi, P->d_J,
+                            P->d_q, P->d_sc, red_part(P), red_counter(P));
+  k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol, 1.0, 0, 1.0);
+  TRY(cudaGetLastError());
+  TRY(final_check(P, QEQ_FP64, false));
+  return QEQ_OK;
 }
 
 }  // namespace
@@ -887,6 +1051,17 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
   const int nc = P->n_chunks, ns = P->n_struct;
   const int prec = P->precision;
   const int max_iter = P->desc.max_iter;
+  const bool two_rhs = (P->desc.flags & QEQ_FLAG_TWO_RHS) != 0;
+  std::vector<int> warm_kept(ns, 0);
+  std::vector<int> tr_iters(ns, 0), tr_rest(ns, 0), tr_status(ns, 0);
+  if (two_rhs) {
+    if (warm != QEQ_WARM_COLD) {
+      P->last_error = "the two-RHS solver starts cold";
+      return QEQ_ERR_INVALID;
+    }
+    if (P->precond == QEQ_PRECOND_FOURIER) TRY(launch_precond_setup(P));
+    TRY_ST(two_rhs_phase(P, d_chi, h_qtot, d_q, tr_iters.data(), tr_rest.data(), tr_status.data()));
+  } else {
   int wm = (warm == QEQ_WARM_USER) ? QEQ_WARM_USER : QEQ_WARM_COLD;
   if (warm == QEQ_WARM_MLP) {
     if (!P->mlp) {
@@ -897,7 +1072,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     wm = QEQ_WARM_MLP;
   }
   // per structure: 1 when the solve starts from the user's or the network's charges
-  std::vector<int> warm_kept(ns, wm != QEQ_WARM_COLD ? 1 : 0);
+  warm_kept.assign(ns, wm != QEQ_WARM_COLD ? 1 : 0);
   const int* reject = nullptr;
   if (P->precond == QEQ_PRECOND_FOURIER) TRY(launch_precond_setup(P));
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -906,7 +1081,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
                               red_part(P), red_counter(P));
     k_project<<<nc, 256, 0, s>>>(P->d_chunks, P->d_q, P->d_sc);
     k_set_tol<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns, P->desc.charge_tol, P->desc.residual_tol,
-                                               prec == QEQ_MIXED ? kMixedInnerTol : 1.0);
+                                               prec == QEQ_MIXED ? kMixedInnerTol : 1.0, 0, 1.0);
     TRY(cudaGetLastError());
     if (P->precond == QEQ_PRECOND_FOURIER) {
       // w1 = M^-1 1 and its sums, for projecting preconditioned residuals onto 1^T z = 0
@@ -959,35 +1134,7 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     TRY(init_scalars(P, h_qtot) == QEQ_OK ? cudaSuccess : cudaErrorUnknown);  // synchronises the copy
     reject = P->d_reject;
   }
-  TRY(precondition(P, 1, 1));
-  count_launch(P);
-  k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
-  TRY(cudaGetLastError());
-  const int max_restarts = kMaxRestarts;
-  if (P->graph_ok) {
-    // device-paced: every round of the PCG in one graph launch
-    if (!P->graph_solve || P->graph_solve_prec != prec) TRY(build_solve_graph(P, prec));
-    TRY(cudaGraphLaunch(P->graph_solve, s));
-  } else {
-    for (int outer = 0; outer <= max_restarts + 1; ++outer) {
-      // inner iterations (structures drop out as they converge); the device stops every
-      // structure at max_iter, the host bound is a second guard
-      const int max_launches = max_iter / kItersPerCheck + 2;
-      for (int l = 0; l < max_launches; ++l) {
-        TRY(run_iterations(P, prec));
-        if (P->h_done[0]) break;
-      }
-      TRY(final_check(P, prec, prec == QEQ_MIXED && outer > 0 && outer < max_restarts));
-      count_launch(P);
-      k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, max_restarts, max_iter, P->d_err, P->d_done);
-      TRY(precondition(P, 1, 1));
-      count_launch(P);
-      k_direction<<<nc, 256, 0, s>>>(P->d_chunks, P->d_z, dir_alt(P), P->d_p, P->d_sc);
-      TRY(cudaGetLastError());
-      TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TRY(cudaStreamSynchronize(s));
-      if (P->h_done[0]) break;
-    }
+    TRY_ST(pcg_rounds(P, prec));
   }
   // energy terms from the final check's A q, outputs in input order
   count_launch(P);
@@ -1003,10 +1150,15 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
   TRY(cudaMemcpyAsync(h.data(), P->d_sc, sizeof(PcgScalars) * ns, cudaMemcpyDeviceToHost, s));
   if (P->graph_ok) TRY(cudaMemcpyAsync(&ctl, P->d_ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
-  if (P->graph_ok) P->launches += P->gk_inner * ctl.replays_total + P->gk_round * ctl.outer;
+  if (P->graph_ok && !two_rhs) P->launches += P->gk_inner * ctl.replays_total + P->gk_round * ctl.outer;
   qeq_status worst = QEQ_OK;
   for (int i = 0; i < ns; ++i) {
-    const PcgScalars& c = h[i];
+    PcgScalars& c = h[i];
+    if (two_rhs) {  // the sub-solves' counts; converged means the combined charges passed the FP64 check
+      c.status = tr_status[i] != QEQ_OK ? tr_status[i] : (c.converged ? QEQ_OK : QEQ_ERR_NOCONV);
+      c.iters = tr_iters[i];
+      c.restarts = tr_rest[i];
+    }
     double n = (double)c.n, mean = c.r_sum / n;
     double pinf = fmax(c.r_max - mean, mean - c.r_min);
     double pl2 = c.r_l2;

@@ -183,6 +183,34 @@ def test_tight_charge_tolerances_converge_or_report(cfg1, precision, pre):
         plan.close()
 
 
+@pytest.mark.parametrize("precision,pre", [("fp64", "jacobi"), ("fp64", "fourier"), ("mixed", "jacobi"),
+                                           ("mixed", "fourier")])
+def test_two_rhs_solver_matches_the_oracle(precision, pre):
+    """The two-RHS formulation (plain PCG on A t = 1 and A s = -chi, q = s + mu' t) on an
+    uneven batch with charged cells: charges within 1e-5 e of the dense oracle, the constraint
+    exact, mu from the combined charges, the same charges as the projected solver."""
+    from paper_2607_17978_b300 import qeq
+    structs = _small_structs()
+    plan = _plan(structs, precision=precision, preconditioner=pre, solver="two_rhs")
+    args = qeq.pack(structs)
+    res = plan.solve(*args)
+    qg = res.q.cpu().numpy()
+    mug = res.mu.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+    for i, st in enumerate(structs):
+        _, q, mu, *_r = _oracle(st)
+        sl = slice(off[i], off[i + 1])
+        assert np.abs(qg[sl] - q).max() < 1e-5, (i, np.abs(qg[sl] - q).max(), res.info[i])
+        assert abs(qg[sl].sum() - st.q_tot) < 1e-9
+        assert abs(mug[i] - mu) < 1e-4 * max(1.0, abs(mu))
+        assert res.info[i]["status"] == 0 and res.info[i]["iterations"] > 0
+    qp = _plan(structs, precision=precision, preconditioner=pre).solve(*args).q.cpu().numpy()
+    assert np.abs(qg - qp).max() < 2e-5
+    with pytest.raises(qeq.QEqError) as e:
+        plan.solve(*args, q0=qp)  # the two-RHS solver starts cold
+    assert e.value.status == qeq.QEQ_ERR_INVALID
+
+
 def test_translation_invariance_within_mesh_error(cfg1):
     from paper_2607_17978_b300 import qeq
     st, (A, q, *_r) = cfg1
