@@ -501,16 +501,22 @@ __global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __res
                              const double* __restrict__ dinv, const double* __restrict__ r, int64_t n,
                              const PcgScalars* __restrict__ sc, int use_active, int ones_input,
                              unsigned long long* __restrict__ imesh) {
-  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n) return;
+  // the 32 lanes of a warp take atoms n/32 apart in the bin order (lane l of global warp
+  // g: atom l * nw + g), so that their 64 additions each go to different mesh regions
+  // instead of queueing on the same addresses; the integer sums do not depend on order
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nw = (n + 31) / 32;
+  const int64_t a = (gid & 31) * nw + (gid >> 5);
+  if ((gid >> 5) >= nw || a >= n) return;
   const int s = sorted_struct[a];
   if (use_active && !sc[s].active) return;
   const StructDev& S = stp[s];
   const int bs = pbase[a];
   const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
   const float* w = pw + a * 12;
-  const float v = (float)(dinv[a] * r[a]);
-  const double scale = pre_fixed_scale(sc[s], ones_input);
+  // the scale is a power of two: scaling the FP32 product is exact, so the integer of each
+  // contribution is that of the FP32 product scaled in FP64 (no FP64 arithmetic per point)
+  const float vs = (float)((double)(float)(dinv[a] * r[a]) * pre_fixed_scale(sc[s], ones_input));  // |vs| <= 2^48
   unsigned long long* m = imesh + S.mesh_off;
   for (int jx = 0; jx < 4; ++jx) {
     int kx = f[0] - jx;
@@ -518,13 +524,12 @@ __global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __res
     for (int jy = 0; jy < 4; ++jy) {
       int ky = f[1] - jy;
       if (ky < 0) ky += S.K[1];
-      const float wxy = v * w[jx] * w[4 + jy];
+      const float wxy = vs * w[jx] * w[4 + jy];
       unsigned long long* row = m + ((int64_t)kx * S.K[1] + ky) * S.P[2];
       for (int jz = 0; jz < 4; ++jz) {
         int kz = f[2] - jz;
         if (kz < 0) kz += S.K[2];
-        const long long c = __double2ll_rn((double)(wxy * w[8 + jz]) * scale);
-        atomicAdd(&row[kz], (unsigned long long)c);
+        atomicAdd(&row[kz], (unsigned long long)__float2ll_rn(wxy * w[8 + jz]));
       }
     }
   }
