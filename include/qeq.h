@@ -80,8 +80,16 @@ enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
  * mu' = (q_tot - sum s) / sum t.  Each sub-solve stops at a quarter of the charge
  * threshold; the combined q gets the same FP64 projected-residual check as the default
  * solver, and qeq_info reports the two sub-solves' iterations together.  Cold start only
- * (another warm mode returns QEQ_ERR_INVALID). */
-enum { QEQ_FLAG_NO_GRAPH = 1, QEQ_FLAG_TEST_STALL = 2, QEQ_FLAG_TWO_RHS = 4 };
+ * (another warm mode returns QEQ_ERR_INVALID).
+ * SQNM: the stabilised quasi-Newton minimiser of the paper's solver comparison (SI solver
+ * figure) instead of CG: steps on the constraint plane in Jacobi-scaled coordinates, a
+ * Newton step in the significant subspace of the last 8 steps (symmetrised secant Hessian,
+ * curvatures enlarged by their residues) and a steepest-descent step alpha in the
+ * complement; a step that raises E_QEq is undone, alpha halved and the history cleared.
+ * One matvec per step (mixed precision: FP64 A q1 at each round's start plus the FP32
+ * product of the change); the same FP64 final check and restarts as the CG.  Host-paced;
+ * the plan allocates its history (16 N doubles) at creation.  Warm starts as for CG. */
+enum { QEQ_FLAG_NO_GRAPH = 1, QEQ_FLAG_TEST_STALL = 2, QEQ_FLAG_TWO_RHS = 4, QEQ_FLAG_SQNM = 8 };
 /* Preconditioners of the PCG.  JACOBI: D^-1, D_i = J_i + k_e/(sigma_i sqrt pi).
  * FOURIER: D^-1 - D^-1 T^T F^-1[h F(T D^-1 r)], the Woodbury inverse of D plus the
  * long-range Coulomb operator with the mesh operator T D^-1 T^T replaced by its

@@ -150,7 +150,8 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems, P->d_pyiitems, P->d_fft_tabs,
                   P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
-                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject,  P->d_xitem_off, P->d_stress_part};
+                  P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject,  P->d_xitem_off, P->d_stress_part,
+                  P->d_sqnm_dx, P->d_sqnm_dg, P->d_sqnm_g, P->d_sqnm_part, P->d_sqnm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->h_done) cudaFreeHost(P->h_done);
@@ -597,6 +598,13 @@ static qeq_status build_plan(qeq_plan_s* P) {
                                   std::max<size_t>((size_t)P->total_bins, (size_t)P->n_chunks * QEQ_GATHER_SPLIT_MAX) + 64));
   ALLOC(dalloc(P, &P->d_counter, (size_t)ns * 4));
   ALLOC(dalloc(P, &P->d_stress_part, (size_t)P->n_chunks * (6 + 2 * QEQ_MAX_SPECIES)));
+  if (D.flags & QEQ_FLAG_SQNM) {
+    ALLOC(dalloc(P, &P->d_sqnm_dx, (size_t)N * QEQ_SQNM_HISTORY));
+    ALLOC(dalloc(P, &P->d_sqnm_dg, (size_t)N * QEQ_SQNM_HISTORY));
+    ALLOC(dalloc(P, &P->d_sqnm_g, (size_t)N));
+    ALLOC(dalloc(P, &P->d_sqnm_part, (size_t)P->n_chunks * (QEQ_SQNM_NDOT + 7)));
+    ALLOC(dalloc(P, &P->d_sqnm, (size_t)ns));
+  }
   ALLOC(cudaMemset(P->d_counter, 0, sizeof(int) * ns * 4));
   ALLOC(dalloc(P, &P->d_sc, ns));
   ALLOC(cudaMemset(P->d_sc, 0, sizeof(PcgScalars) * ns));

@@ -212,8 +212,33 @@ struct PcgScalars {
   int status;
   int n;
   int jacobi;         // 1: the Fourier preconditioner was dropped for Jacobi
+  double drop;        // mixed precision: a round of FP32 iterations ends once its residual fell by this factor
+  double floor_inf, floor_l2;  // ... below the residual of the round's check (0 in FP64)
   int unconstrained;  // 1: plain PCG on (E + diag J) x = b, no charge constraint (two-RHS solver)
   double tsum;        // two-RHS solver: sum of t (A t = 1)
+};
+
+// Stabilised quasi-Newton minimiser (QEQ_FLAG_SQNM): per-structure state.  Vectors live in
+// Jacobi-scaled coordinates x = D^{1/2} q; slots 0..QEQ_SQNM_HISTORY-1 hold the last steps dx
+// and gradient changes dg.
+#define QEQ_SQNM_HISTORY 8
+#define QEQ_SQNM_NDOT (5 * QEQ_SQNM_HISTORY + 1)  // dot products per iteration
+struct SqnmState {
+  double XX[QEQ_SQNM_HISTORY][QEQ_SQNM_HISTORY];  // dx_i . dx_j
+  double XG[QEQ_SQNM_HISTORY][QEQ_SQNM_HISTORY];  // dx_i . dg_j
+  double GG[QEQ_SQNM_HISTORY][QEQ_SQNM_HISTORY];  // dg_i . dg_j
+  double gX[QEQ_SQNM_HISTORY];                    // g . dx_i (current gradient)
+  double coef[QEQ_SQNM_HISTORY];                  // step coefficients of dx_i
+  double gg;                                      // g . g
+  double alpha;                                   // steepest-descent step length in the complement
+  double E, E_prev;                               // energy at the current and at the previous point
+  double c;                                       // D-weighted mean of A q + chi (the projection)
+  int count;                                      // history entries in use
+  int head;                                       // slot of the newest entry
+  int has_prev;                                   // a previous gradient exists
+  int subspace;                                   // significant directions used by the last step
+  int revert;                                     // 1: the last step raised the energy and is undone
+  int pad_;
 };
 
 // Loop counters of the device-paced solve graph (device resident).
@@ -293,6 +318,10 @@ struct qeq_plan_s {
   int4* d_xitems = nullptr;        // x pass {s, z, y0, lines}
   int* d_xitem_off = nullptr;      // n_struct + 1: first x item of each structure
   double* d_stress_part = nullptr; // per-chunk partial sums of the strain derivative (6 + 2 QEQ_MAX_SPECIES each)
+  // SQNM solver (QEQ_FLAG_SQNM only): history dx, dg (QEQ_SQNM_HISTORY x N each), the
+  // scaled gradient (N), per-chunk partial dot products, per-structure state
+  double *d_sqnm_dx = nullptr, *d_sqnm_dg = nullptr, *d_sqnm_g = nullptr, *d_sqnm_part = nullptr;
+  SqnmState* d_sqnm = nullptr;
   int* d_bin_struct = nullptr;     // structure of each global bin
   int* d_brick_struct = nullptr;   // structure of each global brick
   int* d_brick_cand = nullptr;     // QEQ_BRICK_CAND ints per brick (brick_candidates)

@@ -160,10 +160,18 @@ __device__ void residual_test(PcgScalars& c, const double* tot, double ref, int 
   const double f = final_check ? 1.0 : c.inner;
   // a final check adds the bound on its residual's own error (0 when it is FP64)
   const double sl = final_check ? c.slack : 0.0;
-  bool ok = pinf + sl <= f * c.tol_inf && (c.tol_l2 <= 0.0 || pl2 + sl * sqrt(n) <= f * c.tol_l2);
+  // FP32 rounds also end once the residual fell by `drop` below that of the round's check:
+  // each FP32 product carries ~3e-7 of the mesh potentials' size as noise, so FP32 CG
+  // stalls near 1e-6..1e-5 of the starting residual; the next check then restarts on the
+  // correction, whose products are accurate relative to its own (small) size
+  const double ti = final_check ? f * c.tol_inf : fmax(f * c.tol_inf, c.floor_inf);
+  const double tl = final_check ? f * c.tol_l2 : fmax(f * c.tol_l2, c.floor_l2);
+  bool ok = pinf + sl <= ti && (c.tol_l2 <= 0.0 || pl2 + sl * sqrt(n) <= tl);
   if (!isfinite(pinf)) ok = false;
   if (final_check) {
     c.converged = ok ? 1 : 0;
+    c.floor_inf = c.drop * pinf;
+    c.floor_l2 = c.drop * pl2;
   } else {
     if (ok) {
       c.converged = 1;
@@ -621,6 +629,8 @@ const int kItersPerCheck = 4;
 const int kMaxRestarts = 4;  // residual replacements after a failed final check
 // mixed precision: the iterations stop at this fraction of the final check's thresholds
 const double kMixedInnerTol = 0.5;
+// mixed precision: residual reduction of one round of FP32 iterations (see residual_test)
+const double kMixedRoundDrop = 1e-5;
 // bound on the relative error of the FP32 operator, against max|A x| + max D max|x|
 // (measured errors are below 1e-5 of that scale; 1e-4 leaves a margin of ten)
 const double kMixedOpErr = 1e-4;
@@ -873,6 +883,10 @@ __global__ void k_set_tol(PcgScalars* sc, int ns, double charge_tol, double rel_
   c.tol_l2 = rel_tol > 0 ? scale * rel_tol * sqrt(c.chi_p2) : 0.0;
   c.inner = inner;
   c.unconstrained = unconstrained;
+  // mixed precision (inner < 1): a round of FP32 iterations reduces its residual at most
+  // kMixedRoundDrop-fold before the next check (the floors are set by each check)
+  c.drop = inner < 1.0 ? kMixedRoundDrop : 0.0;
+  c.floor_inf = c.floor_l2 = 0.0;
 }
 
 // two-RHS solver: per structure sum s (sorted, in q) and sum t (t in input order, in t_in)
@@ -905,6 +919,400 @@ __global__ void k_two_rhs_combine(const Chunk* __restrict__ chunks, const int* _
     const int i = perm[a];
     t_out[i] = q[a] + m * t_out[i];
   }
+}
+
+// ---------------------------------------------------------------- SQNM solver
+// Stabilised quasi-Newton minimiser of E(q) = chi.q + 1/2 q.(E + diag J) q on the constraint
+// plane (the alternative to CG in the paper's solver comparison, SI solver figure), in the
+// Jacobi-scaled coordinates x = D^{1/2} q where the projected gradient is
+// g = D^{-1/2} (A q + chi - c 1), c = sum D^-1 (A q + chi) / sum D^-1 (the steepest-descent
+// direction -D^{-1/2} g is the PCG's Jacobi direction).  From the last steps dx_i and
+// gradient changes dg_i: the significant subspace of the normalised steps (eigenvalues of
+// their overlap above 1e-4 of the largest), the symmetrised Hessian in it, Newton steps
+// along its eigenvectors with curvatures enlarged by their residues, and a steepest-descent
+// step alpha in the complement; alpha grows by 1.1 while the energy falls and halves, with
+// the history cleared and the step undone, when it rises (the rise judged from the
+// gradients at both ends of the step, exact for the quadratic energy).  A q comes from y = y1 + A (q - q1): y1 = A q1 by the
+// last FP64 matvec (q1 = 0 in FP64 plans), the change in the plan's precision.
+
+// y + chi statistics: [0] sum D^-1 (y + chi), [1] sum (y + chi - ref), [2] sum (..)^2, [3] max,
+// [4] min of y + chi, [5] the energy chi.q + 1/2 q.y; the convergence test on the projected
+// residual -(y + chi) (residual_test's form, negated)
+__global__ void k_sqnm_stats(const Chunk* __restrict__ chunks, const double* __restrict__ y1,
+                             const double* __restrict__ Ad, const double* __restrict__ chi,
+                             const double* __restrict__ dinv, const double* __restrict__ q,
+                             PcgScalars* __restrict__ sc, SqnmState* __restrict__ qs, double* part, int* counter,
+                             int max_iter, int final_check) {
+  const Chunk ch = chunks[blockIdx.x];
+  if (!final_check && !sc[ch.s].active) return;
+  const double ref = qs[ch.s].c;
+  double v[6] = {0, 0, 0, -1e300, 1e300, 0};
+  const int op[6] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX, RED_MIN, RED_SUM};
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    const double ya = (y1 ? y1[a] : 0.0) + Ad[a];
+    const double e = ya + chi[a];
+    v[0] += dinv[a] * e;
+    v[1] += e - ref;
+    v[2] += (e - ref) * (e - ref);
+    v[3] = fmax(v[3], e);
+    v[4] = fmin(v[4], e);
+    v[5] += q[a] * (chi[a] + 0.5 * ya);
+  }
+  double tot[6];
+  if (chunk_reduce<6>(v, op, ch, part, counter, tot)) {
+    PcgScalars& c = sc[ch.s];
+    SqnmState& S = qs[ch.s];
+    const double n = (double)c.n;
+    S.c = tot[0] / c.s0;
+    S.E = tot[5];
+    // residual r = -(y + chi): sum, max, min; ||P r|| about ref
+    c.r_sum = -(ref * n + tot[1]);
+    c.r_max = -tot[4];
+    c.r_min = -tot[3];
+    const double dmean = tot[1] / n, mean = -(ref + dmean);
+    const double pinf = fmax(c.r_max - mean, mean - c.r_min);
+    c.r_l2 = sqrt(fmax(tot[2] - tot[1] * dmean, 0.0));
+    // as residual_test: in mixed precision a round also ends once its residual fell `drop`-fold
+    const double ti = final_check ? c.tol_inf : fmax(c.inner * c.tol_inf, c.floor_inf);
+    const double tl = final_check ? c.tol_l2 : fmax(c.inner * c.tol_l2, c.floor_l2);
+    const bool ok = isfinite(pinf) && pinf <= ti && (c.tol_l2 <= 0.0 || c.r_l2 <= tl);
+    if (final_check) {
+      c.converged = ok ? 1 : 0;
+      c.floor_inf = c.drop * pinf;
+      c.floor_l2 = c.drop * c.r_l2;
+    } else if (ok) {
+      c.converged = 1;
+      c.active = 0;
+    } else if (c.iters >= max_iter) {
+      c.active = 0;
+    }
+  }
+}
+
+// g = D^{-1/2} (y + chi - c) (stored), the new gradient change dg_h = g - g_prev into slot h
+// (when a step was taken), and the dot products of the new history row and of g with the
+// history: [0..H) g.dx_i, [H] g.g, then per slot j: dx_h.dx_j, dx_h.dg_j, dx_j.dg_h, dg_h.dg_j.
+// The structure's last chunk adds the chunk partials in chunk order into its state.
+__global__ void __launch_bounds__(256) k_sqnm_dots(const Chunk* __restrict__ chunks, const double* __restrict__ y1,
+                                                   const double* __restrict__ Ad, const double* __restrict__ chi,
+                                                   const double* __restrict__ dinv, const PcgScalars* __restrict__ sc,
+                                                   SqnmState* __restrict__ qs, int64_t N, double* __restrict__ g,
+                                                   double* __restrict__ dx, double* __restrict__ dg,
+                                                   double* __restrict__ part, int* __restrict__ counter) {
+  constexpr int H = QEQ_SQNM_HISTORY, ND = QEQ_SQNM_NDOT, PS = QEQ_SQNM_NDOT + 7;
+  __shared__ double red[8];
+  __shared__ bool last;
+  const Chunk ch = chunks[blockIdx.x];
+  if (!sc[ch.s].active) return;
+  SqnmState& S = qs[ch.s];
+  const int cnt = S.count, h = S.head, hp = S.has_prev;
+  const double cc = S.c;
+  double v[ND];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) v[k] = 0.0;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    const double ga = sqrt(dinv[a]) * ((y1 ? y1[a] : 0.0) + Ad[a] + chi[a] - cc);
+    double dgh = 0.0;
+    if (hp && cnt > 0) {
+      dgh = ga - g[a];
+      dg[(int64_t)h * N + a] = dgh;
+    }
+    g[a] = ga;
+    v[H] += ga * ga;
+    const double dxh = (cnt > 0) ? dx[(int64_t)h * N + a] : 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      if (j >= cnt) break;
+      const double dxj = dx[(int64_t)j * N + a];
+      const double dgj = (j == h) ? dgh : dg[(int64_t)j * N + a];
+      v[j] += ga * dxj;
+      if (hp) {
+        v[H + 1 + 4 * j] += dxh * dxj;
+        v[H + 2 + 4 * j] += dxh * dgj;
+        v[H + 3 + 4 * j] += dxj * dgh;
+        v[H + 4 + 4 * j] += dgh * dgj;
+      }
+    }
+  }
+  // fixed-order block sums (shuffle tree, warps in order) of every value
+  const int nw = blockDim.x >> 5;
+#pragma unroll 1
+  for (int k = 0; k < ND; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < nw; ++i) t += red[i];
+      part[(size_t)blockIdx.x * PS + k] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(counter + ch.s, 1) == ch.count - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x != 0) return;
+  double t[ND];
+  for (int k = 0; k < ND; ++k) t[k] = 0.0;
+  for (int c = 0; c < ch.count; ++c)
+    for (int k = 0; k < ND; ++k) t[k] += ((volatile double*)part)[(size_t)(ch.first + c) * PS + k];
+  counter[ch.s] = 0;
+  for (int j = 0; j < cnt; ++j) S.gX[j] = t[j];
+  S.gg = t[H];
+  if (hp) {
+    for (int j = 0; j < cnt; ++j) {
+      S.XX[h][j] = S.XX[j][h] = t[H + 1 + 4 * j];
+      S.XG[h][j] = t[H + 2 + 4 * j];
+      S.XG[j][h] = t[H + 3 + 4 * j];
+      S.GG[h][j] = S.GG[j][h] = t[H + 4 + 4 * j];
+    }
+  }
+}
+
+// symmetric eigen-decomposition of an n x n matrix (n <= QEQ_SQNM_HISTORY) by cyclic Jacobi
+// rotations: a is overwritten (its diagonal becomes the eigenvalues), v gets the eigenvectors
+// as columns
+__device__ void sqnm_jacobi_eig(double (*a)[QEQ_SQNM_HISTORY], double (*v)[QEQ_SQNM_HISTORY], int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += a[i][i] * a[i][i];
+      for (int j = i + 1; j < n; ++j) off += a[i][j] * a[i][j];
+    }
+    if (off <= 1e-30 * diag || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (a[p][q] == 0.0) continue;
+        const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = cs * akp - sn * akq;
+          a[k][q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = cs * apk - sn * aqk;
+          a[q][k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = v[k][p], vkq = v[k][q];
+          v[k][p] = cs * vkp - sn * vkq;
+          v[k][q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+}
+
+// one thread per structure: alpha from the energy change, the subspace quantities and the
+// step coefficients; then the slot the coming step is stored in
+__global__ void k_sqnm_plan(const PcgScalars* __restrict__ sc, SqnmState* __restrict__ qs, int ns) {
+  constexpr int H = QEQ_SQNM_HISTORY;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns || !sc[s].active) return;
+  SqnmState& S = qs[s];
+  S.revert = 0;
+  if (S.has_prev && S.count > 0) {
+    // energy change of the last step dx_h, exact for the quadratic E:
+    // dE = 1/2 dx_h . (g_prev + g) = g . dx_h - 1/2 dx_h . dg_h (noise scales with the step,
+    // unlike a difference of two energies in mixed precision)
+    const int h = S.head;
+    const double dE = S.gX[h] - 0.5 * S.XG[h][h];
+    if (dE > 1e-14 * fabs(S.E)) {
+      // the last step raised the energy: undo it (the step kernel subtracts slot head),
+      // halve alpha, forget the history; the next matvec re-evaluates the old point
+      S.revert = 1;
+      S.alpha *= 0.5;
+      S.count = 0;
+      S.has_prev = 0;
+      S.E = S.E_prev;
+      return;
+    }
+    S.alpha = fmin(S.alpha * 1.1, 4.0);
+  }
+  const int n = S.count;
+  for (int i = 0; i < H; ++i) S.coef[i] = 0.0;
+  S.subspace = 0;
+  if (n > 0) {
+    double nrm[H], A[H][H], U[H][H];
+    for (int i = 0; i < n; ++i) nrm[i] = sqrt(fmax(S.XX[i][i], 1e-300));
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[i][j] = S.XX[i][j] / (nrm[i] * nrm[j]);
+    sqnm_jacobi_eig(A, U, n);
+    double lmax = 0.0;
+    for (int l = 0; l < n; ++l) lmax = fmax(lmax, A[l][l]);
+    // V: coefficients of the orthonormal subspace vectors on the raw dx_i
+    double V[H][H];
+    int m = 0;
+    for (int l = 0; l < n; ++l) {
+      if (!(A[l][l] > 1e-4 * lmax)) continue;
+      const double sl = 1.0 / sqrt(A[l][l]);
+      for (int i = 0; i < n; ++i) V[i][m] = U[i][l] * sl / nrm[i];
+      ++m;
+    }
+    // subspace Hessian: 1/2 (V^T XG V + (V^T XG V)^T)
+    double Hs[H][H], Q[H][H];
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) t += V[i][a] * V[j][b] * (S.XG[i][j] + S.XG[j][i]);
+        Hs[a][b] = 0.5 * t;
+      }
+    sqnm_jacobi_eig(Hs, Q, m);
+    for (int jdir = 0; jdir < m; ++jdir) {
+      double B[H];  // coefficients of direction jdir on the raw dx_i
+      for (int i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int a = 0; a < m; ++a) t += V[i][a] * Q[a][jdir];
+        B[i] = t;
+      }
+      const double kap = Hs[jdir][jdir];
+      double yy = 0.0, wy = 0.0, ww = 0.0, gw = 0.0;
+      for (int i = 0; i < n; ++i) {
+        gw += B[i] * S.gX[i];
+        for (int k = 0; k < n; ++k) {
+          yy += B[i] * B[k] * S.GG[i][k];
+          wy += B[i] * B[k] * S.XG[i][k];
+          ww += B[i] * B[k] * S.XX[i][k];
+        }
+      }
+      const double res2 = fmax(yy - 2.0 * kap * wy + kap * kap * ww, 0.0);
+      const double kt = sqrt(kap * kap + res2);
+      if (!(kt > 0.0) || !isfinite(kt)) continue;
+      const double f = (S.alpha - 1.0 / kt) * gw;
+      for (int i = 0; i < n; ++i) S.coef[i] += f * B[i];
+    }
+    S.subspace = m;
+  }
+  // slot of the coming step: the next slot, overwriting the oldest entry once full
+  const int nh = (n == 0) ? 0 : (S.head + 1) % H;
+  S.head = nh;
+  S.count = n < H ? n + 1 : H;
+  S.has_prev = 1;
+  S.E_prev = S.E;
+}
+
+__global__ void k_sqnm_count(PcgScalars* __restrict__ sc, int ns) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < ns && sc[s].active) sc[s].iters += 1;
+}
+
+// dx = -alpha g + sum_i coef_i dx_i (scaled coordinates), q += D^{-1/2} dx, dx into the new slot
+__global__ void k_sqnm_step(const Chunk* __restrict__ chunks, const PcgScalars* __restrict__ sc,
+                            const SqnmState* __restrict__ qs, int64_t N, const double* __restrict__ g,
+                            double* __restrict__ dx, const double* __restrict__ dinv, double* __restrict__ q) {
+  constexpr int H = QEQ_SQNM_HISTORY;
+  const Chunk ch = chunks[blockIdx.x];
+  if (!sc[ch.s].active) return;
+  const SqnmState& S = qs[ch.s];
+  const int cnt = S.count, h = S.head;
+  if (S.revert) {  // back to the point before the last step (slot h holds that step)
+    for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) q[a] -= sqrt(dinv[a]) * dx[(int64_t)h * N + a];
+    return;
+  }
+  // coefficients of the previous entries (the new slot h held the oldest entry when full)
+  double cf[H];
+#pragma unroll
+  for (int i = 0; i < H; ++i) cf[i] = S.coef[i];
+  const double al = S.alpha;
+  for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
+    double d = -al * g[a];
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+      if (i < cnt && cf[i] != 0.0) d += cf[i] * dx[(int64_t)i * N + a];
+    dx[(int64_t)h * N + a] = d;
+    q[a] += sqrt(dinv[a]) * d;
+  }
+}
+
+__global__ void k_sqnm_init(const PcgScalars* __restrict__ sc, SqnmState* __restrict__ qs, int ns) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  SqnmState& S = qs[s];
+  S.count = 0;
+  S.head = 0;
+  S.has_prev = 0;
+  S.alpha = 1.0;
+  S.c = 0.0;
+  S.E = S.E_prev = 0.0;
+  S.subspace = 0;
+  S.revert = 0;
+  (void)sc;
+}
+
+__global__ void k_sub2(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = a[i] - b[i];
+}
+
+// SQNM rounds from the current q (the start of qeq_solve has run: q on the constraint plane,
+// scalars and tolerances set): blocks of SQNM steps paced from the host, an FP64 check per
+// round, restarts (with a fresh history) for the structures whose check fails.
+qeq_status sqnm_rounds(qeq_plan_s* P, int prec) {
+  cudaStream_t s = P->stream;
+  const int nc = P->n_chunks, ns = P->n_struct, max_iter = P->desc.max_iter;
+  const int nb = (int)((P->n_atoms + 255) / 256);
+  const int64_t N = P->n_atoms;
+  const bool mixed = prec == QEQ_MIXED;
+  int* sq_counter = P->d_counter + 3 * ns;
+  for (int outer = 0; outer <= kMaxRestarts + 1; ++outer) {
+    count_launch(P);
+    k_sqnm_init<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, P->d_sqnm, ns);
+    if (mixed) {  // y1 = A q1 in FP64 at the round's start, q1 = q
+      TRY(launch_matvec(P, QEQ_FP64, P->d_q, P->d_r1, 1, 0, 0, nullptr));
+      count_launch(P);
+      k_copy2<<<nb, 256, 0, s>>>(P->d_q, P->d_q, N, P->d_q1, P->d_x);
+    }
+    TRY(cudaGetLastError());
+    const int max_launches = max_iter / kItersPerCheck + 2;
+    for (int l = 0; l < max_launches; ++l) {
+      for (int k = 0; k < kItersPerCheck; ++k) {
+        const double* x = P->d_q;
+        if (mixed) {
+          count_launch(P);
+          k_sub2<<<nb, 256, 0, s>>>(N, P->d_q, P->d_q1, P->d_x);
+          x = P->d_x;
+        }
+        TRY(launch_matvec(P, prec, x, P->d_Ap, 1, 1, 0, nullptr));
+        count_launch(P, 5);
+        k_sqnm_stats<<<nc, 256, 0, s>>>(P->d_chunks, mixed ? P->d_r1 : nullptr, P->d_Ap, P->d_chi, P->d_dinv, P->d_q,
+                                        P->d_sc, P->d_sqnm, red_part(P), red_counter(P), max_iter, 0);
+        k_sqnm_dots<<<nc, 256, 0, s>>>(P->d_chunks, mixed ? P->d_r1 : nullptr, P->d_Ap, P->d_chi, P->d_dinv, P->d_sc,
+                                       P->d_sqnm, N, P->d_sqnm_g, P->d_sqnm_dx, P->d_sqnm_dg, P->d_sqnm_part,
+                                       sq_counter);
+        k_sqnm_plan<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, P->d_sqnm, ns);
+        k_sqnm_step<<<nc, 256, 0, s>>>(P->d_chunks, P->d_sc, P->d_sqnm, N, P->d_sqnm_g, P->d_sqnm_dx, P->d_dinv,
+                                       P->d_q);
+        k_sqnm_count<<<(ns + 127) / 128, 128, 0, s>>>(P->d_sc, ns);
+        TRY(cudaGetLastError());
+      }
+      count_launch(P);
+      k_done<<<1, 256, 0, s>>>(P->d_sc, ns, P->d_err, P->d_done);
+      TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRY(cudaStreamSynchronize(s));
+      if (P->h_done[0]) break;
+    }
+    // FP64 check of every structure: y = A q, the projected residual, the energy terms
+    TRY(launch_matvec(P, QEQ_FP64, P->d_q, P->d_Ap, 1, 0, 0, nullptr));
+    count_launch(P, 2);
+    k_sqnm_stats<<<nc, 256, 0, s>>>(P->d_chunks, nullptr, P->d_Ap, P->d_chi, P->d_dinv, P->d_q, P->d_sc, P->d_sqnm,
+                                    red_part(P), red_counter(P), max_iter, 1);
+    k_after_check<<<1, 256, 0, s>>>(P->d_sc, ns, kMaxRestarts, max_iter, P->d_err, P->d_done);
+    TRY(cudaGetLastError());
+    TRY(cudaMemcpyAsync(P->h_done, P->d_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (P->h_done[0]) break;
+  }
+  return QEQ_OK;
 }
 
 // Every PCG round from the current q and r: the first direction, then the device-paced
@@ -1134,7 +1542,10 @@ extern "C" qeq_status qeq_solve(qeq_plan P, const double* d_pos, const int32_t* 
     TRY(init_scalars(P, h_qtot) == QEQ_OK ? cudaSuccess : cudaErrorUnknown);  // synchronises the copy
     reject = P->d_reject;
   }
-    TRY_ST(pcg_rounds(P, prec));
+    if (P->desc.flags & QEQ_FLAG_SQNM)
+      TRY_ST(sqnm_rounds(P, prec));
+    else
+      TRY_ST(pcg_rounds(P, prec));
   }
   // energy terms from the final check's A q, outputs in input order
   count_launch(P);

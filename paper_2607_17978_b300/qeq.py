@@ -24,6 +24,7 @@ QEQ_WARM_COLD, QEQ_WARM_USER, QEQ_WARM_MLP = 0, 1, 2
 QEQ_FLAG_NO_GRAPH = 1
 QEQ_FLAG_TEST_STALL = 2
 QEQ_FLAG_TWO_RHS = 4
+QEQ_FLAG_SQNM = 8
 QEQ_N_STAGES = 8
 STAGE_NAMES = ["species_sums", "spread", "fft_z", "fft_y", "fft_x_green", "ifft_y", "ifft_z", "gather"]
 
@@ -217,7 +218,7 @@ class Plan:
                      sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), coulomb_k, charge_tol, ewald_tol,
                      r_cut, spline_order, mesh_spacing, prec, max_iter, residual_tol,
                      (0 if graph else QEQ_FLAG_NO_GRAPH) | (QEQ_FLAG_TEST_STALL if test_stall else 0)
-                     | {"projected": 0, "two_rhs": QEQ_FLAG_TWO_RHS}[solver],
+                     | {"projected": 0, "two_rhs": QEQ_FLAG_TWO_RHS, "sqnm": QEQ_FLAG_SQNM}[solver],
                      {"jacobi": 0, "fourier": 1}[preconditioner],
                      precond_spacing, precond_width, precond_scale)
         with torch.cuda.device(self.device):

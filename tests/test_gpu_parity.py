@@ -211,6 +211,34 @@ def test_two_rhs_solver_matches_the_oracle(precision, pre):
     assert e.value.status == qeq.QEQ_ERR_INVALID
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sqnm_solver_matches_the_oracle(precision):
+    """The stabilised quasi-Newton minimiser (QEQ_FLAG_SQNM) on an uneven batch with charged
+    cells: charges within 1e-5 e of the dense oracle, the constraint exact, the same charges as
+    the CG; repeated solves bitwise equal (fixed-order sums, deterministic subspace algebra)."""
+    from paper_2607_17978_b300 import qeq
+    structs = _small_structs()
+    plan = _plan(structs, precision=precision, solver="sqnm")
+    args = qeq.pack(structs)
+    res = plan.solve(*args)
+    qg = res.q.cpu().numpy()
+    mug = res.mu.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
+    for i, st in enumerate(structs):
+        _, q, mu, *_r = _oracle(st)
+        sl = slice(off[i], off[i + 1])
+        print(f"SQNM {precision} structure {i} ({st.n} atoms): {res.info[i]['iterations']} steps, "
+              f"max|dq| {np.abs(qg[sl] - q).max():.2e}")
+        assert np.abs(qg[sl] - q).max() < 1e-5, (i, np.abs(qg[sl] - q).max(), res.info[i])
+        assert abs(qg[sl].sum() - st.q_tot) < 1e-9
+        assert abs(mug[i] - mu) < 1e-4 * max(1.0, abs(mu))
+        assert res.info[i]["status"] == 0 and res.info[i]["iterations"] > 0
+    res2 = plan.solve(*args)
+    assert np.array_equal(qg, res2.q.cpu().numpy())
+    qp = _plan(structs, precision=precision).solve(*args).q.cpu().numpy()
+    assert np.abs(qg - qp).max() < 2e-5
+
+
 def test_translation_invariance_within_mesh_error(cfg1):
     from paper_2607_17978_b300 import qeq
     st, (A, q, *_r) = cfg1
