@@ -508,6 +508,9 @@ inline int fft_ld64(int K) { return K | 1; }
 // Tile sizes for meshes whose largest sizes per direction are maxK[3] (most complex
 // meshes max_ncm): item lines of the y/z passes and of the x pass (2 max_ncm lines per
 // pair); FP64 sub-tiles hold half as many lines (the same bytes).
+#ifndef QEQ_FFT_MAX_LINES
+#define QEQ_FFT_MAX_LINES 64
+#endif
 inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   FftGeom g;
   g.max_ncm = max_ncm;
@@ -517,15 +520,17 @@ inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   g.ldy64 = fft_ld64(maxK[1]);
   g.ldx32 = fft_ld32(maxK[0]);
   g.ldx64 = fft_ld64(maxK[0]);
-  // two buffers per CTA and two CTAs per SM: about 36 KB of lines per buffer
+  // two buffers per CTA and two CTAs per SM: about 36 KB of lines per buffer, as many
+  // lines per work unit as fit (short lines: up to 64, so that a unit's stages and barriers
+  // cover enough points)
   const int ldyz = std::max(g.ldz32, g.ldy32);
   const int64_t budget = 36 * 1024;
-  int tl = 8;
+  int tl = QEQ_FFT_MAX_LINES;
   while (tl > 1 && (int64_t)tl * ldyz * 8 > budget) tl >>= 1;
   g.tl = tl;
   g.sub32 = tl;
   g.sub64 = std::max(1, tl / 2);
-  int tlx = 4;
+  int tlx = QEQ_FFT_MAX_LINES / 2;
   while (tlx > 1 && (int64_t)2 * max_ncm * tlx * g.ldx32 * 8 > budget) tlx >>= 1;
   g.tlx = tlx;
   g.subx32 = tlx;
