@@ -511,6 +511,12 @@ inline int fft_ld64(int K) { return K | 1; }
 #ifndef QEQ_FFT_MAX_LINES
 #define QEQ_FFT_MAX_LINES 64
 #endif
+#ifndef QEQ_FFT_POW2
+#define QEQ_FFT_POW2 1  // line counts rounded down to powers of two (the stores group lines so)
+#endif
+#ifndef QEQ_FFT_BUDGET_KB
+#define QEQ_FFT_BUDGET_KB 36  // lines per FFT buffer (two buffers per CTA, two CTAs per SM)
+#endif
 inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   FftGeom g;
   g.max_ncm = max_ncm;
@@ -524,14 +530,17 @@ inline FftGeom fft_geometry(const int* maxK, int max_ncm) {
   // lines per work unit as fit (short lines: up to 64, so that a unit's stages and barriers
   // cover enough points)
   const int ldyz = std::max(g.ldz32, g.ldy32);
-  const int64_t budget = 36 * 1024;
-  int tl = QEQ_FFT_MAX_LINES;
-  while (tl > 1 && (int64_t)tl * ldyz * 8 > budget) tl >>= 1;
+  const int64_t budget = (int64_t)QEQ_FFT_BUDGET_KB * 1024;
+  int tl = (int)std::max<int64_t>(1, std::min<int64_t>(QEQ_FFT_MAX_LINES, budget / ((int64_t)ldyz * 8)));
+  if (QEQ_FFT_POW2)
+    while (tl & (tl - 1)) tl &= tl - 1;  // largest power of two not above
   g.tl = tl;
   g.sub32 = tl;
   g.sub64 = std::max(1, tl / 2);
-  int tlx = QEQ_FFT_MAX_LINES / 2;
-  while (tlx > 1 && (int64_t)2 * max_ncm * tlx * g.ldx32 * 8 > budget) tlx >>= 1;
+  int tlx = (int)std::max<int64_t>(1, std::min<int64_t>(QEQ_FFT_MAX_LINES / 2,
+                                                         budget / ((int64_t)2 * max_ncm * g.ldx32 * 8)));
+  if (QEQ_FFT_POW2)
+    while (tlx & (tlx - 1)) tlx &= tlx - 1;
   g.tlx = tlx;
   g.subx32 = tlx;
   g.subx64 = std::max(1, tlx / 2);
