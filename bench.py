@@ -265,7 +265,7 @@ def oracle_error_batch(structs, q, mu, every: int = 64):
              "max_dq_e": worst, "dmu_eV": dmu}, len(sample) / t, t)
 
 
-def charge_training_leg(dev, flush, n_struct: int = 256, steps: int = 3):
+def charge_training_leg(dev, flush, n_struct: int = 256, steps: int = 3, precision: str = "mixed"):
     """4G charge training on cached dense matrices (qeq_dense_*): E of a fixed synthetic
     training batch assembled once, then per step a re-inversion with a new (learned) hardness,
     the charges and their backward pass.  Roofline of the inversion kernel against the FP64
@@ -277,7 +277,7 @@ def charge_training_leg(dev, flush, n_struct: int = 256, steps: int = 3):
     pos, spc, chi, J, qt = qeq.pack(structs)
     d_pos, d_spc = torch.tensor(pos, device=dev), torch.tensor(spc, device=dev)
     d_chi, d_J = torch.tensor(chi, device=dev), torch.tensor(J, device=dev)
-    dense = qeq.dense_for_structures(structs, device=dev)
+    dense = qeq.dense_for_structures(structs, device=dev, precision=precision)
     rng = np.random.default_rng(1)
     Js = [d_J * torch.tensor(rng.uniform(0.9, 1.1, len(J)), device=dev) for _ in range(steps + 1)]
     gq = torch.tensor(rng.normal(size=len(J)), device=dev)
@@ -313,20 +313,25 @@ def charge_training_leg(dev, flush, n_struct: int = 256, steps: int = 3):
         inv_ms.append(e0.elapsed_time(e1))
     launches = dense.query(0)["kernel_launches"]
     dense.close()
-    # FP64 operations of the inversion per structure: Cholesky n^3/3, triangular inverse n^3/3,
-    # U^-1 U^-T n^3/3 (multiply and add counted apart), the border O(n^2)
+    # operations of the inversion per structure: Cholesky n^3/3, triangular inverse n^3/3,
+    # U^-1 U^-T n^3/3 (multiply and add counted apart), the border O(n^2).  Peaks: FP64 1.25
+    # TFLOP/s nominal; FP32 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz = 77.0 TFLOP/s
     flops = float(sum(float(n) ** 3 for n in ns))
     t_inv = statistics.median(inv_ms) * 1e-3
-    peak = 1.25
+    peak = 77.0 if precision == "mixed" else 1.25
     return {"structures": len(structs), "atoms": int(sum(ns)), "atoms_per_structure": [min(ns), max(ns)],
             "recipe": "rock-salt training cells (jitter 0.2 A, 2% vacancies), log-uniform 64-512 atoms",
             "assemble_ms": assemble_ms, "step_ms": statistics.median(step_ms),
             "structures_per_s": len(structs) / (statistics.median(step_ms) * 1e-3),
             "step": "re-invert with a new hardness + charges + backward (dL/dchi, dL/dJ)",
+            "precision": ("FP32 inverse, charges and gradients refined to FP64 (2 steps)" if precision == "mixed"
+                          else "FP64 inverse"),
             "invert_ms": statistics.median(inv_ms), "kernel_launches_total": int(launches),
             "roofline": {"kernel": "k_dense_invert", "bound": "alu", "achieved": flops / t_inv / 1e12,
-                         "peak": peak, "unit": "TFLOP/s (FP64)", "frac": flops / t_inv / 1e12 / peak,
-                         "peak_source": "nominal FP64 rate of this part (no measured FP64 peak)",
+                         "peak": peak, "unit": "TFLOP/s (%s)" % ("FP32" if precision == "mixed" else "FP64"),
+                         "frac": flops / t_inv / 1e12 / peak,
+                         "peak_source": ("FP32 CUDA-core rate from unit counts and the 2032 MHz clock"
+                                         if precision == "mixed" else "nominal FP64 rate of this part"),
                          "flops_per_launch": flops}}
 
 
@@ -561,7 +566,8 @@ def run_ours(args):
     box = {}
 
     def trick():
-        box["dEdq"] = plan.matvec(d_pos, d_spc, q_out, fp64=True)
+        # dE/dq = E q only feeds the lambda solve's right-hand side: the plan's precision will do
+        box["dEdq"] = plan.matvec(d_pos, d_spc, q_out, fp64=(args.precision == "fp64"))
         box["lam"] = plan.solve(d_pos, d_spc, box["dEdq"], d_J, zeros)
         box["F"] = plan.forces(d_pos, d_spc, q_out, box["lam"].q)
 
@@ -583,7 +589,7 @@ def run_ours(args):
     trick_ms = timed(trick)
     lam_q = box["lam"].q
     trick_parts = {
-        "dEdq_matvec_ms": timed(lambda: plan.matvec(d_pos, d_spc, q_out, fp64=True)),
+        "dEdq_matvec_ms": timed(lambda: plan.matvec(d_pos, d_spc, q_out, fp64=(args.precision == "fp64"))),
         "lambda_solve_ms": timed(lambda: plan.solve(d_pos, d_spc, box["dEdq"], d_J, zeros)),
         "forces_ms": timed(lambda: plan.forces(d_pos, d_spc, q_out, lam_q)),
         "forces_without_lambda_ms": timed(lambda: plan.forces(d_pos, d_spc, q_out)),
@@ -724,10 +730,14 @@ def run_ours(args):
         "ms_per_step": trick_ms, "atoms_per_s": n_atoms / (trick_ms * 1e-3),
         "lambda_pcg_iterations": trick_iters, "vs_charge_solve": trick_ms / ms,
         "parts_ms": {k: round(v, 4) for k, v in trick_parts.items()},
-        "form": "FP64 potential meshes and gradients; lambda solve in the chosen form, cold start",
+        "form": ("potential meshes in the plan's precision (%s), pair derivative and sums in FP64; "
+                 "stress in FP64; lambda solve in the chosen form, cold start" % args.precision),
     }
     if rank == 0:
-        line["charge_training"] = charge_training_leg(dev, flush)
+        line["charge_training"] = charge_training_leg(dev, flush, precision="mixed")
+        line["charge_training"]["fp64_inverse"] = {
+            k: v for k, v in charge_training_leg(dev, flush, precision="fp64").items()
+            if k in ("step_ms", "structures_per_s", "invert_ms", "roofline")}
     if oracle_err:
         line["oracle_error"] = oracle_err
     if cpu:

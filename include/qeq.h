@@ -223,13 +223,16 @@ qeq_status qeq_matvec(qeq_plan plan, const double* d_pos, const int32_t* d_speci
  * elec_energy), the force when the charges minimise E_QEq itself.  lambda
  * comes from qeq_solve with chi := dE/dq and q_tot = 0.
  *
- * The potential gradients are taken in FP64 through the plane-wave terms of
- * eq. (matvec): the potential meshes (spread, FFT, reciprocal multiply,
- * inverse FFT) are interpolated with the derivative of the B-spline weights
+ * The potential gradients are taken through the plane-wave terms of eq.
+ * (matvec): the potential meshes (spread, FFT, reciprocal multiply, inverse
+ * FFT; FP64 in QEQ_FP64 plans, FP32 in QEQ_MIXED plans, whose meshes carry
+ * ~3e-7 of the potentials' size) are interpolated with the derivative of the
+ * B-spline weights
  * (dM_p(t)/dt = M_{p-1}(t) - M_{p-1}(t - 1)) and mapped to Cartesian
  * derivatives through the cell; the screened real-space pair term of the
- * Ewald split (SI "Ewald Summation") adds its analytic derivative.  The
- * error is that of the matvec's interpolation (ewald_tol).  The cell
+ * Ewald split (SI "Ewald Summation") adds its analytic derivative in FP64.
+ * The error is that of the matvec's interpolation (ewald_tol), plus FP32
+ * rounding in mixed plans.  The cell
  * counterpart is qeq_stress.
  *
  *   d_pos, d_species   as in qeq_solve (device, input order)
@@ -301,10 +304,17 @@ qeq_status qeq_profile_matvec(qeq_plan plan, int32_t n_rep, float* h_ms);
  * ewald_tol (default 1e-12 here); the inverse is FP64 (Cholesky of
  * E + diag J, triangular inverse, bordered by the Schur complement).
  *
+ * Precision (desc.precision): QEQ_FP64 (default) caches the FP64 inverse and
+ * charges are one FP64 matrix-vector product.  QEQ_MIXED inverts in FP32 (this
+ * GPU's FP32 pipe is far wider than its FP64 pipe) and refines every result in
+ * FP64 against the exact bordered matrix: x = K32 b, then twice
+ * x += K32 (b - A' x); each step shrinks the error by about cond(A') eps_FP32,
+ * so the charges and gradients reach FP64 accuracy for QEq matrices.
+ *
  * Handle: qeq_dense_create takes a qeq_plan_desc (n_struct, atom_offsets,
- * cells, n_species, sigma, coulomb_k, ewald_tol are read; the rest is
- * ignored) and the CUDA stream every call runs on; it allocates E, A'^{-1}
- * and a work matrix per structure (3 n^2 doubles) and nothing later.
+ * cells, n_species, sigma, coulomb_k, ewald_tol, precision are read; the rest
+ * is ignored) and the CUDA stream every call runs on; it allocates E, A'^{-1}
+ * and a work matrix per structure (3 n^2 values) and nothing later.
  * Structures have at most QEQ_DENSE_MAX_ATOMS atoms (else QEQ_ERR_CAPACITY).
  * Atom arrays are packed by atom_offsets, device pointers, FP64 / int32.
  * Calls of one handle are ordered on its stream; inputs must be ready there.
@@ -336,8 +346,9 @@ qeq_status qeq_dense_charges(qeq_dense dense, const double* d_chi, const double*
 qeq_status qeq_dense_backward(qeq_dense dense, const double* d_q, const double* d_gq,
                               double* d_gchi, double* d_gJ);
 
-/* Copy E (which = 0, n x n) or A'^{-1} (which = 1, (n+1) x (n+1)) of
- * structure s, row-major, to d_out (device). */
+/* Copy E (which = 0, n x n) or A'^{-1} (which = 1, (n+1) x (n+1); the FP32
+ * inverse widened to FP64 under QEQ_MIXED) of structure s, row-major, to
+ * d_out (device). */
 qeq_status qeq_dense_matrix(qeq_dense dense, int32_t s, int32_t which, double* d_out);
 
 /* The Ewald width and G-vector count chosen for structure s, and the kernels

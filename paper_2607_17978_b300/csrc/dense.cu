@@ -73,6 +73,12 @@ struct qeq_dense_s {
   double* d_E = nullptr;
   double* d_K = nullptr;
   double* d_Y = nullptr;      // U^{-1} during the inversion
+  // QEQ_MIXED: the inverse in FP32 (the B300's FP32 pipe is ~64x its FP64 pipe), charges and
+  // gradients refined in FP64 against the exact bordered matrix (E in FP64, J kept here)
+  int mixed = 0;
+  float* d_K32 = nullptr;
+  float* d_Y32 = nullptr;
+  double* d_Jc = nullptr;
   double* d_qtot = nullptr;
   std::vector<double> h_qtot;
   int* d_err = nullptr;
@@ -246,23 +252,36 @@ __device__ __forceinline__ double dense_block_sum(double a, double* red) {
   return tot;
 }
 
-// A'^{-1} of one structure per CTA (n <= QEQ_DENSE_MAX_ATOMS), in the K buffer (ld n + 1).
+// A'^{-1} of one structure per CTA (n <= QEQ_DENSE_MAX_ATOMS), in the K buffer (ld n + 1),
+// in the arithmetic type T (double; float for the refined FP32 inverse).
+template <typename T>
+__device__ __forceinline__ T dense_block_sum_t(T a, T* red) {
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  T tot = (T)0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];  // every thread, same order
+  __syncthreads();
+  return tot;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_dense_invert(const DenseStructDev* __restrict__ st,
                                                       const double* __restrict__ E, const double* __restrict__ J,
-                                                      double* __restrict__ Kbuf, double* __restrict__ Ybuf,
+                                                      T* __restrict__ Kbuf, T* __restrict__ Ybuf,
                                                       int* __restrict__ err) {
-  __shared__ double col[QEQ_DENSE_MAX_ATOMS];
-  __shared__ double red[8];
+  __shared__ T col[QEQ_DENSE_MAX_ATOMS];
+  __shared__ T red[8];
   __shared__ int fail;
   const DenseStructDev& S = st[blockIdx.x];
   const int n = S.n, ld = n + 1, t = threadIdx.x, nt = blockDim.x;
-  double* U = Kbuf + S.k_off;  // A, then U (upper rows), then A^{-1}, then A'^{-1}
-  double* Y = Ybuf + S.e_off;  // U^{-1}, upper, row-major (ld n)
+  T* U = Kbuf + S.k_off;  // A, then U (upper rows), then A^{-1}, then A'^{-1}
+  T* Y = Ybuf + S.e_off;  // U^{-1}, upper, row-major (ld n)
   const double* Es = E + S.e_off;
   if (t == 0) fail = 0;
   for (int64_t e = t; e < (int64_t)n * n; e += nt) {
     const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
-    U[(int64_t)i * ld + j] = Es[e] + (i == j ? J[S.atom_off + i] : 0.0);
+    U[(int64_t)i * ld + j] = (T)(Es[e] + (i == j ? J[S.atom_off + i] : 0.0));
   }
   __syncthreads();
   // Cholesky A = U^T U, row by row: U_jj = sqrt(A_jj - sum_k U_kj^2),
@@ -270,20 +289,20 @@ __global__ void __launch_bounds__(256) k_dense_invert(const DenseStructDev* __re
   for (int j = 0; j < n; ++j) {
     for (int k = t; k < j; k += nt) col[k] = U[(int64_t)k * ld + j];
     __syncthreads();
-    double part = 0.0;
+    T part = (T)0;
     for (int k = t; k < j; k += nt) part += col[k] * col[k];
-    const double dsum = dense_block_sum(part, red);
-    const double djj = U[(int64_t)j * ld + j] - dsum;
-    if (!(djj > 0.0)) {  // not positive definite (uniform across the block)
+    const T dsum = dense_block_sum_t<T>(part, red);
+    const T djj = U[(int64_t)j * ld + j] - dsum;
+    if (!(djj > (T)0)) {  // not positive definite (uniform across the block)
       if (t == 0) {
         atomicOr(err, DERR_NOT_PD);
         fail = 1;
       }
       break;
     }
-    const double ujj = sqrt(djj);
+    const T ujj = sqrt(djj);
     for (int i = j + 1 + t; i < n; i += nt) {
-      double s = U[(int64_t)j * ld + i];
+      T s = U[(int64_t)j * ld + i];
       for (int k = 0; k < j; ++k) s -= U[(int64_t)k * ld + i] * col[k];
       U[(int64_t)j * ld + i] = s / ujj;
     }
@@ -297,32 +316,32 @@ __global__ void __launch_bounds__(256) k_dense_invert(const DenseStructDev* __re
   for (int i = n - 1; i >= 0; --i) {
     for (int k = i + t; k < n; k += nt) col[k] = U[(int64_t)i * ld + k];
     __syncthreads();
-    const double inv = 1.0 / col[i];
+    const T inv = (T)1 / col[i];
     for (int c = i + t; c < n; c += nt) {
-      double s = (c == i) ? 1.0 : 0.0;
+      T s = (c == i) ? (T)1 : (T)0;
       for (int k = i + 1; k <= c; ++k) s -= col[k] * Y[(int64_t)k * n + c];
       Y[(int64_t)i * n + c] = s * inv;
     }
-    for (int c = t; c < i; c += nt) Y[(int64_t)i * n + c] = 0.0;
+    for (int c = t; c < i; c += nt) Y[(int64_t)i * n + c] = (T)0;
     __syncthreads();
   }
   // A^{-1} = Y Y^T: entry (a, b) = sum_{k >= max(a, b)} Y_ak Y_bk, 32 x 32 tiles through shared memory
-  double* ta = col;  // reuse: 2 x 16 x 32 doubles = 1024 (two half-height staging buffers)
+  T* ta = col;  // reuse: 2 x 16 x 32 values = 1024 (two half-height staging buffers)
   for (int tb = 0; tb * 32 < n; ++tb)
     for (int tA = 0; tA <= tb; ++tA) {
       const int a0 = tA * 32, b0 = tb * 32;
       const int r = t >> 3, c0 = t & 7;
-      double acc[4] = {0, 0, 0, 0};
+      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
       for (int k0 = b0; k0 < n; k0 += 16) {  // Y_ak = 0 for k < a, and a, b < b0 + 32
         __syncthreads();
         for (int e = t; e < 2 * 32 * 16; e += nt) {
           const int side = e >> 9, rem = e & 511, row = rem >> 4, kk = rem & 15;
           const int gr = (side ? b0 : a0) + row, gk = k0 + kk;
-          ta[e] = (gr < n && gk < n) ? Y[(int64_t)gr * n + gk] : 0.0;
+          ta[e] = (gr < n && gk < n) ? Y[(int64_t)gr * n + gk] : (T)0;
         }
         __syncthreads();
         for (int kk = 0; kk < 16; ++kk) {
-          const double ya = ta[(r << 4) + kk];
+          const T ya = ta[(r << 4) + kk];
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[q] += ya * ta[512 + ((c0 + 8 * q) << 4) + kk];
         }
@@ -341,15 +360,15 @@ __global__ void __launch_bounds__(256) k_dense_invert(const DenseStructDev* __re
   __syncthreads();
   // border: v = A^{-1} 1, s = 1^T v; A'^{-1} = [[A^{-1} - v v^T / s, v / s], [v^T / s, -1 / s]]
   for (int a = t; a < n; a += nt) {
-    double v = 0.0;
+    T v = (T)0;
     for (int b = 0; b < n; ++b) v += U[(int64_t)a * ld + b];
     col[a] = v;
   }
   __syncthreads();
-  double part = 0.0;
+  T part = (T)0;
   for (int a = t; a < n; a += nt) part += col[a];
-  const double s = dense_block_sum(part, red);
-  const double is = 1.0 / s;
+  const T s = dense_block_sum_t<T>(part, red);
+  const T is = (T)1 / s;
   for (int64_t e = t; e < (int64_t)n * n; e += nt) {
     const int a = (int)(e / n), b = (int)(e - (int64_t)a * n);
     U[(int64_t)a * ld + b] -= col[a] * col[b] * is;
@@ -393,6 +412,80 @@ __global__ void __launch_bounds__(256) k_dense_apply(const DenseStructDev* __res
   }
 }
 
+// FP64 solution of A' x = b with the FP32 inverse, by iterative refinement:
+// x = K32 b, then twice r = b - A' x (A' = [[E + diag J, 1], [1^T, 0]] in FP64), x += K32 r.
+// Each step shrinks the error by about cond(A') * eps_FP32; two steps give FP64 accuracy for
+// the well-conditioned QEq matrices.  One CTA per structure, x and r in shared memory.
+// MODE 0: b = (-chi, q_tot) -> q = x[:n], mu = -x[n];  MODE 1: b = (dL/dq, 0) ->
+// dL/dchi = -x[:n], dL/dJ = -x[:n] q.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_dense_refine(const DenseStructDev* __restrict__ st,
+                                                      const float* __restrict__ K32, const double* __restrict__ E,
+                                                      const double* __restrict__ J, const double* __restrict__ xin,
+                                                      const double* __restrict__ qtot, const double* __restrict__ q,
+                                                      double* __restrict__ o1, double* __restrict__ o2) {
+  __shared__ double xs[QEQ_DENSE_MAX_ATOMS + 1];
+  __shared__ double bs[QEQ_DENSE_MAX_ATOMS + 1];
+  __shared__ double rs[QEQ_DENSE_MAX_ATOMS + 1];
+  __shared__ double red[8];
+  const DenseStructDev& S = st[blockIdx.x];
+  const int n = S.n, ld = n + 1, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float* K = K32 + S.k_off;
+  const double* Es = E + S.e_off;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    bs[a] = MODE == 0 ? -xin[S.atom_off + a] : xin[S.atom_off + a];
+    xs[a] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    bs[n] = MODE == 0 ? qtot[blockIdx.x] : 0.0;
+    xs[n] = 0.0;
+  }
+  __syncthreads();
+  // r = b initially (x = 0); then three applications of K32, two residuals
+  for (int a = threadIdx.x; a <= n; a += blockDim.x) rs[a] = bs[a];
+  __syncthreads();
+  for (int step = 0; step < 3; ++step) {
+    // x += K32 r, one warp per row, FP64 accumulation
+    for (int a = w; a <= n; a += nw) {
+      double acc = 0.0;
+      for (int b = lane; b <= n; b += 32) acc += (double)K[(int64_t)a * ld + b] * rs[b];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) xs[a] += acc;
+    }
+    __syncthreads();
+    if (step == 2) break;
+    // r = b - A' x in FP64
+    for (int a = w; a < n; a += nw) {
+      double acc = 0.0;
+      for (int b = lane; b < n; b += 32) acc += Es[(int64_t)a * n + b] * xs[b];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) rs[a] = bs[a] - (acc + J[S.atom_off + a] * xs[a] + xs[n]);
+    }
+    double part = 0.0;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) part += xs[a];
+    const double sx = dense_block_sum(part, red);
+    if (threadIdx.x == 0) rs[n] = bs[n] - sx;
+    __syncthreads();
+  }
+  for (int a = threadIdx.x; a <= n; a += blockDim.x) {
+    const double y = xs[a];
+    if (MODE == 0) {
+      if (a < n)
+        o1[S.atom_off + a] = y;
+      else if (o2)
+        o2[blockIdx.x] = -y;
+    } else if (a < n) {
+      o1[S.atom_off + a] = -y;
+      if (o2) o2[S.atom_off + a] = -y * q[S.atom_off + a];
+    }
+  }
+}
+
+__global__ void k_f2d(const float* __restrict__ a, int64_t n, double* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
 qeq_status dfail(qeq_dense_s* D, qeq_status s, const std::string& m) {
   D->last_error = m;
   return s;
@@ -426,7 +519,7 @@ qeq_status dense_check(qeq_dense_s* D) {
 
 void dense_free(qeq_dense_s* D) {
   void* p[] = {D->d_st, D->d_g, D->d_tiles, D->d_atom_struct, D->d_frac, D->d_ph,
-               D->d_E,  D->d_K, D->d_Y,     D->d_qtot,        D->d_err};
+               D->d_E,  D->d_K, D->d_Y,     D->d_qtot,        D->d_err,         D->d_K32, D->d_Y32, D->d_Jc};
   for (void* x : p)
     if (x) cudaFree(x);
 }
@@ -452,6 +545,7 @@ extern "C" qeq_status qeq_dense_create(const qeq_plan_desc* desc, void* cuda_str
   D->n_species = desc->n_species;
   if (desc->coulomb_k > 0) D->k_e = desc->coulomb_k;
   if (desc->ewald_tol > 0) D->tol = desc->ewald_tol;
+  D->mixed = desc->precision == QEQ_MIXED ? 1 : 0;
   const double xr = erfc_inv(D->tol);                   // erfc(r_c / (sqrt2 omega)) = tol
   const double gq = sqrt(2.0 * log(1.0 / D->tol));      // exp(-g_c^2 omega^2 / 2) = tol
   std::vector<DenseG> gl;
@@ -552,8 +646,14 @@ extern "C" qeq_status qeq_dense_create(const qeq_plan_desc* desc, void* cuda_str
   if (e == cudaSuccess) e = cudaMalloc(&D->d_frac, sizeof(double) * 3 * (size_t)D->n_atoms);
   if (e == cudaSuccess) e = cudaMalloc(&D->d_ph, sizeof(double2) * std::max<int64_t>(1, ph_off));
   if (e == cudaSuccess) e = cudaMalloc(&D->d_E, sizeof(double) * std::max<int64_t>(1, e_off));
-  if (e == cudaSuccess) e = cudaMalloc(&D->d_Y, sizeof(double) * std::max<int64_t>(1, e_off));
-  if (e == cudaSuccess) e = cudaMalloc(&D->d_K, sizeof(double) * std::max<int64_t>(1, k_off));
+  if (D->mixed) {
+    if (e == cudaSuccess) e = cudaMalloc(&D->d_Y32, sizeof(float) * std::max<int64_t>(1, e_off));
+    if (e == cudaSuccess) e = cudaMalloc(&D->d_K32, sizeof(float) * std::max<int64_t>(1, k_off));
+    if (e == cudaSuccess) e = cudaMalloc(&D->d_Jc, sizeof(double) * std::max<int64_t>(1, D->n_atoms));
+  } else {
+    if (e == cudaSuccess) e = cudaMalloc(&D->d_Y, sizeof(double) * std::max<int64_t>(1, e_off));
+    if (e == cudaSuccess) e = cudaMalloc(&D->d_K, sizeof(double) * std::max<int64_t>(1, k_off));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&D->d_qtot, sizeof(double) * D->n_struct);
   if (e == cudaSuccess) e = cudaMalloc(&D->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(D->d_err, 0, sizeof(int));
@@ -598,8 +698,14 @@ extern "C" qeq_status qeq_dense_invert(qeq_dense D, const double* d_J) {
   if (!d_J) return dfail(D, QEQ_ERR_INVALID, "null pointer");
   if (!D->assembled) return dfail(D, QEQ_ERR_INVALID, "call qeq_dense_assemble first");
   DTRY(cudaSetDevice(D->device));
-  k_dense_invert<<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_E, d_J, D->d_K, D->d_Y, D->d_err);
-  DTRY(cudaGetLastError());
+  if (D->mixed) {
+    k_dense_invert<float><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_E, d_J, D->d_K32, D->d_Y32, D->d_err);
+    DTRY(cudaGetLastError());
+    DTRY(cudaMemcpyAsync(D->d_Jc, d_J, sizeof(double) * D->n_atoms, cudaMemcpyDeviceToDevice, D->stream));
+  } else {
+    k_dense_invert<double><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_E, d_J, D->d_K, D->d_Y, D->d_err);
+    DTRY(cudaGetLastError());
+  }
   D->launches += 1;
   qeq_status st = dense_check(D);
   D->inverted = (st == QEQ_OK);
@@ -615,7 +721,11 @@ extern "C" qeq_status qeq_dense_charges(qeq_dense D, const double* d_chi, const 
   for (int s = 0; s < D->n_struct; ++s) D->h_qtot[s] = h_qtot ? h_qtot[s] : 0.0;
   DTRY(cudaMemcpyAsync(D->d_qtot, D->h_qtot.data(), sizeof(double) * D->n_struct, cudaMemcpyHostToDevice,
                        D->stream));
-  k_dense_apply<0><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_K, d_chi, D->d_qtot, nullptr, d_q, d_mu);
+  if (D->mixed)
+    k_dense_refine<0><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_K32, D->d_E, D->d_Jc, d_chi, D->d_qtot,
+                                                          nullptr, d_q, d_mu);
+  else
+    k_dense_apply<0><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_K, d_chi, D->d_qtot, nullptr, d_q, d_mu);
   DTRY(cudaGetLastError());
   D->launches += 1;
   DTRY(cudaStreamSynchronize(D->stream));  // h_qtot staging is reused by the next call
@@ -628,7 +738,11 @@ extern "C" qeq_status qeq_dense_backward(qeq_dense D, const double* d_q, const d
   if (!d_gq || !d_gchi || (d_gJ && !d_q)) return dfail(D, QEQ_ERR_INVALID, "null pointer");
   if (!D->inverted) return dfail(D, QEQ_ERR_INVALID, "call qeq_dense_invert first");
   DTRY(cudaSetDevice(D->device));
-  k_dense_apply<1><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_K, d_gq, nullptr, d_q, d_gchi, d_gJ);
+  if (D->mixed)
+    k_dense_refine<1><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_K32, D->d_E, D->d_Jc, d_gq, nullptr, d_q,
+                                                          d_gchi, d_gJ);
+  else
+    k_dense_apply<1><<<D->n_struct, 256, 0, D->stream>>>(D->d_st, D->d_K, d_gq, nullptr, d_q, d_gchi, d_gJ);
   DTRY(cudaGetLastError());
   D->launches += 1;
   return QEQ_OK;
@@ -643,6 +757,11 @@ extern "C" qeq_status qeq_dense_matrix(qeq_dense D, int32_t s, int32_t which, do
   DTRY(cudaSetDevice(D->device));
   const DenseStructDev& T = D->hs[s];
   const int64_t cnt = which == 0 ? (int64_t)T.n * T.n : (int64_t)(T.n + 1) * (T.n + 1);
+  if (which == 1 && D->mixed) {  // the FP32 inverse, widened
+    k_f2d<<<(int)((cnt + 255) / 256), 256, 0, D->stream>>>(D->d_K32 + T.k_off, cnt, d_out);
+    DTRY(cudaGetLastError());
+    return QEQ_OK;
+  }
   const double* src = which == 0 ? D->d_E + T.e_off : D->d_K + T.k_off;
   DTRY(cudaMemcpyAsync(d_out, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, D->stream));
   return QEQ_OK;

@@ -17,26 +17,42 @@
 // E_ij q_j, one FP64 matvec of the charges of each element.
 #include <math.h>
 
+#include <type_traits>
+
 #include "neighbors.cuh"
 #include "qeq_internal.cuh"
 
 namespace {
 
+template <typename T>
+struct C2;
+template <>
+struct C2<float> {
+  using t = float2;
+};
+template <>
+struct C2<double> {
+  using t = double2;
+};
+
 // g_x at every atom (sorted order), one warp per atom: the mesh part differentiates the
 // B-spline weights (dM_p(t)/dt = M_{p-1}(t) - M_{p-1}(t - 1)) and maps mesh to Cartesian
 // derivatives with K_d h^{-1}; the real-space part walks the neighbouring bins.
-template <int P>
+// T: the potential mesh's precision (the plan's: FP32 meshes and weights in QEQ_MIXED); the
+// stencil sums of each lane run in T, the sums over lanes and the pair term in FP64.
+template <typename T, int P>
 __global__ void __launch_bounds__(256) k_force_grad(const StructDev* __restrict__ st,
                                                     const int* __restrict__ sorted_struct, int64_t n,
-                                                    const int* __restrict__ base, const double* __restrict__ wts,
+                                                    const int* __restrict__ base, const T* __restrict__ wts,
                                                     const int* __restrict__ spec, const double* __restrict__ posc,
                                                     const float4* __restrict__ posc32,
                                                     const int* __restrict__ bin_start, const double* __restrict__ x,
-                                                    const double2* __restrict__ mesh, double k_e,
+                                                    const typename C2<T>::t* __restrict__ mesh, double k_e,
                                                     double* __restrict__ g0, double* __restrict__ g1,
                                                     double* __restrict__ g2) {
+  using V = typename C2<T>::t;
   __shared__ NbrWarpSmem ws[8];
-  __shared__ double dw[8][3][QEQ_MAXP];
+  __shared__ T dw[8][3][QEQ_MAXP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t a = (int64_t)blockIdx.x * 8 + w;
   if (a >= n) return;  // whole warp
@@ -44,7 +60,7 @@ __global__ void __launch_bounds__(256) k_force_grad(const StructDev* __restrict_
   const int sp = spec[a];
   const int bs = base[a];
   const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
-  const double* wt = wts + (size_t)a * 3 * QEQ_MAXP;
+  const T* wt = wts + (size_t)a * 3 * QEQ_MAXP;
   if (lane < 3) {  // derivative weights of direction d = lane
     const int d = lane;
     double u = posc[3 * a] * S.hinv[d] + posc[3 * a + 1] * S.hinv[3 + d] + posc[3 * a + 2] * S.hinv[6 + d];
@@ -57,33 +73,34 @@ __global__ void __launch_bounds__(256) k_force_grad(const StructDev* __restrict_
     double m1[QEQ_MAXP];
     bspline_weights(xw, P - 1, m1);  // M_{p-1}(xw + j), j < p - 1
 #pragma unroll
-    for (int j = 0; j < P; ++j) dw[w][d][j] = ((j < P - 1) ? m1[j] : 0.0) - ((j >= 1) ? m1[j - 1] : 0.0);
+    for (int j = 0; j < P; ++j) dw[w][d][j] = (T)(((j < P - 1) ? m1[j] : 0.0) - ((j >= 1) ? m1[j - 1] : 0.0));
   }
   __syncwarp();
   // mesh part: lanes own 8 z x 4 rows of the P^3 stencil
-  const double2* mg = mesh + S.mesh_off + (int64_t)(sp >> 1) * S.Mp;
+  const V* mg = mesh + S.mesh_off + (int64_t)(sp >> 1) * S.Mp;
   const int part = sp & 1;
-  double D0 = 0.0, D1 = 0.0, D2 = 0.0;
+  T D0t = (T)0, D1t = (T)0, D2t = (T)0;
   const int jz = lane & 7, rsub = lane >> 3;
   if (jz < P) {
     int kz = f[2] - (P - 1) + jz;
     if (kz < 0) kz += S.K[2];
-    const double wz = wt[2 * QEQ_MAXP + P - 1 - jz], dz = dw[w][2][P - 1 - jz];
+    const T wz = wt[2 * QEQ_MAXP + P - 1 - jz], dz = dw[w][2][P - 1 - jz];
     for (int r = rsub; r < P * P; r += 4) {
       const int jx = r / P, jy = r - (r / P) * P;
       int kx = f[0] - (P - 1) + jx;
       if (kx < 0) kx += S.K[0];
       int ky = f[1] - (P - 1) + jy;
       if (ky < 0) ky += S.K[1];
-      const double2 v2 = mg[((int64_t)kx * S.K[1] + ky) * S.P[2] + kz];
-      const double v = part ? v2.y : v2.x;
-      const double wx = wt[P - 1 - jx], wy = wt[QEQ_MAXP + P - 1 - jy];
-      const double dx = dw[w][0][P - 1 - jx], dy = dw[w][1][P - 1 - jy];
-      D0 += dx * wy * wz * v;
-      D1 += wx * dy * wz * v;
-      D2 += wx * wy * dz * v;
+      const V v2 = mg[((int64_t)kx * S.K[1] + ky) * S.P[2] + kz];
+      const T v = part ? v2.y : v2.x;
+      const T wx = wt[P - 1 - jx], wy = wt[QEQ_MAXP + P - 1 - jy];
+      const T dx = dw[w][0][P - 1 - jx], dy = dw[w][1][P - 1 - jy];
+      D0t += dx * wy * wz * v;
+      D1t += wx * dy * wz * v;
+      D2t += wx * wy * dz * v;
     }
   }
+  double D0 = (double)D0t, D1 = (double)D1t, D2 = (double)D2t;
   // real-space part: d/dR_a of sum_j x_j v(|R_j' - R_a|) = sum_j x_j v'(r) (R_a - R_j')/r
   double r0 = 0.0, r1 = 0.0, r2s = 0.0;
   if (S.any_narrow && S.narrow[sp]) {
@@ -360,21 +377,31 @@ __global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __r
   if (i < n) c[i] = a[i] - b[i];
 }
 
-template <int P>
+template <typename T, int P>
 cudaError_t launch_force_grad(qeq_plan_s* Pl, const double* x, double* const g[3]) {
   count_launch(Pl);
   const int nbw = (int)((Pl->n_atoms + 7) / 8);  // one warp per atom
-  k_force_grad<P><<<nbw, 256, 0, Pl->stream>>>(Pl->d_st, Pl->d_key, Pl->n_atoms, Pl->d_base, Pl->d_wts, Pl->d_spec,
-                                                Pl->d_posc, Pl->d_posc32, Pl->d_bin_start, x, Pl->d_mesh,
-                                                Pl->desc.coulomb_k, g[0], g[1], g[2]);
+  const T* wts = std::is_same<T, float>::value ? (const T*)(const void*)Pl->d_wts32 : (const T*)(const void*)Pl->d_wts;
+  const typename C2<T>::t* mesh = reinterpret_cast<const typename C2<T>::t*>(Pl->d_mesh);
+  k_force_grad<T, P><<<nbw, 256, 0, Pl->stream>>>(Pl->d_st, Pl->d_key, Pl->n_atoms, Pl->d_base, wts, Pl->d_spec,
+                                                   Pl->d_posc, Pl->d_posc32, Pl->d_bin_start, x, mesh,
+                                                   Pl->desc.coulomb_k, g[0], g[1], g[2]);
   return cudaGetLastError();
 }
 
+// the potential meshes in the plan's precision (FP32 in QEQ_MIXED: the narrow FP64 pipe makes
+// FP64 passes 16-18x slower; FP32 meshes carry ~3e-7 of the potentials' size), then the gradient
 cudaError_t force_grad(qeq_plan_s* P, const double* x, double* const g[3]) {
+  if (P->precision == QEQ_MIXED) {
+    QEQ_CUDA_TRY(launch_mesh_potential32(P, x));
+    if (P->max_p == 4) return launch_force_grad<float, 4>(P, x, g);
+    if (P->max_p == 6) return launch_force_grad<float, 6>(P, x, g);
+    return launch_force_grad<float, 8>(P, x, g);
+  }
   QEQ_CUDA_TRY(launch_mesh_potential(P, x));
-  if (P->max_p == 4) return launch_force_grad<4>(P, x, g);
-  if (P->max_p == 6) return launch_force_grad<6>(P, x, g);
-  return launch_force_grad<8>(P, x, g);
+  if (P->max_p == 4) return launch_force_grad<double, 4>(P, x, g);
+  if (P->max_p == 6) return launch_force_grad<double, 6>(P, x, g);
+  return launch_force_grad<double, 8>(P, x, g);
 }
 
 }  // namespace

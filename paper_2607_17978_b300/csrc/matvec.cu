@@ -852,6 +852,34 @@ cudaError_t launch_mesh_virial(qeq_plan_s* P, const double* x, int* nsub_out) {
   return virial_impl<8>(P, x, nsub_out);
 }
 
+// FP32 potential meshes of x (the mixed-precision path): x in FP32, FP32 spread and passes
+__global__ void k_to_f32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+template <int P>
+cudaError_t potential32_impl(qeq_plan_s* Pl, const double* x) {
+  cudaStream_t s = Pl->stream;
+  float2* mesh = reinterpret_cast<float2*>(Pl->d_mesh);
+  count_launch(Pl, 7);
+  k_to_f32<<<(int)((Pl->n_atoms + 255) / 256), 256, 0, s>>>(x, Pl->n_atoms, Pl->d_x32);
+  k_spread<float, P><<<Pl->total_bricks, 256, spread_smem<float, P>(), s>>>(
+      Pl->d_st, Pl->d_brick_struct, Pl->d_brick_cand, Pl->d_bin_start, Pl->d_base, Pl->d_wts32, Pl->d_spec, x,
+      Pl->d_x32, Pl->d_sc, 0, mesh);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  return launch_fft_passes<float, false>(Pl, Pl->geo, Pl->fft_kmax, Pl->d_st, Pl->d_zitems, Pl->n_zitems,
+                                        Pl->d_yitems, Pl->n_yitems, Pl->d_yiitems, Pl->n_yiitems, Pl->d_xitems,
+                                        Pl->n_xitems, 0, mesh, reinterpret_cast<float2*>(Pl->d_mesh2),
+                                        Pl->max_species, []() { return cudaSuccess; });
+}
+
+cudaError_t launch_mesh_potential32(qeq_plan_s* P, const double* x) {
+  if (P->max_p == 4) return potential32_impl<4>(P, x);
+  if (P->max_p == 6) return potential32_impl<6>(P, x);
+  return potential32_impl<8>(P, x);
+}
+
 cudaError_t launch_mesh_potential(qeq_plan_s* P, const double* x) {
   if (P->max_p == 4) return potential_impl<4>(P, x);
   if (P->max_p == 6) return potential_impl<6>(P, x);

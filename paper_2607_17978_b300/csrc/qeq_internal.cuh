@@ -612,6 +612,8 @@ cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, i
 cudaError_t matvec_set_attributes();
 // FP64 potential meshes of x (sorted order) in d_mesh, layout L0 (no gather)
 cudaError_t launch_mesh_potential(qeq_plan_s* P, const double* x);
+// the same in FP32 (x converted into d_x32; FP32 meshes in d_mesh, layout L0)
+cudaError_t launch_mesh_potential32(qeq_plan_s* P, const double* x);
 // strain-derivative sums of the reciprocal quadratic form of x (FP64): 8 doubles per x-pass
 // unit in d_mesh2; *nsub_out = units per x item
 cudaError_t launch_mesh_virial(qeq_plan_s* P, const double* x, int* nsub_out);

@@ -507,7 +507,8 @@ class Dense:
     """4G charge training on cached dense matrices (qeq_dense_*): E per structure once, the
     bordered inverse per hardness, charges and their backward pass as matrix-vector products."""
 
-    def __init__(self, cells, atom_offsets, sigma, *, coulomb_k=14.3996454784, ewald_tol=0.0, device=None):
+    def __init__(self, cells, atom_offsets, sigma, *, coulomb_k=14.3996454784, ewald_tol=0.0, device=None,
+                 precision="fp64"):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -525,7 +526,7 @@ class Dense:
         d = PlanDesc(self.n_struct, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                      cells.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.n_species,
                      sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), coulomb_k, 0.0, ewald_tol,
-                     0.0, 0, 0.0, 0, 0, 0.0, 0, 0, 0.0, 0.0, 0.0)
+                     0.0, 0, 0.0, {"fp64": QEQ_FP64, "mixed": QEQ_MIXED}[precision], 0, 0.0, 0, 0, 0.0, 0.0, 0.0)
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.Stream(device=self.device)
             h = ctypes.c_void_p()

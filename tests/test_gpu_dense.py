@@ -64,10 +64,14 @@ def test_dense_assembly_matches_the_oracle_matrix(batch_and_oracle):
         assert np.array_equal(E, E.T) or np.abs(E - E.T).max() < 1e-14 * np.abs(E).max()
 
 
-def test_dense_charges_gradients_and_inverse(batch_and_oracle):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dense_charges_gradients_and_inverse(batch_and_oracle, precision):
+    """Charges, multipliers and the backward pass against the oracle at 1e-9 in both modes (the
+    mixed mode's FP32 inverse is refined in FP64); the cached inverse itself at 1e-9 (FP64) or
+    at FP32 accuracy (1e-4 relative to its largest entry, mixed)."""
     from paper_2607_17978_b300 import qeq
     structs, refs = batch_and_oracle
-    d = _dense(structs)
+    d = _dense(structs, precision=precision)
     pos, spc, chi, J, qt = qeq.pack(structs)
     d.assemble(pos, spc)
     rng = np.random.default_rng(7)
@@ -90,7 +94,7 @@ def test_dense_charges_gradients_and_inverse(batch_and_oracle):
             assert _rel(gchi[sl], gcr) < TOL, (i, _rel(gchi[sl], gcr))
             assert _rel(gJ[sl], gJr) < TOL, (i, _rel(gJ[sl], gJr))
             K = d.matrix(i, 1).cpu().numpy()
-            assert _rel(K, Kinv) < TOL, (i, _rel(K, Kinv))
+            assert _rel(K, Kinv) < (TOL if precision == "fp64" else 1e-4), (i, _rel(K, Kinv))
 
 
 def test_dense_matches_the_iterative_solver_and_is_repeatable():

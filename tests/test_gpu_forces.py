@@ -17,6 +17,10 @@ from paper_2607_17978_b300 import synth
 
 KE = synth.COULOMB_K_EV_A
 FORCE_TOL_FACTOR = 30.0
+# mixed-precision plans differentiate FP32 potential meshes: their rounding (~3e-7 of the
+# potentials, which exceed the forces' scale by about an order of magnitude in these ionic
+# cells) sets a floor of a few 1e-6 relative; the tests allow 1e-5
+FP32_FORCE_FLOOR = 1e-5
 pytestmark = pytest.mark.gpu
 
 
@@ -54,12 +58,13 @@ def test_forces_parity_small_cell_every_atom(precision):
         err = _rel_rms(F, ref)
         print(f"216 atoms {precision} lambda={la is not None}: rel RMS {err:.2e}, "
               f"max {np.abs(F - ref).max() / np.abs(ref).max():.2e}")
-        assert err < FORCE_TOL_FACTOR * tol, err
+        assert err < max(FORCE_TOL_FACTOR * tol, FP32_FORCE_FLOOR if precision == "mixed" else 0.0), err
     # three atoms straight from central differences of the dense matrix
     atoms = [0, 101, 215]
     fd = O.electrostatic_forces_fd(st.cell, st.pos, st.sigma, q, lam, k_e=KE, atoms=atoms)
     F = plan.forces(st.pos, st.species, q, lam).cpu().numpy()[atoms]
-    assert np.abs(F - fd).max() < FORCE_TOL_FACTOR * tol * np.abs(fd).max() * 3
+    floor = FP32_FORCE_FLOOR if precision == "mixed" else 0.0
+    assert np.abs(F - fd).max() < max(FORCE_TOL_FACTOR * tol, floor) * np.abs(fd).max() * 3
 
 
 def test_forces_parity_uneven_batch():
