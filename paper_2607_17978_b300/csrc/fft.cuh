@@ -279,9 +279,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// Load nl lines of `elems` complex elements (line l from src + off(l)) into the tile, lines
-// ld elements apart.  All threads call it.  Returns false on every thread if the copy did
-// not complete within the bound (after a second bounded wait for the copies in flight).
 // ------------------------------------------------------------------ mixed-radix stages in shared memory
 // A line of K = R_0 ... R_{m-1} points is transformed in place, stage after stage
 // (decimation in time over blocks): stage s works on Q_s = R_0...R_{s-1} blocks of
@@ -291,6 +288,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // point at position sum_s S_s k_s holds frequency sum_s Q_s k_s ("block order"; the
 // host tables blk / freq / pos translate between the two).  Twiddles come from the
 // K-point table exp(-2 pi i m / K): W_{L_s}^{n k} = tw[n k Q_s] (n k Q_s < K).
+//
+// Work assignment: with exactly 8 lines, and in a stage with S_s = 1 and even R_s, the
+// lanes run over the lines first, else over n first (elements adjacent in a line).
+// Lines are ld = 2 mod 4 elements apart, so 8 lines fill 8 distinct bank pairs and the
+// butterflies of two neighbouring n the other 8: the accesses of a half-warp hit
+// distinct banks, and its lanes read two twiddles.  The blocks of one line in a stage
+// with S_s = 1 start R_s elements apart, which for even R_s would put a warp running
+// over them on a few banks.
+
+__device__ __forceinline__ int ceil_log2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
 
 template <typename T, typename V>
 __device__ __forceinline__ V twiddle(const V* __restrict__ tw, int idx, T sgn) {
@@ -306,10 +317,19 @@ __device__ __forceinline__ void stage_fwd(typename C2<T>::t* tile, int nl, int l
   using V = typename C2<T>::t;
   const int S = fp.S[s], L = fp.L[s], Q = fp.Q[s];
   const int nb = fp.K / R;
-  const int total = nl * nb;
+  const bool lf = (nl == 8) || (R % 2 == 0 && S == 1);  // lanes over lines first (see above)
+  const int lsh = ceil_log2(nl);
+  const int total = lf ? (nb << lsh) : nl * nb;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int l = (int)fdiv((uint32_t)w, fp.fnb[s]);
-    const int j = w - l * nb;
+    int l, j;
+    if (lf) {
+      l = w & ((1 << lsh) - 1);
+      j = w >> lsh;
+      if (l >= nl) continue;
+    } else {
+      l = (int)fdiv((uint32_t)w, fp.fnb[s]);
+      j = w - l * nb;
+    }
     const int beta = (int)fdiv((uint32_t)j, fp.fS[s]);
     const int n = j - beta * S;
     V* b = tile + l * ld + beta * L + n;
@@ -334,10 +354,19 @@ __device__ __forceinline__ void stage_inv(typename C2<T>::t* tile, int nl, int l
   using V = typename C2<T>::t;
   const int S = fp.S[s], L = fp.L[s], Q = fp.Q[s];
   const int nb = fp.K / R;
-  const int total = nl * nb;
+  const bool lf = (nl == 8) || (R % 2 == 0 && S == 1);  // lanes over lines first (see above)
+  const int lsh = ceil_log2(nl);
+  const int total = lf ? (nb << lsh) : nl * nb;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int l = (int)fdiv((uint32_t)w, fp.fnb[s]);
-    const int j = w - l * nb;
+    int l, j;
+    if (lf) {
+      l = w & ((1 << lsh) - 1);
+      j = w >> lsh;
+      if (l >= nl) continue;
+    } else {
+      l = (int)fdiv((uint32_t)w, fp.fnb[s]);
+      j = w - l * nb;
+    }
     const int beta = (int)fdiv((uint32_t)j, fp.fS[s]);
     const int n = j - beta * S;
     V* b = tile + l * ld + beta * L + n;

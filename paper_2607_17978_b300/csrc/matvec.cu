@@ -65,11 +65,12 @@ __device__ __forceinline__ double xval<double>(const double* __restrict__ x, con
 // brick's z-row at (x0 + lx, y0 + ly) and keeps its 16 points (both species
 // parts) in registers.  The candidate atoms (those of the bins whose stencils
 // can reach the brick) are staged in batches of QEQ_SPB as compact records in
-// shared memory: stencil offsets relative to the brick, 16-bit masks of the
-// brick rows the stencil covers in x and y, the x / y weights (x pre-multiplied
-// by the charge) and the z weights at the brick's 16 z positions.  Every thread
-// then adds, atom after atom in a fixed order, its row's contribution: the
-// spread is deterministic and each mesh point is written to global memory once.
+// shared memory: stencil starts relative to the brick, 16-bit masks of the brick
+// rows the stencil covers in x and y, and its weights laid out on the brick's 16
+// positions per direction (0 where the stencil does not reach; x pre-multiplied by
+// the charge).  Every thread then adds, atom after atom in a fixed order, its
+// row's contribution: the spread is deterministic and each mesh point is written
+// to global memory once.
 #define QEQ_SPB 256  // candidate records per batch (one per thread)
 
 // Bits l in [0, ext) of brick rows covered by a stencil of P rows that starts
@@ -87,15 +88,34 @@ __device__ __forceinline__ unsigned stencil_rows(int o, int K, int ext) {
 
 template <typename T, int P>
 struct SpreadRecs {
-  T wz[QEQ_SPB][QEQ_BRICK_Z];  // z weights at the brick's z positions (0 outside the stencil)
-  T wx[QEQ_SPB][P];          // q * x weights, by stencil index
-  T wy[QEQ_SPB][P];
-  unsigned mask[QEQ_SPB];    // x rows (bits 0-15) and y rows (bits 16-31) the stencil covers
-  int off[QEQ_SPB];          // ox | oy << 10 | species part << 20
-  int atom[QEQ_SPB];         // staging: the candidate's atom (sorted index) ...
-  int oz[QEQ_SPB];           // ... its z stencil start relative to the brick
-  unsigned zm[QEQ_SPB];      // ... and the brick z positions it covers
+  T wz[QEQ_SPB][QEQ_BRICK_Z];   // z weights on the brick's z positions (0 outside the stencil)
+  T wx[QEQ_SPB][QEQ_BRICK_XY];  // q * x weights on the brick's x rows
+  T wy[QEQ_SPB][QEQ_BRICK_XY];  // y weights on the brick's y rows
+  unsigned mask[QEQ_SPB];       // x rows (bits 0-15) and y rows (bits 16-31) the stencil covers
+  int off[QEQ_SPB];             // stencil starts ox | oy << 10 | oz << 20, species part << 30
+  int atom[QEQ_SPB];            // the candidate's atom (sorted index)
 };
+
+// The P stored B-spline weights of one direction of atom t (16-byte loads: the weight
+// rows of 3 QEQ_MAXP values start on 16-byte boundaries).
+template <typename T>
+__device__ __forceinline__ void load_weights8(const T* __restrict__ src, T (&w)[QEQ_MAXP]);
+template <>
+__device__ __forceinline__ void load_weights8<float>(const float* __restrict__ src, float (&w)[QEQ_MAXP]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(src)), b = __ldg(reinterpret_cast<const float4*>(src) + 1);
+  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load_weights8<double>(const double* __restrict__ src, double (&w)[QEQ_MAXP]) {
+#pragma unroll
+  for (int i = 0; i < QEQ_MAXP / 2; ++i) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(src) + i);
+    w[2 * i] = a.x;
+    w[2 * i + 1] = a.y;
+  }
+}
+static_assert(QEQ_MAXP == 8 && (3 * QEQ_MAXP * 4) % 16 == 0, "weight rows are loaded as 16-byte vectors");
 
 // the brick's rows as they are written out: 256 rows of 16 z (one pad element per row)
 constexpr int kSpreadStageLd = QEQ_BRICK_Z + 1;
@@ -192,31 +212,31 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
           const unsigned ym = stencil_rows<P>(o[1], K1, B.ext[1]);
           const unsigned zm = stencil_rows<P>(o[2], K2, B.ext[2]);
           if (zm) mask = xm | (ym << 16);
-          R.off[tid] = o[0] | (o[1] << 10) | ((sp & 1) << 20);
-          R.oz[tid] = o[2];
-          R.zm[tid] = zm;
+          R.off[tid] = o[0] | (o[1] << 10) | (o[2] << 20) | ((sp & 1) << 30);
         }
         R.mask[tid] = mask;
         R.atom[tid] = t;
       }
       __syncthreads();
-      // ... then every thread: the weights of the kept records, 32 values per record
-      for (int idx = tid; idx < nbat * 32; idx += blockDim.x) {
-        const int r = idx >> 5, k = idx & 31;
+      // ... then every thread: one direction of a kept record, its P weights read as
+      // 16-byte vectors and laid out on the brick's 16 positions (periodic images added)
+      for (int idx = tid; idx < nbat * 3; idx += blockDim.x) {
+        const int r = idx / 3, d = idx - 3 * r;
         if (!R.mask[r]) continue;
         const int t = R.atom[r];
-        const T* wt = wts + (size_t)t * 3 * QEQ_MAXP;
-        if (k < QEQ_BRICK_Z) {
-          int j = k - R.oz[r];
-          if (j < 0) j += K2;
-          if (j >= K2) j -= K2;
-          R.wz[r][k] = ((R.zm[r] >> k) & 1u) ? wt[2 * QEQ_MAXP + P - 1 - j] : (T)0;
-        } else if (k < QEQ_BRICK_Z + P) {
-          const int j = k - QEQ_BRICK_Z;
-          R.wx[r][j] = xval<T>(x, x32, t) * wt[P - 1 - j];
-        } else if (k >= QEQ_BRICK_Z + 8 && k < QEQ_BRICK_Z + 8 + P) {
-          const int j = k - QEQ_BRICK_Z - 8;
-          R.wy[r][j] = wt[QEQ_MAXP + P - 1 - j];
+        T w[QEQ_MAXP];
+        load_weights8<T>(wts + (size_t)t * 3 * QEQ_MAXP + d * QEQ_MAXP, w);
+        const T scale = (d == 0) ? xval<T>(x, x32, t) : (T)1;
+        T* dst = (d == 0) ? R.wx[r] : (d == 1) ? R.wy[r] : R.wz[r];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[k] = (T)0;
+        const int o = (R.off[r] >> (10 * d)) & 1023, K = S.K[d];
+        const int ext = (d == 0) ? B.ext[0] : (d == 1) ? B.ext[1] : B.ext[2];  // B stays in registers
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          int k = o + j;
+          if (k >= K) k -= K;
+          for (; k < ext; k += K) dst[k] += scale * w[P - 1 - j];
         }
       }
       __syncthreads();
@@ -231,16 +251,10 @@ __global__ void __launch_bounds__(256) k_spread(const StructDev* __restrict__ st
         while (bal) {
           const int k = i0 + __ffs(bal) - 1;
           bal &= bal - 1u;
-          const unsigned m = R.mask[k];
-          if (!((m >> lx) & 1u) || !((m >> (16 + ly)) & 1u)) continue;
-          const int off = R.off[k];
-          int jx = lx - (off & 1023);
-          if (jx < 0) jx += K0;
-          int jy = ly - ((off >> 10) & 1023);
-          if (jy < 0) jy += K1;
-          const T r = R.wx[k][jx] * R.wy[k][jy];
+          // 0 on lanes whose row the stencil does not cover
+          const T r = R.wx[k][lx] * R.wy[k][ly];
           const T* wz = R.wz[k];
-          if ((off >> 20) & 1) {
+          if ((R.off[k] >> 30) & 1) {
 #pragma unroll
             for (int z = 0; z < QEQ_BRICK_Z; ++z) im[z] += r * wz[z];
           } else {
@@ -341,15 +355,41 @@ __global__ void __launch_bounds__(256) k_gather_direct(
         if (kz < 0) kz += S.K[2];
         const T wzj = wt[2 * QEQ_MAXP + P - 1 - jz];
         T racc = (T)0;
+        if constexpr (P == 8) {
+          // lane rows: y = rsub and rsub + 4, all 8 x; the 16 loads are issued before
+          // any is used, the y weights are read once
+          const int K1 = S.K[1];
+          const int64_t P2 = S.P[2];
+          int ky0 = f1 - 7 + rsub;
+          if (ky0 < 0) ky0 += K1;
+          int ky1 = f1 - 3 + rsub;
+          if (ky1 < 0) ky1 += K1;
+          const T wy0 = wt[QEQ_MAXP + 7 - rsub], wy1 = wt[QEQ_MAXP + 3 - rsub];
+          V v0[8], v1[8];
 #pragma unroll
-        for (int r = rsub; r < P * P; r += 4) {
-          const int jx = r / P, jy = r - (r / P) * P;
-          int kx = f0 - (P - 1) + jx;
-          if (kx < 0) kx += S.K[0];
-          int ky = f1 - (P - 1) + jy;
-          if (ky < 0) ky += S.K[1];
-          const V v = __ldg(mg + ((int64_t)kx * S.K[1] + ky) * S.P[2] + kz);
-          racc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
+          for (int jx = 0; jx < 8; ++jx) {
+            int kx = f0 - 7 + jx;
+            if (kx < 0) kx += S.K[0];
+            const V* rowp = mg + (int64_t)kx * K1 * P2 + kz;
+            v0[jx] = __ldg(rowp + ky0 * P2);
+            v1[jx] = __ldg(rowp + ky1 * P2);
+          }
+#pragma unroll
+          for (int jx = 0; jx < 8; ++jx)
+            racc += wt[7 - jx] * (wy0 * (part_ ? v0[jx].y : v0[jx].x) + wy1 * (part_ ? v1[jx].y : v1[jx].x));
+        } else {
+          // a constant trip count (P^2/4 rows per lane) lets the loads be in flight at once
+#pragma unroll
+          for (int i = 0; i < P * P / 4; ++i) {
+            const int r = rsub + 4 * i;
+            const int jx = r / P, jy = r - (r / P) * P;
+            int kx = f0 - (P - 1) + jx;
+            if (kx < 0) kx += S.K[0];
+            int ky = f1 - (P - 1) + jy;
+            if (ky < 0) ky += S.K[1];
+            const V v = __ldg(mg + ((int64_t)kx * S.K[1] + ky) * S.P[2] + kz);
+            racc += wt[P - 1 - jx] * wt[QEQ_MAXP + P - 1 - jy] * (part_ ? v.y : v.x);
+          }
         }
         acc = racc * wzj;
       }
