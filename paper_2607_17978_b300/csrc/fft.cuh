@@ -4,7 +4,11 @@
 // fused into the x pass.  Included by matvec.cu only (its kernels live in that unit).
 #pragma once
 
-// resident CTAs per SM the FP32 FFT kernels are compiled for (register budget 65536 / (256 n))
+// threads per CTA of the FP32 FFT kernels and the resident CTAs per SM they are compiled
+// for (register budget 65536 / (threads n)); FP64 kernels: 256 threads, one CTA per SM
+#ifndef QEQ_FFT_THREADS32
+#define QEQ_FFT_THREADS32 256
+#endif
 #ifndef QEQ_FFT_MIN_BLOCKS32
 #define QEQ_FFT_MIN_BLOCKS32 2
 #endif
@@ -514,7 +518,7 @@ __host__ __device__ __forceinline__ int fft_copy_elems(int K) {
   return sizeof(T) == 4 ? K + (K & 1) : K;
 }
 
-// Issue the bulk copies of one work unit into buffer B (warp 0 only): when `tables`, the
+// Issue the bulk copies of one work unit into buffer B (one warp): when `tables`, the
 // unit's FFT plan, its twiddles and ntab of its int tables (from table t0); then nl mesh
 // lines.  extra_tx > 0 (a test hook, see QEQ_FLAG_TEST_STALL) announces more bytes than
 // the copies deliver.
@@ -551,11 +555,33 @@ __device__ __forceinline__ void give_up(int* err, uint64_t* bar, const uint32_t*
   if (next_issued) mbar_wait_bounded(&bar[b ^ 1], ph[b ^ 1]);
 }
 
+// units of a persistent CTA whose geometry is read once, before the first (static shared
+// memory: a few KB); later units compute theirs when they are issued
+#ifndef QEQ_FFT_GEO_CACHE
+#define QEQ_FFT_GEO_CACHE 128
+#endif
+// Fill cache[k] = geo(blockIdx.x + k gridDim.x) for this CTA's first units (all threads);
+// returns how many.
+template <class G, class F>
+__device__ __forceinline__ int geo_cache_fill(G* cache, int nunits, F geo) {
+  const int G0 = (int)blockIdx.x, GS = (int)gridDim.x;
+  const int nmine = (nunits > G0) ? (nunits - G0 + GS - 1) / GS : 0;
+  const int n = min(nmine, QEQ_FFT_GEO_CACHE);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) cache[k] = geo(G0 + k * GS);
+  __syncthreads();
+  return n;
+}
+
+// The warp that issues a pass's bulk copies: the last one, which the stages leave idle
+// whenever a unit has fewer butterflies than the CTA has threads (the copies of the next
+// unit are issued once the current unit's data has arrived, while the stages run).
+__device__ __forceinline__ bool fft_issuer_warp() { return (threadIdx.x >> 5) == (blockDim.x >> 5) - 1; }
+
 // Persistent, two-slot pipeline: CTA b takes work units b, b + G, b + 2G, ... (a unit is a
 // sub-tile of `sub` lines of an item); the bulk copies of the next unit are in flight while
 // the current one is transformed.
 template <typename T, int PASS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
+__global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
     k_fft_tile(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl, const int4* __restrict__ items,
                int nitems, int TL, int sub, int Kmax, int ldmax, const double2* __restrict__ tw64,
                const float2* __restrict__ tw32, const int* __restrict__ tabs, const PcgScalars* __restrict__ sc,
@@ -568,7 +594,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   const FftBuf L = fft_buf(Kmax, ldmax, sub, (int)sizeof(V), 1, 0);
   unsigned char* bufs = smem_raw + 128;
-  __shared__ int buf_plan[2];  // FFT plan whose tables each buffer holds (read and written by warp 0)
+  __shared__ int buf_plan[2];  // FFT plan whose tables each buffer holds (read and written by the issuer)
   if (threadIdx.x == 0) {
     mbar_init(&bar[0]);
     mbar_init(&bar[1]);
@@ -582,7 +608,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
   // unit u: sub-tile (u mod nsub) of item u / nsub
   struct Geo {
     int ok, plan, K, nl;
-    int64_t in0, ils, out0, ols, oes;
+    int64_t in0, out0;
+    int ils, ols, oes, pad;
   };
   auto geo = [&](int u) {
     Geo g;
@@ -610,10 +637,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
       ib = ((int64_t)it.z * K1 + it.w) * P2; g.ils = P2;
       ob = ib; g.ols = P2; g.oes = 1;
     } else if (PASS == PASS_YF) {
-      ib = ((int64_t)it.w * K2 + it.z) * P1; g.ils = (int64_t)K2 * P1;
+      ib = ((int64_t)it.w * K2 + it.z) * P1; g.ils = K2 * P1;
       ob = (int64_t)it.z * K1 * P0 + it.w; g.ols = 1; g.oes = P0;
     } else {
-      ib = ((int64_t)it.w * K0 + it.z) * P1; g.ils = (int64_t)K0 * P1;
+      ib = ((int64_t)it.w * K0 + it.z) * P1; g.ils = K0 * P1;
       ob = (int64_t)it.z * K1 * P2 + it.w; g.ols = 1; g.oes = P2;
     }
     (void)P0;
@@ -621,26 +648,40 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
     g.out0 = mb + ob + (int64_t)part * sub * g.ols;
     return g;
   };
-  auto issue = [&](const Geo& g, int b) {  // warp 0
+  // the geometry of this CTA's first QEQ_FFT_GEO_CACHE units, read at once: the chain of
+  // global loads behind it would otherwise delay every unit's copies and first barrier
+  __shared__ Geo gcache[QEQ_FFT_GEO_CACHE];
+  const int ncache = geo_cache_fill(gcache, nunits, geo);
+  auto geo_k = [&](int k, int u) { return (k < ncache) ? gcache[k] : geo(u); };
+  auto issue = [&](const Geo& g, int b) {  // the issuer warp
     issue_unit<T>(bufs + (size_t)b * L.bytes, L, &bar[b], fpl + g.plan, twg, tabs, 0, 1, g.nl,
-                  fft_smem_ld<T>(g.K), [&](int l) { return src + g.in0 + l * g.ils; }, 0, buf_plan[b] != g.plan);
+                  fft_smem_ld<T>(g.K), [&](int l) { return src + g.in0 + (int64_t)l * g.ils; }, 0,
+                  buf_plan[b] != g.plan);
     if ((threadIdx.x & 31) == 0) buf_plan[b] = g.plan;
   };
   uint32_t ph[2] = {0u, 0u};
+  const bool issuer = fft_issuer_warp();
   int u = blockIdx.x, k = 0;
-  Geo cur = geo(u);
-  if (threadIdx.x < 32 && cur.ok) issue(cur, 0);
+  if (issuer) {
+    const Geo g0 = geo_k(0, u);
+    if (g0.ok) issue(g0, 0);
+  }
   for (; u < nunits; u += gridDim.x, ++k) {
     const int b = k & 1;
-    const Geo nxt = geo(u + gridDim.x);
-    if (threadIdx.x < 32 && nxt.ok) issue(nxt, b ^ 1);  // buffer b^1 was released at the end of the last unit
+    const Geo cur = geo_k(k, u);
     if (cur.ok) {
       bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], ph[b]));
       if (!ok) {
-        give_up(err, bar, ph, nxt.ok, b);
+        give_up(err, bar, ph, false, b);  // only this unit's copies are in flight
         return;
       }
       ph[b] ^= 1u;
+    }
+    if (issuer) {  // the next unit into buffer b^1 (released at the end of the last unit)
+      const Geo nxt = geo_k(k + 1, u + gridDim.x);
+      if (nxt.ok) issue(nxt, b ^ 1);
+    }
+    if (cur.ok) {
       unsigned char* B = bufs + (size_t)b * L.bytes;
       const FftPlanDev& fp = *reinterpret_cast<const FftPlanDev*>(B);
       const V* tw = reinterpret_cast<const V*>(B + L.tw);
@@ -651,7 +692,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
       int lsh = 0;
       while ((1 << lsh) < nl) ++lsh;
       V* o = dst + cur.out0;
-      const int64_t ols = cur.ols, oes = cur.oes;
+      const int64_t ols = cur.ols, oes = cur.oes;  // 64-bit products below
       auto store = [&](int l, int e, V v) { o[l * ols + e * oes] = v; };
 #define QEQ_CALL(RR)                                                                      \
   if (PASS == PASS_ZI)                                                                    \
@@ -662,7 +703,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
 #undef QEQ_CALL
       __syncthreads();  // the buffer is free for the unit after next
     }
-    cur = nxt;
   }
 }
 
@@ -716,7 +756,7 @@ constexpr double kPreBetaOneX = 150.0;
 // zz, xy, xz, yz} to vir[8 u ..] (dst reinterpreted), in a fixed order: a line that is
 // not its own mirror stands for itself and its mirror (weight 2).
 template <typename T, bool PRE, int MAXS, bool VIR = false>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
+__global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
     k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                   const int4* __restrict__ items, int nitems, int TLX, int sub, int Kmax, int ldmax,
                   const T* __restrict__ bmod, const double2* __restrict__ tw64, const float2* __restrict__ tw32,
@@ -731,7 +771,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
   unsigned char* bufs = smem_raw + 128;
   __shared__ T hw2[QEQ_MAX_SPECIES * QEQ_MAX_SPECIES];
   __shared__ int hw2_s;
-  __shared__ int buf_plan[2];  // FFT plan whose tables each buffer holds (read and written by warp 0)
+  __shared__ int buf_plan[2];  // FFT plan whose tables each buffer holds (read and written by the issuer)
   if (threadIdx.x == 0) {
     mbar_init(&bar[0]);
     mbar_init(&bar[1]);
@@ -761,7 +801,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
     g.y0 = it.z + part * sub;
     return g;
   };
-  // warp 0: slot tables and line constants of the unit in buffer b, then its copies
+  __shared__ Geo gcache[QEQ_FFT_GEO_CACHE];  // this CTA's first units (see geo_cache_fill)
+  const int ncache = geo_cache_fill(gcache, nunits, geo);
+  auto geo_k = [&](int k, int u) { return (k < ncache) ? gcache[k] : geo(u); };
+  // the issuer warp: slot tables and line constants of the unit in buffer b, then its copies
   auto issue = [&](const Geo& g, int b, int extra) {
     const StructDev& S = st[g.s];
     const int K = S.K[0], K1 = S.K[1], K2 = S.K[2], P0 = S.P[0], P1 = S.P[1], ncm = S.ncm;
@@ -797,26 +840,33 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
     if (lane == 0) buf_plan[b] = plan;
   };
   uint32_t ph[2] = {0u, 0u};
+  const bool issuer = fft_issuer_warp();
   int u = blockIdx.x, k = 0;
-  Geo cur = geo(u);
-  if (threadIdx.x < 32 && cur.ok) issue(cur, 0, (stall && blockIdx.x == 0) ? 16 : 0);
+  if (issuer) {
+    const Geo g0 = geo_k(0, u);
+    if (g0.ok) issue(g0, 0, (stall && blockIdx.x == 0) ? 16 : 0);
+  }
   for (; u < nunits; u += gridDim.x, ++k) {
     const int b = k & 1;
-    const Geo nxt = geo(u + gridDim.x);
-    if (threadIdx.x < 32 && nxt.ok) issue(nxt, b ^ 1, 0);
+    const Geo cur = geo_k(k, u);
+    if (cur.ok) {
+      bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], ph[b]));
+      if (!ok) {
+        give_up(err, bar, ph, false, b);  // only this unit's copies are in flight
+        return;
+      }
+      ph[b] ^= 1u;
+    }
+    if (issuer) {  // the next unit into buffer b^1 (released at the end of the last unit)
+      const Geo nxt = geo_k(k + 1, u + gridDim.x);
+      if (nxt.ok) issue(nxt, b ^ 1, 0);
+    }
     if (!cur.ok) {
       if constexpr (VIR) {
         if (threadIdx.x < 8) reinterpret_cast<double*>(dst)[8 * (int64_t)u + threadIdx.x] = 0.0;
       }
-      cur = nxt;
       continue;
     }
-    bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], ph[b]));
-    if (!ok) {
-      give_up(err, bar, ph, nxt.ok, b);
-      return;
-    }
-    ph[b] ^= 1u;
     const StructDev& S = st[cur.s];
     const int K = S.K[0], P1 = S.P[1], ncm = S.ncm, np = cur.np, nsl = 2 * ncm * np;
     const int ld = fft_smem_ld<T>(K);
@@ -898,7 +948,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
         acc[6] += k * Gy * Gz;
       }
       // fixed-order block sums: shuffle tree per warp, then warps in order
-      __shared__ double vred[7][8];
+      __shared__ double vred[7][8];  // VIR: FP64 kernels, 256 threads
 #pragma unroll
       for (int i = 0; i < 7; ++i) {
         double a = acc[i];
@@ -1001,7 +1051,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1
 #undef QEQ_CALL
     __syncthreads();  // the buffer is free for the unit after next
     }  // VIR
-    cur = nxt;
   }
 }
 

@@ -655,7 +655,7 @@ __global__ void k_pre_gather(const Chunk* __restrict__ chunks, const StructDev* 
 
 // ------------------------------------------------------------------ host side
 // Persistent grid of an FFT pass: the resident CTAs of all SMs, at most one per unit.
-int fft_grid(qeq_plan_s* P, const void* fn, size_t smem, int nunits) {
+int fft_grid(qeq_plan_s* P, const void* fn, size_t smem, int nunits, int threads) {
   int blocks = 0;
   for (int i = 0; i < P->n_occ; ++i)
     if (P->occ[i].fn == fn && P->occ[i].smem == smem) {
@@ -663,7 +663,7 @@ int fft_grid(qeq_plan_s* P, const void* fn, size_t smem, int nunits) {
       break;
     }
   if (blocks == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 256, smem) != cudaSuccess || blocks < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess || blocks < 1) {
       cudaGetLastError();
       blocks = 1;
     }
@@ -681,6 +681,7 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
                               int max_species, Mark mark) {
   using V = typename C2<T>::t;
   constexpr bool F32 = std::is_same<T, float>::value;
+  constexpr int FT = F32 ? QEQ_FFT_THREADS32 : 256;  // threads per CTA (the kernels' launch bounds)
   cudaStream_t s = Pl->stream;
   const T* bmod = F32 ? (const T*)(const void*)Pl->d_bmod32 : (const T*)(const void*)Pl->d_bmod;
   const int sub = F32 ? g.sub32 : g.sub64;
@@ -693,14 +694,14 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
   int* err = Pl->d_err;
   {
     auto fn = k_fft_tile<T, PASS_ZF>;
-    fn<<<fft_grid(Pl, (const void*)fn, smz, nz * nsub), 256, smz, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smz, nz * nsub, FT), FT, smz, s>>>(
         st, Pl->d_fft, zit, nz, g.tl, sub, kmax[2], ldz, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, a, b, err);
     QEQ_CUDA_TRY(cudaGetLastError());
     QEQ_CUDA_TRY(mark());
   }
   {
     auto fn = k_fft_tile<T, PASS_YF>;
-    fn<<<fft_grid(Pl, (const void*)fn, smy, ny * nsub), 256, smy, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smy, ny * nsub, FT), FT, smy, s>>>(
         st, Pl->d_fft, yit, ny, g.tl, sub, kmax[1], ldy, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, b, a, err);
     QEQ_CUDA_TRY(cudaGetLastError());
     QEQ_CUDA_TRY(mark());
@@ -711,7 +712,7 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
       auto fn = k_fft_x_green<T, PRE, 2>;
       const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], ldx, 2 * subx, sizeof(V), 2,
                                                    fft_x_extra(subx, 1, sizeof(T))).bytes;
-      fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+      fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx, FT), FT, smx, s>>>(
           st, Pl->d_fft, xit, nx, g.tlx, subx, kmax[0], ldx, bmod, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
           use_active, a, b, err, stall);
     } else {
@@ -719,7 +720,7 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
       auto fn = k_fft_x_green<T, false, QEQ_MAX_SPECIES>;
       const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], ldx, 2 * HX * subx, sizeof(V), 2,
                                                    fft_x_extra(subx, HX, sizeof(T))).bytes;
-      fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+      fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx, FT), FT, smx, s>>>(
           st, Pl->d_fft, xit, nx, g.tlx, subx, kmax[0], ldx, bmod, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc,
           use_active, a, b, err, stall);
     }
@@ -728,7 +729,7 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
   }
   {
     auto fn = k_fft_tile<T, PASS_YI>;
-    fn<<<fft_grid(Pl, (const void*)fn, smy, nyi * nsub), 256, smy, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smy, nyi * nsub, FT), FT, smy, s>>>(
         st, Pl->d_fft, yiit, nyi, g.tl, sub, kmax[1], ldy, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, b, a,
         err);
     QEQ_CUDA_TRY(cudaGetLastError());
@@ -736,7 +737,7 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
   }
   {
     auto fn = k_fft_tile<T, PASS_ZI>;
-    fn<<<fft_grid(Pl, (const void*)fn, smz, nz * nsub), 256, smz, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smz, nz * nsub, FT), FT, smz, s>>>(
         st, Pl->d_fft, zit, nz, g.tl, sub, kmax[2], ldz, Pl->d_tw64, Pl->d_tw32, tabs, Pl->d_sc, use_active, a, a, err);
     QEQ_CUDA_TRY(cudaGetLastError());
     QEQ_CUDA_TRY(mark());
@@ -789,7 +790,7 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
 
 template <typename T, int P>
 cudaError_t set_smem_attrs() {
-  const int big = 227 * 1024 - 1024;  // leaves room for the kernels' static shared arrays
+  const int big = 227 * 1024 - 12 * 1024;  // leaves room for the kernels' static shared arrays
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)spread_smem<T, P>()));
   if (P == 4) {  // the FFT kernels do not depend on the B-spline order: set them once
@@ -835,6 +836,7 @@ cudaError_t potential_impl(qeq_plan_s* Pl, const double* x) {
 // in d_mesh2 (units of structure s: items xitem_off[s] .. xitem_off[s+1], times *nsub_out)
 template <int P>
 cudaError_t virial_impl(qeq_plan_s* Pl, const double* x, int* nsub_out) {
+  constexpr int FT = 256;  // FP64 FFT kernels
   cudaStream_t s = Pl->stream;
   double2* a = Pl->d_mesh;
   double2* b = Pl->d_mesh2;
@@ -851,14 +853,14 @@ cudaError_t virial_impl(qeq_plan_s* Pl, const double* x, int* nsub_out) {
   const size_t smy = 128 + 2 * (size_t)fft_buf(kmax[1], g.ldy64, sub, sizeof(double2), 1, 0).bytes;
   {
     auto fn = k_fft_tile<double, PASS_ZF>;
-    fn<<<fft_grid(Pl, (const void*)fn, smz, Pl->n_zitems * nsub), 256, smz, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smz, Pl->n_zitems * nsub, FT), FT, smz, s>>>(
         Pl->d_st, Pl->d_fft, Pl->d_zitems, Pl->n_zitems, g.tl, sub, kmax[2], g.ldz64, Pl->d_tw64, Pl->d_tw32,
         Pl->d_fft_tabs, Pl->d_sc, 0, a, b, Pl->d_err);
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   {
     auto fn = k_fft_tile<double, PASS_YF>;
-    fn<<<fft_grid(Pl, (const void*)fn, smy, Pl->n_yitems * nsub), 256, smy, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smy, Pl->n_yitems * nsub, FT), FT, smy, s>>>(
         Pl->d_st, Pl->d_fft, Pl->d_yitems, Pl->n_yitems, g.tl, sub, kmax[1], g.ldy64, Pl->d_tw64, Pl->d_tw32,
         Pl->d_fft_tabs, Pl->d_sc, 0, b, a, Pl->d_err);
     QEQ_CUDA_TRY(cudaGetLastError());
@@ -868,7 +870,7 @@ cudaError_t virial_impl(qeq_plan_s* Pl, const double* x, int* nsub_out) {
     auto fn = k_fft_x_green<double, false, 2, true>;
     const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], g.ldx64, 2 * subx, sizeof(double2), 2,
                                                  fft_x_extra(subx, 1, sizeof(double))).bytes;
-    fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx, FT), FT, smx, s>>>(
         Pl->d_st, Pl->d_fft, Pl->d_xitems, nx, g.tlx, subx, kmax[0], g.ldx64, Pl->d_bmod, Pl->d_tw64, Pl->d_tw32,
         Pl->d_fft_tabs, Pl->d_sc, 0, a, b, Pl->d_err, 0);
   } else {
@@ -876,7 +878,7 @@ cudaError_t virial_impl(qeq_plan_s* Pl, const double* x, int* nsub_out) {
     auto fn = k_fft_x_green<double, false, QEQ_MAX_SPECIES, true>;
     const size_t smx = 128 + 2 * (size_t)fft_buf(kmax[0], g.ldx64, 2 * HX * subx, sizeof(double2), 2,
                                                  fft_x_extra(subx, HX, sizeof(double))).bytes;
-    fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx), 256, smx, s>>>(
+    fn<<<fft_grid(Pl, (const void*)fn, smx, nx * nsubx, FT), FT, smx, s>>>(
         Pl->d_st, Pl->d_fft, Pl->d_xitems, nx, g.tlx, subx, kmax[0], g.ldx64, Pl->d_bmod, Pl->d_tw64, Pl->d_tw32,
         Pl->d_fft_tabs, Pl->d_sc, 0, a, b, Pl->d_err, 0);
   }
