@@ -491,17 +491,29 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
 }
 
 // ------------------------------------------------------------------ Fourier preconditioner
-// Power-of-two scale of the fixed-point coarse spread: max |D^-1 r| is at most
-// max|r| max D^-1 (max D^-1 alone for the ones vector), mapped to 2^48; a mesh
-// point sums the B-spline weights (each at most 2/3 per direction) of the atoms
-// around it, far below the 2^15 headroom of a signed 64-bit integer.
+// The coarse spread takes v = D^-1 (r - shift 1) (shift: the PCG's running estimate of
+// mu, 0 for the ones vector).  The preconditioner's output enters the projected
+// direction z = M^-1 r - (1.M^-1 r / 1.M^-1 1) M^-1 1, which the shift leaves unchanged
+// (it adds a multiple of M^-1 1 to M^-1 r); without it r carries mu 1, and near
+// convergence the part of v that matters is ~1e-6 of max|v|.
+__device__ __forceinline__ double pre_shift(const PcgScalars& c, int ones_input) {
+  return ones_input ? 0.0 : c.shift;
+}
+// Power-of-two scale of the fixed-point coarse spread: max |v| is at most
+// max|r - shift| max D^-1 (max D^-1 alone for the ones vector), mapped to 2^23 (the
+// resolution of an FP32 mantissa); a contribution (B-spline weight product at most
+// (2/3)^3) stays below 2^21, so a tile point's 32-bit sum is exact for up to 2^10
+// contributions (a tile group with more atoms than kPreTileMaxAtoms adds straight to
+// the 64-bit mesh).
 __device__ __forceinline__ double pre_fixed_scale(const PcgScalars& c, int ones_input) {
-  double b = c.dinv_max * (ones_input ? 1.0 : fmax(fabs(c.r_max), fabs(c.r_min)));
+  const double sh = pre_shift(c, ones_input);
+  double b = c.dinv_max * (ones_input ? 1.0 : fmax(fabs(c.r_max - sh), fabs(c.r_min - sh)));
   if (!(b > 0.0) || !isfinite(b)) b = 1.0;
   int e;
   frexp(b, &e);                    // b < 2^e
-  return ldexp(1.0, 48 - e);
+  return ldexp(1.0, 23 - e);
 }
+constexpr int kPreTileMaxAtoms = 1024;
 
 // Cubic B-spline (order 4) weights of every atom on its structure's coarse mesh,
 // once per solve: M_4(w + j), j = 0..3, for stencil points f - j.
@@ -530,68 +542,124 @@ __global__ void k_pre_weights(const StructDev* __restrict__ stp, const int* __re
   pbase[a] = f[0] | (f[1] << 10) | (f[2] << 20);
 }
 
-// v = D^-1 r spread on the coarse mesh in 64-bit fixed point: every contribution
-// is rounded to an integer multiple of 2^-e (e per structure, from a bound on
-// max |v|) and added with an integer atomic.  Integer addition does not depend
-// on the order of the atomics, so the coarse mesh, and with it every
-// preconditioned solve, is bitwise reproducible.  k_pre_fixed_to_float turns the
-// sums back into the FP32 mesh.
-__global__ void k_pre_spread(const StructDev* __restrict__ stp, const int* __restrict__ sorted_struct,
-                             const int* __restrict__ pbase, const float* __restrict__ pw,
-                             const double* __restrict__ dinv, const double* __restrict__ r, int64_t n,
-                             const PcgScalars* __restrict__ sc, int use_active, int ones_input,
-                             unsigned long long* __restrict__ imesh) {
-  // the 32 lanes of a warp take atoms n/32 apart in the bin order (lane l of global warp
-  // g: atom l * nw + g), so that their 64 additions each go to different mesh regions
-  // instead of queueing on the same addresses; the integer sums do not depend on order
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nw = (n + 31) / 32;
-  const int64_t a = (gid & 31) * nw + (gid >> 5);
-  if ((gid >> 5) >= nw || a >= n) return;
-  const int s = sorted_struct[a];
+// v = D^-1 r spread on the coarse mesh in fixed point: every contribution is rounded to
+// an integer multiple of 2^-e (e per structure, from a bound on max |v|, pre_fixed_scale)
+// and added with integer atomics.  Integer addition does not depend on the order of the
+// additions, so the coarse mesh, and with it every preconditioned solve, is bitwise
+// reproducible.  One CTA per tile group (plan: QEQ_PRE_TILE_G^2 fine bin columns, a run
+// of z bins): its atoms add their 64 contributions into the group's tile of the coarse
+// mesh in shared memory (32-bit integer atomics), then the tile's nonzero partial sums go
+// to the 64-bit mesh (one global atomic per point instead of one per contribution; a
+// tile point gets the contributions of the ~20 atoms around it).  A contribution outside
+// the tile (only possible through rounding at a bin edge) goes straight to the mesh.
+// The sums are those of one atomic per contribution, bit for bit.
+// k_pre_fixed_to_float turns the sums back into the FP32 mesh.
+__global__ void __launch_bounds__(256) k_pre_spread_tiles(
+    const StructDev* __restrict__ stf, const StructDev* __restrict__ stp, const int4* __restrict__ tiles, int gz,
+    const int* __restrict__ bin_start, const int* __restrict__ pbase, const float* __restrict__ pw,
+    const double* __restrict__ dinv, const double* __restrict__ r, const PcgScalars* __restrict__ sc, int use_active,
+    int ones_input, unsigned long long* __restrict__ imesh) {
+  extern __shared__ __align__(16) int tile[];
+  const int4 tg = tiles[blockIdx.x];
+  const int s = tg.x;
   if (use_active && !sc[s].active) return;
-  const StructDev& S = stp[s];
-  const int bs = pbase[a];
-  const int f[3] = {bs & 1023, (bs >> 10) & 1023, (bs >> 20) & 1023};
-  const float* w = pw + a * 12;
-  // the scale is a power of two: scaling the FP32 product is exact, so the integer of each
-  // contribution is that of the FP32 product scaled in FP64 (no FP64 arithmetic per point)
-  const float vs = (float)((double)(float)(dinv[a] * r[a]) * pre_fixed_scale(sc[s], ones_input));  // |vs| <= 2^48
-  unsigned long long* m = imesh + S.mesh_off;
-  for (int jx = 0; jx < 4; ++jx) {
-    int kx = f[0] - jx;
-    if (kx < 0) kx += S.K[0];
-    for (int jy = 0; jy < 4; ++jy) {
-      int ky = f[1] - jy;
-      if (ky < 0) ky += S.K[1];
+  const StructDev& F = stf[s];
+  const StructDev& C = stp[s];
+  const int K0 = C.K[0], K1 = C.K[1], K2 = C.K[2];
+  int ox, ex, oy, ey, oz, ez;
+  pre_tile_range(tg.y, QEQ_PRE_TILE_G, F.nb[0], K0, F.K[0], ox, ex);
+  pre_tile_range(tg.z, QEQ_PRE_TILE_G, F.nb[1], K1, F.K[1], oy, ey);
+  pre_tile_range(tg.w, gz, F.nb[2], K2, F.K[2], oz, ez);
+  const int npts = ex * ey * ez;
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) tile[i] = 0;
+  const double scale = pre_fixed_scale(sc[s], ones_input);
+  const double sh = pre_shift(sc[s], ones_input);
+  unsigned long long* m = imesh + C.mesh_off;
+  const int bz1 = min(tg.w + gz, F.nb[2]);
+  int ntot = 0;  // atoms of the group (the same on every thread)
+  for (int c = 0; c < QEQ_PRE_TILE_G * QEQ_PRE_TILE_G; ++c) {
+    const int bx = tg.y + c / QEQ_PRE_TILE_G, by = tg.z + c % QEQ_PRE_TILE_G;
+    if (bx >= F.nb[0] || by >= F.nb[1]) continue;
+    const int col = F.bin_off + (bx * F.nb[1] + by) * F.nb[2];
+    ntot += bin_start[col + bz1] - bin_start[col + tg.w];
+  }
+  const bool use_tile = ntot < kPreTileMaxAtoms;
+  __syncthreads();
+  for (int c = 0; c < QEQ_PRE_TILE_G * QEQ_PRE_TILE_G; ++c) {
+    const int bx = tg.y + c / QEQ_PRE_TILE_G, by = tg.z + c % QEQ_PRE_TILE_G;
+    if (bx >= F.nb[0] || by >= F.nb[1]) continue;
+    const int col = F.bin_off + (bx * F.nb[1] + by) * F.nb[2];
+    const int a0 = bin_start[col + tg.w], na = bin_start[col + bz1] - a0;
+    // 16 items per atom: its (x, y) stencil rows, 4 z points each
+    for (int it = threadIdx.x; it < na * 16; it += blockDim.x) {
+      const int a = a0 + (it >> 4), jx = (it >> 2) & 3, jy = it & 3;
+      const int bs = pbase[a];
+      const float* w = pw + (size_t)a * 12;
+      // the scale is a power of two: scaling the FP32 value is exact (|vs| <= 2^23)
+      const float vs = (float)((double)(float)(dinv[a] * (r[a] - sh)) * scale);
+      int kx = (bs & 1023) - jx;
+      if (kx < 0) kx += K0;
+      int ky = ((bs >> 10) & 1023) - jy;
+      if (ky < 0) ky += K1;
+      int tx = kx - ox;
+      if (tx < 0) tx += K0;
+      int ty = ky - oy;
+      if (ty < 0) ty += K1;
       const float wxy = vs * w[jx] * w[4 + jy];
-      unsigned long long* row = m + ((int64_t)kx * S.K[1] + ky) * S.P[2];
+      const int fz = (bs >> 20) & 1023;
+#pragma unroll
       for (int jz = 0; jz < 4; ++jz) {
-        int kz = f[2] - jz;
-        if (kz < 0) kz += S.K[2];
-        atomicAdd(&row[kz], (unsigned long long)__float2ll_rn(wxy * w[8 + jz]));
+        int kz = fz - jz;
+        if (kz < 0) kz += K2;
+        int tz = kz - oz;
+        if (tz < 0) tz += K2;
+        const int v = __float2int_rn(wxy * w[8 + jz]);
+        if (use_tile && tx < ex && ty < ey && tz < ez)
+          atomicAdd(&tile[(tx * ey + ty) * ez + tz], v);
+        else
+          atomicAdd(&m[((int64_t)kx * K1 + ky) * C.P[2] + kz], (unsigned long long)(long long)v);
       }
     }
   }
-}
-
-// fixed-point coarse mesh -> FP32 complex mesh (real part), structure found by bisection
-__global__ void k_pre_fixed_to_float(const StructDev* __restrict__ stp, int ns, int64_t total,
-                                     const PcgScalars* __restrict__ sc, int ones_input,
-                                     const unsigned long long* __restrict__ imesh, float2* __restrict__ mesh) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = ns - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (stp[mid].mesh_off <= i) lo = mid;
-      else hi = mid - 1;
-    }
-    const double inv = 1.0 / pre_fixed_scale(sc[lo], ones_input);
-    mesh[i] = make_float2((float)((double)(long long)imesh[i] * inv), 0.f);
+  __syncthreads();
+  if (!use_tile) return;
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+    const int v = tile[i];
+    if (v == 0) continue;
+    const int tz = i % ez, txy = i / ez, ty = txy % ey, tx = txy / ey;
+    int kx = ox + tx, ky = oy + ty, kz = oz + tz;
+    if (kx >= K0) kx -= K0;
+    if (ky >= K1) ky -= K1;
+    if (kz >= K2) kz -= K2;
+    atomicAdd(&m[((int64_t)kx * K1 + ky) * C.P[2] + kz], (unsigned long long)(long long)v);
   }
 }
 
-// u = D^-1 (r - phi), phi the interpolated coarse potential; per-structure sum of u
+// fixed-point coarse mesh -> FP32 complex mesh (real part), structure found by bisection;
+// the scale is a power of two, so v 2^-e rounds once to FP32 either way
+__global__ void k_pre_fixed_to_float(const StructDev* __restrict__ stp, int ns, int64_t total,
+                                     const PcgScalars* __restrict__ sc, int ones_input,
+                                     const unsigned long long* __restrict__ imesh, float2* __restrict__ mesh) {
+  int cur = -1;
+  float inv = 0.f;
+  int64_t end = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (cur < 0 || i >= end) {
+      int lo = 0, hi = ns - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (stp[mid].mesh_off <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      cur = lo;
+      end = (lo + 1 < ns) ? stp[lo + 1].mesh_off : total;
+      inv = (float)(1.0 / pre_fixed_scale(sc[lo], ones_input));
+    }
+    mesh[i] = make_float2(__ll2float_rn((long long)imesh[i]) * inv, 0.f);
+  }
+}
+
+// u = D^-1 (r - shift - phi), phi the interpolated coarse potential; per-structure sum of u
 __global__ void k_pre_gather(const Chunk* __restrict__ chunks, const StructDev* __restrict__ stp,
                              const int* __restrict__ pbase, const float* __restrict__ pw,
                              const double* __restrict__ dinv, const double* __restrict__ r,
@@ -601,6 +669,7 @@ __global__ void k_pre_gather(const Chunk* __restrict__ chunks, const StructDev* 
   if (use_active && !sc[ch.s].active) return;
   const StructDev& S = stp[ch.s];
   const float2* m = mesh + S.mesh_off;
+  const double sh = pre_shift(sc[ch.s], slot == 1);  // as the spread (k_pre_spread_tiles)
   double acc = 0.0;
   for (int64_t a = ch.begin + threadIdx.x; a < ch.end; a += blockDim.x) {
     const int bs = pbase[a];
@@ -623,7 +692,7 @@ __global__ void k_pre_gather(const Chunk* __restrict__ chunks, const StructDev* 
         phi += w[jx] * w[4 + jy] * rs;
       }
     }
-    double ua = dinv[a] * (r[a] - (double)phi);
+    double ua = dinv[a] * (r[a] - sh - (double)phi);
     u[a] = ua;
     acc += ua;
   }
@@ -935,6 +1004,7 @@ cudaError_t matvec_set_attributes() {
   QEQ_CUDA_TRY((set_smem_attrs<double, 4>()));
   QEQ_CUDA_TRY((set_smem_attrs<double, 6>()));
   QEQ_CUDA_TRY((set_smem_attrs<double, 8>()));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_pre_spread_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   return cudaSuccess;
 }
 
@@ -964,8 +1034,9 @@ cudaError_t launch_precond(qeq_plan_s* P, const double* r, double* u, int slot, 
   // fixed-point sums in the second coarse buffer (8 bytes per point, like the float2 mesh)
   unsigned long long* imesh = reinterpret_cast<unsigned long long*>(P->d_pmesh2);
   QEQ_CUDA_TRY(cudaMemsetAsync(imesh, 0, sizeof(unsigned long long) * (size_t)P->total_pmesh, s));
-  k_pre_spread<<<(int)((P->n_atoms + 255) / 256), 256, 0, s>>>(P->d_stp, P->d_key, P->d_pbase, P->d_pw, P->d_dinv, r,
-                                                               P->n_atoms, P->d_sc, use_active, slot == 1, imesh);
+  k_pre_spread_tiles<<<P->n_pre_tiles, 256, P->pre_tile_smem, s>>>(
+      P->d_st, P->d_stp, P->d_pre_tiles, P->pre_tile_gz, P->d_bin_start, P->d_pbase, P->d_pw, P->d_dinv, r, P->d_sc,
+      use_active, slot == 1, imesh);
   {
     const int nb = (int)std::min<int64_t>((P->total_pmesh + 255) / 256, 148 * 16);
     k_pre_fixed_to_float<<<nb, 256, 0, s>>>(P->d_stp, P->n_struct, P->total_pmesh, P->d_sc, slot == 1, imesh,

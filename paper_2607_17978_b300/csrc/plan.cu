@@ -149,7 +149,7 @@ static void free_plan(qeq_plan_s* P) {
                   P->d_val64,  P->d_val32,   P->d_q,       P->d_r,        P->d_z,       P->d_p,
                   P->d_Ap,     P->d_x,       P->d_mesh,    P->d_mesh2,   P->d_part,     P->d_counter, P->d_sc,
                   P->d_err,    P->d_done,    P->d_stp,     P->d_pzitems,  P->d_pyitems, P->d_pxitems, P->d_pyiitems, P->d_fft_tabs,
-                  P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,
+                  P->d_pmesh,  P->d_pmesh2,  P->d_w1,      P->d_u,        P->d_pbase,   P->d_pw,     P->d_pre_tiles,
                   P->d_x32,    P->d_posc32,  P->d_q1,      P->d_r1,       P->d_reject,  P->d_xitem_off, P->d_stress_part,
                   P->d_sqnm_dx, P->d_sqnm_dg, P->d_sqnm_g, P->d_sqnm_part, P->d_sqnm};
   for (void* p : ptrs)
@@ -497,6 +497,41 @@ static qeq_status build_plan(qeq_plan_s* P) {
                      [&](int4 v) { pxit.push_back(v); });
     }
   }
+  // tile groups of the coarse spread: QEQ_PRE_TILE_G x QEQ_PRE_TILE_G fine bin columns and
+  // gz bins in z, gz as large as keeps the largest tile (8-byte points) within 64 KB
+  std::vector<int4> ptiles;
+  if (D.preconditioner == QEQ_PRECOND_FOURIER) {
+    const int G = QEQ_PRE_TILE_G;
+    auto tile_bytes = [&](int gz) {
+      int mx = 0;
+      for (int s = 0; s < ns; ++s) {
+        const StructDev& F = hs[s];
+        const StructDev& C = hsp[s];
+        int e[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+          const int g = (d == 2) ? gz : G;
+          for (int b0 = 0; b0 < F.nb[d]; b0 += g) {
+            int o, ext;
+            pre_tile_range(b0, g, F.nb[d], C.K[d], F.K[d], o, ext);
+            e[d] = std::max(e[d], ext);
+          }
+        }
+        mx = std::max(mx, e[0] * e[1] * e[2] * 8);
+      }
+      return mx;
+    };
+    int max_nbz = 1;
+    for (int s = 0; s < ns; ++s) max_nbz = std::max(max_nbz, hs[s].nb[2]);
+    int gz = max_nbz;
+    while (gz > 1 && tile_bytes(gz) > 64 * 1024) gz = (gz + 1) / 2;
+    P->pre_tile_gz = gz;
+    P->pre_tile_smem = tile_bytes(gz);
+    for (int s = 0; s < ns; ++s)
+      for (int bx = 0; bx < hs[s].nb[0]; bx += G)
+        for (int by = 0; by < hs[s].nb[1]; by += G)
+          for (int bz = 0; bz < hs[s].nb[2]; bz += gz) ptiles.push_back(make_int4(s, bx, by, bz));
+    P->n_pre_tiles = (int)ptiles.size();
+  }
   P->precond = D.preconditioner;
   P->hsp = hsp;
   P->n_pz = (int)pzit.size();
@@ -628,6 +663,7 @@ static qeq_status build_plan(qeq_plan_s* P) {
     ALLOC(dalloc(P, &P->d_u, N));
     ALLOC(dalloc(P, &P->d_pbase, N));
     ALLOC(dalloc(P, &P->d_pw, (size_t)N * 12));
+    ALLOC(upload(P, &P->d_pre_tiles, ptiles));
   }
   ALLOC(matvec_set_attributes());
 #undef ALLOC

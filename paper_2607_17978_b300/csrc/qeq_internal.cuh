@@ -379,6 +379,10 @@ struct qeq_plan_s {
   double *d_w1 = nullptr, *d_u = nullptr;
   int* d_pbase = nullptr;
   float* d_pw = nullptr;
+  int4* d_pre_tiles = nullptr;     // coarse-spread tile groups {structure, bx0, by0, bz0} (pre_tile_range)
+  int n_pre_tiles = 0;
+  int pre_tile_gz = 0;             // fine bins per tile group in z (QEQ_PRE_TILE_G in x and y)
+  int pre_tile_smem = 0;           // bytes of the largest tile (8 bytes per point)
   struct qeq_mlp_s* mlp = nullptr; // warm-start network (not owned)
   float* d_feat = nullptr;         // descriptors, sorted order
   float* d_pred = nullptr;         // network output, sorted order
@@ -504,6 +508,27 @@ inline int fft_ld32(int K) {
   return (ld & 3) ? ld : ld + 2;
 }
 inline int fft_ld64(int K) { return K | 1; }
+
+// Coarse-spread tiles of the Fourier preconditioner: a group of G consecutive fine atom
+// bins in one direction (bins b0 .. b0 + G - 1 of nb, QEQ_BIN fine points each, fine length
+// Kf) holds atoms whose coarse stencil base f = floor(u Kc) lies in [f0, f1], f0 =
+// floor(QEQ_BIN b0 Kc / Kf), f1 = floor(QEQ_BIN (b0 + G) Kc / Kf); their cubic stencils
+// (points f - 3 .. f) fill coarse points o .. o + ext - 1 (mod Kc), with one point of margin
+// on each side for the rounding of u.  The whole direction when that is no larger.
+#define QEQ_PRE_TILE_G 2
+__host__ __device__ inline void pre_tile_range(int b0, int G, int nb, int Kc, int Kf, int& o, int& ext) {
+  const int b1 = (b0 + G < nb) ? b0 + G : nb;
+  const int f0 = (int)(((long long)QEQ_BIN * b0 * Kc) / Kf);
+  const int f1 = (int)(((long long)QEQ_BIN * b1 * Kc) / Kf);
+  ext = f1 - f0 + 6;
+  o = f0 - 4;
+  if (ext >= Kc) {
+    o = 0;
+    ext = Kc;
+  } else if (o < 0) {
+    o += Kc;
+  }
+}
 
 // Tile sizes for meshes whose largest sizes per direction are maxK[3] (most complex
 // meshes max_ncm): item lines of the y/z passes and of the x pass (2 max_ncm lines per
