@@ -1,6 +1,8 @@
 // Learned warm start for the QEq solve: radial descriptors and a small per-species
-// network that predicts starting charges; forward and backward on BF16 tensor
-// cores (mma.sync m16n8k16, FP32 accumulate) and Adam on FP32 master weights.
+// network that predicts starting charges; inference on the tcgen05 tensor cores
+// (BF16 operands, FP32 accumulators in tensor memory), training forward and
+// backward on warp-level BF16 MMAs (mma.sync m16n8k16, FP32 accumulate) and Adam
+// on FP32 master weights.
 //
 // Descriptors (Sec. 2.2 eq. g2 radial functions with the cosine cutoff of SI
 // "Cutoff Functions"; element-embracing prefactor of SI "Element-Embracing
@@ -317,6 +319,207 @@ __global__ void __launch_bounds__(128) k_mlp(const float* __restrict__ feat, con
   }
 }
 
+// ---------------------------------------------------------------- network forward on tcgen05
+// Inference: one CTA = 4 warps = 128 atoms.  Both layers are M = 128 (atoms) x N = 64
+// (neurons) products on the fifth-generation tensor cores: BF16 operands staged in
+// shared memory in the canonical K-major layout without swizzle (8 x 16-byte core
+// matrices, 128 bytes each: row r, column k of an operand with Kt columns at element
+// ((r / 8) (Kt / 8) + k / 8) 64 + (r % 8) 8 + k % 8; neighbours along K 128 bytes apart,
+// along M or N Kt 16 bytes apart), FP32 accumulators in tensor memory (lane = atom,
+// column = neuron; layer 1 in columns 0-63, layer 2 in 64-127), one elected thread
+// issuing the MMAs, a commit to an mbarrier signalling their completion, and each warp
+// reading its 32 atoms' rows back with tcgen05.ld.  Every thread then owns one atom's
+// row: bias and tanh, the next layer's operand, and the output dot product stay in
+// registers.  For every species present in the tile its weights are staged and the
+// tile is run through that network; atoms of other species keep their earlier result.
+constexpr int TC_TILE = 128;
+struct MlpTcSmem {
+  alignas(128) __nv_bfloat16 X[TC_TILE * NF];    // A of layer 1 (K = NF)
+  alignas(128) __nv_bfloat16 H1[TC_TILE * NH];   // A of layer 2 (K = NH)
+  alignas(128) __nv_bfloat16 W1[NH * NF];        // B of layer 1: W1[n][k], K-major
+  alignas(128) __nv_bfloat16 W2[NH * NH];        // B of layer 2
+  float b1[NH], b2[NH], W3[NH], b3;
+  int sp[TC_TILE];
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ int kmaj_off(int r, int k, int Kt) {
+  return ((r >> 3) * (Kt >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+// shared-memory matrix descriptor of a K-major operand without swizzle (start, leading =
+// K-neighbour core matrix, stride = M/N-neighbour core matrix, all in 16-byte units;
+// descriptor version 1)
+__device__ __forceinline__ uint64_t kmaj_desc(const void* p, int Kt) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  const uint64_t lbo = 128 >> 4, sbo = (uint64_t)(Kt * 16) >> 4;
+  return (uint64_t)((a >> 4) & 0x3FFF) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 accumulator, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool tc_bar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait (0.5 s of the global timer) for the MMAs behind a commit
+__device__ __forceinline__ bool tc_bar_wait(uint64_t* bar, uint32_t parity) {
+  if (tc_bar_test(bar, parity)) return true;
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (tc_bar_test(bar, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 500000000ull) return false;
+  }
+}
+// this warp's 32 tensor-memory lanes, 64 consecutive columns from column c, into v
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t* u = reinterpret_cast<uint32_t*>(v);
+#define QEQ_R8(i) "=r"(u[i]), "=r"(u[i + 1]), "=r"(u[i + 2]), "=r"(u[i + 3]), "=r"(u[i + 4]), "=r"(u[i + 5]), \
+                  "=r"(u[i + 6]), "=r"(u[i + 7])
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, "
+      "%36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, "
+      "%57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : QEQ_R8(0), QEQ_R8(8), QEQ_R8(16), QEQ_R8(24), QEQ_R8(32), QEQ_R8(40), QEQ_R8(48), QEQ_R8(56)
+      : "r"(taddr));
+#undef QEQ_R8
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128) k_mlp_fwd_tc(const float* __restrict__ feat, const int* __restrict__ species,
+                                                    int64_t n, int n_species, const float* __restrict__ params,
+                                                    const float* __restrict__ scale, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // operand tiles on a 1024-byte boundary of the shared window (1024 bytes reserved for it)
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+  MlpTcSmem& M = *reinterpret_cast<MlpTcSmem*>(smem_raw + (((base + 1023u) & ~1023u) - base));
+  const int tid = threadIdx.x, w = tid >> 5;
+  const int64_t a0 = (int64_t)blockIdx.x * TC_TILE, a = a0 + tid;
+  M.sp[tid] = (a < n) ? species[a] : -1;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&M.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) {  // 128 tensor-memory columns: layer 1 in 0-63, layer 2 in 64-127
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&M.tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = M.tmem;
+  const uint32_t lane_base = (uint32_t)(w * 32) << 16;
+  unsigned present = 0;
+  for (int i = 0; i < TC_TILE; ++i)
+    if (M.sp[i] >= 0 && M.sp[i] < n_species) present |= 1u << M.sp[i];
+  const int my_sp = M.sp[tid];
+  float y = 0.f;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int s = 0; s < n_species && ok; ++s) {
+    if (!((present >> s) & 1u)) continue;
+    const float* P = params + (size_t)s * QEQ_MLP_NPARAM;
+    const float* mean = scale + (size_t)s * 2 * NF;
+    const float* inv = mean + NF;
+    // weights in the K-major layout (W[n][k]: neuron n, input k)
+    for (int i = tid; i < NH * NF; i += blockDim.x) {
+      const int nn = i / NF, k = i - nn * NF;
+      M.W1[kmaj_off(nn, k, NF)] = __float2bfloat16(P[P_W1 + i]);
+    }
+    for (int i = tid; i < NH * NH; i += blockDim.x) {
+      const int nn = i / NH, k = i - nn * NH;
+      M.W2[kmaj_off(nn, k, NH)] = __float2bfloat16(P[P_W2 + i]);
+    }
+    for (int i = tid; i < NH; i += blockDim.x) {
+      M.b1[i] = P[P_B1 + i];
+      M.b2[i] = P[P_B2 + i];
+      M.W3[i] = P[P_W3 + i];
+    }
+    if (tid == 0) M.b3 = P[P_B3];
+    // this thread's atom: its scaled features as row tid of X
+    {
+      __align__(16) __nv_bfloat16 xr[NF];
+#pragma unroll
+      for (int k = 0; k < NF; ++k) xr[k] = __float2bfloat16((a < n) ? (feat[a * NF + k] - mean[k]) * inv[k] : 0.f);
+#pragma unroll
+      for (int kg = 0; kg < NF / 8; ++kg)
+        *reinterpret_cast<uint4*>(&M.X[kmaj_off(tid, kg * 8, NF)]) = *reinterpret_cast<const uint4*>(&xr[kg * 8]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, to the tensor cores
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 1: H1 = X W1^T (K = 32: two K = 16 steps of two core matrices)
+    if (tid == 0) {
+#pragma unroll
+      for (int j = 0; j < NF / 16; ++j)
+        tc_mma(tmem, kmaj_desc(&M.X[j * 16 * 8], NF), kmaj_desc(&M.W1[j * 16 * 8], NF), tc_idesc(TC_TILE, NH), j);
+      tc_commit(&M.bar);
+    }
+    ok = __syncthreads_and(tc_bar_wait(&M.bar, phase)) != 0;  // the same verdict on every thread
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float v[NH];
+    tc_ld64(tmem + lane_base, v);
+    {
+      __align__(16) __nv_bfloat16 hr[NH];
+#pragma unroll
+      for (int k = 0; k < NH; ++k) hr[k] = __float2bfloat16(tanhf(v[k] + M.b1[k]));
+#pragma unroll
+      for (int kg = 0; kg < NH / 8; ++kg)
+        *reinterpret_cast<uint4*>(&M.H1[kmaj_off(tid, kg * 8, NH)]) = *reinterpret_cast<const uint4*>(&hr[kg * 8]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 2: H2 = tanh(H1 W2^T + b2) (K = 64: four steps), y = H2 . W3 + b3
+    if (tid == 0 && ok) {
+#pragma unroll
+      for (int j = 0; j < NH / 16; ++j)
+        tc_mma(tmem + NH, kmaj_desc(&M.H1[j * 16 * 8], NH), kmaj_desc(&M.W2[j * 16 * 8], NH), tc_idesc(TC_TILE, NH),
+               j);
+      tc_commit(&M.bar);
+    }
+    ok = __syncthreads_and(ok && tc_bar_wait(&M.bar, phase)) != 0;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_ld64(tmem + lane_base + NH, v);
+    float ys = M.b3;
+#pragma unroll
+    for (int k = 0; k < NH; ++k) ys += tanhf(v[k] + M.b2[k]) * M.W3[k];
+    if (my_sp == s) y = ys;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the staged operands and tensor memory are reused by the next species
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (a < n) out[a] = ok ? y : __int_as_float(0x7fc00000);  // a timed-out MMA wait: NaN (rejected start)
+  __syncthreads();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
 // sum of the per-tile gradient blocks in tile order, then Adam on the FP32 master weights
 __global__ void k_adam(const float* __restrict__ gpart, int ntiles, int nparam, float* __restrict__ params,
                        float* __restrict__ m, float* __restrict__ v, float* __restrict__ grad_out, float lr,
@@ -367,6 +570,7 @@ struct qeq_mlp_s {
 };
 
 static size_t mlp_smem() { return sizeof(MlpSmem); }
+static size_t mlp_tc_smem() { return sizeof(MlpTcSmem) + 1024; }  // + alignment of the operand tiles
 
 extern "C" qeq_status qeq_mlp_create(int32_t n_species, int64_t max_batch, qeq_mlp* out) {
   if (!out || n_species < 1 || n_species > QEQ_MAX_SPECIES || max_batch < 1) return QEQ_ERR_INVALID;
@@ -391,6 +595,7 @@ extern "C" qeq_status qeq_mlp_create(int32_t n_species, int64_t max_batch, qeq_m
   e = e ? e : cudaMemset(m->d_v, 0, np * sizeof(float));
   e = e ? e : cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
   e = e ? e : cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
+  e = e ? e : cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_tc_smem());
   if (e != cudaSuccess) {
     qeq_mlp_destroy(m);
     return e == cudaErrorMemoryAllocation ? QEQ_ERR_OOM : QEQ_ERR_CUDA;
@@ -464,9 +669,9 @@ extern "C" qeq_status qeq_mlp_forward(qeq_mlp m, const float* d_feat, const int3
   if (!m || !d_feat || !d_species || !d_out || n < 0) return QEQ_ERR_INVALID;
   if (n == 0) return QEQ_OK;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  int ntiles = (int)((n + TILE - 1) / TILE);
-  k_mlp<false><<<ntiles, 128, mlp_smem(), s>>>(d_feat, d_species, n, m->n_species, m->d_params, m->d_scale,
-                                                nullptr, 0.f, d_out, nullptr, nullptr);
+  int ntiles = (int)((n + TC_TILE - 1) / TC_TILE);
+  k_mlp_fwd_tc<<<ntiles, 128, mlp_tc_smem(), s>>>(d_feat, d_species, n, m->n_species, m->d_params, m->d_scale,
+                                                  d_out);
   if (cudaGetLastError() != cudaSuccess) return QEQ_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? QEQ_OK : QEQ_ERR_CUDA;
 }
@@ -540,9 +745,9 @@ cudaError_t launch_mlp_warm_start(qeq_plan_s* P, double* d_q_sorted) {
   count_launch(P, 3);
   k_features<true><<<nb, 256, 0, s>>>(P->d_st, P->d_key, P->d_bin_start, P->d_base, P->d_spec, P->d_posc32, P->d_chi,
                                        P->d_J, P->d_perm, P->n_atoms, P->d_feat);
-  int ntiles = (int)((P->n_atoms + TILE - 1) / TILE);
-  k_mlp<false><<<ntiles, 128, mlp_smem(), s>>>(P->d_feat, P->d_spec, P->n_atoms, m->n_species, m->d_params,
-                                                m->d_scale, nullptr, 0.f, P->d_pred, nullptr, nullptr);
+  int ntiles = (int)((P->n_atoms + TC_TILE - 1) / TC_TILE);
+  k_mlp_fwd_tc<<<ntiles, 128, mlp_tc_smem(), s>>>(P->d_feat, P->d_spec, P->n_atoms, m->n_species, m->d_params,
+                                                  m->d_scale, P->d_pred);
   k_pred_to_q<<<(int)((P->n_atoms + 255) / 256), 256, 0, s>>>(P->d_pred, P->n_atoms, d_q_sorted);
   return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
-"""GPU warm start: descriptors, BF16 tensor-core network and its training against the CPU oracle,
-and what the trained network gains over the cold start."""
+"""GPU warm start: descriptors, BF16 tensor-core network (inference on tcgen05, training on
+mma.sync) and its training against the CPU oracle, and what the trained network gains over the
+cold start."""
 import numpy as np
 import pytest
 
@@ -94,6 +95,46 @@ def test_forward_and_gradient_match_oracle():
     exp, _, _ = M.adam_step(before, g.astype(np.float64), 0 * before, 0 * before, 1, 1e-3)
     assert np.abs(after - exp).max() < 1e-6
     mlp.close()
+
+
+@pytest.mark.parametrize("n,S", [(300, 2), (128, 1), (1000, 4), (5, 3)])
+def test_tensor_core_forward_matches_bf16_emulation(n, S):
+    """The inference network on tcgen05 (BF16 operands in shared memory, FP32 accumulators in
+    tensor memory) against the same arithmetic emulated on the CPU: BF16 weights, scaled
+    inputs and first-layer activations, everything else FP64.  Only accumulation order and the
+    rare BF16 rounding of an activation that sits on a rounding boundary differ, so 99 % of the
+    atoms agree to 1e-4 of the output scale and all to 5e-3.  Tiles of 128 atoms: ragged tails,
+    a single full tile, a tile with every species, and fewer atoms than a warp."""
+    import torch
+    from paper_2607_17978_b300 import build, qeq
+    build.build()
+    rng = np.random.default_rng(100 + n + S)
+    feat = rng.normal(size=(n, M.NF)) * 2 + 1
+    feat[:, 27:] = 0
+    sp = rng.integers(0, S, n)
+    params, scale = _random_net(S, 7 + S, feat, sp)
+    p32 = params.astype(np.float32)
+    s32 = scale.astype(np.float32)
+    mlp = qeq.Mlp(S, max_batch=max(n, 128))
+    mlp.set_params(p32, s32)
+    dev = torch.device("cuda")
+    y = mlp.forward(torch.tensor(feat, dtype=torch.float32, device=dev),
+                    torch.tensor(sp, dtype=torch.int32, device=dev)).cpu().numpy().astype(np.float64)
+    mlp.close()
+    ref = np.zeros(n)
+    for s in range(S):
+        idx = np.nonzero(sp == s)[0]
+        if len(idx) == 0:
+            continue
+        W1, b1, W2, b2, W3, b3 = M.unpack(p32[s].astype(np.float64))
+        X = M.bf16_round((feat[idx].astype(np.float32) - s32[s, 0]) * s32[s, 1]).astype(np.float64)
+        h1 = M.bf16_round(np.tanh(X @ M.bf16_round(W1).T + b1))
+        h2 = np.tanh(h1 @ M.bf16_round(W2).T + b2)
+        ref[idx] = h2 @ W3 + b3
+    err = np.abs(y - ref) / max(np.abs(ref).max(), 1e-3)
+    assert np.all(np.isfinite(y))
+    assert np.quantile(err, 0.99) < 1e-4, np.quantile(err, 0.99)
+    assert err.max() < 5e-3, err.max()
 
 
 def test_warm_start_gain_and_fallback():
