@@ -367,10 +367,10 @@ qeq_status qeq_dense_query(qeq_dense dense, int32_t s, double* h_omega, int32_t*
  *   [12..23] the same weighted by chi_j
  *   [24..26] chi_i, J_i, sigma_i ; [27..31] zero
  * Network per species: 32 -> 64 -> 64 -> 1, tanh, tanh, linear, evaluated on
- * BF16 tensor cores with FP32 accumulation (inference: tcgen05 MMAs with the
- * accumulators in tensor memory; training: warp-level MMAs); inputs scaled per
- * species as (G - mean) * inv_range (SI "Feature Scaling"), the scaled inputs
- * and the first layer's activations rounded to BF16 as MMA operands.
+ * BF16 tensor cores (tcgen05 MMAs) with FP32 accumulation in tensor memory,
+ * forward and, in training, backward; inputs scaled per species as
+ * (G - mean) * inv_range (SI "Feature Scaling"), the scaled inputs, activations
+ * and output-side derivatives rounded to BF16 as MMA operands.
  * Parameter block of one species (float32, QEQ_MLP_NPARAM entries):
  *   W1[64][32], b1[64], W2[64][64], b2[64], W3[64], b3, then padding.
  * Scaling block of one species: mean[32], inv_range[32].

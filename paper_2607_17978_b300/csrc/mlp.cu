@@ -1,8 +1,7 @@
 // Learned warm start for the QEq solve: radial descriptors and a small per-species
-// network that predicts starting charges; inference on the tcgen05 tensor cores
-// (BF16 operands, FP32 accumulators in tensor memory), training forward and
-// backward on warp-level BF16 MMAs (mma.sync m16n8k16, FP32 accumulate) and Adam
-// on FP32 master weights.
+// network that predicts starting charges; inference and the training step's forward
+// and backward products on the tcgen05 tensor cores (BF16 operands in shared memory,
+// FP32 accumulators in tensor memory), Adam on FP32 master weights.
 //
 // Descriptors (Sec. 2.2 eq. g2 radial functions with the cosine cutoff of SI
 // "Cutoff Functions"; element-embracing prefactor of SI "Element-Embracing
@@ -29,42 +28,9 @@ namespace {
 
 constexpr int NF = QEQ_MLP_NFEAT;  // 32
 constexpr int NH = QEQ_MLP_NHIDDEN;  // 64
-constexpr int TILE = 64;           // atoms per CTA
 constexpr int P_W1 = 0, P_B1 = P_W1 + NH * NF, P_W2 = P_B1 + NH, P_B2 = P_W2 + NH * NH, P_W3 = P_B2 + NH,
               P_B3 = P_W3 + NH;
 static_assert(P_B3 + 1 <= QEQ_MLP_NPARAM, "parameter block");
-
-__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
-  __nv_bfloat162 v;
-  v.x = *p0;
-  v.y = *p1;
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// c (16x8 FP32 accumulator fragment) += A (16 x K) * B (K x 8), BF16 operands in
-// shared memory with A(m, k) = A[m*sam + k*sak] and B(k, n) = B[k*sbk + n*sbn].
-// Fragment layout of mma.m16n8k16 (row.col): lane = 4*g + t;
-//   A regs: (g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..)
-//   B regs: (2t..2t+1, g), (2t+8..2t+9, g)
-//   C regs: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)
-__device__ __forceinline__ void mma_16x8(float* c, const __nv_bfloat16* A, int sam, int sak, const __nv_bfloat16* B,
-                                         int sbk, int sbn, int K) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const int ka = k0 + 2 * t;
-    uint32_t a0 = pack2(A + g * sam + ka * sak, A + g * sam + (ka + 1) * sak);
-    uint32_t a1 = pack2(A + (g + 8) * sam + ka * sak, A + (g + 8) * sam + (ka + 1) * sak);
-    uint32_t a2 = pack2(A + g * sam + (ka + 8) * sak, A + g * sam + (ka + 9) * sak);
-    uint32_t a3 = pack2(A + (g + 8) * sam + (ka + 8) * sak, A + (g + 8) * sam + (ka + 9) * sak);
-    uint32_t b0 = pack2(B + ka * sbk + g * sbn, B + (ka + 1) * sbk + g * sbn);
-    uint32_t b1 = pack2(B + (ka + 8) * sbk + g * sbn, B + (ka + 9) * sbk + g * sbn);
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-  }
-}
 
 // ---------------------------------------------------------------- descriptors
 // One warp per atom: the lanes take the candidate neighbours of the walk, each
@@ -123,200 +89,6 @@ __global__ void __launch_bounds__(256) k_features(const StructDev* __restrict__ 
   if (lane == 25) v = (float)Js[a];
   if (lane == 26) v = (float)S.sigma_s[spec[a]];
   if (lane < NF) f[lane] = v;
-}
-
-// ---------------------------------------------------------------- network
-// One CTA = 4 warps = 64 atoms (16 per warp).  For every species present in the
-// tile the species' weights are staged in shared memory and the tile is run
-// through that network; atoms of other species are masked.  TRAIN adds the
-// backward pass and writes the tile's gradient to its own partial block.
-struct MlpSmem {
-  __nv_bfloat16 W1[NH * NF];
-  __nv_bfloat16 W2[NH * NH];
-  float b1[NH], b2[NH], W3[NH], b3;
-  __nv_bfloat16 X[TILE * NF];
-  __nv_bfloat16 H1[TILE * NH];
-  __nv_bfloat16 H2[TILE * NH];
-  __nv_bfloat16 D2[TILE * NH];   // dL/dz2
-  __nv_bfloat16 D1[TILE * NH];   // dL/dz1
-  float y[TILE];
-  float dy[TILE];
-  int sp[TILE];
-};
-
-template <bool TRAIN>
-__global__ void __launch_bounds__(128) k_mlp(const float* __restrict__ feat, const int* __restrict__ species, int64_t n,
-                                             int n_species, const float* __restrict__ params,
-                                             const float* __restrict__ scale, const float* __restrict__ target,
-                                             float inv_batch, float* __restrict__ out, float* __restrict__ gpart,
-                                             float* __restrict__ lpart) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MlpSmem& M = *reinterpret_cast<MlpSmem*>(smem_raw);
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int64_t a0 = (int64_t)blockIdx.x * TILE;
-  for (int i = tid; i < TILE; i += blockDim.x) {
-    int64_t a = a0 + i;
-    M.sp[i] = (a < n) ? species[a] : -1;
-    M.y[i] = 0.f;
-  }
-  __syncthreads();
-  unsigned present = 0;
-  for (int i = 0; i < TILE; ++i)
-    if (M.sp[i] >= 0 && M.sp[i] < n_species) present |= 1u << M.sp[i];
-  float loss = 0.f;
-  float* gp = TRAIN ? gpart + (size_t)blockIdx.x * n_species * QEQ_MLP_NPARAM : nullptr;
-  if (TRAIN)
-    for (int i = tid; i < n_species * QEQ_MLP_NPARAM; i += blockDim.x) gp[i] = 0.f;
-  for (int s = 0; s < n_species; ++s) {
-    if (!((present >> s) & 1u)) continue;
-    const float* P = params + (size_t)s * QEQ_MLP_NPARAM;
-    const float* mean = scale + (size_t)s * 2 * NF;
-    const float* inv = mean + NF;
-    __syncthreads();
-    for (int i = tid; i < NH * NF; i += blockDim.x) M.W1[i] = __float2bfloat16(P[P_W1 + i]);
-    for (int i = tid; i < NH * NH; i += blockDim.x) M.W2[i] = __float2bfloat16(P[P_W2 + i]);
-    for (int i = tid; i < NH; i += blockDim.x) {
-      M.b1[i] = P[P_B1 + i];
-      M.b2[i] = P[P_B2 + i];
-      M.W3[i] = P[P_W3 + i];
-    }
-    if (tid == 0) M.b3 = P[P_B3];
-    for (int i = tid; i < TILE * NF; i += blockDim.x) {
-      int r = i / NF, k = i - r * NF;
-      int64_t a = a0 + r;
-      float v = (a < n) ? (feat[a * NF + k] - mean[k]) * inv[k] : 0.f;
-      M.X[i] = __float2bfloat16(v);
-    }
-    __syncthreads();
-    const int r0 = w * 16;  // this warp's rows
-    // layer 1: H1 = tanh(X W1^T + b1)
-    for (int nt = 0; nt < NH / 8; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_16x8(c, M.X + r0 * NF, NF, 1, M.W1 + nt * 8 * NF, 1, NF, NF);
-      int col = nt * 8 + 2 * t;
-      M.H1[(r0 + g) * NH + col] = __float2bfloat16(tanhf(c[0] + M.b1[col]));
-      M.H1[(r0 + g) * NH + col + 1] = __float2bfloat16(tanhf(c[1] + M.b1[col + 1]));
-      M.H1[(r0 + g + 8) * NH + col] = __float2bfloat16(tanhf(c[2] + M.b1[col]));
-      M.H1[(r0 + g + 8) * NH + col + 1] = __float2bfloat16(tanhf(c[3] + M.b1[col + 1]));
-    }
-    __syncwarp();
-    // layer 2: H2 = tanh(H1 W2^T + b2); output y = H2 . W3 + b3
-    float yg = 0.f, yg8 = 0.f;
-    for (int nt = 0; nt < NH / 8; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_16x8(c, M.H1 + r0 * NH, NH, 1, M.W2 + nt * 8 * NH, 1, NH, NH);
-      int col = nt * 8 + 2 * t;
-      float h00 = tanhf(c[0] + M.b2[col]), h01 = tanhf(c[1] + M.b2[col + 1]);
-      float h10 = tanhf(c[2] + M.b2[col]), h11 = tanhf(c[3] + M.b2[col + 1]);
-      M.H2[(r0 + g) * NH + col] = __float2bfloat16(h00);
-      M.H2[(r0 + g) * NH + col + 1] = __float2bfloat16(h01);
-      M.H2[(r0 + g + 8) * NH + col] = __float2bfloat16(h10);
-      M.H2[(r0 + g + 8) * NH + col + 1] = __float2bfloat16(h11);
-      yg += h00 * M.W3[col] + h01 * M.W3[col + 1];
-      yg8 += h10 * M.W3[col] + h11 * M.W3[col + 1];
-    }
-    yg += __shfl_xor_sync(0xffffffffu, yg, 1);
-    yg += __shfl_xor_sync(0xffffffffu, yg, 2);
-    yg8 += __shfl_xor_sync(0xffffffffu, yg8, 1);
-    yg8 += __shfl_xor_sync(0xffffffffu, yg8, 2);
-    if (t == 0) {
-      if (M.sp[r0 + g] == s) M.y[r0 + g] = yg + M.b3;
-      if (M.sp[r0 + g + 8] == s) M.y[r0 + g + 8] = yg8 + M.b3;
-    }
-    if (!TRAIN) continue;
-    __syncthreads();
-    // ---------------- backward (MSE 1/2 mean): dy = (y - target) / batch for atoms of species s
-    for (int i = tid; i < TILE; i += blockDim.x) {
-      int64_t a = a0 + i;
-      float d = 0.f;
-      if (a < n && M.sp[i] == s) {
-        float e = M.y[i] - target[a];
-        d = e * inv_batch;
-        loss += 0.5f * e * e * inv_batch;
-      }
-      M.dy[i] = d;
-    }
-    __syncthreads();
-    // dz2 = dy W3 (1 - h2^2);  grads of W3, b3
-    for (int i = tid; i < TILE * NH; i += blockDim.x) {
-      int r = i / NH, f = i - r * NH;
-      float h = __bfloat162float(M.H2[i]);
-      M.D2[i] = __float2bfloat16(M.dy[r] * M.W3[f] * (1.f - h * h));
-    }
-    for (int f = tid; f < NH; f += blockDim.x) {
-      float acc = 0.f;
-      for (int r = 0; r < TILE; ++r) acc += M.dy[r] * __bfloat162float(M.H2[r * NH + f]);
-      gp[s * QEQ_MLP_NPARAM + P_W3 + f] += acc;
-    }
-    if (tid == 0) {
-      float acc = 0.f;
-      for (int r = 0; r < TILE; ++r) acc += M.dy[r];
-      gp[s * QEQ_MLP_NPARAM + P_B3] += acc;
-    }
-    __syncthreads();
-    // dL/dW2 (64 x 64) = D2^T H1 over the tile's 64 atoms: 32 output fragments, 8 per warp
-    for (int q = w; q < (NH / 16) * (NH / 8); q += 4) {
-      int mt = q / (NH / 8), nt = q - mt * (NH / 8);
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      // A(m = out feature, k = atom) = D2[atom][out], B(k = atom, n = in feature) = H1[atom][in]
-      mma_16x8(c, M.D2 + mt * 16, 1, NH, M.H1 + nt * 8, NH, 1, TILE);
-      int row = mt * 16 + g, col = nt * 8 + 2 * t;
-      float* G2 = gp + s * QEQ_MLP_NPARAM + P_W2;
-      G2[row * NH + col] += c[0];
-      G2[row * NH + col + 1] += c[1];
-      G2[(row + 8) * NH + col] += c[2];
-      G2[(row + 8) * NH + col + 1] += c[3];
-    }
-    for (int f = tid; f < NH; f += blockDim.x) {
-      float acc = 0.f;
-      for (int r = 0; r < TILE; ++r) acc += __bfloat162float(M.D2[r * NH + f]);
-      gp[s * QEQ_MLP_NPARAM + P_B2 + f] += acc;
-    }
-    // dz1 = (D2 W2) (1 - h1^2), per warp rows
-    for (int nt = 0; nt < NH / 8; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      // A(m = atom, k = out feature) = D2, B(k = out feature, n = in feature) = W2[out][in]
-      mma_16x8(c, M.D2 + r0 * NH, NH, 1, M.W2 + nt * 8, NH, 1, NH);
-      int col = nt * 8 + 2 * t;
-      float h00 = __bfloat162float(M.H1[(r0 + g) * NH + col]), h01 = __bfloat162float(M.H1[(r0 + g) * NH + col + 1]);
-      float h10 = __bfloat162float(M.H1[(r0 + g + 8) * NH + col]),
-            h11 = __bfloat162float(M.H1[(r0 + g + 8) * NH + col + 1]);
-      M.D1[(r0 + g) * NH + col] = __float2bfloat16(c[0] * (1.f - h00 * h00));
-      M.D1[(r0 + g) * NH + col + 1] = __float2bfloat16(c[1] * (1.f - h01 * h01));
-      M.D1[(r0 + g + 8) * NH + col] = __float2bfloat16(c[2] * (1.f - h10 * h10));
-      M.D1[(r0 + g + 8) * NH + col + 1] = __float2bfloat16(c[3] * (1.f - h11 * h11));
-    }
-    __syncthreads();
-    // dL/dW1 (64 x 32) = D1^T X over the tile: 16 output fragments, 4 per warp
-    for (int q = w; q < (NH / 16) * (NF / 8); q += 4) {
-      int mt = q / (NF / 8), nt = q - mt * (NF / 8);
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_16x8(c, M.D1 + mt * 16, 1, NH, M.X + nt * 8, NF, 1, TILE);
-      int row = mt * 16 + g, col = nt * 8 + 2 * t;
-      float* G1 = gp + s * QEQ_MLP_NPARAM + P_W1;
-      G1[row * NF + col] += c[0];
-      G1[row * NF + col + 1] += c[1];
-      G1[(row + 8) * NF + col] += c[2];
-      G1[(row + 8) * NF + col + 1] += c[3];
-    }
-    for (int f = tid; f < NH; f += blockDim.x) {
-      float acc = 0.f;
-      for (int r = 0; r < TILE; ++r) acc += __bfloat162float(M.D1[r * NH + f]);
-      gp[s * QEQ_MLP_NPARAM + P_B1 + f] += acc;
-    }
-  }
-  __syncthreads();
-  if (out)
-    for (int i = tid; i < TILE; i += blockDim.x)
-      if (a0 + i < n) out[a0 + i] = M.y[i];
-  if (TRAIN) {
-    // deterministic per-tile loss: warp sums, then thread 0 in warp order
-    __shared__ float wl[4];
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-    if (lane == 0) wl[w] = loss;
-    __syncthreads();
-    if (tid == 0) lpart[blockIdx.x] = wl[0] + wl[1] + wl[2] + wl[3];
-  }
 }
 
 // ---------------------------------------------------------------- network forward on tcgen05
@@ -520,6 +292,247 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_tc(const float* __restrict__ fe
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
+// this warp's 32 tensor-memory lanes, 32 consecutive columns from column c, into v
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t* u = reinterpret_cast<uint32_t*>(v);
+#define QEQ_R8(i) "=r"(u[i]), "=r"(u[i + 1]), "=r"(u[i + 2]), "=r"(u[i + 3]), "=r"(u[i + 4]), "=r"(u[i + 5]), \
+                  "=r"(u[i + 6]), "=r"(u[i + 7])
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : QEQ_R8(0), QEQ_R8(8), QEQ_R8(16), QEQ_R8(24)
+      : "r"(taddr));
+#undef QEQ_R8
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- network training step on tcgen05
+// One CTA = 4 warps = 128 atoms, the loss 1/(2n) sum (y - t)^2 and its gradient for every
+// species present in the tile, written to the tile's own partial block.  All five products
+// run on the tensor cores with both operands K-major (the transposed operands are written
+// transposed into shared memory): forward H1 = X W1^T, H2 = H1 W2^T (M = atoms); backward
+// dW2 = D2^T H1 and dW1 = D1^T X (M = output neurons padded to 128 with zero rows, K =
+// atoms), dZ1 = D2 W2 (M = atoms).  Tensor memory: columns 0-63 layer 1 (later dW1),
+// 64-127 layer 2, 128-191 dW2, 192-255 dZ1.  Bias and output-layer gradients are column
+// sums over the tile's atoms in a fixed order.
+struct MlpTrainSmem {
+  alignas(128) __nv_bfloat16 X[TC_TILE * NF];    // [atom][k]        A of layer 1
+  alignas(128) __nv_bfloat16 XT[NF * TC_TILE];   // [k][atom]        B of dW1
+  alignas(128) __nv_bfloat16 H1[TC_TILE * NH];   // [atom][f]        A of layer 2
+  alignas(128) __nv_bfloat16 H1T[NH * TC_TILE];  // [f][atom]        B of dW2
+  alignas(128) __nv_bfloat16 D2[TC_TILE * NH];   // [atom][f]        A of dZ1
+  alignas(128) __nv_bfloat16 DT[128 * TC_TILE];  // [f][atom], rows >= NH zero: A of dW2, then of dW1
+  alignas(128) __nv_bfloat16 W1[NH * NF];        // [n][k]           B of layer 1
+  alignas(128) __nv_bfloat16 W2[NH * NH];        // [n][k]           B of layer 2
+  alignas(128) __nv_bfloat16 W2T[NH * NH];       // [k][n]           B of dZ1
+  float red[TC_TILE][NH + 1];                    // per-atom values of column sums
+  float dyv[TC_TILE];
+  float b1[NH], b2[NH], W3[NH], b3;
+  int sp[TC_TILE];
+  float lw[4];
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(128) k_mlp_train_tc(const float* __restrict__ feat,
+                                                      const int* __restrict__ species, int64_t n, int n_species,
+                                                      const float* __restrict__ params,
+                                                      const float* __restrict__ scale,
+                                                      const float* __restrict__ target, float inv_batch,
+                                                      float* __restrict__ gpart, float* __restrict__ lpart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+  MlpTrainSmem& M = *reinterpret_cast<MlpTrainSmem*>(smem_raw + (((base + 1023u) & ~1023u) - base));
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int64_t a0 = (int64_t)blockIdx.x * TC_TILE, a = a0 + tid;
+  M.sp[tid] = (a < n) ? species[a] : -1;
+  for (int i = tid; i < (128 - NH) * TC_TILE; i += blockDim.x) M.DT[NH * TC_TILE + i] = __float2bfloat16(0.f);
+  float* gp = gpart + (size_t)blockIdx.x * n_species * QEQ_MLP_NPARAM;
+  for (int i = tid; i < n_species * QEQ_MLP_NPARAM; i += blockDim.x) gp[i] = 0.f;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&M.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&M.tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = M.tmem, lane_base = (uint32_t)(w * 32) << 16;
+  unsigned present = 0;
+  for (int i = 0; i < TC_TILE; ++i)
+    if (M.sp[i] >= 0 && M.sp[i] < n_species) present |= 1u << M.sp[i];
+  const int my_sp = M.sp[tid];
+  float loss = 0.f;
+  uint32_t phase = 0;
+  bool ok = true;
+  // all threads: operands written by threads -> tensor cores; tcgen05 ops ordered by the barrier
+  auto sync_operands = [&]() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+  auto wait_mma = [&]() {  // the commit issued by thread 0 (CTA-uniform verdict)
+    ok = __syncthreads_and(ok && tc_bar_wait(&M.bar, phase)) != 0;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+  for (int s = 0; s < n_species && ok; ++s) {
+    if (!((present >> s) & 1u)) continue;
+    const float* P = params + (size_t)s * QEQ_MLP_NPARAM;
+    float* G = gp + (size_t)s * QEQ_MLP_NPARAM;
+    const float* mean = scale + (size_t)s * 2 * NF;
+    const float* inv = mean + NF;
+    for (int i = tid; i < NH * NF; i += blockDim.x) {
+      const int nn = i / NF, k = i - nn * NF;
+      M.W1[kmaj_off(nn, k, NF)] = __float2bfloat16(P[P_W1 + i]);
+    }
+    for (int i = tid; i < NH * NH; i += blockDim.x) {
+      const int nn = i / NH, k = i - nn * NH;
+      const __nv_bfloat16 v = __float2bfloat16(P[P_W2 + i]);
+      M.W2[kmaj_off(nn, k, NH)] = v;
+      M.W2T[kmaj_off(k, nn, NH)] = v;
+    }
+    for (int i = tid; i < NH; i += blockDim.x) {
+      M.b1[i] = P[P_B1 + i];
+      M.b2[i] = P[P_B2 + i];
+      M.W3[i] = P[P_W3 + i];
+    }
+    if (tid == 0) M.b3 = P[P_B3];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const __nv_bfloat16 v = __float2bfloat16((a < n) ? (feat[a * NF + k] - mean[k]) * inv[k] : 0.f);
+      M.X[kmaj_off(tid, k, NF)] = v;
+      M.XT[kmaj_off(k, tid, TC_TILE)] = v;
+    }
+    sync_operands();
+    if (tid == 0) {
+#pragma unroll
+      for (int j = 0; j < NF / 16; ++j)
+        tc_mma(tmem, kmaj_desc(&M.X[j * 128], NF), kmaj_desc(&M.W1[j * 128], NF), tc_idesc(TC_TILE, NH), j);
+      tc_commit(&M.bar);
+    }
+    wait_mma();
+    float v[NH];
+    tc_ld64(tmem + lane_base, v);
+#pragma unroll
+    for (int f = 0; f < NH; ++f) {
+      const __nv_bfloat16 h = __float2bfloat16(tanhf(v[f] + M.b1[f]));
+      M.H1[kmaj_off(tid, f, NH)] = h;
+      M.H1T[kmaj_off(f, tid, TC_TILE)] = h;
+    }
+    sync_operands();
+    if (tid == 0 && ok) {
+#pragma unroll
+      for (int j = 0; j < NH / 16; ++j)
+        tc_mma(tmem + 64, kmaj_desc(&M.H1[j * 128], NH), kmaj_desc(&M.W2[j * 128], NH), tc_idesc(TC_TILE, NH), j);
+      tc_commit(&M.bar);
+    }
+    wait_mma();
+    tc_ld64(tmem + lane_base + 64, v);
+    float y = M.b3;
+#pragma unroll
+    for (int f = 0; f < NH; ++f) {
+      v[f] = tanhf(v[f] + M.b2[f]);  // h2
+      y += v[f] * M.W3[f];
+    }
+    float dy = 0.f;
+    if (a < n && my_sp == s) {
+      const float e = y - target[a];
+      dy = e * inv_batch;
+      loss += 0.5f * e * e * inv_batch;
+    }
+    M.dyv[tid] = dy;
+    // dZ2 = dy W3 (1 - h2^2): rows of D2, columns of DT; dy h2 for dW3
+#pragma unroll
+    for (int f = 0; f < NH; ++f) {
+      M.red[tid][f] = dy * v[f];
+      const __nv_bfloat16 d = __float2bfloat16(dy * M.W3[f] * (1.f - v[f] * v[f]));
+      M.D2[kmaj_off(tid, f, NH)] = d;
+      M.DT[kmaj_off(f, tid, TC_TILE)] = d;
+    }
+    sync_operands();
+    if (tid == 0 && ok) {
+      // dW2 (rows 0-63 of a 128-row product) and dZ1 = D2 W2, one commit
+#pragma unroll
+      for (int j = 0; j < TC_TILE / 16; ++j)
+        tc_mma(tmem + 128, kmaj_desc(&M.DT[j * 128], TC_TILE), kmaj_desc(&M.H1T[j * 128], TC_TILE),
+               tc_idesc(128, NH), j);
+#pragma unroll
+      for (int j = 0; j < NH / 16; ++j)
+        tc_mma(tmem + 192, kmaj_desc(&M.D2[j * 128], NH), kmaj_desc(&M.W2T[j * 128], NH), tc_idesc(TC_TILE, NH), j);
+      tc_commit(&M.bar);
+    }
+    if (tid < NH) {  // dW3, fixed order over the tile's atoms
+      float acc = 0.f;
+      for (int r = 0; r < TC_TILE; ++r) acc += M.red[r][tid];
+      G[P_W3 + tid] = acc;
+    } else if (tid == NH) {
+      float acc = 0.f;
+      for (int r = 0; r < TC_TILE; ++r) acc += M.dyv[r];
+      G[P_B3] = acc;
+    }
+    __syncthreads();  // red is rewritten below
+#pragma unroll
+    for (int f = 0; f < NH; ++f) M.red[tid][f] = __bfloat162float(M.D2[kmaj_off(tid, f, NH)]);
+    __syncthreads();
+    if (tid < NH) {  // db2
+      float acc = 0.f;
+      for (int r = 0; r < TC_TILE; ++r) acc += M.red[r][tid];
+      G[P_B2 + tid] = acc;
+    }
+    wait_mma();
+    // dZ1 (1 - h1^2) -> D1, transposed into DT (dW2 has been read by the MMA)
+    tc_ld64(tmem + lane_base + 192, v);
+    __syncthreads();  // db2 has read red
+#pragma unroll
+    for (int f = 0; f < NH; ++f) {
+      const float h = __bfloat162float(M.H1[kmaj_off(tid, f, NH)]);
+      const __nv_bfloat16 d = __float2bfloat16(v[f] * (1.f - h * h));
+      M.DT[kmaj_off(f, tid, TC_TILE)] = d;
+      M.red[tid][f] = __bfloat162float(d);
+    }
+    if (w < 2) {  // dW2: rows 0-63 live in the lanes of warps 0 and 1
+      tc_ld64(tmem + lane_base + 128, v);
+#pragma unroll
+      for (int f = 0; f < NH; ++f) G[P_W2 + tid * NH + f] = v[f];
+    }
+    sync_operands();
+    if (tid == 0 && ok) {
+#pragma unroll
+      for (int j = 0; j < TC_TILE / 16; ++j)
+        tc_mma(tmem, kmaj_desc(&M.DT[j * 128], TC_TILE), kmaj_desc(&M.XT[j * 128], TC_TILE), tc_idesc(128, NF), j);
+      tc_commit(&M.bar);
+    }
+    if (tid < NH) {  // db1
+      float acc = 0.f;
+      for (int r = 0; r < TC_TILE; ++r) acc += M.red[r][tid];
+      G[P_B1 + tid] = acc;
+    }
+    wait_mma();
+    if (w < 2) {
+      float u[NF];
+      tc_ld32(tmem + lane_base, u);
+#pragma unroll
+      for (int k = 0; k < NF; ++k) G[P_W1 + tid * NF + k] = u[k];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // operands, red and tensor memory are reused by the next species
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // deterministic per-tile loss: warp sums, then the warps in order
+  for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+  if (lane == 0) M.lw[w] = loss;
+  __syncthreads();
+  if (tid == 0) lpart[blockIdx.x] = ok ? (M.lw[0] + M.lw[1] + M.lw[2] + M.lw[3]) : __int_as_float(0x7fc00000);
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
 // sum of the per-tile gradient blocks in tile order, then Adam on the FP32 master weights
 __global__ void k_adam(const float* __restrict__ gpart, int ntiles, int nparam, float* __restrict__ params,
                        float* __restrict__ m, float* __restrict__ v, float* __restrict__ grad_out, float lr,
@@ -569,8 +582,8 @@ struct qeq_mlp_s {
   std::string err;
 };
 
-static size_t mlp_smem() { return sizeof(MlpSmem); }
 static size_t mlp_tc_smem() { return sizeof(MlpTcSmem) + 1024; }  // + alignment of the operand tiles
+static size_t mlp_train_smem() { return sizeof(MlpTrainSmem) + 1024; }
 
 extern "C" qeq_status qeq_mlp_create(int32_t n_species, int64_t max_batch, qeq_mlp* out) {
   if (!out || n_species < 1 || n_species > QEQ_MAX_SPECIES || max_batch < 1) return QEQ_ERR_INVALID;
@@ -580,7 +593,7 @@ extern "C" qeq_status qeq_mlp_create(int32_t n_species, int64_t max_batch, qeq_m
   m->max_batch = max_batch;
   cudaGetDevice(&m->device);
   size_t np = (size_t)n_species * QEQ_MLP_NPARAM;
-  int64_t ntiles = (max_batch + TILE - 1) / TILE;
+  int64_t ntiles = (max_batch + TC_TILE - 1) / TC_TILE;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMalloc(&m->d_params, np * sizeof(float));
   e = e ? e : cudaMalloc(&m->d_scale, (size_t)n_species * 2 * NF * sizeof(float));
@@ -593,9 +606,9 @@ extern "C" qeq_status qeq_mlp_create(int32_t n_species, int64_t max_batch, qeq_m
   e = e ? e : cudaMemset(m->d_params, 0, np * sizeof(float));
   e = e ? e : cudaMemset(m->d_m, 0, np * sizeof(float));
   e = e ? e : cudaMemset(m->d_v, 0, np * sizeof(float));
-  e = e ? e : cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
-  e = e ? e : cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
   e = e ? e : cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_tc_smem());
+  e = e ? e : cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)mlp_train_smem());
   if (e != cudaSuccess) {
     qeq_mlp_destroy(m);
     return e == cudaErrorMemoryAllocation ? QEQ_ERR_OOM : QEQ_ERR_CUDA;
@@ -682,10 +695,10 @@ extern "C" qeq_status qeq_mlp_train_step(qeq_mlp m, const float* d_feat, const i
   if (!m || !d_feat || !d_species || !d_target || n < 1) return QEQ_ERR_INVALID;
   if (n > m->max_batch) return QEQ_ERR_CAPACITY;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  int ntiles = (int)((n + TILE - 1) / TILE);
+  int ntiles = (int)((n + TC_TILE - 1) / TC_TILE);
   int np = m->n_species * QEQ_MLP_NPARAM;
-  k_mlp<true><<<ntiles, 128, mlp_smem(), s>>>(d_feat, d_species, n, m->n_species, m->d_params, m->d_scale, d_target,
-                                               1.0f / (float)n, nullptr, m->d_gpart, m->d_lpart);
+  k_mlp_train_tc<<<ntiles, 128, mlp_train_smem(), s>>>(d_feat, d_species, n, m->n_species, m->d_params, m->d_scale,
+                                                       d_target, 1.0f / (float)n, m->d_gpart, m->d_lpart);
   if (apply_update) m->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   float bc1 = 1.f - powf(b1, (float)std::max<int64_t>(m->step, 1));

@@ -1,6 +1,6 @@
-"""GPU warm start: descriptors, BF16 tensor-core network (inference on tcgen05, training on
-mma.sync) and its training against the CPU oracle, and what the trained network gains over the
-cold start."""
+"""GPU warm start: descriptors, the BF16 tensor-core network (tcgen05, inference and training)
+and its training against the CPU oracle, and what the trained network gains over the cold
+start."""
 import numpy as np
 import pytest
 
@@ -95,6 +95,51 @@ def test_forward_and_gradient_match_oracle():
     exp, _, _ = M.adam_step(before, g.astype(np.float64), 0 * before, 0 * before, 1, 1e-3)
     assert np.abs(after - exp).max() < 1e-6
     mlp.close()
+
+
+def test_adam_over_several_steps_matches_oracle():
+    """Four Adam steps (bias corrections 1 - beta^t for t = 1..4, moments carried between steps)
+    equal the oracle's updates applied to the gradients the GPU reports for each step; a fifth
+    step from a restored state (set_adam_state) continues the same sequence."""
+    import torch
+    from paper_2607_17978_b300 import qeq
+    rng = np.random.default_rng(11)
+    n, S = 400, 2
+    feat = rng.normal(size=(n, M.NF)) * 2 + 1
+    feat[:, 27:] = 0
+    sp = rng.integers(0, S, n)
+    tgt = rng.normal(size=n) * 0.5
+    params, scale = _random_net(S, 12, feat, sp)
+    mlp = qeq.Mlp(S, max_batch=1024)
+    mlp.set_params(params.astype(np.float32), scale.astype(np.float32))
+    dev = torch.device("cuda")
+    f_t = torch.tensor(feat, dtype=torch.float32, device=dev)
+    s_t = torch.tensor(sp, dtype=torch.int32, device=dev)
+    t_t = torch.tensor(tgt, dtype=torch.float32, device=dev)
+    p = params.astype(np.float32).astype(np.float64).reshape(-1)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for step in range(1, 5):
+        _, g = mlp.train_step(f_t, s_t, t_t, lr=2e-3, apply=True, want_grad=True)
+        g = g.cpu().numpy().astype(np.float64)
+        # the GPU holds beta1, beta2 as FP32 constants (1 - 0.999f is 4.7e-5 above 1e-3)
+        p, m, v = M.adam_step(p, g, m, v, step, 2e-3, b1=float(np.float32(0.9)), b2=float(np.float32(0.999)))
+        st = mlp.get_state()
+        assert st["step"] == step
+        assert np.abs(st["params"] - p).max() < 2e-6, (step, np.abs(st["params"] - p).max())
+        assert np.abs(st["adam_m"] - m).max() < 1e-6 * max(1.0, np.abs(m).max())
+        assert np.abs(st["adam_v"] - v).max() < 1e-6 * max(1e-6, np.abs(v).max())
+    # restore the state into a fresh network and take step 5 in both
+    st = mlp.get_state()
+    mlp2 = qeq.Mlp(S, max_batch=1024)
+    mlp2.set_params(st["params"].reshape(S, -1), st["scale"].reshape(S, 2, -1))
+    mlp2.set_adam_state(st["adam_m"], st["adam_v"], st["step"])
+    _, g1 = mlp.train_step(f_t, s_t, t_t, lr=2e-3, apply=True, want_grad=True)
+    _, g2 = mlp2.train_step(f_t, s_t, t_t, lr=2e-3, apply=True, want_grad=True)
+    assert torch.equal(g1, g2)
+    assert np.array_equal(mlp.get_state()["params"], mlp2.get_state()["params"])
+    mlp.close()
+    mlp2.close()
 
 
 @pytest.mark.parametrize("n,S", [(300, 2), (128, 1), (1000, 4), (5, 3)])
