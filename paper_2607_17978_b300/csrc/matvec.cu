@@ -448,6 +448,7 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
                                int* __restrict__ counter, float* __restrict__ x32) {
   const Chunk ch = chunks[blockIdx.x];
   if (use_active && !sc[ch.s].active) return;
+  const int nspec = st[ch.s].S;  // FP64 work only for the structure's own species
   __shared__ double red[QEQ_MAX_SPECIES][33];
   double loc[QEQ_MAX_SPECIES];
 #pragma unroll
@@ -457,15 +458,18 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
     const double xa = x[a];
     if (x32) x32[a] = (float)xa;
 #pragma unroll
-    for (int k = 0; k < QEQ_MAX_SPECIES; ++k) loc[k] += (sp == k) ? xa : 0.0;
+    for (int k = 0; k < QEQ_MAX_SPECIES; ++k)
+      if (k < nspec) loc[k] += (sp == k) ? xa : 0.0;
   }
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
   for (int k = 0; k < QEQ_MAX_SPECIES; ++k) {
+    if (k >= nspec) break;
     double v = warp_sum<double>(loc[k]);
     if (lane == 0) red[k][w] = v;
   }
   __syncthreads();
-  if (threadIdx.x < QEQ_MAX_SPECIES) {
+  if (threadIdx.x < nspec) {
     double v = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[threadIdx.x][i];
     part[(size_t)blockIdx.x * QEQ_MAX_SPECIES + threadIdx.x] = v;
@@ -483,7 +487,7 @@ __global__ void k_species_sums(const Chunk* __restrict__ chunks, const StructDev
   if (last) {
     __threadfence();
     for (int k = 0; k < QEQ_MAX_SPECIES; ++k) {
-      double tot = ordered_block_sum(part, ch.first, ch.count, QEQ_MAX_SPECIES, k, red2);
+      const double tot = (k < nspec) ? ordered_block_sum(part, ch.first, ch.count, QEQ_MAX_SPECIES, k, red2) : 0.0;
       if (threadIdx.x == 0) sc[ch.s].xsum[k] = tot;
     }
     if (threadIdx.x == 0) counter[ch.s] = 0;
