@@ -445,11 +445,11 @@ qeq_status qeq_plan_set_warm_start(qeq_plan plan, qeq_mlp mlp);
  *   coulomb_k, ewald_tol, r_cut   as in qeq_plan_desc (<= 0: defaults)
  *   cuda_stream                   a cudaStream_t (NULL = legacy stream)
  * Each call reads the device's error bits back to the host and returns after
- * the stream has finished its work.  All calls share the scratch array, which
- * keeps the last call's contents: calls that overlap on the GPU, or come from
- * several host threads at once, race.  The first call on a device sets up that
- * device (it looks up the array's device address and the kernels'
- * shared-memory limits); make that first call before any stream capture. */
+ * the stream has finished its work, so no call can be captured into a CUDA
+ * graph.  All calls share the scratch array, which keeps the last call's
+ * contents: calls that overlap on the GPU, or come from several host threads at
+ * once, race.  The first call on a device also sets up that device (it looks up
+ * the array's device address and the kernels' shared-memory limits). */
 #define QEQ_STATIC_MAX_ATOMS 4096
 #define QEQ_STATIC_MAX_SPECIES 4
 #define QEQ_STATIC_MAX_MESH 64

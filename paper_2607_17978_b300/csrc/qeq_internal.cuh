@@ -19,7 +19,9 @@
 #define QEQ_BRICK_CAND 28  // per brick: candidate-bin counts per direction (3, pad), bins (3 x 8)
 #define QEQ_MAXP 8         // largest supported B-spline order
 #define QEQ_MAX_STAGES 12  // radix stages of one FFT length
+#ifndef QEQ_CHUNK
 #define QEQ_CHUNK 512      // atoms per reduction chunk (one CTA)
+#endif
 #define QEQ_GATHER_SPLIT_MAX 64  // gather CTAs per reduction chunk
 
 // ---------------------------------------------------------------------------
