@@ -88,8 +88,20 @@ enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
  * complement; a step that raises E_QEq is undone, alpha halved and the history cleared.
  * One matvec per step (mixed precision: FP64 A q1 at each round's start plus the FP32
  * product of the change); the same FP64 final check and restarts as the CG.  Host-paced;
- * the plan allocates its history (16 N doubles) at creation.  Warm starts as for CG. */
-enum { QEQ_FLAG_NO_GRAPH = 1, QEQ_FLAG_TEST_STALL = 2, QEQ_FLAG_TWO_RHS = 4, QEQ_FLAG_SQNM = 8 };
+ * the plan allocates its history (16 N doubles) at creation.  Warm starts as for CG.
+ * CHECK_DD, CHECK_FP64 (QEQ_MIXED plans): the FP64-accurate products of a mixed plan (its
+ * final checks, qeq_energy, qeq_matvec with force_fp64) run spread, gather and local terms
+ * in FP64 and the FFT passes either in FP64 or in double-float arithmetic (pairs of FP32
+ * values, ~2^-44 relative per operation, on the FP32 pipes); by default double-float when
+ * some structure's mesh has 2^21 points or more.  The two flags force one or the other. */
+enum {
+  QEQ_FLAG_NO_GRAPH = 1,
+  QEQ_FLAG_TEST_STALL = 2,
+  QEQ_FLAG_TWO_RHS = 4,
+  QEQ_FLAG_SQNM = 8,
+  QEQ_FLAG_CHECK_DD = 16,
+  QEQ_FLAG_CHECK_FP64 = 32
+};
 /* Preconditioners of the PCG.  JACOBI: D^-1, D_i = J_i + k_e/(sigma_i sqrt pi).
  * FOURIER: D^-1 - D^-1 T^T F^-1[h F(T D^-1 r)], the Woodbury inverse of D plus the
  * long-range Coulomb operator with the mesh operator T D^-1 T^T replaced by its

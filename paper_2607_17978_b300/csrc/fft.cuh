@@ -17,10 +17,13 @@
 #include <type_traits>
 #include <utility>
 
+#include "dd.cuh"
 #include "qeq_internal.cuh"
 
 namespace {
 
+// complex element of a mesh of real type T: FP32, FP64, or double-float (the final check
+// of mixed-precision solves; dd.cuh)
 template <typename T>
 struct C2;
 template <>
@@ -31,6 +34,23 @@ template <>
 struct C2<double> {
   using t = double2;
 };
+template <>
+struct C2<dd> {
+  using t = ddc;
+};
+// resident CTAs per SM the FFT kernels of type T are compiled for: FP64 one (its stages
+// need ~150 registers), double-float two (128 registers, a few spilled, ran the final
+// check's passes 1.3x faster than one CTA with 200 registers)
+template <typename T>
+__host__ __device__ constexpr int fft_min_blocks() {
+  return std::is_same<T, float>::value ? QEQ_FFT_MIN_BLOCKS32 : (std::is_same<T, dd>::value ? 2 : 1);
+}
+// which of a length's three FFT plans a pass of type T uses: FP32 stages (radices up to
+// 24), FP64 stages (up to 16) with FP64 twiddles, the same stages with double-float twiddles
+template <typename T>
+__host__ __device__ constexpr int fft_plan_variant() {
+  return std::is_same<T, float>::value ? 0 : (std::is_same<T, double>::value ? 1 : 2);
+}
 
 template <typename V>
 __device__ __forceinline__ V cadd(V a, V b) {
@@ -63,6 +83,10 @@ __device__ __forceinline__ const float2* twiddles<float>(const double2*, const f
 template <>
 __device__ __forceinline__ const double2* twiddles<double>(const double2* tw64, const float2*) {
   return tw64;
+}
+template <>
+__device__ __forceinline__ const ddc* twiddles<dd>(const double2* tw64, const float2*) {
+  return reinterpret_cast<const ddc*>(tw64);  // the double-float tables share the FP64 array (16 bytes each)
 }
 
 // ------------------------------------------------------------------ small DFTs
@@ -581,7 +605,7 @@ __device__ __forceinline__ bool fft_issuer_warp() { return (threadIdx.x >> 5) ==
 // sub-tile of `sub` lines of an item); the bulk copies of the next unit are in flight while
 // the current one is transformed.
 template <typename T, int PASS>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
+__global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, fft_min_blocks<T>())
     k_fft_tile(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl, const int4* __restrict__ items,
                int nitems, int TL, int sub, int Kmax, int ldmax, const double2* __restrict__ tw64,
                const float2* __restrict__ tw32, const int* __restrict__ tabs, const PcgScalars* __restrict__ sc,
@@ -625,7 +649,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, size
     g.nl = min(sub, nitem - part * sub);
     if (g.nl <= 0) return g;
     g.ok = 1;
-    g.plan = S.fft_plan[isZ ? 2 : 1] + (sizeof(T) == 8 ? 1 : 0);
+    g.plan = S.fft_plan[isZ ? 2 : 1] + fft_plan_variant<T>();
     g.K = isZ ? K2 : K1;
     const int64_t mb = S.mesh_off + (int64_t)it.y * S.Mp;
     // line l starts at in0 + l ils; element e of line l goes to out0 + l ols + e oes
@@ -732,6 +756,15 @@ template <>
 __device__ __forceinline__ double recip<double>(double x) {
   return 1.0 / x;
 }
+// double-float: through FP64 (once per reciprocal-space point, not per butterfly)
+template <>
+__device__ __forceinline__ dd exp2_mesh<dd>(dd x) {
+  return dd(exp2((double)x));
+}
+template <>
+__device__ __forceinline__ dd recip<dd>(dd x) {
+  return dd(1.0 / (double)x);
+}
 
 // largest x = s0 g0 of the smoothest preconditioner mode for which beta = 1 is used
 // (112 on a 13.8k-atom rock-salt cell: 17 iterations against 25 with beta = 0.98;
@@ -756,7 +789,7 @@ constexpr double kPreBetaOneX = 150.0;
 // zz, xy, xz, yz} to vir[8 u ..] (dst reinterpreted), in a fixed order: a line that is
 // not its own mirror stands for itself and its mirror (weight 2).
 template <typename T, bool PRE, int MAXS, bool VIR = false>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, sizeof(T) == 4 ? QEQ_FFT_MIN_BLOCKS32 : 1)
+__global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, fft_min_blocks<T>())
     k_fft_x_green(const StructDev* __restrict__ st, const FftPlanDev* __restrict__ fpl,
                   const int4* __restrict__ items, int nitems, int TLX, int sub, int Kmax, int ldmax,
                   const T* __restrict__ bmod, const double2* __restrict__ tw64, const float2* __restrict__ tw32,
@@ -834,7 +867,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? QEQ_FFT_THREADS32 : 256, size
       lineg[l][3] = (T)S.green_pref * bm1[my] * bm2[z];
     }
     __syncwarp();
-    const int plan = S.fft_plan[0] + (sizeof(T) == 8 ? 1 : 0);
+    const int plan = S.fft_plan[0] + fft_plan_variant<T>();
     issue_unit<T>(B, L, &bar[b], fpl + plan, twg, tabs, 1, 2, nsl, fft_smem_ld<T>(K),
                   [&](int sl) { return src + slot_in[sl]; }, extra, buf_plan[b] != plan);
     if (lane == 0) buf_plan[b] = plan;

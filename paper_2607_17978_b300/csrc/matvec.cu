@@ -756,7 +756,8 @@ cudaError_t launch_fft_passes(qeq_plan_s* Pl, const FftGeom& g, const int* kmax,
   constexpr bool F32 = std::is_same<T, float>::value;
   constexpr int FT = F32 ? QEQ_FFT_THREADS32 : 256;  // threads per CTA (the kernels' launch bounds)
   cudaStream_t s = Pl->stream;
-  const T* bmod = F32 ? (const T*)(const void*)Pl->d_bmod32 : (const T*)(const void*)Pl->d_bmod;
+  const T* bmod = (const T*)(F32 ? (const void*)Pl->d_bmod32
+                                 : (std::is_same<T, dd>::value ? (const void*)Pl->d_bmod_dd : (const void*)Pl->d_bmod));
   const int sub = F32 ? g.sub32 : g.sub64;
   const int subx = F32 ? g.subx32 : g.subx64;
   const int nsub = (g.tl + sub - 1) / sub, nsubx = (g.tlx + subx - 1) / subx;
@@ -858,6 +859,78 @@ cudaError_t matvec_impl(qeq_plan_s* Pl, const double* x, double* y, int with_J, 
     QEQ_CUDA_TRY(cudaGetLastError());
   }
   QEQ_CUDA_TRY(mark());
+  return cudaSuccess;
+}
+
+// FP64 mesh <-> double-float mesh, in place (16 bytes per complex point either way)
+__global__ void k_mesh_to_dd(double2* __restrict__ m, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = m[i];
+    ddc c;
+    c.x = dd(v.x);
+    c.y = dd(v.y);
+    reinterpret_cast<ddc*>(m)[i] = c;
+  }
+}
+__global__ void k_mesh_from_dd(double2* __restrict__ m, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const ddc c = reinterpret_cast<const ddc*>(m)[i];
+    m[i] = make_double2((double)c.x, (double)c.y);
+  }
+}
+
+// The FP64-accurate matvec of a mixed-precision plan (final checks, energies, force_fp64):
+// FP64 species sums, spread, gather and local terms as matvec_impl<double>, the five FFT
+// passes in double-float arithmetic on the FP32 pipes (dd.cuh; ~2^-44 relative per
+// operation, far below what the checks resolve).
+template <int P>
+cudaError_t matvec_check_dd(qeq_plan_s* Pl, const double* x, double* y, int with_J, int use_active, int fuse_pAp,
+                            cudaEvent_t* ev) {
+  cudaStream_t s = Pl->stream;
+  double2* mesh = Pl->d_mesh;
+  int rec = 0;
+  auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[rec++], s) : cudaSuccess; };
+  count_launch(Pl, 10);
+  QEQ_CUDA_TRY(mark());
+  k_species_sums<<<Pl->n_chunks, 256, 0, s>>>(Pl->d_chunks, Pl->d_st, Pl->d_spec, x, Pl->d_sc, use_active,
+                                               Pl->d_part, Pl->d_counter, nullptr);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  QEQ_CUDA_TRY(mark());
+  k_spread<double, P><<<Pl->total_bricks, 256, spread_smem<double, P>(), s>>>(
+      Pl->d_st, Pl->d_brick_struct, Pl->d_brick_cand, Pl->d_bin_start, Pl->d_base, Pl->d_wts, Pl->d_spec, x, nullptr,
+      Pl->d_sc, use_active, mesh);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  const int nb = (int)std::min<int64_t>((Pl->total_mesh + 255) / 256, (int64_t)Pl->num_sms * 16);
+  k_mesh_to_dd<<<nb, 256, 0, s>>>(mesh, Pl->total_mesh);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  QEQ_CUDA_TRY(mark());
+  QEQ_CUDA_TRY((launch_fft_passes<dd, false>(Pl, Pl->geo, Pl->fft_kmax, Pl->d_st, Pl->d_zitems, Pl->n_zitems,
+                                             Pl->d_yitems, Pl->n_yitems, Pl->d_yiitems, Pl->n_yiitems, Pl->d_xitems,
+                                             Pl->n_xitems, use_active, reinterpret_cast<ddc*>(mesh),
+                                             reinterpret_cast<ddc*>(Pl->d_mesh2), Pl->max_species, mark)));
+  k_mesh_from_dd<<<nb, 256, 0, s>>>(mesh, Pl->total_mesh);
+  QEQ_CUDA_TRY(cudaGetLastError());
+  {
+    const int with_pairs = Pl->pair_cap > 0;
+    k_gather_direct<double, P><<<Pl->n_chunks * Pl->gather_split, 256, 0, s>>>(
+        Pl->d_chunks, Pl->d_st, Pl->d_base, Pl->d_wts, Pl->d_spec, Pl->d_J, x, nullptr, Pl->d_row, Pl->d_col,
+        Pl->d_val64, Pl->d_val32, with_J, with_pairs, Pl->d_sc, use_active, fuse_pAp,
+        Pl->d_part + (size_t)Pl->n_chunks * QEQ_MAX_SPECIES, Pl->d_counter + Pl->n_struct, mesh, y, Pl->gather_split);
+    QEQ_CUDA_TRY(cudaGetLastError());
+  }
+  QEQ_CUDA_TRY(mark());
+  return cudaSuccess;
+}
+
+cudaError_t set_smem_attrs_dd() {
+  const int big = 227 * 1024 - 12 * 1024;
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_tile<dd, PASS_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_tile<dd, PASS_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_tile<dd, PASS_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_tile<dd, PASS_ZI>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<dd, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  QEQ_CUDA_TRY(cudaFuncSetAttribute(k_fft_x_green<dd, false, QEQ_MAX_SPECIES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return cudaSuccess;
 }
 
@@ -1009,6 +1082,7 @@ cudaError_t matvec_set_attributes() {
   QEQ_CUDA_TRY((set_smem_attrs<double, 6>()));
   QEQ_CUDA_TRY((set_smem_attrs<double, 8>()));
   QEQ_CUDA_TRY(cudaFuncSetAttribute(k_pre_spread_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  QEQ_CUDA_TRY(set_smem_attrs_dd());
   return cudaSuccess;
 }
 
@@ -1019,6 +1093,11 @@ cudaError_t launch_matvec(qeq_plan_s* P, int prec, const double* x, double* y, i
     if (p == 4) return matvec_impl<float, 4>(P, x, y, with_J, use_active, fuse_pAp, ev);
     if (p == 6) return matvec_impl<float, 6>(P, x, y, with_J, use_active, fuse_pAp, ev);
     return matvec_impl<float, 8>(P, x, y, with_J, use_active, fuse_pAp, ev);
+  }
+  if (P->precision == QEQ_MIXED && P->dd_check) {  // FP64-accurate product of a mixed plan, large meshes
+    if (p == 4) return matvec_check_dd<4>(P, x, y, with_J, use_active, fuse_pAp, ev);
+    if (p == 6) return matvec_check_dd<6>(P, x, y, with_J, use_active, fuse_pAp, ev);
+    return matvec_check_dd<8>(P, x, y, with_J, use_active, fuse_pAp, ev);
   }
   if (p == 4) return matvec_impl<double, 4>(P, x, y, with_J, use_active, fuse_pAp, ev);
   if (p == 6) return matvec_impl<double, 6>(P, x, y, with_J, use_active, fuse_pAp, ev);

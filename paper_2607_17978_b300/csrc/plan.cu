@@ -141,7 +141,7 @@ static qeq_status fail(qeq_plan_s* P, qeq_status st, const std::string& msg) {
 
 static void free_plan(qeq_plan_s* P) {
   if (!P) return;
-  void* ptrs[] = {P->d_st,     P->d_fft,     P->d_tw64,    P->d_tw32,     P->d_bmod,    P->d_bmod32,
+  void* ptrs[] = {P->d_st,     P->d_fft,     P->d_tw64,    P->d_tw32,     P->d_bmod,    P->d_bmod32,   P->d_bmod_dd,
                   P->d_zitems, P->d_yitems,  P->d_xitems,  P->d_yiitems,  P->d_bin_struct, P->d_atom_struct, P->d_brick_struct, P->d_brick_cand,
                   P->d_chunks, P->d_key,     P->d_bin_count, P->d_bin_start, P->d_bin_fill, P->d_perm,
                   P->d_scan_tmp, P->d_base,  P->d_wts,     P->d_wts32,    P->d_spec,    P->d_J,
@@ -262,7 +262,8 @@ static qeq_status build_plan(qeq_plan_s* P) {
     if (pbest == 0) return fail(P, QEQ_ERR_INVALID, "no mesh meets ewald_tol within 1000 points per direction");
   }
   P->max_p = pbest;
-  // two plans per FFT length: FP32 stages (radices up to 32), then FP64 stages (up to 16)
+  // three plans per FFT length: FP32 stages (radices up to 24), FP64 stages (up to 16), and the
+  // FP64 stages with double-float twiddles
   auto fft_plan_for = [&](int K) {
     auto it = fft_index.find(K);
     if (it != fft_index.end()) return it->second;
@@ -278,6 +279,25 @@ static qeq_status build_plan(qeq_plan_s* P) {
       tabs.resize(tabs.size() + 3 * (size_t)((K + 3) & ~3));
       if (!fft_plan_fill(K, f, tw64.data() + f.tw_off, tw32.data() + f.tw_off, tabs.data() + f.tab_off, maxR))
         return -1;
+      fplans.push_back(f);
+    }
+    {  // third plan: the FP64 stages with double-float twiddles (hi, lo of cos, then of sin) in
+       // 16-byte slots of the FP64 array
+      FftPlanDev f = fplans[idx + 1];
+      const int padK = K + (K & 1);
+      const int off64 = f.tw_off;
+      f.tw_off = (int)tw64.size();
+      tw64.resize(tw64.size() + padK);
+      tw32.resize(tw32.size() + padK);
+      for (int m = 0; m < padK; ++m) {
+        const double2 t = tw64[off64 + m];
+        float q[4];
+        q[0] = (float)t.x;
+        q[1] = (float)(t.x - (double)q[0]);
+        q[2] = (float)t.y;
+        q[3] = (float)(t.y - (double)q[2]);
+        memcpy(&tw64[f.tw_off + m], q, sizeof(q));
+      }
       fplans.push_back(f);
     }
     fft_index[K] = idx;
@@ -543,6 +563,14 @@ static qeq_status build_plan(qeq_plan_s* P) {
   P->hfft = fplans;
   P->total_bins = bin_off;
   P->total_bricks = (int)brick_struct.size();
+  // the FP64-accurate products of a mixed plan (final checks) run their FFT passes in
+  // double-float arithmetic when some structure's mesh has 2^21 points or more (measured:
+  // 980,000 atoms on 480^3, check matvec 66 -> 41 ms; on small meshes of a batch the FP64
+  // passes were faster)
+  for (int s = 0; s < ns; ++s)
+    if ((int64_t)hs[s].K[0] * hs[s].K[1] * hs[s].K[2] >= (int64_t(1) << 21)) P->dd_check = 1;
+  if (D.flags & QEQ_FLAG_CHECK_DD) P->dd_check = 1;
+  if (D.flags & QEQ_FLAG_CHECK_FP64) P->dd_check = 0;
   P->total_mesh = mesh_off;
   P->pair_cap = pair_cap;
   P->n_chunks = (int)chunks.size();
@@ -590,6 +618,14 @@ static qeq_status build_plan(qeq_plan_s* P) {
   ALLOC(upload(P, &P->d_tw32, tw32));
   ALLOC(upload(P, &P->d_bmod, bmod));
   ALLOC(upload(P, &P->d_bmod32, bmod32));
+  {  // double-float copy (hi, lo) for the final-check passes of mixed-precision plans
+    std::vector<float> bdd(2 * bmod.size());
+    for (size_t i = 0; i < bmod.size(); ++i) {
+      bdd[2 * i] = (float)bmod[i];
+      bdd[2 * i + 1] = (float)(bmod[i] - (double)bdd[2 * i]);
+    }
+    ALLOC(upload(P, &P->d_bmod_dd, bdd));
+  }
   ALLOC(upload(P, &P->d_zitems, zit));
   ALLOC(upload(P, &P->d_yitems, yit));
   ALLOC(upload(P, &P->d_xitems, xit));

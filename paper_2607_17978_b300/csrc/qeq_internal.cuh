@@ -46,7 +46,7 @@ struct StructDev {
   int64_t mesh_off;       // complex-element offset of this structure's complex mesh 0
   int64_t atom_begin, atom_end;
   int bin_off;            // first global bin of this structure
-  int fft_plan[3];        // FFT plan index per direction (FP32 stages; the FP64 plan follows it)
+  int fft_plan[3];        // FFT plan index per direction (FP32 stages; the FP64 and the double-float plans follow it)
   int bmod_off[3];        // offsets into the B-spline modulus table per direction
   int P[3];               // padded line lengths K_d + (K_d & 1) (innermost stride of each layout)
   int brick_off;          // first global brick of this structure
@@ -278,6 +278,7 @@ struct qeq_plan_s {
   int n_struct = 0;
   int64_t n_atoms = 0;
   int precision = QEQ_FP64;
+  int dd_check = 0;                // mixed plans: FP64-accurate products with double-float FFT passes
   int max_S = 0, max_p = 6;
   std::string last_error;
   std::vector<StructDev> hs;       // host copies
@@ -301,6 +302,7 @@ struct qeq_plan_s {
   float2* d_tw32 = nullptr;
   double* d_bmod = nullptr;
   float* d_bmod32 = nullptr;
+  float* d_bmod_dd = nullptr;      // hi, lo pairs of d_bmod (double-float passes)
   int* d_fft_tabs = nullptr;       // per FFT length: block offsets, frequency of position, position of frequency
   int max_ncm = 1;                 // largest complex-mesh count of any structure
   FftGeom geo;                     // tile sizes of the FFT passes of the matvec mesh

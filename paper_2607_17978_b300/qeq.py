@@ -25,6 +25,8 @@ QEQ_FLAG_NO_GRAPH = 1
 QEQ_FLAG_TEST_STALL = 2
 QEQ_FLAG_TWO_RHS = 4
 QEQ_FLAG_SQNM = 8
+QEQ_FLAG_CHECK_DD = 16
+QEQ_FLAG_CHECK_FP64 = 32
 QEQ_N_STAGES = 8
 STAGE_NAMES = ["species_sums", "spread", "fft_z", "fft_y", "fft_x_green", "ifft_y", "ifft_z", "gather"]
 
@@ -197,7 +199,7 @@ class Plan:
                  ewald_tol=1e-6, r_cut=8.0, spline_order=0, mesh_spacing=0.0, precision="fp64",
                  max_iter=1000, residual_tol=0.0, graph=True, device=None, preconditioner="jacobi",
                  precond_spacing=0.0, precond_width=0.0, precond_scale=0.0, test_stall=False,
-                 solver="projected"):
+                 solver="projected", check="auto"):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -218,7 +220,8 @@ class Plan:
                      sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), coulomb_k, charge_tol, ewald_tol,
                      r_cut, spline_order, mesh_spacing, prec, max_iter, residual_tol,
                      (0 if graph else QEQ_FLAG_NO_GRAPH) | (QEQ_FLAG_TEST_STALL if test_stall else 0)
-                     | {"projected": 0, "two_rhs": QEQ_FLAG_TWO_RHS, "sqnm": QEQ_FLAG_SQNM}[solver],
+                     | {"projected": 0, "two_rhs": QEQ_FLAG_TWO_RHS, "sqnm": QEQ_FLAG_SQNM}[solver]
+                     | {"auto": 0, "dd": QEQ_FLAG_CHECK_DD, "fp64": QEQ_FLAG_CHECK_FP64}[check],
                      {"jacobi": 0, "fourier": 1}[preconditioner],
                      precond_spacing, precond_width, precond_scale)
         with torch.cuda.device(self.device):

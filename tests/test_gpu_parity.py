@@ -53,6 +53,53 @@ def test_matvec_parity_config1(cfg1, precision):
     assert np.sqrt(np.mean((y64 - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)) < tol
 
 
+def test_double_float_checks_in_a_mixed_solve():
+    """A mixed-precision solve whose final checks run on double-float FFT passes (forced) gives
+    the charges of the dense oracle to 1e-5 e and the same charges as with FP64 checks to the
+    certification's resolution (both certify max|P r| below the same threshold)."""
+    from paper_2607_17978_b300 import qeq
+    st = synth.rocksalt(5, 5.64, 0.15, synth.rng_for(73, 0), vacancy_frac=0.05, shear_deg=10.0)
+    A = O.coulomb_matrix(st.cell, st.pos, st.sigma, k_e=synth.COULOMB_K_EV_A)
+    q_ref, _ = O.solve_bordered(A, st.J, st.chi, st.q_tot)
+    pos, spc, chi, J, qt = qeq.pack([st])
+    qs = {}
+    for check in ("dd", "fp64"):
+        plan = _plan([st], precision="mixed", ewald_tol=1e-7, r_cut=9.0, check=check, preconditioner="fourier")
+        res = plan.solve(pos, spc, chi, J, qt)
+        qs[check] = res.q.cpu().numpy()
+        assert res.info[0]["status"] == 0
+        assert np.abs(qs[check] - q_ref).max() < 1e-5, (check, np.abs(qs[check] - q_ref).max())
+        plan.close()
+    assert np.abs(qs["dd"] - qs["fp64"]).max() < 2e-6
+
+
+def test_double_float_check_matvec_equals_fp64():
+    """The FP64-accurate matvec of a mixed-precision plan (final checks, energies) with its FFT
+    passes in double-float arithmetic (forced here; by default on meshes of 2^21 points or more)
+    equals the FP64 plan's matvec on the same mesh to ~1e-13 of the potentials' size (FP64
+    rounding is ~1e-16, double-float ~2^-44 per operation): a rock-salt cell, a sheared cell
+    with vacancies, and a batch with 2-4 species (the general reciprocal multiply)."""
+    from paper_2607_17978_b300 import qeq
+    cases = [[synth.workload(1)],
+             [synth.rocksalt(5, 5.64, 0.15, synth.rng_for(71, 0), vacancy_frac=0.05, shear_deg=10.0)],
+             synth.batch_workload(3, cfg_id=72, n_min=100, n_max=600)]
+    for structs in cases:
+        p_mix = _plan(structs, precision="mixed", ewald_tol=1e-6, r_cut=8.0, check="dd")
+        p_64 = _plan(structs, precision="fp64", ewald_tol=1e-6, r_cut=8.0)
+        assert [p_mix.query(i)["mesh"] for i in range(len(structs))] == \
+            [p_64.query(i)["mesh"] for i in range(len(structs))]
+        pos, spc, chi, J, _ = qeq.pack(structs)
+        x = np.random.default_rng(5).normal(size=len(spc))
+        y_dd = p_mix.matvec(pos, spc, x, J=J, fp64=True).cpu().numpy()
+        y_64 = p_64.matvec(pos, spc, x, J=J).cpu().numpy()
+        scale = np.sqrt(np.mean(y_64 ** 2))
+        err = np.abs(y_dd - y_64).max() / scale
+        print(f"{len(structs)} structure(s), {len(spc)} atoms: max |y_dd - y_fp64| / rms = {err:.2e}")
+        assert err < 1e-11, err
+        p_mix.close()
+        p_64.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_solve_parity_config1(cfg1, precision):
     from paper_2607_17978_b300 import qeq
