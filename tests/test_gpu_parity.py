@@ -190,8 +190,9 @@ def test_user_warm_start_and_repeatability(cfg1):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_preconditioned_solves_are_bitwise_repeatable(precision):
-    """The Fourier preconditioner's coarse spread adds in 64-bit fixed point, so repeated
-    preconditioned solves (and batches of them) give identical charges and iteration counts."""
+    """The Fourier preconditioner's coarse spread adds integers (fixed-point contributions, 32-bit
+    tile sums, 64-bit mesh sums), whose order does not matter, so repeated preconditioned solves
+    (and batches of them) give identical charges and iteration counts."""
     from paper_2607_17978_b300 import qeq
     structs = [synth.rocksalt(6, 5.64, 0.2, synth.rng_for(5, 6), vacancy_frac=0.02)]
     structs += synth.batch_workload(4, n_min=64, n_max=800)
