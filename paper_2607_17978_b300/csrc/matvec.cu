@@ -506,9 +506,9 @@ __device__ __forceinline__ double pre_shift(const PcgScalars& c, int ones_input)
 // Power-of-two scale of the fixed-point coarse spread: max |v| is at most
 // max|r - shift| max D^-1 (max D^-1 alone for the ones vector), mapped to 2^23 (the
 // resolution of an FP32 mantissa); a contribution (B-spline weight product at most
-// (2/3)^3) stays below 2^21, so a tile point's 32-bit sum is exact for up to 2^10
-// contributions (a tile group with more atoms than kPreTileMaxAtoms adds straight to
-// the 64-bit mesh).
+// (2/3)^3 < 2^-1.75) stays below 2^21.25, so a tile point's 32-bit sum is exact for
+// fewer than 2^9 contributions: a tile group with kPreTileMaxAtoms atoms or more adds
+// straight to the 64-bit mesh (a point gets ~20 in dense matter).
 __device__ __forceinline__ double pre_fixed_scale(const PcgScalars& c, int ones_input) {
   const double sh = pre_shift(c, ones_input);
   double b = c.dinv_max * (ones_input ? 1.0 : fmax(fabs(c.r_max - sh), fabs(c.r_min - sh)));
@@ -517,7 +517,7 @@ __device__ __forceinline__ double pre_fixed_scale(const PcgScalars& c, int ones_
   frexp(b, &e);                    // b < 2^e
   return ldexp(1.0, 23 - e);
 }
-constexpr int kPreTileMaxAtoms = 1024;
+constexpr int kPreTileMaxAtoms = 512;
 
 // Cubic B-spline (order 4) weights of every atom on its structure's coarse mesh,
 // once per solve: M_4(w + j), j = 0..3, for stencil points f - j.
