@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_tc(const float* __restrict__ fe
         tc_mma(tmem, kmaj_desc(&M.X[j * 16 * 8], NF), kmaj_desc(&M.W1[j * 16 * 8], NF), tc_idesc(TC_TILE, NH), j);
       tc_commit(&M.bar);
     }
-    ok = __syncthreads_and(tc_bar_wait(&M.bar, phase)) != 0;  // the same verdict on every thread
+    ok = __syncthreads_and(tc_bar_wait(&M.bar, phase)) != 0;  // the same outcome on every thread
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float v[NH];
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(128) k_mlp_train_tc(const float* __restrict__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   };
-  auto wait_mma = [&]() {  // the commit issued by thread 0 (CTA-uniform verdict)
+  auto wait_mma = [&]() {  // the commit issued by thread 0 (CTA-uniform outcome)
     ok = __syncthreads_and(ok && tc_bar_wait(&M.bar, phase)) != 0;
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
