@@ -175,8 +175,15 @@ def load_traffic():
 
 # ----------------------------------------------------------------------------- CPU oracle
 def _cores():
+    """All host cores for the CPU oracle's OpenMP loops (torchrun sets OMP_NUM_THREADS=1 in every
+    rank, so the setting is overridden here and in the OpenMP runtime the oracle links)."""
     cores = len(os.sched_getaffinity(0))
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    try:
+        import ctypes
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(cores)
+    except OSError:
+        pass
     return cores
 
 
