@@ -10,6 +10,14 @@
 // linear transform needs (its errors are measured against the norm of the data).
 #pragma once
 
+#include <cmath>
+
+#ifdef __CUDA_ARCH__
+#define QEQ_DD_FMA(a, b, c) __fmaf_rn(a, b, c)
+#else
+#define QEQ_DD_FMA(a, b, c) std::fmaf(a, b, c)
+#endif
+
 struct dd {
   float hi, lo;
   dd() = default;  // trivial: shared-memory arrays of dd need no constructor
@@ -24,28 +32,28 @@ struct __align__(16) ddc {
   dd x, y;
 };
 
-__device__ __forceinline__ dd dd_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ dd dd_two_sum(float a, float b) {
   const float s = a + b;
   const float bb = s - a;
   return dd(s, (a - (s - bb)) + (b - bb));
 }
-__device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {  // |a| >= |b|
+__host__ __device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {  // |a| >= |b|
   const float s = a + b;
   return dd(s, b - (s - a));
 }
-__device__ __forceinline__ dd operator+(dd a, dd b) {
+__host__ __device__ __forceinline__ dd operator+(dd a, dd b) {
   dd s = dd_two_sum(a.hi, b.hi);
   return dd_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
-__device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
-__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
-__device__ __forceinline__ dd operator*(dd a, dd b) {
+__host__ __device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__host__ __device__ __forceinline__ dd operator*(dd a, dd b) {
   const float p = a.hi * b.hi;
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  float e = QEQ_DD_FMA(a.hi, b.hi, -p);
+  e = QEQ_DD_FMA(a.hi, b.lo, QEQ_DD_FMA(a.lo, b.hi, e));
   return dd_fast_two_sum(p, e);
 }
-__device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
-__device__ __forceinline__ dd& operator*=(dd& a, dd b) { return a = a * b; }
-__device__ __forceinline__ bool operator>(dd a, dd b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
-__device__ __forceinline__ bool operator<=(dd a, dd b) { return !(a > b); }
+__host__ __device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
+__host__ __device__ __forceinline__ dd& operator*=(dd& a, dd b) { return a = a * b; }
+__host__ __device__ __forceinline__ bool operator>(dd a, dd b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__host__ __device__ __forceinline__ bool operator<=(dd a, dd b) { return !(a > b); }
