@@ -21,6 +21,20 @@ def test_partition_covers_every_index_once_and_balances():
         assert parts == shard.partition(costs, n)  # deterministic
 
 
+def test_partition_meets_grahams_bound_against_brute_force():
+    """Largest-first greedy scheduling on m parts has makespan <= (4/3 - 1/(3m)) of the optimum
+    (Graham 1969); the optimum here is found by trying every assignment of small batches."""
+    import itertools
+    rng = np.random.default_rng(2)
+    for trial in range(60):
+        m = int(rng.integers(2, 4))
+        costs = [float(c) for c in rng.integers(1, 50, size=int(rng.integers(m + 1, 9)))]
+        greedy = max(sum(costs[i] for i in p) for p in shard.partition(costs, m))
+        best = min(max(sum(c for c, a in zip(costs, assign) if a == k) for k in range(m))
+                   for assign in itertools.product(range(m), repeat=len(costs)))
+        assert best <= greedy <= (4.0 / 3.0 - 1.0 / (3 * m)) * best + 1e-9, (costs, m)
+
+
 def test_partition_edge_cases():
     assert shard.partition([], 3) == [[], [], []]
     assert shard.partition([5.0], 2) == [[0], []]
