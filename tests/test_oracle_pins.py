@@ -47,6 +47,24 @@ def test_madelung_rocksalt_point_charges(ncell, omega):
     assert abs(M - MADELUNG) < 1e-11
 
 
+@pytest.mark.parametrize("omega", [0.8, 1.2, 2.0])
+def test_madelung_constants_of_other_lattices_and_a_primitive_triclinic_cell(omega):
+    """Rock salt on its two-atom primitive fcc cell (60-degree angles, so the reciprocal rows and the
+    volume of a non-orthogonal cell enter), zinc blende on the same cell and caesium chloride on a
+    simple cubic cell, each against its textbook Madelung constant."""
+    a = 5.0
+    fcc = 0.5 * a * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    cases = [(fcc, [0.5 * a, 0.0, 0.0], 0.5 * a, MADELUNG),
+             (fcc, [0.25 * a] * 3, a * math.sqrt(3) / 4, GOLD["madelung_zincblende_nn"]["value"]),
+             (np.eye(3) * a, [0.5 * a] * 3, a * math.sqrt(3) / 2, GOLD["madelung_cscl_nn"]["value"])]
+    q = np.array([1.0, -1.0])
+    for cell, second, r0, expect in cases:
+        pos = np.array([[0.0, 0.0, 0.0], second])
+        A = O.coulomb_matrix(cell, pos, np.zeros(2), omega=omega)
+        M = -(0.5 * q @ A @ q) * r0
+        assert abs(M - expect) < 1e-9, (expect, M)
+
+
 def test_madelung_via_large_cell_matvec():
     frac, spec = synth.rocksalt_sites(2, 2, 2)
     a = 5.64
