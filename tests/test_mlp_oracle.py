@@ -77,3 +77,38 @@ def test_bf16_rounding():
     r = M.bf16_round(x)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7
     assert abs(r[3] + 3.14159) < 2 ** -6
+
+
+def test_adam_matches_the_library_optimiser_over_several_steps():
+    """Adam's bias-corrected update (Kingma & Ba 2015) against torch.optim.Adam in FP64, ten steps of
+    random gradients with non-default betas: a slip in a bias correction or in where eps enters fails."""
+    import torch
+    rng = np.random.default_rng(3)
+    p0 = rng.normal(size=50)
+    b1, b2, eps, lr = 0.85, 0.99, 1e-6, 3e-2
+    w = torch.tensor(p0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([w], lr=lr, betas=(b1, b2), eps=eps)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for step in range(1, 11):
+        g = rng.normal(size=50) * (0.1 if step % 3 else 5.0)
+        p, m, v = M.adam_step(p, g, m, v, step, lr, b1, b2, eps)
+        w.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        assert np.abs(p - w.detach().numpy()).max() < 1e-13 * max(1.0, np.abs(p).max()), step
+
+
+def test_bf16_rounding_matches_the_library_conversion():
+    """Round to nearest even into bfloat16 against torch's conversion: random magnitudes over many
+    binades, exact ties with an even and an odd kept bit, the largest finite values and subnormals."""
+    import torch
+    rng = np.random.default_rng(4)
+    x = (rng.normal(size=20000) * np.exp2(rng.integers(-30, 30, size=20000))).astype(np.float32)
+    hi = rng.integers(0, 1 << 16, size=4000, dtype=np.uint32) << np.uint32(16)
+    ties = (hi | np.uint32(0x8000)).view(np.float32)            # exactly halfway between two bf16 values
+    ties = ties[np.isfinite(ties) & (np.abs(ties) < 3e38)]
+    edge = np.array([3.38e38, -3.38e38, 1e-39, -1e-39, 1e-45, 0.0, -0.0], np.float32)
+    for arr in (x, ties, edge):
+        expect = torch.from_numpy(arr.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+        got = M.bf16_round(arr)
+        assert np.array_equal(got.view(np.uint64), expect.view(np.uint64))
+
