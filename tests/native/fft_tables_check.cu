@@ -1,0 +1,131 @@
+// Host check of the FFT plan tables and the magic-number division the FFT kernels index
+// with (csrc/qeq_internal.cuh: fft_radices, fft_plan_fill, make_fastdiv), for every mesh
+// length the plan can choose (2^a 3^b 5^c up to 1024) and both radix limits (FP32 and
+// FP64 passes):
+//   * the stage radices are register radices no larger than the limit, their product is
+//     K, there are at most QEQ_MAX_STAGES of them, and no ordered factorisation with
+//     fewer stages exists (brute force over the same radix set);
+//   * the stage constants satisfy Q_s L_s = K, S_s R_s = L_s, Q_{s+1} = Q_s R_s;
+//   * the frequency table (block-order position -> frequency) and the position table
+//     (frequency -> position) are inverse permutations of 0 .. K-1, and every block
+//     offset lies inside the line;
+//   * the division (mulhi(n, m) + n) >> s with make_fastdiv's (m, s) equals n / d for
+//     every divisor the plans carry, exhaustively for n < 2^22 (the kernels divide
+//     indices of one shared-memory tile, far below that) and on seeded samples up to
+//     2^31 - 1.
+// Prints a summary and exits non-zero on the first violated property.
+#include <cstdio>
+#include <cstdint>
+#include <random>
+#include <set>
+#include <vector>
+
+#include "../../paper_2607_17978_b300/csrc/qeq_internal.cuh"
+
+static bool smooth(int n) {
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// fewest stages of any ordered factorisation of k into the radices {2..24} allowed by maxR
+static int min_stages(int k, int maxR) {
+  static const int kR[] = {24, 20, 18, 16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  std::vector<int> best(k + 1, 1 << 20);
+  best[1] = 0;
+  for (int v = 2; v <= k; ++v)
+    for (int r : kR)
+      if (r <= maxR && v % r == 0 && best[v / r] + 1 < best[v]) best[v] = best[v / r] + 1;
+  return best[k];
+}
+
+static uint32_t div_magic(uint32_t n, const FastDiv& f) {
+  const uint32_t hi = (uint32_t)(((uint64_t)n * f.m) >> 32);
+  return (hi + n) >> f.s;
+}
+
+int main() {
+  const int allowed[] = {2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16, 18, 20, 24};
+  std::set<uint32_t> divisors;
+  int lengths = 0;
+  for (int maxR : {24, QEQ_MAXR64}) {
+    for (int K = 2; K <= 1024; ++K) {
+      if (!smooth(K)) continue;
+      ++lengths;
+      const int K4 = (K + 3) & ~3;
+      FftPlanDev f{};
+      std::vector<double2> tw64(K);
+      std::vector<float2> tw32(K);
+      std::vector<int> tab(3 * K4, -1);
+      if (!fft_plan_fill(K, f, tw64.data(), tw32.data(), tab.data(), maxR)) {
+        printf("FAIL K=%d maxR=%d: no plan\n", K, maxR);
+        return 1;
+      }
+      if (f.nst < 1 || f.nst > QEQ_MAX_STAGES || f.nst != min_stages(K, maxR)) {
+        printf("FAIL K=%d maxR=%d: %d stages, fewest possible %d\n", K, maxR, f.nst, min_stages(K, maxR));
+        return 1;
+      }
+      long long prod = 1;
+      for (int s = 0; s < f.nst; ++s) {
+        bool ok = false;
+        for (int r : allowed) ok |= (f.radix[s] == r);
+        if (!ok || f.radix[s] > maxR) {
+          printf("FAIL K=%d maxR=%d: radix %d at stage %d\n", K, maxR, f.radix[s], s);
+          return 1;
+        }
+        prod *= f.radix[s];
+        if ((long long)f.Q[s] * f.L[s] != K || f.S[s] * f.radix[s] != f.L[s] ||
+            (s + 1 < f.nst && f.Q[s + 1] != f.Q[s] * f.radix[s])) {
+          printf("FAIL K=%d maxR=%d: stage constants at stage %d\n", K, maxR, s);
+          return 1;
+        }
+        divisors.insert((uint32_t)(K / f.radix[s]));
+        divisors.insert((uint32_t)f.S[s]);
+        if (f.fnb[s].d != (uint32_t)(K / f.radix[s]) || f.fS[s].d != (uint32_t)f.S[s]) {
+          printf("FAIL K=%d maxR=%d: divisor tables at stage %d\n", K, maxR, s);
+          return 1;
+        }
+      }
+      divisors.insert((uint32_t)K);
+      if (prod != K || f.fK.d != (uint32_t)K) {
+        printf("FAIL K=%d maxR=%d: radices multiply to %lld\n", K, maxR, prod);
+        return 1;
+      }
+      const int* freq = tab.data() + K4;
+      const int* pos = tab.data() + 2 * K4;
+      std::vector<int> seen(K, 0);
+      for (int p = 0; p < K; ++p) {
+        const int fq = freq[p];
+        if (fq < 0 || fq >= K || seen[fq]++ || pos[fq] != p) {
+          printf("FAIL K=%d maxR=%d: frequency/position tables at %d\n", K, maxR, p);
+          return 1;
+        }
+      }
+      const int nblk = K / f.radix[f.nst - 1];
+      for (int u = 0; u < nblk; ++u)
+        if (tab[u] < 0 || tab[u] >= K) {
+          printf("FAIL K=%d maxR=%d: block offset %d of base %d\n", K, maxR, tab[u], u);
+          return 1;
+        }
+    }
+  }
+  std::mt19937_64 gen(20260);
+  std::uniform_int_distribution<uint32_t> big(0, 0x7FFFFFFFu);
+  for (uint32_t d : divisors) {
+    const FastDiv f = make_fastdiv(d);
+    for (uint32_t n = 0; n < (1u << 22); ++n)
+      if (div_magic(n, f) != n / d) {
+        printf("FAIL division: %u / %u gives %u\n", n, d, div_magic(n, f));
+        return 1;
+      }
+    for (int t = 0; t < 200000; ++t) {
+      const uint32_t n = (t == 0) ? 0x7FFFFFFFu : big(gen);
+      if (div_magic(n, f) != n / d) {
+        printf("FAIL division: %u / %u gives %u\n", n, d, div_magic(n, f));
+        return 1;
+      }
+    }
+  }
+  printf("fft tables: %d (length, radix limit) plans, %zu divisors exact: ok\n", lengths, divisors.size());
+  return 0;
+}
