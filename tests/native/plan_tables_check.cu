@@ -1,6 +1,6 @@
-// Host check of the FFT plan tables and the magic-number division the FFT kernels index
-// with (csrc/qeq_internal.cuh: fft_radices, fft_plan_fill, make_fastdiv), for every mesh
-// length the plan can choose (2^a 3^b 5^c up to 1024) and both radix limits (FP32 and
+// Host check of the plan tables the matvec kernels index with (csrc/qeq_internal.cuh:
+// fft_radices, fft_plan_fill, make_fastdiv, brick_candidates, fft_work_lists).  For every
+// mesh length the plan can choose (2^a 3^b 5^c up to 1024) and both radix limits (FP32 and
 // FP64 passes):
 //   * the stage radices are register radices no larger than the limit, their product is
 //     K, there are at most QEQ_MAX_STAGES of them, and no ordered factorisation with
@@ -13,6 +13,11 @@
 //     every divisor the plans carry, exhaustively for n < 2^22 (the kernels divide
 //     indices of one shared-memory tile, far below that) and on seeded samples up to
 //     2^31 - 1.
+// For every such length and B-spline order 4, 6, 8, each spread brick's candidate bins
+// hold, without repeats, every bin whose atoms (stencil base f, points f - p + 1 .. f mod K,
+// bin f / 8) reach the brick (brute force over f).  For the FFT work lists of a set of
+// mesh shapes and line counts: every z, y and inverse-y line is covered exactly once, and
+// every x line (y, z) exactly once as itself or as its mirror (-y, -z) of an x item.
 // Prints a summary and exits non-zero on the first violated property.
 #include <cstdio>
 #include <cstdint>
@@ -42,6 +47,81 @@ static int min_stages(int k, int maxR) {
 static uint32_t div_magic(uint32_t n, const FastDiv& f) {
   const uint32_t hi = (uint32_t)(((uint64_t)n * f.m) >> 32);
   return (hi + n) >> f.s;
+}
+
+// every base position whose stencil reaches a brick has its bin among the candidates
+static bool check_bricks(int K, int p) {
+  StructDev T{};
+  T.K[0] = T.K[1] = T.K[2] = K;
+  const int nbins = (K + QEQ_BIN - 1) / QEQ_BIN;
+  for (int d = 0; d < 3; ++d) {
+    const int e = (d == 2) ? QEQ_BRICK_Z : QEQ_BRICK_XY;
+    for (int b = 0; b * e < K; ++b) {
+      int bc[3] = {0, 0, 0};
+      bc[d] = b;
+      int out[QEQ_BRICK_CAND];
+      brick_candidates(T, p, bc, out);
+      const int nc = out[d];
+      const int* cand = out + 4 + 8 * d;
+      if (nc < 1 || nc > 8) return false;
+      for (int i = 0; i < nc; ++i) {
+        if (cand[i] < 0 || cand[i] >= nbins) return false;
+        for (int j = 0; j < i; ++j)
+          if (cand[j] == cand[i]) return false;  // a repeated bin would spread its atoms twice
+      }
+      const int x0 = b * e, x1 = std::min(x0 + e, K);
+      for (int f = 0; f < K; ++f) {
+        bool reaches = false;
+        for (int j = 0; j < p; ++j) {
+          const int x = ((f - j) % K + K) % K;
+          reaches |= (x >= x0 && x < x1);
+        }
+        if (!reaches) continue;
+        bool found = false;
+        for (int i = 0; i < nc; ++i) found |= (cand[i] == f / QEQ_BIN);
+        if (!found) {
+          printf("FAIL bricks K=%d p=%d d=%d brick %d: bin %d of base %d missing\n", K, p, d, b, f / QEQ_BIN, f);
+          return false;
+        }
+      }
+    }
+  }
+  return true;
+}
+
+static bool check_work_lists(int K0, int K1, int K2, int ncm, int tl, int tlx) {
+  StructDev T{};
+  T.K[0] = K0;
+  T.K[1] = K1;
+  T.K[2] = K2;
+  T.ncm = ncm;
+  std::vector<int> z((size_t)ncm * K0 * K1), y((size_t)ncm * K2 * K0), yi((size_t)ncm * K0 * K2), x((size_t)K1 * K2);
+  bool ok = true;
+  fft_work_lists(
+      T, 0, tl, tlx,
+      [&](int4 it) {  // {s, c, x, y0}: lines y0 .. y0 + tl - 1 of column x
+        for (int l = 0; l < tl && it.w + l < K1; ++l) z[((size_t)it.y * K0 + it.z) * K1 + it.w + l]++;
+      },
+      [&](int4 it) {  // {s, c, z, x0}
+        for (int l = 0; l < tl && it.w + l < K0; ++l) y[((size_t)it.y * K2 + it.z) * K0 + it.w + l]++;
+      },
+      [&](int4 it) {  // {s, c, x, z0}
+        for (int l = 0; l < tl && it.w + l < K2; ++l) yi[((size_t)it.y * K0 + it.z) * K2 + it.w + l]++;
+      },
+      [&](int4 it) {  // {s, z, y0, lines}: lines (y, z) and their mirrors (-y, -z)
+        if (it.w < 1 || it.w > tlx || it.z + it.w > K1 || 2 * it.y > K2) ok = false;
+        for (int l = 0; l < it.w; ++l) {
+          const int yy = it.z + l, my = (K1 - yy) % K1, mz = (K2 - it.y) % K2;
+          x[(size_t)yy * K2 + it.y]++;
+          if (my != yy || mz != it.y) x[(size_t)my * K2 + mz]++;
+        }
+      });
+  for (int v : z) ok &= (v == 1);
+  for (int v : y) ok &= (v == 1);
+  for (int v : yi) ok &= (v == 1);
+  for (int v : x) ok &= (v == 1);
+  if (!ok) printf("FAIL work lists K=(%d,%d,%d) ncm=%d tl=%d tlx=%d\n", K0, K1, K2, ncm, tl, tlx);
+  return ok;
 }
 
 int main() {
@@ -126,6 +206,30 @@ int main() {
       }
     }
   }
-  printf("fft tables: %d (length, radix limit) plans, %zu divisors exact: ok\n", lengths, divisors.size());
+  int bricks = 0;
+  for (int K = 12; K <= 1024; ++K) {
+    if (!smooth(K)) continue;
+    for (int p : {4, 6, 8}) {
+      if (K < 2 * p) continue;
+      if (!check_bricks(K, p)) {
+        printf("FAIL bricks K=%d p=%d\n", K, p);
+        return 1;
+      }
+      ++bricks;
+    }
+  }
+  const int shapes[][3] = {{12, 12, 12}, {15, 16, 18}, {16, 20, 25}, {27, 30, 32}, {45, 40, 36}, {64, 64, 64},
+                           {81, 75, 72}, {96, 100, 90}, {135, 128, 120}, {288, 288, 288}, {480, 480, 480},
+                           {1000, 27, 1000}};
+  int lists = 0;
+  for (const auto& k : shapes)
+    for (int ncm : {1, 2})
+      for (int tl : {1, 8, 64})
+        for (int tlx : {1, 4, 32}) {
+          if (!check_work_lists(k[0], k[1], k[2], ncm, tl, tlx)) return 1;
+          ++lists;
+        }
+  printf("plan tables: %d (length, radix limit) FFT plans, %zu divisors exact, %d (length, order) brick tables, "
+         "%d work-list cases: ok\n", lengths, divisors.size(), bricks, lists);
   return 0;
 }
