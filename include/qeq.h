@@ -141,7 +141,9 @@ typedef struct {
   double residual_tol;          /* optional extra stop: ||P r||_2 <= residual_tol*||P chi||_2 */
   int32_t flags;                /* QEQ_FLAG_*                                                 */
   int32_t preconditioner;       /* QEQ_PRECOND_JACOBI (default) or QEQ_PRECOND_FOURIER        */
-  double precond_spacing;       /* FOURIER: coarse mesh spacing [A]; <= 0: 2.0                */
+  double precond_spacing;       /* FOURIER: coarse mesh spacing [A]; <= 0: 2.0; a spacing so  */
+                                /* fine that the coarse spread's tiles exceed 64 KB of shared */
+                                /* memory: QEQ_ERR_INVALID                                    */
   double precond_width;         /* FOURIER: Gaussian width w [A]; <= 0: 3.0 for cells up to   */
                                 /* 80 A wide, 4.5 above                                       */
   double precond_scale;         /* FOURIER: safety factor beta of large cells, 0 < beta <= 1;  */

@@ -546,6 +546,10 @@ static qeq_status build_plan(qeq_plan_s* P) {
     while (gz > 1 && tile_bytes(gz) > 64 * 1024) gz = (gz + 1) / 2;
     P->pre_tile_gz = gz;
     P->pre_tile_smem = tile_bytes(gz);
+    // the coarse spread launches with at most 64 KB of tile (its function attribute): a
+    // coarse mesh so fine that a single-bin tile exceeds that is refused here
+    if (P->pre_tile_smem > 64 * 1024)
+      return fail(P, QEQ_ERR_INVALID, "preconditioner mesh too fine for its shared-memory tiles (raise precond_spacing)");
     for (int s = 0; s < ns; ++s)
       for (int bx = 0; bx < hs[s].nb[0]; bx += G)
         for (int by = 0; by < hs[s].nb[1]; by += G)
