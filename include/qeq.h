@@ -93,7 +93,9 @@ enum { QEQ_WARM_COLD = 0, QEQ_WARM_USER = 1, QEQ_WARM_MLP = 2 };
  * final checks, qeq_energy, qeq_matvec with force_fp64) run spread, gather and local terms
  * in FP64 and the FFT passes either in FP64 or in double-float arithmetic (pairs of FP32
  * values, ~2^-44 relative per operation, on the FP32 pipes); by default double-float when
- * some structure's mesh has 2^21 points or more.  The two flags force one or the other. */
+ * some structure's mesh has 2^21 points or more and no structure has more than two
+ * species (with more, the double-float x pass spills registers and FP64 stays the default).
+ * The two flags force one or the other. */
 enum {
   QEQ_FLAG_NO_GRAPH = 1,
   QEQ_FLAG_TEST_STALL = 2,

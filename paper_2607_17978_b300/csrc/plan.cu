@@ -570,9 +570,12 @@ static qeq_status build_plan(qeq_plan_s* P) {
   // the FP64-accurate products of a mixed plan (final checks) run their FFT passes in
   // double-float arithmetic when some structure's mesh has 2^21 points or more (measured:
   // 980,000 atoms on 480^3, check matvec 66 -> 41 ms; on small meshes of a batch the FP64
-  // passes were faster)
-  for (int s = 0; s < ns; ++s)
-    if ((int64_t)hs[s].K[0] * hs[s].K[1] * hs[s].K[2] >= (int64_t(1) << 21)) P->dd_check = 1;
+  // passes were faster) and no structure has more than two species: the x pass of up to
+  // eight species keeps four complex meshes per line in registers and, in double-float,
+  // spills ~2 KB per thread (its FP64 form does not), so there the FP64 passes stay
+  if (max_s <= 2)
+    for (int s = 0; s < ns; ++s)
+      if ((int64_t)hs[s].K[0] * hs[s].K[1] * hs[s].K[2] >= (int64_t(1) << 21)) P->dd_check = 1;
   if (D.flags & QEQ_FLAG_CHECK_DD) P->dd_check = 1;
   if (D.flags & QEQ_FLAG_CHECK_FP64) P->dd_check = 0;
   P->total_mesh = mesh_off;
