@@ -75,10 +75,11 @@ def test_double_float_checks_in_a_mixed_solve():
 
 def test_double_float_check_matvec_equals_fp64():
     """The FP64-accurate matvec of a mixed-precision plan (final checks, energies) with its FFT
-    passes in double-float arithmetic (forced here; by default on meshes of 2^21 points or more with at most two species)
-    equals the FP64 plan's matvec on the same mesh to ~1e-13 of the potentials' size (FP64
-    rounding is ~1e-16, double-float ~2^-44 per operation): a rock-salt cell, a sheared cell
-    with vacancies, and a batch with 2-4 species (the general reciprocal multiply)."""
+    passes in double-float arithmetic (forced here; by default on meshes of 2^21 points or more
+    with at most two species) equals the FP64 plan's matvec on the same mesh to ~1e-13 of the
+    potentials' size (FP64 rounding is ~1e-16, double-float ~2^-44 per operation): a rock-salt
+    cell, a sheared cell with vacancies, and a batch with 2-4 species (the general reciprocal
+    multiply)."""
     from paper_2607_17978_b300 import qeq
     cases = [[synth.workload(1)],
              [synth.rocksalt(5, 5.64, 0.15, synth.rng_for(71, 0), vacancy_frac=0.05, shear_deg=10.0)],
