@@ -18,6 +18,11 @@
 // bin f / 8) reach the brick (brute force over f).  For the FFT work lists of a set of
 // mesh shapes and line counts: every z, y and inverse-y line is covered exactly once, and
 // every x line (y, z) exactly once as itself or as its mirror (-y, -z) of an x item.
+// For the preconditioner's coarse-spread tiles (pre_tile_range) over pairs of fine and
+// coarse lengths and group sizes: the tile start lies on the coarse line, its extent is at
+// most the line, and the cubic stencils (points f - 3 .. f) of every coarse base f that an
+// atom of the group's fine bins can have, widened by one point each way for the rounding
+// of its coordinate, lie in the tile.
 // Prints a summary and exits non-zero on the first violated property.
 #include <cstdio>
 #include <cstdint>
@@ -122,6 +127,30 @@ static bool check_work_lists(int K0, int K1, int K2, int ncm, int tl, int tlx) {
   for (int v : x) ok &= (v == 1);
   if (!ok) printf("FAIL work lists K=(%d,%d,%d) ncm=%d tl=%d tlx=%d\n", K0, K1, K2, ncm, tl, tlx);
   return ok;
+}
+
+static bool check_pre_tiles(int Kf, int Kc, int g) {
+  const int nb = (Kf + QEQ_BIN - 1) / QEQ_BIN;
+  for (int b0 = 0; b0 < nb; b0 += g) {
+    int o, ext;
+    pre_tile_range(b0, g, nb, Kc, Kf, o, ext);
+    if (o < 0 || o >= Kc || ext < 1 || ext > Kc) return false;
+    const int b1 = std::min(b0 + g, nb);
+    // coordinates u in [8 b0 / Kf, min(8 b1, Kf) / Kf): coarse bases floor(u Kc), +-1
+    const int lo = (int)(((long long)QEQ_BIN * b0 * Kc) / Kf) - 1;
+    const int hi = (int)(((long long)std::min(QEQ_BIN * b1, Kf) * Kc + Kf - 1) / Kf);  // largest base + 1
+    for (int f = lo; f <= hi; ++f)
+      for (int j = 0; j < 4; ++j) {
+        const int x = (((f - j) % Kc) + Kc) % Kc;
+        const int t = ((x - o) % Kc + Kc) % Kc;
+        if (t >= ext) {
+          printf("FAIL pre tiles Kf=%d Kc=%d g=%d b0=%d: point %d outside [%d, %d + %d)\n", Kf, Kc, g, b0, x, o, o,
+                 ext);
+          return false;
+        }
+      }
+  }
+  return true;
 }
 
 int main() {
@@ -229,7 +258,19 @@ int main() {
           if (!check_work_lists(k[0], k[1], k[2], ncm, tl, tlx)) return 1;
           ++lists;
         }
+  int tiles = 0;
+  for (int Kf = 12; Kf <= 1000; ++Kf) {
+    if (!smooth(Kf)) continue;
+    for (int Kc = 4; Kc <= Kf; ++Kc) {
+      if (!smooth(Kc)) continue;
+      const int nb = (Kf + QEQ_BIN - 1) / QEQ_BIN;
+      for (int g : {1, QEQ_PRE_TILE_G, 3, 5, nb}) {
+        if (!check_pre_tiles(Kf, Kc, g)) return 1;
+        ++tiles;
+      }
+    }
+  }
   printf("plan tables: %d (length, radix limit) FFT plans, %zu divisors exact, %d (length, order) brick tables, "
-         "%d work-list cases: ok\n", lengths, divisors.size(), bricks, lists);
+         "%d work-list cases, %d coarse-tile cases: ok\n", lengths, divisors.size(), bricks, lists, tiles);
   return 0;
 }

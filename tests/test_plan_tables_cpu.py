@@ -5,7 +5,8 @@ constants of both radix limits, the frequency and position tables as inverse per
 magic-number index division equal to n / d for every divisor the plans carry (exhaustive below 2^22),
 and, for B-spline orders 4, 6 and 8, each spread brick's candidate bins against a brute-force search of
 the stencil bases that reach it.  For a set of mesh shapes and line counts: every FFT line of the z, y
-and inverse-y work lists covered once, every x line once as itself or as its mirror."""
+and inverse-y work lists covered once, every x line once as itself or as its mirror.  For pairs of fine
+and coarse lengths: the preconditioner's coarse-spread tiles hold every stencil point of their atoms."""
 import os
 import shutil
 import subprocess
